@@ -1,0 +1,78 @@
+"""Pins for the oracle's Philox4x32-10 and its uniform / normal transforms.
+
+The oracle's Philox is checked bit for bit against an independent
+implementation (Triton's, executed by its CPU interpreter); the transforms
+against their distributions.  Section 2.5 of the paper (parallel streams with
+skip-ahead) is realised here by a counter-based generator."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _triton_philox(seeds, ctrs):
+    pytest.importorskip("triton")
+    req = json.dumps({"seeds": [int(s) for s in seeds], "ctr": [[int(v) for v in c] for c in ctrs]})
+    out = subprocess.run([sys.executable, os.path.join(HERE, "_triton_philox.py")], input=req,
+                         capture_output=True, text=True, timeout=600)
+    if out.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + out.stderr[-300:])
+    return json.loads(out.stdout)
+
+
+def test_philox_matches_independent_implementation():
+    g = np.random.default_rng(0)
+    ctrs = g.integers(0, 2**32, size=(64, 4), dtype=np.uint64)
+    ctrs[0] = 0
+    ctrs[1] = 0xFFFFFFFF
+    seeds = [0, 1, 0xFFFFFFFFFFFFFFFF, 0x243F6A8885A308D3, 1234]
+    ref = _triton_philox(seeds, ctrs)
+    for s in seeds:
+        key = np.array([s & 0xFFFFFFFF, (s >> 32) & 0xFFFFFFFF], np.uint32)
+        for c, want in zip(ctrs, ref[str(s)]):
+            got = oracle.philox4x32_10(c.astype(np.uint32), key)
+            assert got.tolist() == want, (s, c)
+
+
+def test_counter_layout():
+    """draw_words puts (index, block, step lo, purpose | step hi << 8) in the counter."""
+    seed, purpose, step, index, block = 0x1122334455667788, 3, (5 << 32) | 77, 9, 2
+    key = np.array([seed & 0xFFFFFFFF, seed >> 32], np.uint32)
+    ctr = np.array([index, block, 77, purpose | (5 << 8)], np.uint32)
+    assert oracle.draw_words(seed, purpose, step, index, block).tolist() == \
+        oracle.philox4x32_10(ctr, key).tolist()
+
+
+def test_u01_endpoints_and_exactness():
+    assert oracle.u01(0) == 2.0**-24
+    assert oracle.u01(0xFFFFFFFF) == 1.0 - 2.0**-24
+    # every value is an odd multiple of 2^-24, representable in float32
+    for x in [1, 511, 512, 12345678, 0x80000000, 0xDEADBEEF]:
+        u = oracle.u01(x)
+        assert float(np.float32(u)) == u
+        assert (u * 2**24) % 2 == 1
+
+
+def test_uniform_and_normal_distributions():
+    w = np.concatenate([oracle.draw_words(7, 1, 0, i, 0) for i in range(5000)])
+    u = np.array([oracle.u01(int(x)) for x in w])
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    z = np.concatenate([oracle.normals(7, 1, 3, i, 5) for i in range(4000)])
+    assert abs(z.mean()) < 4 / np.sqrt(z.size)
+    assert abs(z.var() - 1) < 4 * np.sqrt(2 / z.size)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # odd n: the last pair contributes only its cosine normal
+    z5 = oracle.normals(7, 1, 3, 11, 5)
+    z6 = oracle.normals(7, 1, 3, 11, 6)
+    assert np.array_equal(z5, z6[:5])
+    # pairs are uncorrelated
+    zz = np.array([oracle.normals(9, 1, 0, i, 2) for i in range(20000)])
+    assert abs(np.corrcoef(zz.T)[0, 1]) < 4 / np.sqrt(20000)
