@@ -1,0 +1,271 @@
+/*
+ * smc.h -- C ABI of the GB300 (sm_103a) library for the data-parallel hot
+ * path of population-based MCMC and SMC samplers, after Lee, Yau, Giles,
+ * Doucet & Holmes (2009), "On the utility of graphics cards to perform
+ * massively parallel simulation of advanced Monte Carlo methods".
+ *
+ * Conventions (every entry point):
+ *   - Data pointers are DEVICE pointers owned by the caller, unless the
+ *     argument says "host".  The library keeps no pointer after a call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *     Every compute call is asynchronous on that stream and returns before
+ *     the work finishes.
+ *   - Argument errors are detected on the host and returned at once
+ *     (SMC_ERR_ARG); nothing is launched then.  Errors found by a kernel
+ *     (non-finite likelihood, zero total weight, weights outside [0,1],
+ *     exhausted wait limit) are latched in a device status word of the
+ *     context and reported by smc_ctx_check().
+ *   - Scratch memory (reduction partials, scan tile descriptors, queue
+ *     counters, the status word) lives in the context.  smc_reserve() sizes
+ *     it up front; a call that needs more grows it, which is refused with
+ *     SMC_ERR_ARG while the stream is being captured into a CUDA graph.
+ *   - Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11)
+ *     in place of the MRG32k3a / xorshift skip-ahead streams of Section
+ *     2.5.  key = (seed mod 2^32, seed div 2^32); counter = (index, block,
+ *     step mod 2^32, purpose | (step div 2^32) << 8).  Uniforms are
+ *     ((w >> 9) + 1/2) 2^-23 in (0,1); normals are Box-Muller on word pairs.
+ *     No RNG state is passed or kept: (seed, step) select the draws.
+ *   - Layouts: 1-D mixture particles theta are SoA float[K][M] (theta[k*M+p]
+ *     is mu_k of particle p); diagonal d-dimensional mixture particles are
+ *     float[M][K][d]; log-likelihoods, log-weights and normalised weights
+ *     are double[M]; ancestors are int32[M]; particle-filter states are
+ *     float[d][M].
+ */
+#ifndef SMC_GB300_H
+#define SMC_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum smc_status {
+    SMC_OK = 0,
+    SMC_ERR_ARG = -1,          /* bad argument, or workspace growth during capture */
+    SMC_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    SMC_ERR_NONFINITE = -3,    /* NaN log-likelihood / log-weight seen by a kernel */
+    SMC_ERR_ZERO_WEIGHT = -4,  /* every weight is zero (all log-weights -inf) */
+    SMC_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
+    SMC_ERR_UNSUPPORTED = -6   /* configuration not built (e.g. K too large) */
+} smc_status;
+
+typedef struct smc_ctx smc_ctx;
+
+/* Stream purposes of the Philox counter (the fourth counter word). */
+enum { SMC_RNG_MOVE = 1, SMC_RNG_ACCEPT = 2, SMC_RNG_RESAMPLE = 3,
+       SMC_RNG_EXCHANGE = 4, SMC_RNG_PFNOISE = 5 };
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device` (made current for the call).
+ * Allocates the status word and a small initial workspace.  *out receives
+ * the handle; SMC_ERR_CUDA if the device cannot be used. */
+smc_status smc_create(smc_ctx** out, int device);
+
+/* Free the context and its workspace (synchronises the device first). */
+smc_status smc_destroy(smc_ctx* ctx);
+
+/* Size the workspace for up to `max_particles` particles (or chains) and
+ * `max_pops` populations so that no later call grows it (required before
+ * graph capture).  May allocate; not to be called while capturing. */
+smc_status smc_reserve(smc_ctx* ctx, int64_t max_particles, int32_t max_pops);
+
+/* Synchronise `stream`, read and clear the device status word, and return
+ * the first error a kernel latched since the last check (SMC_OK if none). */
+smc_status smc_ctx_check(smc_ctx* ctx, void* stream);
+
+/* Static English description of a status code. */
+const char* smc_status_string(smc_status s);
+
+/* Launch-shape override used by the autotuner.  `op` is one of SMC_OP_*;
+ * `lanes` = threads cooperating on one particle's likelihood (1,2,4,8,16,32;
+ * Section 4.1.3 splits one likelihood over threads when N is large),
+ * `threads` = threads per block (64..1024, multiple of 32).  lanes = 0
+ * restores the built-in heuristic. */
+enum { SMC_OP_LOGLIK = 0, SMC_OP_MOVE = 1, SMC_OP_POPMCMC = 2, SMC_OP_COUNT = 3 };
+smc_status smc_set_launch(smc_ctx* ctx, int32_t op, int32_t lanes, int32_t threads);
+smc_status smc_get_launch(smc_ctx* ctx, int32_t op, int64_t M, int64_t N, int32_t K,
+                          int32_t* lanes, int32_t* threads);
+
+/* ------------------------------------------------------------------ models */
+
+enum { SMC_GMM_1D = 0, SMC_GMM_DIAG = 1 };
+enum { SMC_PREC_FP32 = 0, SMC_PREC_BF16SPLIT = 1 };
+
+/* Gaussian mixture with known weights and a common known sigma
+ * (Section 4.1: p(y_j|mu) = sum_i w_i f(y_j|mu_i, sigma); the density of
+ * y is the product over j) and a uniform prior on the box [lo, hi]^(K d). */
+typedef struct smc_gmm {
+    int32_t kind;          /* SMC_GMM_1D or SMC_GMM_DIAG */
+    int32_t K;             /* components: 1..64 (1-D), 1..64 (diag) */
+    int32_t d;             /* dimension: 1 for SMC_GMM_1D; 1..64 for diag */
+    int32_t precision;     /* SMC_PREC_FP32, or SMC_PREC_BF16SPLIT (diag only) */
+    const float* log_w;    /* HOST pointer, [K] log mixture weights, copied per call */
+    float sigma;           /* component standard deviation (> 0) */
+    float lo, hi;          /* prior box, lo < hi */
+} smc_gmm;
+
+/* ------------------------------------------------------------ likelihood */
+
+/* Per-particle mixture log-likelihood (Section 4.1), the sum over the N
+ * observations of a log-sum-exp over the K components (Section 2.3: log
+ * domain; compensated summation over N):
+ *   loglik_out[p] = sum_n log sum_k w_k N(y_n | mu_pk, sigma^2 I_d).
+ *   y:     1-D float[N]; diag float[N][d].
+ *   theta: 1-D float[K][M]; diag float[M][K][d].
+ *   loglik_out: double[M].
+ *   grad_out (nullable, 1-D only): float[K][M], d loglik / d mu_k =
+ *     sum_n r_nk (y_n - mu_k) / sigma^2 with r the responsibilities.
+ * The prior box is not applied here.  Diag with SMC_PREC_BF16SPLIT forms
+ * mu.y on the tensor cores from bf16 hi/lo splits.  Errors: SMC_ERR_ARG for
+ * M < 0, N < 0, K/d out of range, sigma <= 0, NULL pointers with M, N > 0;
+ * M == 0 is a no-op; N == 0 gives loglik 0. */
+smc_status smc_loglik_batch(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
+                            const float* theta, int64_t M, double* loglik_out, float* grad_out,
+                            void* stream);
+
+/* ------------------------------------------------------------------ weights */
+
+/* Incremental reweighting and normalisation (Section 3: W = w / sum w;
+ * Section 4.1.2: incremental weight pi_t(x)/pi_{t-1}(x) = exp(dbeta l(x))
+ * under the uniform prior; Section 3.2: effective sample size):
+ *   logw[i] += dbeta * loglik[i]   (skipped if loglik == NULL or dbeta == 0)
+ *   W_out[i] = exp(logw[i] - max) / S1,  S1 = sum exp(logw - max)
+ *   scalars_out (device double[4]) = { log Z increment
+ *        = LSE(logw new) - LSE(logw old), ESS = S1^2 / S2, max, LSE(new) }
+ *   resample_flag_out (device int32, nullable) = ESS < ess_frac * M.
+ * logw is in/out (double[M]); W_out is double[M] (nullable: scalars only).
+ * Differences are formed in FP64 and exponentiated in FP32 on the reduced
+ * argument; sums are FP64.  A NaN latches SMC_ERR_NONFINITE, an all -inf
+ * logw SMC_ERR_ZERO_WEIGHT (then W and the scalars are not written). */
+smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
+                        int64_t M, double* W_out, double* scalars_out,
+                        int32_t* resample_flag_out, double ess_frac, void* stream);
+
+/* ESS of unnormalised log-weights, (sum w)^2 / sum w^2 (Section 3.2);
+ * ess_out is a device double. */
+smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, double* ess_out, void* stream);
+
+/* ---------------------------------------------------------------- resampling */
+
+/* Systematic resampling (Section 3.2: build the empirical CDF of the
+ * weights and draw M times from it; the parallel scan of Section 4.2), in
+ * exact integer arithmetic so the result does not depend on summation
+ * order:  q_j = floor(W_j 2^52), C_j = q_0 + ... + q_j, S = C_{M-1}; slot i
+ * takes ancestors_out[i] = min { j : C_j M 2^32 > (i 2^32 + u32) S } with
+ * u32 the Philox word (seed, RESAMPLE, step, index 0, block 0, word 0).
+ *   W: double[M], each in [0,1] (normalised weights; sum <= 2).
+ *   ancestors_out: int32[M], non-decreasing.  counts_out: int32[M] offspring
+ *     counts (nullable).
+ *   do_flag (device int32, nullable): when it holds 0 nothing is resampled;
+ *     ancestors_out becomes the identity and counts 1.
+ *   logw_reset (nullable): double[M] set to 0 when resampling happened.
+ * Single pass: block scan plus decoupled look-back with a bounded wait.
+ * A weight outside [0,1] or NaN latches SMC_ERR_ARG, S == 0
+ * SMC_ERR_ZERO_WEIGHT, an exhausted wait SMC_ERR_TIMEOUT; the outputs are
+ * then unspecified. */
+smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uint64_t seed,
+                                   uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
+                                   const int32_t* do_flag, double* logw_reset, void* stream);
+
+/* Gather particles by ancestor: for r < rows_f32, dst_f32[r*M + i] =
+ * src_f32[r*M + anc[i]] (SoA float[rows][M]); and dst_f64[i] =
+ * src_f64[anc[i]] if both are non-NULL.  anc NULL means identity (copy).
+ * Source and destination must not overlap. */
+smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, int32_t rows_f32,
+                      const float* src_f32, float* dst_f32, const double* src_f64,
+                      double* dst_f64, void* stream);
+
+/* ---------------------------------------------------------------------- moves */
+
+enum { SMC_MOVE_RW = 0, SMC_MOVE_MALA = 1 };
+
+/* One Metropolis-Hastings move per particle on the tempered target
+ * prior(mu) L(mu)^beta (Sections 4.1.1-4.1.2), 1-D mixture only.
+ *   Slot p starts from particle src = anc[p] (anc NULL, or *do_flag == 0
+ *   when do_flag is given: src = p) -- the gather after resampling fused
+ *   into the move.
+ *   RW:   mu' = mu + scale z, z ~ N(0, I_K) (purpose MOVE, index p).
+ *   MALA: mu' = mu + (h^2/2) beta grad l(mu) + h z with h = scale, and the
+ *         log proposal-density ratio added to log alpha.  grad_in / grad_out
+ *         are float[K][M] (the gradient at the state; required for MALA).
+ *   A proposal outside the prior box is rejected without evaluating l.
+ *   Accept iff log u < log alpha, u from purpose ACCEPT word 0 (FP64 test).
+ *   beta: device float, beta[p * beta_stride] (stride 0: one temperature).
+ *   theta_in/loglik_in/grad_in and theta_out/loglik_out/grad_out must not
+ *   overlap when anc is non-NULL; with anc NULL they may be identical.
+ *   accept_count (device uint32, nullable) is incremented by the number of
+ *   accepted moves. */
+smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
+                       const float* theta_in, const double* loglik_in, const float* grad_in,
+                       const int32_t* anc, const int32_t* do_flag,
+                       float* theta_out, double* loglik_out, float* grad_out, int64_t M,
+                       const float* beta, int64_t beta_stride, float scale, int32_t kind,
+                       uint64_t seed, uint64_t step, uint32_t* accept_count, void* stream);
+
+/* One sweep of population MCMC over many independent populations in ONE
+ * persistent launch (Section 3.1; Section 4.1.1).  Population q owns chains
+ * pop_offsets[q] .. pop_offsets[q+1]-1 of theta (float[K][M_total]) and
+ * loglik (double[M_total]), updated in place; beta is float[M_total].
+ * Stage 1: a random-walk MH move for every chain (as smc_mh_move with
+ *   particle index = chain index, step = sweep).
+ * Stage 2: exchange moves between adjacent chains of each population, on
+ *   the pair set {0,1},{2,3},... (parity bit 0) or {1,2},{3,4},...,{M_q-1,0}
+ *   (parity bit 1, the wrap pair only when M_q is even); the bit is
+ *   word 0 bit 0 of (seed, EXCHANGE, sweep, index q); pair j swaps iff
+ *   log u_j < (beta_a - beta_b)(l_b - l_a), u_j from word 4 + j.
+ * pop_order (device int32[n_pops], nullable) is the order in which the work
+ *   queue hands out populations (e.g. largest first).
+ * stats (device uint64[3], nullable) accumulates {MH accepts, swaps
+ *   accepted, swaps attempted}. */
+smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
+                             float* theta, double* loglik, int64_t M_total, const float* beta,
+                             const int32_t* pop_offsets, const int32_t* pop_order, int32_t n_pops,
+                             float scale, uint64_t seed, uint64_t sweep, uint64_t* stats,
+                             void* stream);
+
+/* ------------------------------------------------------------ particle filter */
+
+enum { SMC_PF_MSV = 0, SMC_PF_LG = 1 };
+
+/* State-space model for pf_step, passed by value through a host pointer. */
+typedef struct smc_pf_model {
+    int32_t kind;          /* SMC_PF_MSV or SMC_PF_LG */
+    int32_t d;             /* state dimension, 1..8 */
+    float phi[8];          /* x_t = phi (.) x_{t-1} + L z */
+    float chol[64];        /* row-major lower Cholesky factor L of Sigma (d x d) */
+    float beta;            /* observation scale */
+} smc_pf_model;
+
+/* One bootstrap particle-filter step (Section 3.2; the model of Section 4.2
+ * with multivariate stochastic volatility):
+ *   x_out[:, i] = phi (.) x_in[:, anc[i]] + L z_i, z_i ~ N(0, I_d)
+ *                 (purpose PFNOISE, index i, step t); anc NULL = identity.
+ *   logg_out[i] = log g(y_t | x_out[:, i]):
+ *     MSV: sum_j [ -1/2 log(2 pi beta^2) - x_j/2 - y_j^2 exp(-x_j) / (2 beta^2) ]
+ *     LG:  sum_j [ -1/2 log(2 pi beta^2) - (y_j - x_j)^2 / (2 beta^2) ]
+ *   y_t: device float[d];  x_in, x_out: float[d][M] (must not overlap);
+ *   logg_out: double[M].  Feed logg_out to smc_reweight (dbeta = 1) and
+ *   the weights to smc_resample_systematic for the next step's anc. */
+smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
+                   const float* x_in, const int32_t* anc, float* x_out, double* logg_out,
+                   int64_t M, uint64_t seed, uint64_t t, void* stream);
+
+/* ------------------------------------------------------------------- streams */
+
+/* Raw Philox words: out[(i*n_block + b)*4 + w] = word w of
+ * (seed, purpose, step, index i, block b), i < n_index, b < n_block. */
+smc_status smc_rng_words(smc_ctx* ctx, uint64_t seed, uint32_t purpose, uint64_t step,
+                         uint32_t n_index, uint32_t n_block, uint32_t* out, void* stream);
+
+/* Box-Muller normals as the moves draw them: out[i*n + j] = normal j of
+ * (seed, purpose, step, index i), float. */
+smc_status smc_rng_normals(smc_ctx* ctx, uint64_t seed, uint32_t purpose, uint64_t step,
+                           uint32_t n_index, uint32_t n, float* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SMC_GB300_H */

@@ -79,9 +79,11 @@ def _declare(L):
     L.orc_rwmh_move.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double, C.c_double,
                                 _f32p, _f64p, _vp, _f32p, _f64p, _i64, _f32p, _i64, C.c_float,
                                 _u64, _u64, _i32p]
+    L.orc_rwmh_move_slots.argtypes = L.orc_rwmh_move.argtypes + [_vp, _i64, _vp]
     L.orc_mala_move.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double, C.c_double,
                                 _f32p, _f64p, _f32p, _vp, _f32p, _f64p, _f32p, _i64, _f32p, _i64,
                                 C.c_float, _u64, _u64, _i32p]
+    L.orc_mala_move_slots.argtypes = L.orc_mala_move.argtypes + [_vp, _i64, _vp]
     L.orc_popmcmc_sweep.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double,
                                     C.c_double, _f32p, _f64p, _i64, _f32p, _i32p, C.c_int32,
                                     C.c_float, _u64, _u64, _i64p]
@@ -225,34 +227,46 @@ def _beta_arr(beta, M):
     return _f32(b), (0 if b.size == 1 else 1)
 
 
-def rwmh_move(y, logw, sigma, box, theta, loglik, beta, scale, seed, step, anc=None):
-    """Random-walk MH on prior * L^beta (Sections 4.1.1-4.1.2)."""
+def rwmh_move(y, logw, sigma, box, theta, loglik, beta, scale, seed, step, anc=None,
+              slots=None, want_log_alpha=False):
+    """Random-walk MH on prior * L^beta (Sections 4.1.1-4.1.2).
+
+    slots (optional): compute only these output slots; outputs are compact.
+    want_log_alpha: also return the log acceptance ratios (-inf outside the box)."""
     y, theta, loglik, logw = _f32(y), _f32(theta), _f64(loglik), _f64(logw)
     K, M = theta.shape
     b, bs = _beta_arr(beta, M)
-    th_out = np.zeros_like(theta)
-    l_out = np.zeros(M, np.float64)
-    acc = np.zeros(M, np.int32)
+    sl = None if slots is None else np.ascontiguousarray(slots, np.int32)
+    n = M if sl is None else sl.size
+    th_out = np.zeros((K, n), np.float32)
+    l_out = np.zeros(n, np.float64)
+    acc = np.zeros(n, np.int32)
     a = None if anc is None else np.ascontiguousarray(anc, np.int32)
-    lib().orc_rwmh_move(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]), theta,
-                        loglik, _ptr(a), th_out, l_out, M, b, bs, float(scale), seed, step, acc)
-    return th_out, l_out, acc
+    la = np.zeros(n, np.float64)
+    lib().orc_rwmh_move_slots(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]),
+                              theta, loglik, _ptr(a), th_out, l_out, M, b, bs, float(scale), seed,
+                              step, acc, _ptr(sl), n, _ptr(la))
+    return (th_out, l_out, acc, la) if want_log_alpha else (th_out, l_out, acc)
 
 
-def mala_move(y, logw, sigma, box, theta, loglik, grad, beta, h, seed, step, anc=None):
-    """MALA move on prior * L^beta with the adjoint gradient."""
+def mala_move(y, logw, sigma, box, theta, loglik, grad, beta, h, seed, step, anc=None,
+              slots=None, want_log_alpha=False):
+    """MALA move on prior * L^beta with the adjoint gradient (slots as rwmh_move)."""
     y, theta, loglik, logw, grad = _f32(y), _f32(theta), _f64(loglik), _f64(logw), _f32(grad)
     K, M = theta.shape
     b, bs = _beta_arr(beta, M)
-    th_out = np.zeros_like(theta)
-    g_out = np.zeros_like(theta)
-    l_out = np.zeros(M, np.float64)
-    acc = np.zeros(M, np.int32)
+    sl = None if slots is None else np.ascontiguousarray(slots, np.int32)
+    n = M if sl is None else sl.size
+    th_out = np.zeros((K, n), np.float32)
+    g_out = np.zeros((K, n), np.float32)
+    l_out = np.zeros(n, np.float64)
+    acc = np.zeros(n, np.int32)
     a = None if anc is None else np.ascontiguousarray(anc, np.int32)
-    lib().orc_mala_move(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]), theta,
-                        loglik, grad, _ptr(a), th_out, l_out, g_out, M, b, bs, float(h), seed,
-                        step, acc)
-    return th_out, l_out, g_out, acc
+    la = np.zeros(n, np.float64)
+    lib().orc_mala_move_slots(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]),
+                              theta, loglik, grad, _ptr(a), th_out, l_out, g_out, M, b, bs,
+                              float(h), seed, step, acc, _ptr(sl), n, _ptr(la))
+    return (th_out, l_out, g_out, acc, la) if want_log_alpha else (th_out, l_out, g_out, acc)
 
 
 def popmcmc_sweep(y, logw, sigma, box, theta, loglik, beta, offsets, scale, seed, sweep):

@@ -358,15 +358,20 @@ static int orc_in_box(const double* v, int K, double lo, double hi)
     return 1;
 }
 
-void orc_rwmh_move(const float* y, int64_t N, int K, const double* logw, double sigma,
-                   double lo, double hi,
-                   const float* theta_in, const double* loglik_in, const int32_t* anc,
-                   float* theta_out, double* loglik_out, int64_t M,
-                   const float* beta, int64_t beta_stride, float scale,
-                   uint64_t seed, uint64_t step, int32_t* accepted)
+void orc_rwmh_move_slots(const float* y, int64_t N, int K, const double* logw, double sigma,
+                         double lo, double hi,
+                         const float* theta_in, const double* loglik_in, const int32_t* anc,
+                         float* theta_out, double* loglik_out, int64_t M,
+                         const float* beta, int64_t beta_stride, float scale,
+                         uint64_t seed, uint64_t step, int32_t* accepted,
+                         const int32_t* slots, int64_t n_out, double* log_alpha_out)
 {
+    /* slots (nullable): compute only output slots slots[0..n_out); results
+     * are stored compactly at position s (theta_out is [K][n_out]).
+     * log_alpha_out (nullable): log acceptance ratio, -inf outside the box. */
     double mu[64], prop[64], z[64];
-    for (int64_t p = 0; p < M; ++p) {
+    for (int64_t s = 0; s < n_out; ++s) {
+        int64_t p = slots ? (int64_t)slots[s] : s;
         int64_t src = anc ? (int64_t)anc[p] : p;
         for (int k = 0; k < K; ++k) mu[k] = (double)theta_in[(int64_t)k * M + src];
         double l = loglik_in[src];
@@ -374,17 +379,31 @@ void orc_rwmh_move(const float* y, int64_t N, int K, const double* logw, double 
         orc_normals(seed, ORC_P_MOVE, step, (uint32_t)p, K, z);
         for (int k = 0; k < K; ++k) prop[k] = (double)(float)(mu[k] + (double)scale * z[k]);
         int acc = 0;
-        double lp = 0.0;
+        double lp = 0.0, la = -INFINITY;
         if (orc_in_box(prop, K, lo, hi)) {
             lp = orc_gmm1d_loglik_one(y, N, K, logw, sigma, prop);
             double u = orc_u01(orc_word(seed, ORC_P_ACCEPT, step, (uint32_t)p, 0));
-            if (log(u) < b * (lp - l)) acc = 1;
+            la = b * (lp - l);
+            if (log(u) < la) acc = 1;
         }
+        if (log_alpha_out) log_alpha_out[s] = la;
         for (int k = 0; k < K; ++k)
-            theta_out[(int64_t)k * M + p] = (float)(acc ? prop[k] : mu[k]);
-        loglik_out[p] = acc ? lp : l;
-        accepted[p] = acc;
+            theta_out[(int64_t)k * n_out + s] = (float)(acc ? prop[k] : mu[k]);
+        loglik_out[s] = acc ? lp : l;
+        accepted[s] = acc;
     }
+}
+
+void orc_rwmh_move(const float* y, int64_t N, int K, const double* logw, double sigma,
+                   double lo, double hi,
+                   const float* theta_in, const double* loglik_in, const int32_t* anc,
+                   float* theta_out, double* loglik_out, int64_t M,
+                   const float* beta, int64_t beta_stride, float scale,
+                   uint64_t seed, uint64_t step, int32_t* accepted)
+{
+    orc_rwmh_move_slots(y, N, K, logw, sigma, lo, hi, theta_in, loglik_in, anc, theta_out,
+                        loglik_out, M, beta, beta_stride, scale, seed, step, accepted, NULL, M,
+                        NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -396,17 +415,19 @@ void orc_rwmh_move(const float* y, int64_t N, int K, const double* logw, double 
 /*   log q(a | b) = -|a - m(b)|^2 / (2 h^2)                                  */
 /* Draws as for the RW move.  grad_in / grad_out are [K][M].                 */
 /* ------------------------------------------------------------------------ */
-void orc_mala_move(const float* y, int64_t N, int K, const double* logw, double sigma,
-                   double lo, double hi,
-                   const float* theta_in, const double* loglik_in, const float* grad_in,
-                   const int32_t* anc,
-                   float* theta_out, double* loglik_out, float* grad_out, int64_t M,
-                   const float* beta, int64_t beta_stride, float h,
-                   uint64_t seed, uint64_t step, int32_t* accepted)
+void orc_mala_move_slots(const float* y, int64_t N, int K, const double* logw, double sigma,
+                         double lo, double hi,
+                         const float* theta_in, const double* loglik_in, const float* grad_in,
+                         const int32_t* anc,
+                         float* theta_out, double* loglik_out, float* grad_out, int64_t M,
+                         const float* beta, int64_t beta_stride, float h,
+                         uint64_t seed, uint64_t step, int32_t* accepted,
+                         const int32_t* slots, int64_t n_out, double* log_alpha_out)
 {
     double mu[64], g[64], prop[64], gp[64], z[64], mf[64], mb[64];
     double hh = (double)h;
-    for (int64_t p = 0; p < M; ++p) {
+    for (int64_t s = 0; s < n_out; ++s) {
+        int64_t p = slots ? (int64_t)slots[s] : s;
         int64_t src = anc ? (int64_t)anc[p] : p;
         for (int k = 0; k < K; ++k) {
             mu[k] = (double)theta_in[(int64_t)k * M + src];
@@ -420,7 +441,7 @@ void orc_mala_move(const float* y, int64_t N, int K, const double* logw, double 
             prop[k] = (double)(float)(mf[k] + hh * z[k]);
         }
         int acc = 0;
-        double lp = 0.0;
+        double lp = 0.0, la = -INFINITY;
         if (orc_in_box(prop, K, lo, hi)) {
             lp = orc_gmm1d_loglik_one(y, N, K, logw, sigma, prop);
             orc_gmm1d_grad_one(y, N, K, logw, sigma, prop, gp);
@@ -434,15 +455,30 @@ void orc_mala_move(const float* y, int64_t N, int K, const double* logw, double 
             }
             double log_alpha = b * (lp - l) + (-bwd / (2.0 * hh * hh)) - (-fwd / (2.0 * hh * hh));
             double u = orc_u01(orc_word(seed, ORC_P_ACCEPT, step, (uint32_t)p, 0));
+            la = log_alpha;
             if (log(u) < log_alpha) acc = 1;
         }
+        if (log_alpha_out) log_alpha_out[s] = la;
         for (int k = 0; k < K; ++k) {
-            theta_out[(int64_t)k * M + p] = (float)(acc ? prop[k] : mu[k]);
-            grad_out[(int64_t)k * M + p] = (float)(acc ? gp[k] : g[k]);
+            theta_out[(int64_t)k * n_out + s] = (float)(acc ? prop[k] : mu[k]);
+            grad_out[(int64_t)k * n_out + s] = (float)(acc ? gp[k] : g[k]);
         }
-        loglik_out[p] = acc ? lp : l;
-        accepted[p] = acc;
+        loglik_out[s] = acc ? lp : l;
+        accepted[s] = acc;
     }
+}
+
+void orc_mala_move(const float* y, int64_t N, int K, const double* logw, double sigma,
+                   double lo, double hi,
+                   const float* theta_in, const double* loglik_in, const float* grad_in,
+                   const int32_t* anc,
+                   float* theta_out, double* loglik_out, float* grad_out, int64_t M,
+                   const float* beta, int64_t beta_stride, float h,
+                   uint64_t seed, uint64_t step, int32_t* accepted)
+{
+    orc_mala_move_slots(y, N, K, logw, sigma, lo, hi, theta_in, loglik_in, grad_in, anc,
+                        theta_out, loglik_out, grad_out, M, beta, beta_stride, h, seed, step,
+                        accepted, NULL, M, NULL);
 }
 
 /* ------------------------------------------------------------------------ */

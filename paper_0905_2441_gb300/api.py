@@ -1,0 +1,287 @@
+"""Thin Python binding of the C ABI (include/smc.h) over torch CUDA tensors.
+
+Every function checks dtypes / devices / shapes, passes ``data_ptr()`` and
+the current CUDA stream, and raises :class:`SmcError` on a non-zero status.
+All arithmetic happens in the CUDA kernels of libsmc.so; nothing here
+computes any part of the method.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+class SmcError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        msg = L.load().smc_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+def _chk(st: int, where: str):
+    if st != 0:
+        raise SmcError(st, where)
+
+
+def _stream(stream=None) -> C.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _need(t, dtype, name, shape=None):
+    if t is None:
+        return
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+# ------------------------------------------------------------------ context
+class Context:
+    """Owns an smc_ctx (status word, scratch, launch overrides) on one device."""
+
+    def __init__(self, device: int | None = None):
+        self._lib = L.load()
+        dev = torch.cuda.current_device() if device is None else int(device)
+        h = C.c_void_p()
+        _chk(self._lib.smc_create(C.byref(h), dev), "smc_create")
+        self.handle = h
+        self.device = dev
+
+    def close(self):
+        if self.handle:
+            self._lib.smc_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, max_particles: int, max_pops: int = 0):
+        _chk(self._lib.smc_reserve(self.handle, int(max_particles), int(max_pops)), "smc_reserve")
+
+    def check(self, stream=None):
+        """Synchronise the stream and raise the first device-latched error."""
+        _chk(self._lib.smc_ctx_check(self.handle, _stream(stream)), "device status")
+
+    def set_launch(self, op: int, lanes: int, threads: int = 256):
+        _chk(self._lib.smc_set_launch(self.handle, op, lanes, threads), "smc_set_launch")
+
+    def get_launch(self, op: int, M: int, N: int, K: int):
+        l, t = C.c_int32(), C.c_int32()
+        _chk(self._lib.smc_get_launch(self.handle, op, M, N, K, C.byref(l), C.byref(t)),
+             "smc_get_launch")
+        return l.value, t.value
+
+
+# ------------------------------------------------------------------ models
+@dataclass
+class GMM:
+    """Gaussian mixture with known weights and sigma (Section 4.1), prior box."""
+    K: int
+    sigma: float
+    log_w: np.ndarray = None
+    lo: float = -10.0
+    hi: float = 10.0
+    d: int = 1
+    precision: int = L.PREC_FP32
+    _w: object = field(default=None, repr=False)
+
+    def __post_init__(self):
+        if self.log_w is None:
+            self.log_w = np.full(self.K, -np.log(self.K))
+        self.log_w = np.asarray(self.log_w, np.float64)
+        self._w = (C.c_float * self.K)(*[float(v) for v in self.log_w])
+
+    def cstruct(self) -> L.SmcGmm:
+        return L.SmcGmm(L.GMM_1D, self.K, 1, L.PREC_FP32, self._w, self.sigma, self.lo, self.hi)
+
+
+@dataclass
+class DiagGMM(GMM):
+    """d-dimensional mixture with N(mu_k, sigma^2 I_d) components."""
+
+    def cstruct(self) -> L.SmcGmm:
+        return L.SmcGmm(L.GMM_DIAG, self.K, self.d, self.precision, self._w, self.sigma,
+                        self.lo, self.hi)
+
+
+@dataclass
+class PFModel:
+    """State-space model for pf_step: MSV (Section 4.2 family) or linear-Gaussian."""
+    kind: int
+    phi: np.ndarray
+    chol: np.ndarray
+    beta: float
+
+    def cstruct(self) -> L.SmcPfModel:
+        phi = np.asarray(self.phi, np.float64)
+        ch = np.asarray(self.chol, np.float64)
+        d = phi.size
+        m = L.SmcPfModel()
+        m.kind = self.kind
+        m.d = d
+        for i in range(d):
+            m.phi[i] = float(phi[i])
+            for j in range(d):
+                m.chol[i * d + j] = float(ch[i, j])
+        m.beta = float(self.beta)
+        return m
+
+
+# ------------------------------------------------------------------ calls
+def loglik_batch(ctx: Context, model: GMM, y, theta, out=None, grad=None, stream=None):
+    """Per-particle mixture log-likelihood (and optional gradient)."""
+    if isinstance(model, DiagGMM):
+        N = y.shape[0]
+        M = theta.shape[0]
+    else:
+        N = y.numel()
+        M = theta.shape[1]
+    out = torch.empty(M, dtype=torch.float64, device=theta.device) if out is None else out
+    _need(y, torch.float32, "y")
+    _need(theta, torch.float32, "theta")
+    _need(out, torch.float64, "loglik_out", (M,))
+    _need(grad, torch.float32, "grad_out", tuple(theta.shape))
+    m = model.cstruct()
+    _chk(L.load().smc_loglik_batch(ctx.handle, C.byref(m), _ptr(y), N, _ptr(theta), M,
+                                   _ptr(out), _ptr(grad), _stream(stream)), "smc_loglik_batch")
+    return out
+
+
+def reweight(ctx: Context, loglik, dbeta: float, logw, W_out=None, scalars=None, flag=None,
+             ess_frac: float = 0.5, stream=None):
+    M = logw.numel()
+    _need(loglik, torch.float64, "loglik", (M,))
+    _need(logw, torch.float64, "logw", (M,))
+    _need(W_out, torch.float64, "W_out", (M,))
+    _need(scalars, torch.float64, "scalars", (4,))
+    _need(flag, torch.int32, "flag", (1,))
+    _chk(L.load().smc_reweight(ctx.handle, _ptr(loglik), float(dbeta), _ptr(logw), M, _ptr(W_out),
+                               _ptr(scalars), _ptr(flag), float(ess_frac), _stream(stream)),
+         "smc_reweight")
+
+
+def ess(ctx: Context, logw, out=None, stream=None):
+    M = logw.numel()
+    out = torch.empty(1, dtype=torch.float64, device=logw.device) if out is None else out
+    _need(logw, torch.float64, "logw", (M,))
+    _need(out, torch.float64, "ess_out", (1,))
+    _chk(L.load().smc_ess(ctx.handle, _ptr(logw), M, _ptr(out), _stream(stream)), "smc_ess")
+    return out
+
+
+def resample_systematic(ctx: Context, W, seed: int, step: int, anc=None, counts=None,
+                        do_flag=None, logw_reset=None, stream=None):
+    M = W.numel()
+    anc = torch.empty(M, dtype=torch.int32, device=W.device) if anc is None else anc
+    _need(W, torch.float64, "W", (M,))
+    _need(anc, torch.int32, "ancestors", (M,))
+    _need(counts, torch.int32, "counts", (M,))
+    _need(do_flag, torch.int32, "do_flag", (1,))
+    _need(logw_reset, torch.float64, "logw_reset", (M,))
+    _chk(L.load().smc_resample_systematic(ctx.handle, _ptr(W), M, int(seed), int(step), _ptr(anc),
+                                          _ptr(counts), _ptr(do_flag), _ptr(logw_reset),
+                                          _stream(stream)), "smc_resample_systematic")
+    return anc
+
+
+def gather(ctx: Context, anc, src32=None, dst32=None, src64=None, dst64=None, stream=None):
+    M = (dst64 if dst64 is not None else dst32).shape[-1]
+    rows = 0 if src32 is None else (src32.shape[0] if src32.dim() == 2 else 1)
+    _need(anc, torch.int32, "anc", (M,))
+    _need(src32, torch.float32, "src_f32")
+    _need(dst32, torch.float32, "dst_f32")
+    _need(src64, torch.float64, "src_f64", (M,))
+    _need(dst64, torch.float64, "dst_f64", (M,))
+    _chk(L.load().smc_gather(ctx.handle, _ptr(anc), M, rows, _ptr(src32), _ptr(dst32), _ptr(src64),
+                             _ptr(dst64), _stream(stream)), "smc_gather")
+
+
+def mh_move(ctx: Context, model: GMM, y, theta_in, ll_in, theta_out, ll_out, beta, scale: float,
+            seed: int, step: int, kind: int = L.MOVE_RW, grad_in=None, grad_out=None, anc=None,
+            do_flag=None, accept_count=None, stream=None):
+    K, M = theta_in.shape
+    _need(y, torch.float32, "y")
+    for t, n in ((theta_in, "theta_in"), (theta_out, "theta_out")):
+        _need(t, torch.float32, n, (K, M))
+    for t, n in ((grad_in, "grad_in"), (grad_out, "grad_out")):
+        _need(t, torch.float32, n, (K, M))
+    _need(ll_in, torch.float64, "loglik_in", (M,))
+    _need(ll_out, torch.float64, "loglik_out", (M,))
+    _need(beta, torch.float32, "beta")
+    _need(anc, torch.int32, "anc", (M,))
+    _need(do_flag, torch.int32, "do_flag", (1,))
+    _need(accept_count, torch.int32, "accept_count", (1,))
+    bstride = 0 if beta.numel() == 1 else 1
+    if bstride and beta.numel() != M:
+        raise ValueError("beta must have 1 or M entries")
+    m = model.cstruct()
+    _chk(L.load().smc_mh_move(ctx.handle, C.byref(m), _ptr(y), y.numel(), _ptr(theta_in),
+                              _ptr(ll_in), _ptr(grad_in), _ptr(anc), _ptr(do_flag),
+                              _ptr(theta_out), _ptr(ll_out), _ptr(grad_out), M, _ptr(beta),
+                              bstride, float(scale), int(kind), int(seed), int(step),
+                              _ptr(accept_count), _stream(stream)), "smc_mh_move")
+
+
+def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, scale: float,
+                  seed: int, sweep: int, order=None, stats=None, stream=None):
+    K, M = theta.shape
+    n_pops = offsets.numel() - 1
+    _need(y, torch.float32, "y")
+    _need(theta, torch.float32, "theta", (K, M))
+    _need(loglik, torch.float64, "loglik", (M,))
+    _need(beta, torch.float32, "beta", (M,))
+    _need(offsets, torch.int32, "pop_offsets", (n_pops + 1,))
+    _need(order, torch.int32, "pop_order", (n_pops,))
+    _need(stats, torch.int64, "stats", (3,))
+    m = model.cstruct()
+    _chk(L.load().smc_popmcmc_sweep(ctx.handle, C.byref(m), _ptr(y), y.numel(), _ptr(theta),
+                                    _ptr(loglik), M, _ptr(beta), _ptr(offsets), _ptr(order),
+                                    n_pops, float(scale), int(seed), int(sweep), _ptr(stats),
+                                    _stream(stream)), "smc_popmcmc_sweep")
+
+
+def pf_step(ctx: Context, model: PFModel, y_t, x_in, x_out, logg_out, seed: int, t: int,
+            anc=None, stream=None):
+    d, M = x_in.shape
+    _need(y_t, torch.float32, "y_t", (d,))
+    _need(x_in, torch.float32, "x_in", (d, M))
+    _need(x_out, torch.float32, "x_out", (d, M))
+    _need(logg_out, torch.float64, "logg_out", (M,))
+    _need(anc, torch.int32, "anc", (M,))
+    m = model.cstruct()
+    _chk(L.load().pf_step(ctx.handle, C.byref(m), _ptr(y_t), _ptr(x_in), _ptr(anc), _ptr(x_out),
+                          _ptr(logg_out), M, int(seed), int(t), _stream(stream)), "pf_step")
+
+
+def rng_words(ctx: Context, seed: int, purpose: int, step: int, n_index: int, n_block: int = 1,
+              stream=None):
+    out = torch.empty(n_index * n_block * 4, dtype=torch.int32, device="cuda")
+    _chk(L.load().smc_rng_words(ctx.handle, int(seed), purpose, int(step), n_index, n_block,
+                                _ptr(out), _stream(stream)), "smc_rng_words")
+    return out.view(n_index, n_block, 4)
+
+
+def rng_normals(ctx: Context, seed: int, purpose: int, step: int, n_index: int, n: int,
+                stream=None):
+    out = torch.empty(n_index * n, dtype=torch.float32, device="cuda")
+    _chk(L.load().smc_rng_normals(ctx.handle, int(seed), purpose, int(step), n_index, n,
+                                  _ptr(out), _stream(stream)), "smc_rng_normals")
+    return out.view(n_index, n)

@@ -1,0 +1,65 @@
+// ctx.hpp -- host-side context: device status word, workspace, launch
+// overrides.  Shared by the host halves of every translation unit.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "smc.h"
+
+struct smc_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int max_threads_per_sm = 0;
+    uint32_t* d_status = nullptr;     // latched device errors (bit set)
+    // fixed small area: counters and reduction partials
+    unsigned long long* d_counters = nullptr;  // [kCounters] zero-initialised
+    double* d_partials = nullptr;              // [kMaxPartialBlocks * 8]
+    // growable area: resampling tile descriptors, staging buffers
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int32_t lanes[SMC_OP_COUNT] = {0, 0, 0};
+    int32_t threads[SMC_OP_COUNT] = {0, 0, 0};
+};
+
+namespace smc_host {
+
+// counter slots in d_counters (each call that uses one leaves it at zero)
+enum : int {
+    CNT_REWEIGHT_TICKET = 0,
+    CNT_ESS_TICKET = 1,
+    CNT_RESAMPLE_TILE = 2,
+    CNT_RESAMPLE_SUM = 3,       // exact uint64 total S of the quantised weights
+    CNT_POP_QUEUE = 4,
+    CNT_POP_DONE = 5,
+    CNT_DIAG_TICKET = 6,
+    CNT_RESAMPLE_DONE = 7,
+    kCounters = 16
+};
+constexpr int kMaxPartialBlocks = 2048;
+
+// CUDA error -> status, remembering nothing (errors are returned)
+inline smc_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? SMC_OK : SMC_ERR_CUDA; }
+
+#define SMC_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) return SMC_ERR_CUDA;     \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// True while `s` is being captured into a graph.
+bool capturing(cudaStream_t s);
+
+// Make sure the growable workspace holds `bytes`; grows only outside capture.
+smc_status ensure_ws(smc_ctx* ctx, size_t bytes, cudaStream_t s);
+
+// Set the context's device current for the calling thread.
+smc_status use_device(smc_ctx* ctx);
+
+// Launch shape: lanes per particle and threads per block for `op`.
+void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* lanes,
+                  int* threads);
+
+}  // namespace smc_host

@@ -1,0 +1,183 @@
+// device.cuh -- device primitives shared by the sm_103a kernels.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) written from its
+// published definition, the uniform and Box-Muller transforms of the
+// library's random streams, MUFU wrappers, warp reductions, the device
+// status word and the helpers that keep FP64 instructions out of per-element
+// loops (GB300 has very little FP64 throughput).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace smc {
+
+// ---------------------------------------------------------------- status
+enum : uint32_t {
+    ST_NONFINITE = 1u, ST_ZERO_WEIGHT = 2u, ST_TIMEOUT = 4u, ST_BADARG = 8u
+};
+
+__device__ __forceinline__ void raise_status(uint32_t* st, uint32_t bit) {
+    if (st) atomicOr(st, bit);
+}
+
+// Upper bound on polls of a flag written by another CTA; with the
+// nanosleep back-off this is a few seconds, far beyond any legal wait.
+constexpr uint32_t kSpinLimit = 4u << 20;
+
+// ---------------------------------------------------------------- Philox
+enum : uint32_t { RNG_MOVE = 1, RNG_ACCEPT = 2, RNG_RESAMPLE = 3, RNG_EXCHANGE = 4, RNG_PFNOISE = 5 };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t m0 = 0xD2511F53u, m1 = 0xCD9E8D57u;
+        uint32_t hi0 = __umulhi(m0, c.x), lo0 = m0 * c.x;
+        uint32_t hi1 = __umulhi(m1, c.z), lo1 = m1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// counter = (index, block, step lo, purpose | step hi << 8), key = seed halves
+__device__ __forceinline__ uint4 draw(uint64_t seed, uint32_t purpose, uint64_t step,
+                                      uint32_t index, uint32_t block) {
+    uint4 c = make_uint4(index, block, (uint32_t)step,
+                         (purpose & 0xFFu) | ((uint32_t)(step >> 32) << 8));
+    return philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ __forceinline__ uint32_t word_of(uint4 w, int i) {
+    return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
+}
+
+// (2k+1) 2^-24 with k the top 23 bits: exact in float, strictly inside (0,1)
+__device__ __forceinline__ float u01(uint32_t w) {
+    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+}
+
+// Box-Muller on one word pair: r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2)
+__device__ __forceinline__ void box_muller(uint32_t a, uint32_t b, float& z0, float& z1) {
+    float r = sqrtf(-2.0f * logf(u01(a)));
+    float s, c;
+    sincospif(2.0f * u01(b), &s, &c);
+    z0 = r * c;
+    z1 = r * s;
+}
+
+// normals j < n of (seed, purpose, step, index): pair p uses words 2p, 2p+1
+template <int NMAX>
+__device__ __forceinline__ void normals(uint64_t seed, uint32_t purpose, uint64_t step,
+                                        uint32_t index, int n, float (&z)[NMAX]) {
+#pragma unroll
+    for (int b = 0; b < (NMAX + 3) / 4; ++b) {
+        if (4 * b < n) {
+            uint4 w = draw(seed, purpose, step, index, (uint32_t)b);
+            float z0, z1, z2, z3;
+            box_muller(w.x, w.y, z0, z1);
+            box_muller(w.z, w.w, z2, z3);
+            if (4 * b + 0 < NMAX) z[4 * b + 0] = z0;
+            if (4 * b + 1 < NMAX) z[4 * b + 1] = z1;
+            if (4 * b + 2 < NMAX) z[4 * b + 2] = z2;
+            if (4 * b + 3 < NMAX) z[4 * b + 3] = z3;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- MUFU
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float lg2(float x) {
+    float y;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+constexpr double kLn2 = 0.6931471805599453094;
+constexpr double kLog2e = 1.4426950408889634074;
+
+// ---------------------------------------------------------------- FP64-light helpers
+// Exact split of a double into hi + lo floats by integer operations only
+// (no FP64 pipe): hi keeps the top 24 significant bits (truncated), lo the
+// next 24 (rounded).  Magnitudes below 2^-74 give 0 and magnitudes of 2^100
+// and above (and infinities) give +-1e30: the callers only exponentiate
+// non-positive differences, for which both ends are exact enough.
+__device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
+    int e = (int)((hw >> 20) & 0x7FFu);
+    uint32_t sign = hw & 0x80000000u;
+    if (e < 949) { hi = 0.0f; lo = 0.0f; return; }
+    if (e >= 1023 + 100) { hi = sign ? -1e30f : 1e30f; lo = 0.0f; return; }
+    uint32_t fh = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
+    hi = __uint_as_float(fh);
+    float r = (float)(lw & 0x1FFFFFFFu);                        // 29-bit remainder
+    float scale = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);  // 2^(e-1075)
+    lo = sign ? -(r * scale) : r * scale;
+}
+
+// exp(d) for an FP64 d <= 0 given as hi + lo floats, in FP32: the argument
+// is reduced in double-float (Cody-Waite style split of log2 e), 2^f comes
+// from ex2.approx and 2^k is assembled in the exponent.  Results below
+// 2^-126 flush to 0.  Relative error ~ 2^-22.
+__device__ __forceinline__ float exp_hilo(float hi, float lo) {
+    const float L2E_HI = 1.44269502162933349609375f;   // log2(e) rounded to float
+    const float L2E_LO = 1.925963033500011e-08f;       // log2(e) - L2E_HI
+    float ph = hi * L2E_HI;
+    float k = rintf(ph);
+    if (k < -126.0f) return 0.0f;
+    float pl = fmaf(hi, L2E_HI, -ph);
+    float f = (ph - k) + (pl + fmaf(hi, L2E_LO, lo * L2E_HI));
+    float p2 = __uint_as_float((uint32_t)((int)k + 127) << 23);
+    return ex2(f) * p2;
+}
+
+// FP64 -> sortable signed 64-bit key (total order for non-NaN values)
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
+}
+__device__ __forceinline__ bool disnan(double x) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+}
+
+// float (normal or zero) -> double by integer operations
+__device__ __forceinline__ double f2d_bits(float f) {
+    uint32_t u = __float_as_uint(f);
+    uint32_t e = (u >> 23) & 0xFFu;
+    if (e == 0) return 0.0;
+    unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                           ((unsigned long long)(e - 127 + 1023) << 52) |
+                           ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
+// ---------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum_d(double v, unsigned mask = 0xFFFFFFFFu) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+// Kahan accumulation in FP32 (the accumulated values share one sign here)
+struct Kahan {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        float y = v - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+}  // namespace smc

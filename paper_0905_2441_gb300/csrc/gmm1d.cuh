@@ -1,0 +1,207 @@
+// gmm1d.cuh -- the univariate mixture log-likelihood of one particle,
+// evaluated by a slice of L cooperating lanes over data staged in shared
+// memory (Section 4.1 product-sum; Section 4.1.3: one likelihood split over
+// several threads when the data are many).
+//
+// Arithmetic, per datum n and component k, in base-2 log units:
+//   t_k   = (y_n - mu_k) r            r = sqrt(log2(e) / (2 sigma^2))
+//         = fma(y_n, r, nu_k)         nu_k = -mu_k r
+//   a_k   = log2 w_k - t_k^2
+//   m_n   = max_k a_k,  s_n = sum_k 2^(a_k - m_n) in [1, K]
+//   log2 p(y_n | mu) = m_n + log2 s_n + const
+// The products of 16 consecutive s_n are formed before one lg2 (each
+// s_n <= K <= 32, so the product stays below 2^80), the m_n of the same 16
+// data are summed in FP32 and each group total enters a Kahan accumulator.
+// The lane partials meet in FP64.  Gradient: d l / d mu_k =
+// sum_n r_nk (y_n - mu_k) / sigma^2 = (1/(sigma^2 r)) sum_n (e_k / s_n) t_k.
+#pragma once
+#include "device.cuh"
+
+namespace smc {
+
+constexpr int kMaxK1d = 32;
+
+struct Gmm1dArgs {
+    float r;            // sqrt(log2(e) / (2 sigma^2))
+    float gscale;       // 1 / (sigma^2 r)
+    float lo, hi;       // prior box
+    double cst;         // N (-1/2 ln(2 pi sigma^2)) [+ N ln w when weights are equal]
+    float lw2[kMaxK1d]; // log2 w_k (padding components: -inf)
+};
+
+// Stage y[n0, n0+cnt) into shared memory.  A bulk asynchronous copy moves
+// the 16-byte aligned body (completion on an mbarrier, bounded wait); the
+// unaligned head and tail use plain loads.  Ends with __syncthreads().
+__device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, int64_t n0,
+                                        int cnt, uint64_t* mbar, uint32_t& phase,
+                                        uint32_t* status) {
+    const float* src = y + n0;
+    uintptr_t a = reinterpret_cast<uintptr_t>(src);
+    int head = (int)(((16u - (uint32_t)(a & 15u)) & 15u) / 4u);
+    if ((a & 3u) != 0) head = cnt;  // not even float-aligned: plain loads only
+    if (head > cnt) head = cnt;
+    int body = ((cnt - head) / 4) * 4;
+    // the shared destination must share the source's 16-byte phase
+    bool bulk = body >= 64 && ((reinterpret_cast<uintptr_t>(ys + head) & 15u) == 0);
+    if (!bulk) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) ys[i] = src[i];
+        __syncthreads();
+        return;
+    }
+    uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+    if (threadIdx.x == 0) {
+        // order earlier generic-proxy reads of this buffer before the async write
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        uint32_t bytes = (uint32_t)body * 4u;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                     :: "r"(mb), "r"(bytes) : "memory");
+        uint32_t dst = (uint32_t)__cvta_generic_to_shared(ys + head);
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+            :: "r"(dst), "l"(src + head), "r"(bytes), "r"(mb) : "memory");
+    }
+    for (int i = threadIdx.x; i < head; i += blockDim.x) ys[i] = src[i];
+    for (int i = head + body + threadIdx.x; i < cnt; i += blockDim.x) ys[i] = src[i];
+    // bounded wait for the copy
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(mb), "r"(phase) : "memory");
+        if (!done && it > 64) __nanosleep(64);
+    }
+    if (!done) {
+        raise_status(status, ST_TIMEOUT);
+        // wait once more, again bounded, so no copy is left in flight
+        for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                "selp.u32 %0, 1, 0, p;\n\t}"
+                : "=r"(done) : "r"(mb), "r"(phase) : "memory");
+            __nanosleep(256);
+        }
+    }
+    phase ^= 1u;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void init_mbar(uint64_t* mbar) {
+    if (threadIdx.x == 0) {
+        uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(mb) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+}
+
+// Per-lane partial over the data this lane owns in a staged chunk
+// ys[0, cnt): n = lane, lane + L, ...  The state carries across chunks.
+template <int K, bool GRAD, bool EQW>
+struct SliceAcc {
+    static constexpr int KG = GRAD ? K : 1;
+    Kahan ll;          // sum over groups of (sum m_n + log2 prod s_n)
+    float msum = 0.0f; // current group's sum of m_n
+    float prod = 1.0f; // current group's product of s_n
+    int cnt = 0;
+    float gch[KG];
+    Kahan gacc[KG];
+
+    __device__ __forceinline__ SliceAcc() {
+#pragma unroll
+        for (int k = 0; k < KG; ++k) gch[k] = 0.0f;
+    }
+
+    __device__ __forceinline__ void flush() {
+        ll.add(msum + lg2(prod));
+        msum = 0.0f;
+        prod = 1.0f;
+        cnt = 0;
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int k = 0; k < KG; ++k) {
+                gacc[k].add(gch[k]);
+                gch[k] = 0.0f;
+            }
+        }
+    }
+
+    __device__ __forceinline__ void run(const float* ys, int cnt_total, int lane, int L,
+                                        const float (&nu)[K], const float (&lw2)[K], float r) {
+#pragma unroll 2
+        for (int n = lane; n < cnt_total; n += L) {
+            float yv = ys[n];
+            float t[K], a[K];
+            float m = -INFINITY;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                t[k] = fmaf(yv, r, nu[k]);
+                if constexpr (EQW) a[k] = -t[k] * t[k];
+                else a[k] = fmaf(-t[k], t[k], lw2[k]);
+                m = fmaxf(m, a[k]);
+            }
+            float s = 0.0f;
+            float e[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                e[k] = ex2(a[k] - m);
+                s += e[k];
+            }
+            msum += m;
+            prod *= s;
+            if constexpr (GRAD) {
+                float rs = rcp(s);
+#pragma unroll
+                for (int k = 0; k < KG; ++k) gch[k] = fmaf(e[k] * rs, t[k], gch[k]);
+            }
+            if (++cnt == 16) flush();
+        }
+    }
+
+    // Reduce over the slice; every lane of the warp must call this.
+    // Returns the particle's log-likelihood; g receives the gradient.
+    __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P, float (&g)[K]) {
+        if (cnt) flush();
+        double part = (double)ll.s - (double)ll.c;
+        for (int o = L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float v = gacc[k].s - gacc[k].c;
+                for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                g[k] = v * P.gscale;
+            }
+        }
+        return part * kLn2 + P.cst;
+    }
+};
+
+// Chunk size of the staged data (floats) and the shared-memory bytes a
+// kernel using the slice evaluator needs: data buffer + mbarrier.
+constexpr int kYChunk = 8192;
+constexpr size_t kYSmemBytes = kYChunk * sizeof(float) + 16;
+
+__device__ __forceinline__ uint64_t* ychunk_mbar(float* ys) {
+    return reinterpret_cast<uint64_t*>(ys + kYChunk);
+}
+
+// Run one slice accumulator over all N data, staging chunk by chunk.  The
+// whole block calls this (it contains barriers); `active` slices compute.
+template <int K, bool GRAD, bool EQW>
+__device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, float* ys,
+                                                const float* __restrict__ y, int64_t N,
+                                                bool active, int lane, int L,
+                                                const float (&nu)[K], const float (&lw2)[K],
+                                                float r, uint32_t& phase, uint32_t* status) {
+    uint64_t* mbar = ychunk_mbar(ys);
+    for (int64_t c0 = 0; c0 < N; c0 += kYChunk) {
+        int cnt = (int)((N - c0) < kYChunk ? (N - c0) : kYChunk);
+        stage_y(ys, y, c0, cnt, mbar, phase, status);
+        if (active) acc.run(ys, cnt, lane, L, nu, lw2, r);
+        __syncthreads();
+    }
+}
+
+}  // namespace smc

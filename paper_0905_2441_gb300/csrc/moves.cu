@@ -1,0 +1,389 @@
+// moves.cu -- smc_mh_move (random-walk MH and MALA with the gather after
+// resampling fused in) and smc_popmcmc_sweep (many independent populations
+// of tempered chains in one persistent launch with a work queue).
+// Sections 3.1, 4.1.1, 4.1.2 of Lee, Yau, Giles, Doucet & Holmes (2009).
+#include <cmath>
+
+#include "ctx.hpp"
+#include "gmm1d.cuh"
+
+using namespace smc_host;
+
+namespace smc {
+
+// accept test in FP64 on FP32 inputs: log u < log alpha
+__device__ __forceinline__ bool accept(uint32_t w, double log_alpha) {
+    return (double)logf(u01(w)) < log_alpha;
+}
+
+// Block-wide count of accepted moves, one global atomic per block.
+__device__ __forceinline__ void count_accepts(bool a, uint32_t* accept_count, uint32_t* s_cnt) {
+    unsigned m = __ballot_sync(0xFFFFFFFFu, a);
+    if ((threadIdx.x & 31) == 0 && m) atomicAdd(s_cnt, (uint32_t)__popc(m));
+    __syncthreads();
+    if (threadIdx.x == 0 && accept_count && *s_cnt) atomicAdd(accept_count, *s_cnt);
+}
+
+template <int K, bool MALA, bool EQW>
+__global__ void __launch_bounds__(256) k_mh_move(
+    const float* __restrict__ y, int64_t N, const float* theta_in, const double* ll_in,
+    const float* grad_in, const int32_t* __restrict__ anc, const int32_t* __restrict__ do_flag,
+    float* theta_out, double* ll_out, float* grad_out, int64_t M, const float* __restrict__ beta,
+    int64_t beta_stride, float scale, uint64_t seed, uint64_t step, uint32_t* accept_count,
+    Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
+    extern __shared__ __align__(16) float ys[];
+    __shared__ uint32_t s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    init_mbar(ychunk_mbar(ys));
+    const int lane = threadIdx.x % L;
+    const int ppb = blockDim.x / L;
+    const int64_t p = (int64_t)blockIdx.x * ppb + threadIdx.x / L;
+    const bool active = p < M;
+
+    int64_t src = p;
+    if (active && anc && (!do_flag || *do_flag != 0)) src = anc[p];
+    float mu[K], g[K], z[K], prop[K];
+    double l = 0.0;
+    float b = 0.0f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) { mu[k] = 0.0f; g[k] = 0.0f; z[k] = 0.0f; }
+    if (active) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k < Kreal) {
+                mu[k] = theta_in[(int64_t)k * M + src];
+                if (MALA) g[k] = grad_in[(int64_t)k * M + src];
+            }
+        }
+        l = ll_in[src];
+        b = beta[p * beta_stride];
+        normals<K>(seed, RNG_MOVE, step, (uint32_t)p, Kreal, z);
+    }
+    const float hh2 = 0.5f * scale * scale;
+    bool in_box = active;
+    float mf[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        mf[k] = MALA ? fmaf(hh2 * b, g[k], mu[k]) : mu[k];
+        prop[k] = k < Kreal ? fmaf(scale, z[k], mf[k]) : 0.0f;
+        if (k < Kreal) in_box &= (prop[k] >= P.lo) & (prop[k] <= P.hi);
+    }
+    float nu[K], lw2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        nu[k] = -prop[k] * P.r;
+        lw2[k] = P.lw2[k];
+    }
+    SliceAcc<K, MALA, EQW> acc;
+    uint32_t phase = 0;
+    slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+    float gp[K];
+    double lp = acc.finish(L, P, gp);
+
+    bool acc_ok = false;
+    if (in_box && lane == 0) {
+        double log_alpha = (double)b * (lp - l);
+        if (MALA) {
+            float fwd = 0.0f, bwd = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (k < Kreal) {
+                    float df = prop[k] - mf[k];
+                    float db = mu[k] - fmaf(hh2 * b, gp[k], prop[k]);
+                    fwd = fmaf(df, df, fwd);
+                    bwd = fmaf(db, db, bwd);
+                }
+            }
+            log_alpha += (double)((fwd - bwd) / (2.0f * scale * scale));
+        }
+        if (lp != lp) raise_status(status, ST_NONFINITE);
+        acc_ok = accept(draw(seed, RNG_ACCEPT, step, (uint32_t)p, 0u).x, log_alpha);
+    }
+    if (active && lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (k < Kreal) {
+                theta_out[(int64_t)k * M + p] = acc_ok ? prop[k] : mu[k];
+                if (MALA) grad_out[(int64_t)k * M + p] = acc_ok ? gp[k] : g[k];
+            }
+        }
+        ll_out[p] = acc_ok ? lp : l;
+    }
+    count_accepts(acc_ok, accept_count, &s_cnt);
+}
+
+// ------------------------------------------------------------------ population MCMC
+// Work queue: blocks take populations in `order` until the queue is empty;
+// the last block to leave resets the queue.  Stage 1 runs the RW-MH move of
+// every chain of the population (passes of blockDim/L chains), stage 2 the
+// disjoint adjacent exchanges, one thread per pair.
+template <int K, bool EQW>
+__global__ void __launch_bounds__(256) k_popmcmc_sweep(
+    const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
+    const float* __restrict__ beta, const int32_t* __restrict__ offsets,
+    const int32_t* __restrict__ order, int32_t n_pops, float scale, uint64_t seed,
+    uint64_t sweep, unsigned long long* stats, unsigned long long* queue,
+    unsigned long long* done, Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
+    extern __shared__ __align__(16) float ys[];
+    __shared__ int32_t s_pop;
+    __shared__ uint32_t s_mh, s_sw, s_try;
+    init_mbar(ychunk_mbar(ys));
+    if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
+    const int lane = threadIdx.x % L;
+    const int ppb = blockDim.x / L;
+    uint32_t phase = 0;
+    // all data resident in shared memory when they fit: stage once
+    const bool resident = N <= kYChunk;
+    if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys), phase, status);
+    float lw2[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) lw2[k] = P.lw2[k];
+
+    while (true) {
+        if (threadIdx.x == 0) {
+            unsigned long long t = atomicAdd(queue, 1ull);
+            s_pop = t < (unsigned long long)n_pops ? (int32_t)t : -1;
+        }
+        __syncthreads();
+        const int32_t qi = s_pop;
+        __syncthreads();
+        if (qi < 0) break;
+        const int32_t q = order ? order[qi] : qi;
+        const int64_t base = offsets[q];
+        const int Mq = (int)(offsets[q + 1] - base);
+        // ---- stage 1: random-walk MH for every chain
+        for (int c0 = 0; c0 < Mq; c0 += ppb) {
+            const int c = c0 + (int)threadIdx.x / L;
+            const bool active = c < Mq;
+            const int64_t gidx = base + c;
+            float mu[K], z[K], prop[K], nu[K];
+            double l = 0.0;
+            float b = 0.0f;
+#pragma unroll
+            for (int k = 0; k < K; ++k) { mu[k] = 0.0f; z[k] = 0.0f; }
+            if (active) {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (k < Kreal) mu[k] = theta[(int64_t)k * Mtot + gidx];
+                l = ll[gidx];
+                b = beta[gidx];
+                normals<K>(seed, RNG_MOVE, sweep, (uint32_t)gidx, Kreal, z);
+            }
+            bool in_box = active;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                prop[k] = k < Kreal ? fmaf(scale, z[k], mu[k]) : 0.0f;
+                if (k < Kreal) in_box &= (prop[k] >= P.lo) & (prop[k] <= P.hi);
+                nu[k] = -prop[k] * P.r;
+            }
+            SliceAcc<K, false, EQW> acc;
+            if (resident) {
+                if (in_box) acc.run(ys, (int)N, lane, L, nu, lw2, P.r);
+            } else {
+                slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+            }
+            float gdummy[K];
+            double lp = acc.finish(L, P, gdummy);
+            bool ok = false;
+            if (in_box && lane == 0) {
+                if (lp != lp) raise_status(status, ST_NONFINITE);
+                ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)gidx, 0u).x,
+                            (double)b * (lp - l));
+            }
+            if (active && lane == 0 && ok) {
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (k < Kreal) theta[(int64_t)k * Mtot + gidx] = prop[k];
+                ll[gidx] = lp;
+            }
+            unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
+            if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s_mh, (uint32_t)__popc(m));
+        }
+        __syncthreads();
+        // ---- stage 2: exchange moves on disjoint adjacent pairs
+        if (Mq >= 2) {
+            const uint32_t par = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
+            const int npairs = par == 0 ? Mq / 2 : (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
+            for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
+                int ia, ib;
+                if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
+                else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
+                else { ia = Mq - 1; ib = 0; }
+                const int64_t ga = base + ia, gb = base + ib;
+                const double la = ll[ga], lb = ll[gb];
+                const double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
+                uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
+                if (accept(word_of(w, j & 3), log_alpha)) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        if (k < Kreal) {
+                            float t = theta[(int64_t)k * Mtot + ga];
+                            theta[(int64_t)k * Mtot + ga] = theta[(int64_t)k * Mtot + gb];
+                            theta[(int64_t)k * Mtot + gb] = t;
+                        }
+                    }
+                    ll[ga] = lb;
+                    ll[gb] = la;
+                    atomicAdd(&s_sw, 1u);
+                }
+            }
+            if (threadIdx.x == 0) atomicAdd(&s_try, (uint32_t)npairs);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (stats) {
+            if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
+            if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
+            if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
+        }
+        __threadfence();
+        unsigned long long d = atomicAdd(done, 1ull);
+        if (d == (unsigned long long)gridDim.x - 1) {
+            *queue = 0ull;
+            __threadfence();
+            *done = 0ull;
+        }
+    }
+}
+
+}  // namespace smc
+
+namespace smc_host {
+
+smc_status gmm1d_prepare(const smc_gmm* model, int64_t N, smc::Gmm1dArgs* P, int* Kpad,
+                         bool* eqw);
+
+template <int K, bool MALA, bool EQW>
+static smc_status launch_move(int blocks, int threads, cudaStream_t s, const float* y, int64_t N,
+                              const float* th, const double* l, const float* g, const int32_t* anc,
+                              const int32_t* flag, float* tho, double* lo, float* go, int64_t M,
+                              const float* beta, int64_t bs, float scale, uint64_t seed,
+                              uint64_t step, uint32_t* acc, const smc::Gmm1dArgs& P, int L, int Kr,
+                              uint32_t* st) {
+    smc::k_mh_move<K, MALA, EQW><<<blocks, threads, smc::kYSmemBytes, s>>>(
+        y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs, scale, seed, step, acc, P, L, Kr, st);
+    return cuda_ok(cudaGetLastError());
+}
+
+template <int K>
+static smc_status dispatch_move(bool mala, bool eqw, int blocks, int threads, cudaStream_t s,
+                                const float* y, int64_t N, const float* th, const double* l,
+                                const float* g, const int32_t* anc, const int32_t* flag,
+                                float* tho, double* lo, float* go, int64_t M, const float* beta,
+                                int64_t bs, float scale, uint64_t seed, uint64_t step,
+                                uint32_t* acc, const smc::Gmm1dArgs& P, int L, int Kr,
+                                uint32_t* st) {
+#define SMC_MV(MA, EQ) \
+    launch_move<K, MA, EQ>(blocks, threads, s, y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs, \
+                           scale, seed, step, acc, P, L, Kr, st)
+    if (mala) return eqw ? SMC_MV(true, true) : SMC_MV(true, false);
+    return eqw ? SMC_MV(false, true) : SMC_MV(false, false);
+#undef SMC_MV
+}
+
+template <int K, bool EQW>
+static smc_status launch_pop(const smc_ctx* ctx, int threads, cudaStream_t s, const float* y,
+                             int64_t N, float* th, double* l, int64_t Mt, const float* beta,
+                             const int32_t* off, const int32_t* order, int32_t n_pops,
+                             float scale, uint64_t seed, uint64_t sweep, uint64_t* stats,
+                             const smc::Gmm1dArgs& P, int L, int Kr) {
+    auto kern = smc::k_popmcmc_sweep<K, EQW>;
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smc::kYSmemBytes) !=
+            cudaSuccess || occ < 1)
+        occ = 1;
+    int64_t grid = (int64_t)ctx->num_sms * occ;
+    if (grid > n_pops) grid = n_pops;
+    kern<<<(unsigned)grid, threads, smc::kYSmemBytes, s>>>(
+        y, N, th, l, Mt, beta, off, order, n_pops, scale, seed, sweep,
+        reinterpret_cast<unsigned long long*>(stats), ctx->d_counters + CNT_POP_QUEUE,
+        ctx->d_counters + CNT_POP_DONE, P, L, Kr, ctx->d_status);
+    return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace smc_host
+
+extern "C" smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
+                                  const float* theta_in, const double* loglik_in,
+                                  const float* grad_in, const int32_t* anc,
+                                  const int32_t* do_flag, float* theta_out, double* loglik_out,
+                                  float* grad_out, int64_t M, const float* beta,
+                                  int64_t beta_stride, float scale, int32_t kind, uint64_t seed,
+                                  uint64_t step, uint32_t* accept_count, void* stream) {
+    if (!ctx || M < 0 || N < 0 || (kind != SMC_MOVE_RW && kind != SMC_MOVE_MALA)) return SMC_ERR_ARG;
+    if (M == 0) return SMC_OK;
+    if (!theta_in || !loglik_in || !theta_out || !loglik_out || !beta || (N > 0 && !y) ||
+        beta_stride < 0 || !(scale >= 0.0f) || !std::isfinite(scale))
+        return SMC_ERR_ARG;
+    if (kind == SMC_MOVE_MALA && (!grad_in || !grad_out)) return SMC_ERR_ARG;
+    if (anc && (theta_in == theta_out || loglik_in == loglik_out ||
+                (kind == SMC_MOVE_MALA && grad_in == grad_out)))
+        return SMC_ERR_ARG;
+    smc::Gmm1dArgs P;
+    int Kp;
+    bool eqw;
+    smc_status st = gmm1d_prepare(model, N, &P, &Kp, &eqw);
+    if (st != SMC_OK) return st;
+    st = use_device(ctx);
+    if (st != SMC_OK) return st;
+    int L, threads;
+    launch_shape(ctx, SMC_OP_MOVE, M, N, model->K, &L, &threads);
+    int ppb = threads / L;
+    int64_t blocks = (M + ppb - 1) / ppb;
+    if (blocks > 0x7FFFFFFF) return SMC_ERR_ARG;
+    cudaStream_t s = as_stream(stream);
+    bool mala = kind == SMC_MOVE_MALA;
+    const int Kr = model->K;
+#define SMC_DM(KK)                                                                              \
+    dispatch_move<KK>(mala, eqw, (int)blocks, threads, s, y, N, theta_in, loglik_in, grad_in,  \
+                      anc, do_flag, theta_out, loglik_out, grad_out, M, beta, beta_stride,     \
+                      scale, seed, step, accept_count, P, L, Kr, ctx->d_status)
+    switch (Kp) {
+        case 1: return SMC_DM(1);
+        case 2: return SMC_DM(2);
+        case 4: return SMC_DM(4);
+        case 8: return SMC_DM(8);
+        case 16: return SMC_DM(16);
+        case 32: return SMC_DM(32);
+        default: return SMC_ERR_UNSUPPORTED;
+    }
+#undef SMC_DM
+}
+
+extern "C" smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y,
+                                        int64_t N, float* theta, double* loglik, int64_t M_total,
+                                        const float* beta, const int32_t* pop_offsets,
+                                        const int32_t* pop_order, int32_t n_pops, float scale,
+                                        uint64_t seed, uint64_t sweep, uint64_t* stats,
+                                        void* stream) {
+    if (!ctx || M_total < 0 || N < 0 || n_pops < 0) return SMC_ERR_ARG;
+    if (n_pops == 0 || M_total == 0) return SMC_OK;
+    if (!theta || !loglik || !beta || !pop_offsets || (N > 0 && !y) || !(scale >= 0.0f) ||
+        !std::isfinite(scale) || M_total > 0x7FFFFFFF)
+        return SMC_ERR_ARG;
+    smc::Gmm1dArgs P;
+    int Kp;
+    bool eqw;
+    smc_status st = gmm1d_prepare(model, N, &P, &Kp, &eqw);
+    if (st != SMC_OK) return st;
+    st = use_device(ctx);
+    if (st != SMC_OK) return st;
+    int L, threads;
+    launch_shape(ctx, SMC_OP_POPMCMC, M_total, N, model->K, &L, &threads);
+    cudaStream_t s = as_stream(stream);
+    const int Kr = model->K;
+#define SMC_PP(KK, EQ)                                                                       \
+    launch_pop<KK, EQ>(ctx, threads, s, y, N, theta, loglik, M_total, beta, pop_offsets,      \
+                       pop_order, n_pops, scale, seed, sweep, stats, P, L, Kr)
+    switch (Kp) {
+        case 1: return eqw ? SMC_PP(1, true) : SMC_PP(1, false);
+        case 2: return eqw ? SMC_PP(2, true) : SMC_PP(2, false);
+        case 4: return eqw ? SMC_PP(4, true) : SMC_PP(4, false);
+        case 8: return eqw ? SMC_PP(8, true) : SMC_PP(8, false);
+        case 16: return eqw ? SMC_PP(16, true) : SMC_PP(16, false);
+        case 32: return eqw ? SMC_PP(32, true) : SMC_PP(32, false);
+        default: return SMC_ERR_UNSUPPORTED;
+    }
+#undef SMC_PP
+}

@@ -1,0 +1,199 @@
+"""Sampler drivers over the C ABI: the tempered SMC sampler (Sections 3.3,
+4.1.2), population MCMC over many populations (Sections 3.1, 4.1.1) and the
+bootstrap particle filter (Sections 3.2, 4.2).
+
+Each driver owns its device buffers (torch tensors), issues the C-ABI calls
+of one step on the current stream, and can capture a whole run into one CUDA
+graph: every per-step decision (resample or not) is taken on the device
+(the ESS flag), so nothing syncs with the host until the run ends.  The
+plain and captured forms issue identical kernels with identical Philox
+counters, so their outputs are bitwise equal.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import _lib as L
+from . import api
+
+
+def _dev(a, dtype):
+    if isinstance(a, torch.Tensor):
+        return a.to(device="cuda", dtype=dtype).contiguous()
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+class _Graphable:
+    """run(graph=True) captures `_body(...)` once and replays it."""
+
+    def _capture(self, fn):
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                fn()
+        torch.cuda.current_stream().wait_stream(s)
+        return g
+
+
+class SMCSampler(_Graphable):
+    """Tempered SMC sampler: particles from the uniform prior, beta_0 = 0; per
+    step t: reweight by (beta_t - beta_{t-1}) l, resample (systematic) iff
+    ESS < ess_frac * M, one RW-MH or MALA move targeting prior * L^beta_t."""
+
+    def __init__(self, ctx: api.Context, model: api.GMM, y, theta0, betas, kind=L.MOVE_RW,
+                 scale=0.1, seed=1234, ess_frac=0.5):
+        self.ctx, self.model, self.kind = ctx, model, kind
+        self.scale, self.seed, self.ess_frac = float(scale), int(seed), float(ess_frac)
+        self.y = _dev(y, torch.float32)
+        th = _dev(theta0, torch.float32)
+        self.K, self.M = th.shape
+        self.betas_host = np.asarray(betas, np.float64)
+        self.T = self.betas_host.size - 1
+        self.betas = _dev(self.betas_host.astype(np.float32), torch.float32)
+        self.theta = [th.clone(), torch.empty_like(th)]
+        self.ll = [torch.empty(self.M, dtype=torch.float64, device="cuda") for _ in range(2)]
+        mala = kind == L.MOVE_MALA
+        self.grad = [torch.empty_like(th) for _ in range(2)] if mala else [None, None]
+        self.lw = torch.zeros(self.M, dtype=torch.float64, device="cuda")
+        self.W = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self.anc = torch.empty(self.M, dtype=torch.int32, device="cuda")
+        self.flags = torch.zeros(self.T + 1, dtype=torch.int32, device="cuda")
+        self.hist = torch.zeros(self.T + 1, 4, dtype=torch.float64, device="cuda")
+        self.accepts = torch.zeros(self.T + 1, dtype=torch.int32, device="cuda")
+        ctx.reserve(self.M)
+        self.reset(theta0)
+
+    def reset(self, theta0=None):
+        if theta0 is not None:
+            self.theta[0].copy_(_dev(theta0, torch.float32))
+        self.cur = 0
+        self.lw.zero_()
+        self.accepts.zero_()
+        api.loglik_batch(self.ctx, self.model, self.y, self.theta[0], out=self.ll[0],
+                         grad=self.grad[0])
+
+    def step(self, t: int):
+        c, n = self.cur, 1 - self.cur
+        ctx = self.ctx
+        db = float(self.betas_host[t] - self.betas_host[t - 1])
+        flag = self.flags[t:t + 1]
+        api.reweight(ctx, self.ll[c], db, self.lw, self.W, self.hist[t], flag, self.ess_frac)
+        api.resample_systematic(ctx, self.W, self.seed, t, anc=self.anc, do_flag=flag,
+                                logw_reset=self.lw)
+        api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n], self.ll[n],
+                    self.betas[t:t + 1], self.scale, self.seed, t, kind=self.kind,
+                    grad_in=self.grad[c], grad_out=self.grad[n], anc=self.anc, do_flag=flag,
+                    accept_count=self.accepts[t:t + 1])
+        self.cur = n
+
+    def _body(self):
+        for t in range(1, self.T + 1):
+            self.step(t)
+
+    def run(self, graph: bool = False):
+        """Run all T steps; returns log Z (sum of the per-step increments)."""
+        if graph:
+            start = self.cur
+            g = self._capture(self._body)
+            self.cur = start
+            # the capture recorded the buffer swaps; replay from the same state
+            self._graph = g
+            g.replay()
+            self.cur = (start + self.T) % 2
+        else:
+            self._body()
+        return self.log_evidence()
+
+    def log_evidence(self) -> float:
+        return float(self.hist[1:, 0].sum().item())
+
+    @property
+    def state(self):
+        return self.theta[self.cur], self.ll[self.cur]
+
+
+class PopulationMCMC(_Graphable):
+    """Many independent populations of tempered chains (ragged sizes), one
+    persistent launch per sweep: RW-MH for every chain, then the exchange
+    moves on the paper's alternating adjacent pairs."""
+
+    def __init__(self, ctx: api.Context, model: api.GMM, y, offsets, betas, theta0, scale=0.1,
+                 seed=1):
+        self.ctx, self.model, self.scale, self.seed = ctx, model, float(scale), int(seed)
+        self.y = _dev(y, torch.float32)
+        off = np.asarray(offsets, np.int32)
+        self.offsets = _dev(off, torch.int32)
+        sizes = np.diff(off)
+        # longest populations first: the work queue then balances the SMs
+        self.order = _dev(np.argsort(-sizes, kind="stable").astype(np.int32), torch.int32)
+        self.n_pops = off.size - 1
+        self.beta = _dev(betas, torch.float32)
+        self.theta = _dev(theta0, torch.float32).clone()
+        self.K, self.M = self.theta.shape
+        self.ll = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self.stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+        api.loglik_batch(ctx, model, self.y, self.theta, out=self.ll)
+
+    def sweep(self, s: int):
+        api.popmcmc_sweep(self.ctx, self.model, self.y, self.theta, self.ll, self.beta,
+                          self.offsets, self.scale, self.seed, s, order=self.order,
+                          stats=self.stats)
+
+    def run(self, n_sweeps: int, start: int = 0, graph: bool = False):
+        if graph:
+            g = self._capture(lambda: [self.sweep(start + i) for i in range(n_sweeps)])
+            g.replay()
+            self._graph = g
+        else:
+            for i in range(n_sweeps):
+                self.sweep(start + i)
+
+
+class ParticleFilter(_Graphable):
+    """Bootstrap particle filter with systematic resampling after every step;
+    log Z = sum_t [LSE(log g_t) - log M]."""
+
+    def __init__(self, ctx: api.Context, model: api.PFModel, y, M: int, seed: int = 77):
+        self.ctx, self.model, self.M, self.seed = ctx, model, int(M), int(seed)
+        self.y = _dev(y, torch.float32)
+        self.T, self.d = self.y.shape
+        self.x = [torch.zeros(self.d, self.M, device="cuda") for _ in range(2)]
+        self.logg = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self.lw = torch.zeros(self.M, dtype=torch.float64, device="cuda")
+        self.W = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self.anc = torch.arange(self.M, dtype=torch.int32, device="cuda")
+        self.hist = torch.zeros(self.T + 1, 4, dtype=torch.float64, device="cuda")
+        ctx.reserve(self.M)
+        self.cur = 0
+
+    def reset(self):
+        for x in self.x:
+            x.zero_()
+        self.lw.zero_()
+        self.anc.copy_(torch.arange(self.M, dtype=torch.int32, device="cuda"))
+        self.cur = 0
+
+    def step(self, t: int):
+        c, n = self.cur, 1 - self.cur
+        api.pf_step(self.ctx, self.model, self.y[t - 1], self.x[c], self.x[n], self.logg,
+                    self.seed, t, anc=self.anc)
+        api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, self.hist[t], None, 0.5)
+        api.resample_systematic(self.ctx, self.W, self.seed, t, anc=self.anc, logw_reset=self.lw)
+        self.cur = n
+
+    def run(self, graph: bool = False, steps: int | None = None):
+        T = self.T if steps is None else steps
+        if graph:
+            start = self.cur
+            g = self._capture(lambda: [self.step(t) for t in range(1, T + 1)])
+            self.cur = start
+            g.replay()
+            self._graph = g
+            self.cur = (start + T) % 2
+        else:
+            for t in range(1, T + 1):
+                self.step(t)
+        return float(self.hist[1:T + 1, 0].sum().item())
