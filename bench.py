@@ -1,0 +1,466 @@
+#!/usr/bin/env python
+"""Benchmark of the SMC / population-MCMC hot path on GB300.
+
+Default workload (the batched population-MCMC configuration): 512
+independent populations with 8..128 tempered chains each (34.8k chains),
+univariate 8-component mixture, N = 1000 observations.  One step = one sweep
+= one persistent launch (random-walk MH with the fused likelihood for every
+chain, then the exchange moves).  Metric: particle-datum log-likelihood
+evaluations per second (chains x N per sweep).
+
+Other workloads (--workload): smc (4-component tempered SMC sampler,
+M = 8192, 20 temperatures; step = one SMC step), mala (differentiable
+sampler, M = 65536, K = 8, N = 1000, 50 temperatures), pf (d = 3 MSV
+particle filter, M = 2^20; step = one filter step), resample (reweight +
+systematic resampling bandwidth at M = 2^24).
+
+Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun each rank runs its own independent copy of the workload
+(weak scaling, no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 2**20
+FLUSH_BYTES = 256 * 2**20
+
+
+# ------------------------------------------------------------------ helpers
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "_fallback": True}
+
+
+def profile_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e:
+        return None
+    from paper_0905_2441_gb300 import build as b
+    if e.get("source_digest") != b.source_digest():
+        return None  # the kernel changed since the counters were taken
+    return e.get("bytes_per_launch")
+
+
+class Dist:
+    def __init__(self):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = False
+
+    def init(self, torch):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = True
+
+    def barrier(self, torch):
+        if self.pg:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, torch, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, torch, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+# ------------------------------------------------------------------ CPU baseline (oracle)
+def cpu_popmcmc(w, budget_s=10.0, sample_pops=16, max_sweeps=50):
+    """The FP64 oracle on a bounded sample: the first `sample_pops`
+    populations of the same workload, as many sweeps as fit in ~budget_s."""
+    import oracle
+    import synth
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    y = w.data()
+    th = synth.population_particles(w.K, off)
+    beta = synth.population_betas(off)
+    sub = off[: sample_pops + 1].copy()
+    m = int(sub[-1])
+    ths, bs = th[:, :m].copy(), beta[:m].copy()
+    ll = oracle.gmm1d_loglik(y, w.logw(), w.sigma, ths)
+    t0 = time.perf_counter()
+    n = 0
+    while n < max_sweeps and (time.perf_counter() - t0) < budget_s:
+        ths, ll, _ = oracle.popmcmc_sweep(y, w.logw(), w.sigma, (-10, 10), ths, ll, bs, sub,
+                                          w.scale, 3, n)
+        n += 1
+    dt = time.perf_counter() - t0
+    pd = m * w.N * n
+    return {"value": pd / dt, "unit": "p*d/s", "cores": 1, "kind": "oracle",
+            "sample": f"{sample_pops} of {w.n_pops} populations ({m} chains), {n} sweeps, "
+                      f"{dt:.1f} s single-threaded FP64"}
+
+
+# ------------------------------------------------------------------ GPU workloads
+def bench_popmcmc(args, torch, dist):
+    import paper_0905_2441_gb300 as P
+    from paper_0905_2441_gb300 import autotune, samplers
+    import synth
+    w = synth.GMM8_POP
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    y = w.data()
+    th0 = synth.population_particles(w.K, off, seed=4 + dist.rank)
+    beta = synth.population_betas(off)
+    ctx = P.Context()
+    model = P.GMM(w.K, w.sigma)
+    smp = samplers.PopulationMCMC(ctx, model, y, off, beta, th0, scale=w.scale, seed=3 + dist.rank)
+    M, N = smp.M, w.N
+    # launch shape: autotuned on this workload (cached per GPU model)
+    lanes, threads, tune = autotune.tune_popmcmc(ctx, smp, use_cache=not args.retune)
+    smp.theta.copy_(torch.from_numpy(th0).cuda())
+    P.loglik_batch(ctx, model, smp.y, smp.theta, out=smp.ll)
+    ctx.check()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for s in range(args.warmup):
+        smp.sweep(s)
+    torch.cuda.synchronize()
+    # ---- timed: K plain sweeps, L2 flushed before each, CUDA events per sweep
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    dist.barrier(torch)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            ev[i][0].record(stream)
+            smp.sweep(args.warmup + i)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+    dist.barrier(torch)
+    ctx.check()
+    per = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(per) / 1e3
+    t_max = dist.max(torch, t_dev)
+    pd_rank = float(M) * N * args.steps
+    pd_total = dist.sum(torch, pd_rank)
+    value = pd_total / t_max
+    # ---- CUDA-graph form: the configuration's 1000 captured sweeps
+    G = args.graph_sweeps
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    capt = torch.cuda.Stream()
+    capt.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    base = args.warmup + args.steps
+    with torch.cuda.stream(capt):
+        with torch.cuda.graph(g, stream=capt):
+            for i in range(G):
+                smp.sweep(base + i)
+    stream.wait_stream(capt)
+    g.replay()  # warm
+    flush.fill_(1.0)
+    ga.record(stream)
+    g.replay()
+    gb.record(stream)
+    gb.synchronize()
+    t_graph = ga.elapsed_time(gb) / 1e3
+    ctx.check()
+    # ---- end to end through the public API with host buffers
+    e2e = e2e_popmcmc(args, torch, P, ctx, smp)
+    # ---- roofline: MUFU ops of the sweep kernel vs the measured ex2 rate
+    ex2_rate, ex2_ms = measure_peak(P, 0)
+    mufu_per_launch = float(M) * N * (w.K + 1)  # K ex2 + 1 lg2 per particle-datum
+    achieved = mufu_per_launch / (t_dev / args.steps)
+    sm_mhz = clk.summary()["sm_mhz"]
+    roof = {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": achieved / 1e9,
+            "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": achieved / ex2_rate,
+            "traffic": profile_traffic("k_popmcmc_sweep"),
+            "kernel": "k_popmcmc_sweep<8,true>",
+            "ops_per_launch": mufu_per_launch,
+            "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
+                           f"{ex2_ms:.2f} ms microbenchmark",
+            "frac_issued_count": (float(M) * N * (w.K + 1.0 / 16)) / (t_dev / args.steps) / ex2_rate}
+    out = {
+        "metric": "particle-datum loglik evals/s (population MCMC sweeps)",
+        "value": value, "unit": "p*d/s", "n_gpus": dist.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded mixture data and chain states; no dataset)",
+        "config": {"workload": w.name, "n_pops": w.n_pops, "chains": M, "K": w.K, "N": N,
+                   "pop_sizes": "uniform 8..128", "temperatures": "geometric 1e-3..1 per population",
+                   "rw_scale": w.scale, "lanes_per_chain": lanes, "threads_per_block": threads,
+                   "l2": "256 MiB buffer (2x L2) written before every timed sweep, outside its events",
+                   "parallelism": f"independent populations per rank x{dist.world}"},
+        "forms": {"plain_per_step": {"value": value, "ms_per_sweep": 1e3 * t_dev / args.steps},
+                  "graph_captured": {"sweeps": G, "value": float(M) * N * G / t_graph,
+                                     "ms_per_sweep": 1e3 * t_graph / G}},
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+        "clocks": clk.summary(), "wall_s": wall, "autotune": tune,
+    }
+    if sm_mhz:
+        out["roofline"]["sm_mhz_under_load"] = sm_mhz
+    ctx.close()
+    return out
+
+
+def e2e_popmcmc(args, torch, P, ctx, smp):
+    """Per step: pinned host -> device copy of the chain state, one sweep
+    through the public API, device -> host copy of the new state."""
+    M, K, N = smp.M, smp.K, smp.y.numel()
+    h_th = torch.empty(K, M, dtype=torch.float32).pin_memory()
+    h_ll = torch.empty(M, dtype=torch.float64).pin_memory()
+    h_th.copy_(smp.theta.cpu())
+    h_ll.copy_(smp.ll.cpu())
+    stream = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for i in range(steps):
+        smp.theta.copy_(h_th, non_blocking=True)
+        smp.ll.copy_(h_ll, non_blocking=True)
+        smp.sweep(50_000 + i)
+        h_th.copy_(smp.theta, non_blocking=True)
+        h_ll.copy_(smp.ll, non_blocking=True)
+    b.record(stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    nb = K * M * 4 + M * 8
+    return {"value": float(M) * N * steps / t, "unit": "p*d/s", "h2d_bytes_per_step": nb,
+            "d2h_bytes_per_step": nb, "steps": steps}
+
+
+def measure_peak(P, kind):
+    import ctypes as C
+    from paper_0905_2441_gb300 import _lib
+    ops, ms = C.c_double(), C.c_double()
+    st = _lib.load().smc_measure_peak(kind, 8, 4096, C.byref(ops), C.byref(ms))
+    if st != 0:
+        raise RuntimeError(f"smc_measure_peak failed ({st})")
+    return ops.value, ms.value
+
+
+def bench_secondary(torch, P):
+    """Plain per-step vs CUDA-graph forms of the SMC sampler (4-component
+    mixture, M = 8192, 20 temperatures), the differentiable MALA sampler
+    (M = 65536, K = 8, N = 1000, 50 temperatures) and the particle filter
+    (d = 3 MSV, M = 2^20, T = 200): steps/s of each, same kernels and Philox
+    counters in both forms (bitwise-equal outputs)."""
+    from paper_0905_2441_gb300 import samplers
+    import synth
+    out = {}
+    ctx = P.Context()
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    for name, w, kind in (("smc_sampler", synth.GMM4, P.MOVE_RW),
+                          ("mala_sampler", synth.GMM8_MALA, P.MOVE_MALA)):
+        y = w.data()
+        th0 = synth.prior_particles(w.K, w.M, seed=w.particle_seed)
+        betas = synth.geometric_betas(w.T, w.beta_min)
+        smp = samplers.SMCSampler(ctx, P.GMM(w.K, w.sigma), y, th0, betas, kind=kind,
+                                  scale=w.scale, seed=w.method_seed)
+        smp.run()  # warm
+        smp.reset(th0)
+        t_plain = timed(lambda: smp.run())
+        z_plain = smp.log_evidence()
+        th_plain = smp.state[0].clone()
+        smp.reset(th0)
+        g = smp._capture(smp._body)
+        smp.reset(th0)
+        t_graph = timed(lambda: g.replay())
+        z_graph = smp.log_evidence()
+        th_graph = smp.theta[(smp.T) % 2]
+        out[name] = {"workload": w.name, "steps": w.T, "M": w.M, "K": w.K, "N": w.N,
+                     "plain_steps_per_s": w.T / t_plain, "graph_steps_per_s": w.T / t_graph,
+                     "plain_pd_per_s": w.M * w.N * w.T / t_plain,
+                     "graph_pd_per_s": w.M * w.N * w.T / t_graph,
+                     "logZ_plain": z_plain, "logZ_graph": z_graph,
+                     "graph_equals_plain": bool(torch.equal(th_plain, th_graph)) and z_plain == z_graph,
+                     "resampled_steps": int(smp.flags[1:].sum().item())}
+        ctx.check()
+    w = synth.MSV3
+    phi, Sigma, beta = synth.msv_params(w.d, w.phi, w.rho, w.beta)
+    _, yobs = synth.simulate_ssm("msv", w.T, phi, Sigma, beta, seed=w.data_seed)
+    pf = samplers.ParticleFilter(ctx, P.PFModel(P.PF_MSV, phi, synth.chol(Sigma), beta), yobs, w.M,
+                                 seed=w.method_seed)
+    pf.run()
+    pf.reset()
+    t_plain = timed(lambda: pf.run())
+    z_plain = float(pf.hist[1:, 0].sum().item())
+    pf.reset()
+    g = pf._capture(lambda: [pf.step(t) for t in range(1, w.T + 1)])
+    pf.reset()
+    t_graph = timed(lambda: g.replay())
+    z_graph = float(pf.hist[1:, 0].sum().item())
+    out["particle_filter"] = {"workload": w.name, "steps": w.T, "M": w.M,
+                              "plain_particle_steps_per_s": w.M * w.T / t_plain,
+                              "graph_particle_steps_per_s": w.M * w.T / t_graph,
+                              "ms_per_step_graph": 1e3 * t_graph / w.T,
+                              "logZ_plain": z_plain, "logZ_graph": z_graph}
+    ctx.check()
+    ctx.close()
+    return out
+
+
+# ------------------------------------------------------------------ reference arm
+def reference_arm(args):
+    """The oracle timed on the host cores on bounded samples of the same workload."""
+    import synth
+    w = synth.GMM8_POP
+    vals = []
+    for _ in range(args.warmup):
+        cpu_popmcmc(w, budget_s=1.0, sample_pops=2, max_sweeps=1)
+    samples = []
+    for i in range(args.steps):
+        r = cpu_popmcmc(w, budget_s=args.ref_budget, sample_pops=4, max_sweeps=1000)
+        vals.append(r["value"])
+        samples.append(r["sample"])
+    v = statistics.median(vals)
+    return {"impl": "reference", "metric": "particle-datum loglik evals/s (population MCMC sweeps)",
+            "value": v, "unit": "p*d/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": w.name, "K": w.K, "N": w.N},
+            "cpu_baseline": {"value": v, "unit": "p*d/s", "cores": 1, "kind": "oracle",
+                             "sample": samples[0] + f"; median of {args.steps} samples"},
+            "e2e": {"value": v, "unit": "p*d/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="popmcmc", choices=["popmcmc"])
+    ap.add_argument("--graph-sweeps", type=int, default=1000)
+    ap.add_argument("--retune", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-secondary", action="store_true", help="skip the sampler / filter lines")
+    ap.add_argument("--ref-budget", type=float, default=3.0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    dist = Dist()
+    if args.impl == "reference":
+        if dist.rank == 0:
+            print(json.dumps(reference_arm(args)), flush=True)
+        return 0
+    import torch
+    torch.cuda.set_device(dist.local)
+    dist.init(torch)
+    from paper_0905_2441_gb300 import build as b
+    if dist.rank == 0 and not os.path.exists(b.LIB):
+        b.build()
+    dist.barrier(torch)
+    out = bench_popmcmc(args, torch, dist)
+    if dist.rank == 0 and not args.no_secondary:
+        import paper_0905_2441_gb300 as P
+        out["secondary"] = bench_secondary(torch, P)
+    if dist.rank == 0:
+        if not args.no_cpu and dist.world == 1:
+            import synth
+            out["cpu_baseline"] = cpu_popmcmc(synth.GMM8_POP)
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -215,15 +215,17 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
  *   (parity bit 1, the wrap pair only when M_q is even); the bit is
  *   word 0 bit 0 of (seed, EXCHANGE, sweep, index q); pair j swaps iff
  *   log u_j < (beta_a - beta_b)(l_b - l_a), u_j from word 4 + j.
- * pop_order (device int32[n_pops], nullable) is the order in which the work
- *   queue hands out populations (e.g. largest first).
+ * The CTAs take equal chunks of chains from a work queue; a population's
+ * exchange runs as soon as its last chain has moved, so populations of any
+ * size mix freely.  pop_offsets must be non-decreasing with
+ * pop_offsets[0] = 0 and pop_offsets[n_pops] = M_total.
  * stats (device uint64[3], nullable) accumulates {MH accepts, swaps
- *   accepted, swaps attempted}. */
+ *   accepted, swaps attempted}.  Uses n_pops counters of context scratch
+ *   (smc_reserve's max_pops sizes them before graph capture). */
 smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
                              float* theta, double* loglik, int64_t M_total, const float* beta,
-                             const int32_t* pop_offsets, const int32_t* pop_order, int32_t n_pops,
-                             float scale, uint64_t seed, uint64_t sweep, uint64_t* stats,
-                             void* stream);
+                             const int32_t* pop_offsets, int32_t n_pops, float scale,
+                             uint64_t seed, uint64_t sweep, uint64_t* stats, void* stream);
 
 /* ------------------------------------------------------------ particle filter */
 

@@ -20,7 +20,8 @@ PF_MSV, PF_LG = 0, 1
 EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_status_string",
            "smc_set_launch", "smc_get_launch", "smc_loglik_batch", "smc_reweight", "smc_ess",
            "smc_resample_systematic", "smc_gather", "smc_mh_move", "smc_popmcmc_sweep",
-           "pf_step", "smc_rng_words", "smc_rng_normals")
+           "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak")
+PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
 class SmcGmm(C.Structure):
@@ -55,11 +56,12 @@ def _declare(L):
     L.smc_mh_move.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                               _vp, _i64, _vp, _i64, C.c_float, _i32, _u64, _u64, _vp, _vp]
     L.smc_popmcmc_sweep.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _i64, _vp, _vp,
-                                    _vp, _i32, C.c_float, _u64, _u64, _vp, _vp]
+                                    _i32, C.c_float, _u64, _u64, _vp, _vp]
     L.pf_step.argtypes = [_vp, C.POINTER(SmcPfModel), _vp, _vp, _vp, _vp, _vp, _i64, _u64, _u64,
                           _vp]
     L.smc_rng_words.argtypes = [_vp, _u64, _u32, _u64, _u32, _u32, _vp, _vp]
     L.smc_rng_normals.argtypes = [_vp, _u64, _u32, _u64, _u32, _u32, _vp, _vp]
+    L.smc_measure_peak.argtypes = [_i32, _i32, _i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     for name in EXPORTS:
         if name != "smc_status_string":
             getattr(L, name).restype = _st

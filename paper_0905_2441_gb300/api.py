@@ -241,7 +241,7 @@ def mh_move(ctx: Context, model: GMM, y, theta_in, ll_in, theta_out, ll_out, bet
 
 
 def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, scale: float,
-                  seed: int, sweep: int, order=None, stats=None, stream=None):
+                  seed: int, sweep: int, stats=None, stream=None):
     K, M = theta.shape
     n_pops = offsets.numel() - 1
     _need(y, torch.float32, "y")
@@ -249,12 +249,10 @@ def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, sca
     _need(loglik, torch.float64, "loglik", (M,))
     _need(beta, torch.float32, "beta", (M,))
     _need(offsets, torch.int32, "pop_offsets", (n_pops + 1,))
-    _need(order, torch.int32, "pop_order", (n_pops,))
     _need(stats, torch.int64, "stats", (3,))
     m = model.cstruct()
     _chk(L.load().smc_popmcmc_sweep(ctx.handle, C.byref(m), _ptr(y), y.numel(), _ptr(theta),
-                                    _ptr(loglik), M, _ptr(beta), _ptr(offsets), _ptr(order),
-                                    n_pops, float(scale), int(seed), int(sweep), _ptr(stats),
+                                    _ptr(loglik), M, _ptr(beta), _ptr(offsets), n_pops, float(scale), int(seed), int(sweep), _ptr(stats),
                                     _stream(stream)), "smc_popmcmc_sweep")
 
 

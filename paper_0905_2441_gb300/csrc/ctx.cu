@@ -38,6 +38,20 @@ smc_status ensure_ws(smc_ctx* ctx, size_t bytes, cudaStream_t s) {
     return SMC_OK;
 }
 
+smc_status ensure_popdone(smc_ctx* ctx, int64_t n, cudaStream_t s) {
+    if (n <= ctx->popdone_cap) return SMC_OK;
+    if (capturing(s)) return SMC_ERR_ARG;
+    int64_t cap = n + n / 4 + 64;
+    SMC_CUDA(cudaStreamSynchronize(s));
+    if (ctx->d_popdone) SMC_CUDA(cudaFree(ctx->d_popdone));
+    ctx->d_popdone = nullptr;
+    ctx->popdone_cap = 0;
+    SMC_CUDA(cudaMalloc(&ctx->d_popdone, (size_t)cap * sizeof(uint32_t)));
+    SMC_CUDA(cudaMemset(ctx->d_popdone, 0, (size_t)cap * sizeof(uint32_t)));
+    ctx->popdone_cap = cap;
+    return SMC_OK;
+}
+
 void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* lanes,
                   int* threads) {
     if (op >= 0 && op < SMC_OP_COUNT && ctx->lanes[op] > 0) {
@@ -97,6 +111,7 @@ extern "C" smc_status smc_destroy(smc_ctx* ctx) {
     if (ctx->d_counters) cudaFree(ctx->d_counters);
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->ws) cudaFree(ctx->ws);
+    if (ctx->d_popdone) cudaFree(ctx->d_popdone);
     delete ctx;
     return SMC_OK;
 }
@@ -108,7 +123,8 @@ extern "C" smc_status smc_reserve(smc_ctx* ctx, int64_t max_particles, int32_t m
     if (!ctx || max_particles < 0 || max_pops < 0) return SMC_ERR_ARG;
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
-    (void)max_pops;
+    st = ensure_popdone(ctx, max_pops, nullptr);
+    if (st != SMC_OK) return st;
     return ensure_ws(ctx, smc_resample_ws_bytes(max_particles), nullptr);
 }
 

@@ -18,6 +18,9 @@ struct smc_ctx {
     // growable area: resampling tile descriptors, staging buffers
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    // per-population completion counters of the population sweep (zeroed)
+    uint32_t* d_popdone = nullptr;
+    int64_t popdone_cap = 0;
     int32_t lanes[SMC_OP_COUNT] = {0, 0, 0};
     int32_t threads[SMC_OP_COUNT] = {0, 0, 0};
 };
@@ -54,6 +57,9 @@ bool capturing(cudaStream_t s);
 
 // Make sure the growable workspace holds `bytes`; grows only outside capture.
 smc_status ensure_ws(smc_ctx* ctx, size_t bytes, cudaStream_t s);
+
+// Make sure there are n zeroed population counters; grows only outside capture.
+smc_status ensure_popdone(smc_ctx* ctx, int64_t n, cudaStream_t s);
 
 // Set the context's device current for the calling thread.
 smc_status use_device(smc_ctx* ctx);

@@ -178,6 +178,95 @@ struct SliceAcc {
     }
 };
 
+// Equal component weights, no gradient: the common case, written for the
+// issue rate of sm_103a.  Two data are evaluated at once in packed f32x2
+// registers (one FFMA2 / FADD2 / FMUL2 instruction per pair), and the max
+// shift is folded into the exponent argument:
+//   t_k = y r + nu_k,  tmin = min_k |t_k|,  c = -tmin^2  (= max_k a_k)
+//   2^(a_k - max) = 2^(-(t_k^2 + c)) = ex2(-fma(t_k, t_k, c))
+// which leaves per datum and component one packed FFMA (t), one min, half a
+// packed FFMA (the argument), one MUFU ex2 and half a packed FADD (the sum).
+// Groups of 16 pairs keep per-half products of s_n below 2^80 before lg2.
+__device__ __forceinline__ float ex2_neg(float p) {
+    float y;
+    asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "=f"(y) : "f"(p));
+    return y;
+}
+
+template <int K>
+struct SliceAccEqW {
+    Kahan ll;
+    float2 ms = make_float2(0.0f, 0.0f);  // sum of c over the current group (two halves)
+    float2 pr = make_float2(1.0f, 1.0f);  // product of s over the current group
+    int cnt = 0;
+
+    __device__ __forceinline__ void flush() {
+        ll.add((ms.x + ms.y) + (lg2(pr.x) + lg2(pr.y)));
+        ms = make_float2(0.0f, 0.0f);
+        pr = make_float2(1.0f, 1.0f);
+        cnt = 0;
+    }
+
+    // one datum on the scalar path (odd tail of a chunk)
+    __device__ __forceinline__ void one(float yv, const float (&nu)[K], float r) {
+        float t[K];
+        float tm = INFINITY;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            t[k] = fmaf(yv, r, nu[k]);
+            tm = fminf(tm, fabsf(t[k]));
+        }
+        float c = -tm * tm;
+        float s = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) s += ex2_neg(fmaf(t[k], t[k], c));
+        ll.add(c + lg2(s));
+    }
+
+    // data ys[0, cnt_total): pairs p = lane, lane + L, ...; the odd last
+    // datum (if any) goes to lane 0
+    __device__ __forceinline__ void run(const float* ys, int cnt_total, int lane, int L,
+                                        const float (&nu)[K], float r) {
+        const float2* ys2 = reinterpret_cast<const float2*>(ys);
+        const int np = cnt_total >> 1;
+        const float2 R2 = make_float2(r, r);
+        float2 NU[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) NU[k] = make_float2(nu[k], nu[k]);
+#pragma unroll 2
+        for (int p = lane; p < np; p += L) {
+            const float2 Y = ys2[p];
+            float2 T[K];
+            float m0 = INFINITY, m1 = INFINITY;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                T[k] = __ffma2_rn(Y, R2, NU[k]);
+                m0 = fminf(m0, fabsf(T[k].x));
+                m1 = fminf(m1, fabsf(T[k].y));
+            }
+            const float2 C = make_float2(-m0 * m0, -m1 * m1);
+            float2 S;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float2 P = __ffma2_rn(T[k], T[k], C);
+                const float2 E = make_float2(ex2_neg(P.x), ex2_neg(P.y));
+                S = k == 0 ? E : __fadd2_rn(S, E);
+            }
+            ms = __fadd2_rn(ms, C);
+            pr = __fmul2_rn(pr, S);
+            if (++cnt == 16) flush();
+        }
+        if ((cnt_total & 1) && lane == 0) one(ys[cnt_total - 1], nu, r);
+    }
+
+    __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P) {
+        if (cnt) flush();
+        double part = (double)ll.s - (double)ll.c;
+        for (int o = L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        return part * kLn2 + P.cst;
+    }
+};
+
 // Chunk size of the staged data (floats) and the shared-memory bytes a
 // kernel using the slice evaluator needs: data buffer + mbarrier.
 constexpr int kYChunk = 8192;
@@ -200,6 +289,22 @@ __device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, flo
         int cnt = (int)((N - c0) < kYChunk ? (N - c0) : kYChunk);
         stage_y(ys, y, c0, cnt, mbar, phase, status);
         if (active) acc.run(ys, cnt, lane, L, nu, lw2, r);
+        __syncthreads();
+    }
+}
+
+// The same chunked streaming for the packed equal-weight accumulator.
+template <int K>
+__device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K>& acc, float* ys,
+                                                   const float* __restrict__ y, int64_t N,
+                                                   bool active, int lane, int L,
+                                                   const float (&nu)[K], float r,
+                                                   uint32_t& phase, uint32_t* status) {
+    uint64_t* mbar = ychunk_mbar(ys);
+    for (int64_t c0 = 0; c0 < N; c0 += kYChunk) {
+        int cnt = (int)((N - c0) < kYChunk ? (N - c0) : kYChunk);
+        stage_y(ys, y, c0, cnt, mbar, phase, status);
+        if (active) acc.run(ys, cnt, lane, L, nu, r);
         __syncthreads();
     }
 }

@@ -34,11 +34,18 @@ __global__ void __launch_bounds__(256) k_loglik_gmm1d(const float* __restrict__ 
         nu[k] = -mu * P.r;
         lw2[k] = P.lw2[k];
     }
-    SliceAcc<K, GRAD, EQW> acc;
     uint32_t phase = 0;
-    slice_over_data(acc, ys, y, N, active, lane, L, nu, lw2, P.r, phase, status);
     float g[K];
-    double ll = acc.finish(L, P, g);
+    double ll;
+    if constexpr (EQW && !GRAD) {
+        SliceAccEqW<K> acc;
+        slice_over_data_eq(acc, ys, y, N, active, lane, L, nu, P.r, phase, status);
+        ll = acc.finish(L, P);
+    } else {
+        SliceAcc<K, GRAD, EQW> acc;
+        slice_over_data(acc, ys, y, N, active, lane, L, nu, lw2, P.r, phase, status);
+        ll = acc.finish(L, P, g);
+    }
     if (active && lane == 0) {
         if (ll != ll) raise_status(status, ST_NONFINITE);
         loglik_out[p] = ll;

@@ -74,11 +74,18 @@ __global__ void __launch_bounds__(256) k_mh_move(
         nu[k] = -prop[k] * P.r;
         lw2[k] = P.lw2[k];
     }
-    SliceAcc<K, MALA, EQW> acc;
     uint32_t phase = 0;
-    slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
     float gp[K];
-    double lp = acc.finish(L, P, gp);
+    double lp;
+    if constexpr (EQW && !MALA) {
+        SliceAccEqW<K> acc;
+        slice_over_data_eq(acc, ys, y, N, in_box, lane, L, nu, P.r, phase, status);
+        lp = acc.finish(L, P);
+    } else {
+        SliceAcc<K, MALA, EQW> acc;
+        slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+        lp = acc.finish(L, P, gp);
+    }
 
     bool acc_ok = false;
     if (in_box && lane == 0) {
@@ -113,27 +120,77 @@ __global__ void __launch_bounds__(256) k_mh_move(
 }
 
 // ------------------------------------------------------------------ population MCMC
-// Work queue: blocks take populations in `order` until the queue is empty;
-// the last block to leave resets the queue.  Stage 1 runs the RW-MH move of
-// every chain of the population (passes of blockDim/L chains), stage 2 the
-// disjoint adjacent exchanges, one thread per pair.
+// Work items are chunks of (blockDim / L) consecutive chains of the flat
+// chain array, handed out by a queue, so every item costs the same whatever
+// the population sizes.  After a chain's move, lane 0 of its slice
+// publishes it (fence + atomic count of the population's finished chains);
+// the slice that finishes a population's last chain runs that population's
+// exchange moves at once (reads through L2), so no CTA ever waits on another.
+// The counters and the queue are left at zero for the next sweep.
+__device__ __forceinline__ int pop_of(const int32_t* __restrict__ offsets, int n_pops, int64_t c) {
+    int lo = 0, hi = n_pops;  // largest q with offsets[q] <= c
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(offsets + mid) <= c) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int K>
+__device__ __forceinline__ void exchange_population(
+    float* theta, double* ll, int64_t Mtot, const float* __restrict__ beta, int64_t base, int Mq,
+    int q, int lane, int L, int Kreal, uint64_t seed, uint64_t sweep, uint32_t* s_sw,
+    uint32_t* s_try) {
+    const uint32_t par = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
+    const int npairs = par == 0 ? Mq / 2 : (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
+    uint32_t swaps = 0;
+    for (int j = lane; j < npairs; j += L) {
+        int ia, ib;
+        if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
+        else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
+        else { ia = Mq - 1; ib = 0; }
+        const int64_t ga = base + ia, gb = base + ib;
+        const double la = __ldcg(ll + ga), lb = __ldcg(ll + gb);
+        const double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
+        const uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
+        if (accept(word_of(w, j & 3), log_alpha)) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (k < Kreal) {
+                    const float ta = __ldcg(theta + (int64_t)k * Mtot + ga);
+                    const float tb = __ldcg(theta + (int64_t)k * Mtot + gb);
+                    __stcg(theta + (int64_t)k * Mtot + ga, tb);
+                    __stcg(theta + (int64_t)k * Mtot + gb, ta);
+                }
+            }
+            __stcg(ll + ga, lb);
+            __stcg(ll + gb, la);
+            ++swaps;
+        }
+    }
+    if (swaps) atomicAdd(s_sw, swaps);
+    if (lane == 0) atomicAdd(s_try, (uint32_t)npairs);
+}
+
 template <int K, bool EQW>
 __global__ void __launch_bounds__(256) k_popmcmc_sweep(
     const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
-    const float* __restrict__ beta, const int32_t* __restrict__ offsets,
-    const int32_t* __restrict__ order, int32_t n_pops, float scale, uint64_t seed,
-    uint64_t sweep, unsigned long long* stats, unsigned long long* queue,
-    unsigned long long* done, Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
+    const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
+    float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats,
+    unsigned long long* queue, unsigned long long* done, uint32_t* pop_done, Gmm1dArgs P, int L,
+    int Kreal, uint32_t* status) {
     extern __shared__ __align__(16) float ys[];
-    __shared__ int32_t s_pop;
+    __shared__ long long s_item;
     __shared__ uint32_t s_mh, s_sw, s_try;
     init_mbar(ychunk_mbar(ys));
     if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
+    const int slice0 = (int)(threadIdx.x & 31) / L * L;  // warp lane of this slice's lane 0
+    const long long nitems = (Mtot + ppb - 1) / ppb;
     uint32_t phase = 0;
-    // all data resident in shared memory when they fit: stage once
-    const bool resident = N <= kYChunk;
+    const bool resident = N <= kYChunk;  // all data in shared memory: stage once
     if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys), phase, status);
     float lw2[K];
 #pragma unroll
@@ -142,95 +199,92 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
     while (true) {
         if (threadIdx.x == 0) {
             unsigned long long t = atomicAdd(queue, 1ull);
-            s_pop = t < (unsigned long long)n_pops ? (int32_t)t : -1;
+            s_item = t < (unsigned long long)nitems ? (long long)t : -1ll;
         }
         __syncthreads();
-        const int32_t qi = s_pop;
+        const long long item = s_item;
         __syncthreads();
-        if (qi < 0) break;
-        const int32_t q = order ? order[qi] : qi;
-        const int64_t base = offsets[q];
-        const int Mq = (int)(offsets[q + 1] - base);
-        // ---- stage 1: random-walk MH for every chain
-        for (int c0 = 0; c0 < Mq; c0 += ppb) {
-            const int c = c0 + (int)threadIdx.x / L;
-            const bool active = c < Mq;
-            const int64_t gidx = base + c;
-            float mu[K], z[K], prop[K], nu[K];
-            double l = 0.0;
-            float b = 0.0f;
+        if (item < 0) break;
+        const int64_t c = item * ppb + threadIdx.x / L;
+        const bool active = c < Mtot;
+        // ---- random-walk MH move of chain c
+        float mu[K], z[K], prop[K], nu[K];
+        double l = 0.0;
+        float b = 0.0f;
 #pragma unroll
-            for (int k = 0; k < K; ++k) { mu[k] = 0.0f; z[k] = 0.0f; }
-            if (active) {
+        for (int k = 0; k < K; ++k) { mu[k] = 0.0f; z[k] = 0.0f; }
+        if (active) {
 #pragma unroll
-                for (int k = 0; k < K; ++k)
-                    if (k < Kreal) mu[k] = theta[(int64_t)k * Mtot + gidx];
-                l = ll[gidx];
-                b = beta[gidx];
-                normals<K>(seed, RNG_MOVE, sweep, (uint32_t)gidx, Kreal, z);
+            for (int k = 0; k < K; ++k)
+                if (k < Kreal) mu[k] = theta[(int64_t)k * Mtot + c];
+            l = ll[c];
+            b = beta[c];
+            normals<K>(seed, RNG_MOVE, sweep, (uint32_t)c, Kreal, z);
+        }
+        bool in_box = active;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            prop[k] = k < Kreal ? fmaf(scale, z[k], mu[k]) : 0.0f;
+            if (k < Kreal) in_box &= (prop[k] >= P.lo) & (prop[k] <= P.hi);
+            nu[k] = -prop[k] * P.r;
+        }
+        double lp;
+        if constexpr (EQW) {
+            SliceAccEqW<K> acc;
+            if (resident) {
+                if (in_box) acc.run(ys, (int)N, lane, L, nu, P.r);
+            } else {
+                slice_over_data_eq(acc, ys, y, N, in_box, lane, L, nu, P.r, phase, status);
             }
-            bool in_box = active;
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                prop[k] = k < Kreal ? fmaf(scale, z[k], mu[k]) : 0.0f;
-                if (k < Kreal) in_box &= (prop[k] >= P.lo) & (prop[k] <= P.hi);
-                nu[k] = -prop[k] * P.r;
-            }
-            SliceAcc<K, false, EQW> acc;
+            lp = acc.finish(L, P);
+        } else {
+            SliceAcc<K, false, false> acc;
             if (resident) {
                 if (in_box) acc.run(ys, (int)N, lane, L, nu, lw2, P.r);
             } else {
                 slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
             }
-            float gdummy[K];
-            double lp = acc.finish(L, P, gdummy);
-            bool ok = false;
-            if (in_box && lane == 0) {
-                if (lp != lp) raise_status(status, ST_NONFINITE);
-                ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)gidx, 0u).x,
-                            (double)b * (lp - l));
-            }
-            if (active && lane == 0 && ok) {
+            float gd[K];
+            lp = acc.finish(L, P, gd);
+        }
+        bool ok = false;
+        if (in_box && lane == 0) {
+            if (lp != lp) raise_status(status, ST_NONFINITE);
+            ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)c, 0u).x, (double)b * (lp - l));
+        }
+        // ---- publish the chain; the population's last chain runs its exchange
+        int q = 0, Mq = 0;
+        int64_t base = 0;
+        bool last = false;
+        if (active && lane == 0) {
+            if (ok) {
 #pragma unroll
                 for (int k = 0; k < K; ++k)
-                    if (k < Kreal) theta[(int64_t)k * Mtot + gidx] = prop[k];
-                ll[gidx] = lp;
+                    if (k < Kreal) theta[(int64_t)k * Mtot + c] = prop[k];
+                ll[c] = lp;
             }
-            unsigned m = __ballot_sync(0xFFFFFFFFu, ok);
-            if ((threadIdx.x & 31) == 0 && m) atomicAdd(&s_mh, (uint32_t)__popc(m));
+            q = pop_of(offsets, n_pops, c);
+            base = offsets[q];
+            Mq = (int)(offsets[q + 1] - base);
+            __threadfence();
+            const uint32_t old = atomicAdd(pop_done + q, 1u);
+            last = old == (uint32_t)(Mq - 1);
         }
-        __syncthreads();
-        // ---- stage 2: exchange moves on disjoint adjacent pairs
-        if (Mq >= 2) {
-            const uint32_t par = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
-            const int npairs = par == 0 ? Mq / 2 : (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
-            for (int j = threadIdx.x; j < npairs; j += blockDim.x) {
-                int ia, ib;
-                if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
-                else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
-                else { ia = Mq - 1; ib = 0; }
-                const int64_t ga = base + ia, gb = base + ib;
-                const double la = ll[ga], lb = ll[gb];
-                const double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
-                uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
-                if (accept(word_of(w, j & 3), log_alpha)) {
-#pragma unroll
-                    for (int k = 0; k < K; ++k) {
-                        if (k < Kreal) {
-                            float t = theta[(int64_t)k * Mtot + ga];
-                            theta[(int64_t)k * Mtot + ga] = theta[(int64_t)k * Mtot + gb];
-                            theta[(int64_t)k * Mtot + gb] = t;
-                        }
-                    }
-                    ll[ga] = lb;
-                    ll[gb] = la;
-                    atomicAdd(&s_sw, 1u);
-                }
-            }
-            if (threadIdx.x == 0) atomicAdd(&s_try, (uint32_t)npairs);
+        const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, ok);
+        if ((threadIdx.x & 31) == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
+        last = __shfl_sync(0xFFFFFFFFu, last, slice0);
+        q = __shfl_sync(0xFFFFFFFFu, q, slice0);
+        Mq = __shfl_sync(0xFFFFFFFFu, Mq, slice0);
+        base = __shfl_sync(0xFFFFFFFFu, base, slice0);
+        if (last) {
+            __threadfence();
+            if (Mq >= 2)
+                exchange_population<K>(theta, ll, Mtot, beta, base, Mq, q, lane, L, Kreal, seed,
+                                       sweep, &s_sw, &s_try);
+            if (lane == 0) pop_done[q] = 0u;
         }
-        __syncthreads();
     }
+    __syncthreads();
     if (threadIdx.x == 0) {
         if (stats) {
             if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
@@ -238,7 +292,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
             if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
         }
         __threadfence();
-        unsigned long long d = atomicAdd(done, 1ull);
+        const unsigned long long d = atomicAdd(done, 1ull);
         if (d == (unsigned long long)gridDim.x - 1) {
             *queue = 0ull;
             __threadfence();
@@ -283,22 +337,24 @@ static smc_status dispatch_move(bool mala, bool eqw, int blocks, int threads, cu
 }
 
 template <int K, bool EQW>
-static smc_status launch_pop(const smc_ctx* ctx, int threads, cudaStream_t s, const float* y,
+static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const float* y,
                              int64_t N, float* th, double* l, int64_t Mt, const float* beta,
-                             const int32_t* off, const int32_t* order, int32_t n_pops,
-                             float scale, uint64_t seed, uint64_t sweep, uint64_t* stats,
-                             const smc::Gmm1dArgs& P, int L, int Kr) {
+                             const int32_t* off, int32_t n_pops, float scale, uint64_t seed,
+                             uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P, int L,
+                             int Kr) {
     auto kern = smc::k_popmcmc_sweep<K, EQW>;
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smc::kYSmemBytes) !=
             cudaSuccess || occ < 1)
         occ = 1;
+    const int ppb = threads / L;
+    int64_t items = (Mt + ppb - 1) / ppb;
     int64_t grid = (int64_t)ctx->num_sms * occ;
-    if (grid > n_pops) grid = n_pops;
+    if (grid > items) grid = items;
     kern<<<(unsigned)grid, threads, smc::kYSmemBytes, s>>>(
-        y, N, th, l, Mt, beta, off, order, n_pops, scale, seed, sweep,
+        y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
         reinterpret_cast<unsigned long long*>(stats), ctx->d_counters + CNT_POP_QUEUE,
-        ctx->d_counters + CNT_POP_DONE, P, L, Kr, ctx->d_status);
+        ctx->d_counters + CNT_POP_DONE, ctx->d_popdone, P, L, Kr, ctx->d_status);
     return cuda_ok(cudaGetLastError());
 }
 
@@ -354,7 +410,7 @@ extern "C" smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const floa
 extern "C" smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y,
                                         int64_t N, float* theta, double* loglik, int64_t M_total,
                                         const float* beta, const int32_t* pop_offsets,
-                                        const int32_t* pop_order, int32_t n_pops, float scale,
+                                        int32_t n_pops, float scale,
                                         uint64_t seed, uint64_t sweep, uint64_t* stats,
                                         void* stream) {
     if (!ctx || M_total < 0 || N < 0 || n_pops < 0) return SMC_ERR_ARG;
@@ -372,10 +428,12 @@ extern "C" smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, cons
     int L, threads;
     launch_shape(ctx, SMC_OP_POPMCMC, M_total, N, model->K, &L, &threads);
     cudaStream_t s = as_stream(stream);
+    st = ensure_popdone(ctx, n_pops, s);
+    if (st != SMC_OK) return st;
     const int Kr = model->K;
 #define SMC_PP(KK, EQ)                                                                       \
     launch_pop<KK, EQ>(ctx, threads, s, y, N, theta, loglik, M_total, beta, pop_offsets,      \
-                       pop_order, n_pops, scale, seed, sweep, stats, P, L, Kr)
+                       n_pops, scale, seed, sweep, stats, P, L, Kr)
     switch (Kp) {
         case 1: return eqw ? SMC_PP(1, true) : SMC_PP(1, false);
         case 2: return eqw ? SMC_PP(2, true) : SMC_PP(2, false);

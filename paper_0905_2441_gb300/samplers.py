@@ -126,21 +126,18 @@ class PopulationMCMC(_Graphable):
         self.y = _dev(y, torch.float32)
         off = np.asarray(offsets, np.int32)
         self.offsets = _dev(off, torch.int32)
-        sizes = np.diff(off)
-        # longest populations first: the work queue then balances the SMs
-        self.order = _dev(np.argsort(-sizes, kind="stable").astype(np.int32), torch.int32)
         self.n_pops = off.size - 1
         self.beta = _dev(betas, torch.float32)
         self.theta = _dev(theta0, torch.float32).clone()
         self.K, self.M = self.theta.shape
         self.ll = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+        ctx.reserve(self.M, self.n_pops)
         api.loglik_batch(ctx, model, self.y, self.theta, out=self.ll)
 
     def sweep(self, s: int):
         api.popmcmc_sweep(self.ctx, self.model, self.y, self.theta, self.ll, self.beta,
-                          self.offsets, self.scale, self.seed, s, order=self.order,
-                          stats=self.stats)
+                          self.offsets, self.scale, self.seed, s, stats=self.stats)
 
     def run(self, n_sweeps: int, start: int = 0, graph: bool = False):
         if graph:

@@ -15,7 +15,7 @@ def _declared():
         if h.endswith(".h"):
             txt = open(os.path.join(ROOT, "include", h)).read()
             txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-            names |= set(re.findall(r"^\s*(?:smc_status|const char\*)\s+(\w+)\s*\(", txt, re.M))
+            names |= set(re.findall(r"^\s*(?:smc_status|const char\*|int)\s+(\w+)\s*\(", txt, re.M))
     return names
 
 

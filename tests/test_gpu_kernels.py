@@ -421,9 +421,8 @@ def test_popmcmc_sweep_parity(smc):
     ll = oracle.gmm1d_loglik(y, logw, SIG, th)
     tt, lt = cu(th), cu(ll)
     stats = torch.zeros(3, dtype=torch.int64, device="cuda")
-    order = np.argsort(-np.diff(off), kind="stable").astype(np.int32)
     P.popmcmc_sweep(ctx, P.GMM(K, SIG), cu(y), tt, lt, cu(beta), cu(off), 0.3, 55, 0,
-                    order=cu(order), stats=stats)
+                    stats=stats)
     ctx.check()
     rt, rl, rst = oracle.popmcmc_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 55, 0)
     # a flipped decision changes a whole population; every population must match
