@@ -169,6 +169,31 @@ smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uin
                                    uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
                                    const int32_t* do_flag, double* logw_reset, void* stream);
 
+/* The same systematic resampling as smc_resample_systematic (identical
+ * arguments and results, bit for bit), for callers that cannot allocate
+ * device memory: processes whose device memory is owned by a pool or a
+ * fixed budget they must not bypass, and latency-critical loops that cannot
+ * pay the device synchronisation cudaMalloc / cudaFree imply.  It needs no
+ * smc_ctx and allocates nothing: its scratch is a 64 KiB static device
+ * array inside libsmc.so, which every GPU that loads the library holds
+ * until the process exits.  The paper has no counterpart to this entry
+ * point; it exists for how the library is called, not for the method.
+ *   M must be <= 16,777,216 (2^24); larger M returns SMC_ERR_ARG.
+ *   status_out (device uint32, nullable) receives the error bits a kernel
+ *   finds, OR-ed in: 8 = a weight outside [0,1] or NaN (or weights far
+ *   from normalised), 2 = all weights zero, 4 = a bounded wait expired.
+ *   The first call on a device (with that device current) looks up the
+ *   array's device address; make that first call before any stream capture.
+ *   Every call shares the one array and each call starts by clearing its
+ *   counters, so calls whose work overlaps on the GPU (different streams,
+ *   or several host threads on one device) race and give wrong results:
+ *   serialise them, e.g. on one stream. */
+smc_status smc_resample_systematic_noalloc(const double* W, int64_t M, uint64_t seed,
+                                           uint64_t step, int32_t* ancestors_out,
+                                           int32_t* counts_out, const int32_t* do_flag,
+                                           double* logw_reset, uint32_t* status_out,
+                                           void* stream);
+
 /* Gather particles by ancestor: for r < rows_f32, dst_f32[r*M + i] =
  * src_f32[r*M + anc[i]] (SoA float[rows][M]); and dst_f64[i] =
  * src_f64[anc[i]] if both are non-NULL.  anc NULL means identity (copy).

@@ -20,7 +20,8 @@ PF_MSV, PF_LG = 0, 1
 EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_status_string",
            "smc_set_launch", "smc_get_launch", "smc_loglik_batch", "smc_reweight", "smc_ess",
            "smc_resample_systematic", "smc_gather", "smc_mh_move", "smc_popmcmc_sweep",
-           "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak")
+           "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
+           "smc_resample_systematic_noalloc")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -52,6 +53,8 @@ def _declare(L):
     L.smc_reweight.argtypes = [_vp, _vp, C.c_double, _vp, _i64, _vp, _vp, _vp, C.c_double, _vp]
     L.smc_ess.argtypes = [_vp, _vp, _i64, _vp, _vp]
     L.smc_resample_systematic.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp, _vp]
+    L.smc_resample_systematic_noalloc.argtypes = [_vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp, _vp,
+                                                  _vp]
     L.smc_gather.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp]
     L.smc_mh_move.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                               _vp, _i64, _vp, _i64, C.c_float, _i32, _u64, _u64, _vp, _vp]

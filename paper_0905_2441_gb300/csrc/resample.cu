@@ -97,3 +97,73 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
                                                               src_f64, dst_f64);
     return cuda_ok(cudaGetLastError());
 }
+
+// ------------------------------------------------------------------ no-allocation variant
+// Systematic resampling for callers that must not allocate device memory:
+// processes whose device memory is all reserved up front by an allocator
+// they do not own (a framework's caching pool, a serving runtime with a
+// fixed memory budget), and latency-critical loops that cannot afford the
+// implicit device synchronisation of cudaMalloc / cudaFree.  No context is
+// created: the scan's scratch (tile descriptors and three counters) lives in
+// a file-scope device array that every GPU loading this library holds until
+// the process exits.
+#include <mutex>
+
+namespace {
+
+constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;                  // 16,777,216 weights
+constexpr int64_t kNoAllocTiles = kNoAllocMaxM / smc::kRsTile;      // 8192 tiles
+constexpr int64_t kNoAllocWords = kNoAllocTiles + 8;                // + ticket, sum, done
+// 64 KiB + 64 B of scratch per device
+static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
+
+std::mutex g_noalloc_mu;
+unsigned long long* g_noalloc_ptr[256] = {};  // device address of the array, per device
+
+// Device address of the scratch array for the current device.  The first
+// call on a device looks it up (cudaGetSymbolAddress); host code must not
+// use the array's name as a device pointer.
+smc_status noalloc_scratch(unsigned long long** out) {
+    int dev = -1;
+    SMC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 256) return SMC_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) return SMC_ERR_CUDA;
+        g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SMC_OK;
+}
+
+}  // namespace
+
+extern "C" smc_status smc_resample_systematic_noalloc(const double* W, int64_t M, uint64_t seed,
+                                                      uint64_t step, int32_t* ancestors_out,
+                                                      int32_t* counts_out, const int32_t* do_flag,
+                                                      double* logw_reset, uint32_t* status_out,
+                                                      void* stream) {
+    if (M < 0) return SMC_ERR_ARG;
+    if (M > kNoAllocMaxM) return SMC_ERR_ARG;  // larger than the static scratch
+    if (M == 0) return SMC_OK;
+    if (!W || !ancestors_out) return SMC_ERR_ARG;
+    unsigned long long* scratch = nullptr;
+    smc_status st = noalloc_scratch(&scratch);
+    if (st != SMC_OK) return st;
+    int dev = 0, sms = 0;
+    SMC_CUDA(cudaGetDevice(&dev));
+    SMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaStream_t s = as_stream(stream);
+    smc::RsScratch sc;
+    sc.tiles = scratch;
+    sc.ticket = scratch + kNoAllocTiles;
+    sc.sum = scratch + kNoAllocTiles + 1;
+    sc.done = scratch + kNoAllocTiles + 2;
+    // the counters must start at zero; an earlier call that stopped on an
+    // error may have left them set (the tile words are cleared by pass 1)
+    SMC_CUDA(cudaMemsetAsync(sc.ticket, 0, 3 * sizeof(unsigned long long), s));
+    return resample_launch(sms, W, M, seed, step, ancestors_out, counts_out, do_flag, logw_reset,
+                           sc, status_out, s);
+}
