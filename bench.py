@@ -399,6 +399,148 @@ def bench_secondary(torch, P):
     return out
 
 
+def _flush_timed(torch, flush, stream, fns):
+    """Flush L2, then time each callable of one step with CUDA events on the
+    launching stream; returns per-callable elapsed seconds."""
+    flush.fill_(0.5)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)]
+    evs[0].record(stream)
+    for i, f in enumerate(fns):
+        f()
+        evs[i + 1].record(stream)
+    return evs
+
+
+def bench_pf(args, torch, dist):
+    """One step = pf_step (gather + propagate + weight) -> reweight (log Z
+    increment, W) -> systematic resampling, M = 2^20 particles (d = 3 MSV)."""
+    import paper_0905_2441_gb300 as P
+    from paper_0905_2441_gb300 import samplers
+    import synth
+    w = synth.MSV3
+    phi, Sigma, beta = synth.msv_params(w.d, w.phi, w.rho, w.beta)
+    _, yobs = synth.simulate_ssm("msv", w.T, phi, Sigma, beta, seed=w.data_seed)
+    ctx = P.Context()
+    pf = samplers.ParticleFilter(ctx, P.PFModel(P.PF_MSV, phi, synth.chol(Sigma), beta), yobs,
+                                 w.M, seed=w.method_seed + dist.rank)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for t in range(1, args.warmup + 1):
+        pf.step(t)
+    torch.cuda.synchronize()
+    K = min(args.steps, w.T - args.warmup)
+    names = ["pf_step", "reweight", "resample"]
+    rec = []
+    dist.barrier(torch)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for t in range(args.warmup + 1, args.warmup + 1 + K):
+            c, n = pf.cur, 1 - pf.cur
+            fns = [lambda c=c, n=n, t=t: P.pf_step(ctx, pf.model, pf.y[t - 1], pf.x[c], pf.x[n],
+                                                  pf.logg, pf.seed, t, anc=pf.anc),
+                   lambda t=t: P.reweight(ctx, pf.logg, 1.0, pf.lw, pf.W, pf.hist[t], None, 0.5),
+                   lambda t=t: P.resample_systematic(ctx, pf.W, pf.seed, t, anc=pf.anc,
+                                                     logw_reset=pf.lw)]
+            rec.append(_flush_timed(torch, flush, stream, fns))
+            pf.cur = n
+        torch.cuda.synchronize()
+    ctx.check()
+    per = np.array([[e[i].elapsed_time(e[i + 1]) / 1e3 for i in range(3)] for e in rec])
+    t_dev = float(per.sum())
+    t_max = dist.max(torch, t_dev)
+    units = float(w.M) * K
+    value = dist.sum(torch, units) / t_max
+    share = per.sum(0) / per.sum()
+    # algorithmic bytes per particle of each call
+    bytes_pp = {"pf_step": 4 + 12 + 12 + 8,          # anc, x gather, x write, log g
+                "reweight": 8 + 8 + 8 + 8,            # log g r, lw r/w, W w
+                "resample": 8 + 4 + 8}                # W r, anc w, lw reset w
+    i_dom = int(np.argmax(share))
+    dom = names[i_dom]
+    hbm = measured_peaks()["hbm_gbs"]
+    ach = bytes_pp[dom] * w.M / (per[:, i_dom].mean()) / 1e9
+    out = {"metric": "particle-steps/s (bootstrap particle filter, d=3 MSV)", "value": value,
+           "unit": "particle-steps/s", "n_gpus": dist.world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MSV observations)",
+           "config": {"workload": w.name, "M": w.M, "d": w.d,
+                      "l2": "256 MiB buffer written before every timed step, outside its events",
+                      "parallelism": f"independent filters per rank x{dist.world}"},
+           "per_call_ms": {n: 1e3 * float(per[:, i].mean()) for i, n in enumerate(names)},
+           "per_call_share": {n: float(share[i]) for i, n in enumerate(names)},
+           "per_call_gbs": {n: bytes_pp[n] * w.M / float(per[:, i].mean()) / 1e9
+                            for i, n in enumerate(names)},
+           "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                        "frac": ach / hbm, "traffic": None, "kernel": dom,
+                        "bytes_per_particle": bytes_pp[dom],
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+           "gpu_launches": 5 * K, "clocks": clk.summary()}
+    ctx.close()
+    return out
+
+
+def bench_resample(args, torch, dist):
+    """One step = smc_reweight (lw += l, W, scalars) + smc_resample_systematic
+    (exact-integer systematic resampling) at M = 2^24: HBM-bound kernels."""
+    import paper_0905_2441_gb300 as P
+    M = 1 << 24
+    ctx = P.Context()
+    ctx.reserve(M)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5 + dist.rank)
+    ll = torch.randn(M, dtype=torch.float64, device="cuda", generator=g)
+    lw = torch.zeros(M, dtype=torch.float64, device="cuda")
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    anc = torch.empty(M, dtype=torch.int32, device="cuda")
+    sc = torch.empty(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    fns = [lambda: P.reweight(ctx, ll, 1.0, lw, W, sc, None, 0.5),
+           lambda: P.resample_systematic(ctx, W, 9, 1, anc=anc, logw_reset=lw)]
+    for _ in range(args.warmup):
+        for f in fns:
+            f()
+    torch.cuda.synchronize()
+    K = min(args.steps, 200)
+    rec = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for i in range(K):
+            rec.append(_flush_timed(torch, flush, stream, fns))
+        torch.cuda.synchronize()
+    ctx.check()
+    per = np.array([[e[i].elapsed_time(e[i + 1]) / 1e3 for i in range(2)] for e in rec])
+    t_max = dist.max(torch, float(per.sum()))
+    hbm = measured_peaks()["hbm_gbs"]
+    b_rw, b_rs = 32, 20
+    ach_rs = b_rs * M / per[:, 1].mean() / 1e9
+    out = {"metric": "particles/s (reweight + systematic resampling)",
+           "value": dist.sum(torch, float(M) * K) / t_max, "unit": "particles/s",
+           "n_gpus": dist.world, "steps": K, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic (log-likelihoods ~ N(0,1))",
+           "config": {"workload": "reweight+resample-M16777216", "M": M,
+                      "l2": "256 MiB buffer written before every timed step, outside its events"},
+           "per_call_gbs": {"reweight": b_rw * M / per[:, 0].mean() / 1e9,
+                            "resample": ach_rs},
+           "per_call_ms": {"reweight": 1e3 * per[:, 0].mean(), "resample": 1e3 * per[:, 1].mean()},
+           "roofline": {"bound": "hbm", "achieved": ach_rs, "peak": hbm, "unit": "GB/s",
+                        "frac": ach_rs / hbm, "traffic": None, "kernel": "resample (2 kernels)",
+                        "bytes_per_particle": b_rs,
+                        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
+           "gpu_launches": 4 * K, "clocks": clk.summary()}
+    ctx.close()
+    return out
+
+
+def all_peaks(torch):
+    import paper_0905_2441_gb300 as P
+    out = {}
+    for k, n in enumerate(["ex2", "lg2", "ffma", "dfma"]):
+        ops, ms = measure_peak(P, k)
+        out[n] = ops
+    return out
+
+
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
     """The oracle timed on the host cores on bounded samples of the same workload."""
@@ -429,7 +571,8 @@ def main():
     ap.add_argument("--steps", type=int, default=4000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="popmcmc", choices=["popmcmc"])
+    ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
+                                                              "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -449,12 +592,19 @@ def main():
     if dist.rank == 0 and not os.path.exists(b.LIB):
         b.build()
     dist.barrier(torch)
-    out = bench_popmcmc(args, torch, dist)
-    if dist.rank == 0 and not args.no_secondary:
+    if args.workload == "pf":
+        out = bench_pf(args, torch, dist)
+    elif args.workload == "resample":
+        out = bench_resample(args, torch, dist)
+    elif args.workload == "peaks":
+        out = {"peaks_ops_per_s": all_peaks(torch)}
+    else:
+        out = bench_popmcmc(args, torch, dist)
+    if dist.rank == 0 and not args.no_secondary and args.workload == "popmcmc":
         import paper_0905_2441_gb300 as P
         out["secondary"] = bench_secondary(torch, P)
     if dist.rank == 0:
-        if not args.no_cpu and dist.world == 1:
+        if not args.no_cpu and dist.world == 1 and args.workload == "popmcmc":
             import synth
             out["cpu_baseline"] = cpu_popmcmc(synth.GMM8_POP)
         print(json.dumps(out), flush=True)
