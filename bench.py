@@ -535,7 +535,7 @@ def bench_resample(args, torch, dist):
 def all_peaks(torch):
     import paper_0905_2441_gb300 as P
     out = {}
-    for k, n in enumerate(["ex2", "lg2", "ffma", "dfma"]):
+    for k, n in enumerate(["ex2", "lg2", "ffma", "dfma", "i2f", "frnd"]):
         ops, ms = measure_peak(P, k)
         out[n] = ops
     return out

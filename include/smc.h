@@ -161,9 +161,11 @@ smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, double* ess_out,
  *   do_flag (device int32, nullable): when it holds 0 nothing is resampled;
  *     ancestors_out becomes the identity and counts 1.
  *   logw_reset (nullable): double[M] set to 0 when resampling happened.
- * Single pass: block scan plus decoupled look-back with a bounded wait.
- * A weight outside [0,1] or NaN latches SMC_ERR_ARG, S == 0
- * SMC_ERR_ZERO_WEIGHT, an exhausted wait SMC_ERR_TIMEOUT; the outputs are
+ * Two passes: exact integer sums per tile of 2048 weights, per group of 64
+ * tiles and in total; then one CTA per tile reads its prefix from those
+ * sums, scans the tile and expands its output range.  No CTA waits on
+ * another.  A weight outside [0,1] or NaN (or weights summing to 2^9 or
+ * more) latches SMC_ERR_ARG, S == 0 SMC_ERR_ZERO_WEIGHT; the outputs are
  * then unspecified. */
 smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uint64_t seed,
                                    uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
@@ -174,19 +176,19 @@ smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uin
  * device memory: processes whose device memory is owned by a pool or a
  * fixed budget they must not bypass, and latency-critical loops that cannot
  * pay the device synchronisation cudaMalloc / cudaFree imply.  It needs no
- * smc_ctx and allocates nothing: its scratch is a 64 KiB static device
+ * smc_ctx and allocates nothing: its scratch is a 65 KiB static device
  * array inside libsmc.so, which every GPU that loads the library holds
  * until the process exits.  The paper has no counterpart to this entry
  * point; it exists for how the library is called, not for the method.
  *   M must be <= 16,777,216 (2^24); larger M returns SMC_ERR_ARG.
  *   status_out (device uint32, nullable) receives the error bits a kernel
  *   finds, OR-ed in: 8 = a weight outside [0,1] or NaN (or weights far
- *   from normalised), 2 = all weights zero, 4 = a bounded wait expired.
+ *   from normalised), 2 = all weights zero.
  *   The first call on a device (with that device current) looks up the
  *   array's device address; make that first call before any stream capture.
  *   Every call shares the one array and each call starts by clearing its
- *   counters, so calls whose work overlaps on the GPU (different streams,
- *   or several host threads on one device) race and give wrong results:
+ *   sums, so calls whose work overlaps on the GPU (different streams, or
+ *   several host threads on one device) race and give wrong results:
  *   serialise them, e.g. on one stream. */
 smc_status smc_resample_systematic_noalloc(const double* W, int64_t M, uint64_t seed,
                                            uint64_t step, int32_t* ancestors_out,

@@ -15,7 +15,9 @@
 extern "C" {
 #endif
 
-enum { SMC_PEAK_EX2 = 0, SMC_PEAK_LG2 = 1, SMC_PEAK_FFMA = 2, SMC_PEAK_DFMA = 3 };
+enum { SMC_PEAK_EX2 = 0, SMC_PEAK_LG2 = 1, SMC_PEAK_FFMA = 2, SMC_PEAK_DFMA = 3,
+       SMC_PEAK_I2F = 4,   /* int -> float conversion (plus an integer shift) */
+       SMC_PEAK_FRND = 5   /* float round to integer (plus an FMUL and FADD) */ };
 
 /* Run the `kind` issue-rate kernel on the current device over `blocks_per_sm`
  * x (#SMs) blocks of 256 threads, `iters` iterations of 8 independent

@@ -52,9 +52,24 @@ __device__ __forceinline__ uint32_t word_of(uint4 w, int i) {
     return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w;
 }
 
+// Integer <-> float helpers built from float bit patterns.  On sm_103a the
+// conversion instructions share the narrow FP64 pipe, so per-element code
+// avoids them.
+// m in [0, 2^23) -> float, exactly (m is the mantissa of 2^23 + m)
+__device__ __forceinline__ float u23_to_f(uint32_t m) {
+    return __uint_as_float(0x4B000000u | m) - 8388608.0f;
+}
+// round to the nearest integer for |x| < 2^22: float value and int value
+__device__ __forceinline__ float round_magic(float x, int& ki) {
+    const float t = x + 12582912.0f;  // 1.5 * 2^23
+    ki = (int)__float_as_uint(t) - 0x4B400000;
+    return t - 12582912.0f;
+}
+
 // (2k+1) 2^-24 with k the top 23 bits: exact in float, strictly inside (0,1)
+// (k 2^-23 is 1.k - 1 read from the bits, then + 2^-24, both exact)
 __device__ __forceinline__ float u01(uint32_t w) {
-    return ((float)(w >> 9) + 0.5f) * 1.1920928955078125e-07f;
+    return (__uint_as_float(0x3F800000u | (w >> 9)) - 1.0f) + 5.9604644775390625e-08f;
 }
 
 // Box-Muller on one word pair: r = sqrt(-2 ln u1), (r cos 2 pi u2, r sin 2 pi u2)
@@ -120,8 +135,10 @@ __device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
     if (e >= 1023 + 100) { hi = sign ? -1e30f : 1e30f; lo = 0.0f; return; }
     uint32_t fh = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
     hi = __uint_as_float(fh);
-    float r = (float)(lw & 0x1FFFFFFFu);                        // 29-bit remainder
-    float scale = __uint_as_float((uint32_t)(e - 1075 + 127) << 23);  // 2^(e-1075)
+    // the top 23 of the 29 remaining bits, times 2^(e-1069): the 6 dropped
+    // bits lie 2^-46 below hi
+    const float r = u23_to_f((lw & 0x1FFFFFFFu) >> 6);
+    const float scale = __uint_as_float((uint32_t)(e - 1069 + 127) << 23);
     lo = sign ? -(r * scale) : r * scale;
 }
 
@@ -132,12 +149,14 @@ __device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
 __device__ __forceinline__ float exp_hilo(float hi, float lo) {
     const float L2E_HI = 1.44269502162933349609375f;   // log2(e) rounded to float
     const float L2E_LO = 1.925963033500011e-08f;       // log2(e) - L2E_HI
-    float ph = hi * L2E_HI;
-    float k = rintf(ph);
-    if (k < -126.0f) return 0.0f;
-    float pl = fmaf(hi, L2E_HI, -ph);
-    float f = (ph - k) + (pl + fmaf(hi, L2E_LO, lo * L2E_HI));
-    float p2 = __uint_as_float((uint32_t)((int)k + 127) << 23);
+    const float ph = hi * L2E_HI;
+    if (ph < -127.0f) return 0.0f;                     // below 2^-126 (also -inf, NaN-free)
+    int ki;
+    const float k = round_magic(ph, ki);               // |ph| < 2^22 here
+    if (ki < -126) return 0.0f;
+    const float pl = fmaf(hi, L2E_HI, -ph);
+    const float f = (ph - k) + (pl + fmaf(hi, L2E_LO, lo * L2E_HI));
+    const float p2 = __uint_as_float((uint32_t)(ki + 127) << 23);
     return ex2(f) * p2;
 }
 
@@ -151,11 +170,12 @@ __device__ __forceinline__ bool disnan(double x) {
     return (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
 }
 
-// float (normal or zero) -> double by integer operations
+// float -> double by integer operations (subnormal floats give 0)
 __device__ __forceinline__ double f2d_bits(float f) {
     uint32_t u = __float_as_uint(f);
     uint32_t e = (u >> 23) & 0xFFu;
     if (e == 0) return 0.0;
+    if (e == 255) return (double)f;  // inf / NaN
     unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
                            ((unsigned long long)(e - 127 + 1023) << 52) |
                            ((unsigned long long)(u & 0x7FFFFFu) << 29);

@@ -12,7 +12,7 @@
 // The products of 16 consecutive s_n are formed before one lg2 (each
 // s_n <= K <= 32, so the product stays below 2^80), the m_n of the same 16
 // data are summed in FP32 and each group total enters a Kahan accumulator.
-// The lane partials meet in FP64.  Gradient: d l / d mu_k =
+// The lane partials meet in FP32 (two-sum), the FP64 total forms once.  Gradient: d l / d mu_k =
 // sum_n r_nk (y_n - mu_k) / sigma^2 = (1/(sigma^2 r)) sum_n (e_k / s_n) t_k.
 #pragma once
 #include "device.cuh"
@@ -20,6 +20,22 @@
 namespace smc {
 
 constexpr int kMaxK1d = 32;
+
+// Reduce Kahan pairs (s, c) (true sum s - c) over the L lanes of a slice in
+// FP32 with error-free additions, then form the FP64 total once.
+__device__ __forceinline__ double slice_total(float s, float c, int L) {
+    for (int o = L >> 1; o > 0; o >>= 1) {
+        const float s2 = __shfl_xor_sync(0xFFFFFFFFu, s, o);
+        const float c2 = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+        const float t = s + s2;                 // two-sum: t + err == s + s2 exactly
+        const float bp = t - s;
+        const float err = (s - (t - bp)) + (s2 - bp);
+        s = t;
+        c = (c + c2) - err;
+    }
+    return f2d_bits(s) - f2d_bits(c);  // conversions by integer ops (no FP64-pipe convert)
+}
+
 
 struct Gmm1dArgs {
     float r;            // sqrt(log2(e) / (2 sigma^2))
@@ -164,8 +180,7 @@ struct SliceAcc {
     // Returns the particle's log-likelihood; g receives the gradient.
     __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P, float (&g)[K]) {
         if (cnt) flush();
-        double part = (double)ll.s - (double)ll.c;
-        for (int o = L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        const double part = slice_total(ll.s, ll.c, L);
         if constexpr (GRAD) {
 #pragma unroll
             for (int k = 0; k < K; ++k) {
@@ -261,8 +276,7 @@ struct SliceAccEqW {
 
     __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P) {
         if (cnt) flush();
-        double part = (double)ll.s - (double)ll.c;
-        for (int o = L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(0xFFFFFFFFu, part, o);
+        const double part = slice_total(ll.s, ll.c, L);
         return part * kLn2 + P.cst;
     }
 };

@@ -11,9 +11,21 @@ using namespace smc_host;
 
 namespace smc {
 
-// accept test in FP64 on FP32 inputs: log u < log alpha
-__device__ __forceinline__ bool accept(uint32_t w, double log_alpha) {
-    return (double)logf(u01(w)) < log_alpha;
+// accept test: log u < log alpha, compared in FP32 (log alpha arrives as a
+// float hi/lo pair from an FP64 difference; the FP32 likelihoods already
+// set a decision band far wider than this rounding)
+__device__ __forceinline__ bool accept(uint32_t w, float log_alpha) {
+    return logf(u01(w)) < log_alpha;
+}
+
+// beta (l' - l) with one FP64 subtraction; the product in FP32.  A NaN
+// difference gives -inf, so the move is rejected.
+__device__ __forceinline__ float tempered_diff(float beta, double lp, double l) {
+    const double d = lp - l;
+    if (disnan(d)) return -INFINITY;
+    float hi, lo;
+    split_double(d, hi, lo);
+    return beta * (hi + lo);
 }
 
 // Block-wide count of accepted moves, one global atomic per block.
@@ -89,7 +101,7 @@ __global__ void __launch_bounds__(256) k_mh_move(
 
     bool acc_ok = false;
     if (in_box && lane == 0) {
-        double log_alpha = (double)b * (lp - l);
+        float log_alpha = tempered_diff(b, lp, l);
         if (MALA) {
             float fwd = 0.0f, bwd = 0.0f;
 #pragma unroll
@@ -101,7 +113,7 @@ __global__ void __launch_bounds__(256) k_mh_move(
                     bwd = fmaf(db, db, bwd);
                 }
             }
-            log_alpha += (double)((fwd - bwd) / (2.0f * scale * scale));
+            log_alpha += (fwd - bwd) / (2.0f * scale * scale);
         }
         if (lp != lp) raise_status(status, ST_NONFINITE);
         acc_ok = accept(draw(seed, RNG_ACCEPT, step, (uint32_t)p, 0u).x, log_alpha);
@@ -152,7 +164,7 @@ __device__ __forceinline__ void exchange_population(
         else { ia = Mq - 1; ib = 0; }
         const int64_t ga = base + ia, gb = base + ib;
         const double la = __ldcg(ll + ga), lb = __ldcg(ll + gb);
-        const double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
+        const float log_alpha = tempered_diff(beta[ga] - beta[gb], lb, la);
         const uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
         if (accept(word_of(w, j & 3), log_alpha)) {
 #pragma unroll
@@ -250,7 +262,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
         bool ok = false;
         if (in_box && lane == 0) {
             if (lp != lp) raise_status(status, ST_NONFINITE);
-            ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)c, 0u).x, (double)b * (lp - l));
+            ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)c, 0u).x, tempered_diff(b, lp, l));
         }
         // ---- publish the chain; the population's last chain runs its exchange
         int q = 0, Mq = 0;

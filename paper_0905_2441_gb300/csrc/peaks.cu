@@ -34,6 +34,9 @@ __global__ void __launch_bounds__(256) k_peak(int iters, float seed, float* sink
             if constexpr (KIND == SMC_PEAK_EX2) a[j] = smc::ex2(-a[j]);          // stays in [0.5, 1]
             if constexpr (KIND == SMC_PEAK_LG2) a[j] = smc::lg2(a[j] + 1.5f);     // stays in [0.58, 1.9]
             if constexpr (KIND == SMC_PEAK_FFMA) a[j] = fmaf(a[j], 0.999999f, 1e-7f);
+            if constexpr (KIND == SMC_PEAK_I2F)  // int -> float -> int round trip
+                a[j] = (float)(__float_as_int(a[j]) >> 9);
+            if constexpr (KIND == SMC_PEAK_FRND) a[j] = rintf(a[j] * 0.5f) + 0.75f;
         }
     }
     float s = 0;
@@ -81,6 +84,8 @@ extern "C" int smc_measure_peak(int32_t kind, int32_t blocks_per_sm, int32_t ite
         case SMC_PEAK_LG2: return run<SMC_PEAK_LG2>(blocks, iters, ops_per_s, ms);
         case SMC_PEAK_FFMA: return run<SMC_PEAK_FFMA>(blocks, iters, ops_per_s, ms);
         case SMC_PEAK_DFMA: return run<SMC_PEAK_DFMA>(blocks, iters, ops_per_s, ms);
+        case SMC_PEAK_I2F: return run<SMC_PEAK_I2F>(blocks, iters, ops_per_s, ms);
+        case SMC_PEAK_FRND: return run<SMC_PEAK_FRND>(blocks, iters, ops_per_s, ms);
     }
     return SMC_ERR_ARG;
 }

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_pf_step(PfArgs A, const float* __restri
             }
         }
         if (lg != lg) raise_status(status, ST_NONFINITE);
-        logg[i] = (double)lg;
+        logg[i] = f2d_bits(lg);  // normal floats only (log g is finite, |log g| >= 2^-126 or 0)
     }
 }
 

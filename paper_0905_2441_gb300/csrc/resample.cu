@@ -7,12 +7,12 @@
 //   C_j = q_0 + ... + q_j,  S = C_{M-1}
 //   F(c) = #{ i in [0,M) : (i 2^32 + u32) S < c M 2^32 }
 //   particle j fills output slots [F(C_{j-1}), F(C_j)).
-// Pass 1 sums q exactly (integer atomics, order-free) and clears the tile
-// descriptors.  Pass 2 is a single-pass scan over tiles of 2048 weights:
-// block scan, then decoupled look-back over the predecessors' published
-// aggregates / inclusive prefixes (bounded wait), then F at every prefix by
-// an estimate and an exact 128-bit fix-up, and a balanced expansion of the
-// tile's contiguous output range through shared memory.
+// Pass 1 sums q exactly per tile and per group of 64 tiles (integer
+// atomics: order-free).  Pass 2 takes one tile of 2048 weights per CTA: the
+// total and its exclusive prefix are one parallel read of the group and
+// tile sums (no CTA waits on another), then a block scan, F at every prefix
+// by an FP32 estimate and an exact 128-bit fix-up, and a balanced expansion
+// of the tile's contiguous output range through shared memory.
 #include "ctx.hpp"
 #include "device.cuh"
 #include "resample.cuh"
@@ -20,8 +20,7 @@
 using namespace smc_host;
 
 size_t smc_resample_ws_bytes(int64_t M) {
-    int64_t tiles = (M + smc::kRsTile - 1) / smc::kRsTile;
-    return (size_t)(tiles + 1) * sizeof(unsigned long long) + 256;
+    return (size_t)smc::rs_words(M) * sizeof(unsigned long long) + 256;
 }
 
 namespace smc {
@@ -46,16 +45,26 @@ namespace smc_host {
 smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t seed, uint64_t step,
                            int32_t* anc, int32_t* counts, const int32_t* do_flag, double* lwreset,
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s) {
-    int64_t tiles = (M + smc::kRsTile - 1) / smc::kRsTile;
+    const int64_t tiles = smc::rs_tiles(M);
     if (tiles > 0x7FFFFFFF) return SMC_ERR_ARG;
-    int64_t b1 = (M + 256 * 8 - 1) / (256 * 8);
-    if (b1 > (int64_t)num_sms * 8) b1 = (int64_t)num_sms * 8;
-    if (b1 < 1) b1 = 1;
-    smc::k_resample_total<<<(unsigned)b1, 256, 0, s>>>(W, M, do_flag, sc, tiles, status);
+    // the group sums must start at zero
+    SMC_CUDA(cudaMemsetAsync(sc.group_sum, 0,
+                             (size_t)smc::rs_groups(M) * sizeof(unsigned long long), s));
+    int64_t b1 = tiles;
+    if (b1 > (int64_t)num_sms * 4) b1 = (int64_t)num_sms * 4;
+    smc::k_resample_total<<<(unsigned)b1, smc::kRsThreads, 0, s>>>(W, M, do_flag, sc, status);
     SMC_CUDA(cudaGetLastError());
     smc::k_resample_scan<<<(unsigned)tiles, smc::kRsThreads, 0, s>>>(
-        W, M, seed, step, do_flag, sc, (uint32_t)tiles, anc, counts, lwreset, status);
+        W, M, seed, step, do_flag, sc, anc, counts, lwreset, status);
     return cuda_ok(cudaGetLastError());
+}
+
+// scratch layout inside `base`: tile sums, then group sums
+smc::RsScratch resample_scratch(unsigned long long* base, int64_t M) {
+    smc::RsScratch sc;
+    sc.tile_sum = base;
+    sc.group_sum = base + smc::rs_tiles(M);
+    return sc;
 }
 
 }  // namespace smc_host
@@ -73,11 +82,7 @@ extern "C" smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int
     cudaStream_t s = as_stream(stream);
     st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
     if (st != SMC_OK) return st;
-    smc::RsScratch sc;
-    sc.tiles = reinterpret_cast<unsigned long long*>(ctx->ws);
-    sc.ticket = ctx->d_counters + CNT_RESAMPLE_TILE;
-    sc.sum = ctx->d_counters + CNT_RESAMPLE_SUM;
-    sc.done = ctx->d_counters + CNT_RESAMPLE_DONE;
+    const smc::RsScratch sc = resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M);
     return resample_launch(ctx->num_sms, W, M, seed, step, ancestors_out, counts_out, do_flag,
                            logw_reset, sc, ctx->d_status, s);
 }
@@ -104,17 +109,17 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 // they do not own (a framework's caching pool, a serving runtime with a
 // fixed memory budget), and latency-critical loops that cannot afford the
 // implicit device synchronisation of cudaMalloc / cudaFree.  No context is
-// created: the scan's scratch (tile descriptors and three counters) lives in
-// a file-scope device array that every GPU loading this library holds until
+// created: the scan's scratch (tile, group and total sums) lives in a
+// file-scope device array that every GPU loading this library holds until
 // the process exits.
 #include <mutex>
 
 namespace {
 
-constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;                  // 16,777,216 weights
-constexpr int64_t kNoAllocTiles = kNoAllocMaxM / smc::kRsTile;      // 8192 tiles
-constexpr int64_t kNoAllocWords = kNoAllocTiles + 8;                // + ticket, sum, done
-// 64 KiB + 64 B of scratch per device
+constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;   // 16,777,216 weights
+// 8192 tile sums + 128 group sums (+ spare words): about 65 KiB per device
+constexpr int64_t kNoAllocWords = (kNoAllocMaxM / smc::kRsTile) +
+                                  (kNoAllocMaxM / smc::kRsTile / smc::kRsGroup) + 8;
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
 
 std::mutex g_noalloc_mu;
@@ -156,14 +161,9 @@ extern "C" smc_status smc_resample_systematic_noalloc(const double* W, int64_t M
     SMC_CUDA(cudaGetDevice(&dev));
     SMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaStream_t s = as_stream(stream);
-    smc::RsScratch sc;
-    sc.tiles = scratch;
-    sc.ticket = scratch + kNoAllocTiles;
-    sc.sum = scratch + kNoAllocTiles + 1;
-    sc.done = scratch + kNoAllocTiles + 2;
-    // the counters must start at zero; an earlier call that stopped on an
-    // error may have left them set (the tile words are cleared by pass 1)
-    SMC_CUDA(cudaMemsetAsync(sc.ticket, 0, 3 * sizeof(unsigned long long), s));
+    // resample_launch clears the group sums before pass 1; pass 1
+    // overwrites every tile sum it uses
+    const smc::RsScratch sc = resample_scratch(scratch, M);
     return resample_launch(sms, W, M, seed, step, ancestors_out, counts_out, do_flag, logw_reset,
                            sc, status_out, s);
 }

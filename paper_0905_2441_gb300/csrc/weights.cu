@@ -4,11 +4,13 @@
 // exp(dbeta l(x)); Section 3.2: ESS).
 //
 // One grid-stride pass reads l and logw, writes the new logw and reduces
-// (max, sum e, sum e^2) of the new log-weights and (max, sum e) of the old
-// ones online; the last block to finish combines the per-block partials
-// and writes the scalars.  A second pass writes W = e / S1.  Per element the
-// only FP64 instructions are the logw update and one subtraction; the
-// exponential runs in FP32 on the exactly split difference.
+// (sum e, sum e^2) of the new log-weights and (sum e) of the old ones
+// against slack references, plus the exact maximum (integer keys); the last
+// block to finish combines the per-block partials in FP64 and writes the
+// scalars.  A second pass writes W = e / S1.  Per element the only FP64
+// instruction is the log-weight update (GB300 issues FP64 at ~1/64 of
+// FP32); differences and exponentials run in FP32 on hi/lo splits.
+#include <climits>
 #include <cmath>
 
 #include "ctx.hpp"
@@ -18,78 +20,217 @@ using namespace smc_host;
 
 namespace smc {
 
-// exp(x) for an FP64 x <= 0, FP32 accuracy, as float
+// exp(x) for an FP64 x <= 64 (FP32 accuracy, float result)
 __device__ __forceinline__ float expd(double x) {
     float hi, lo;
     split_double(x, hi, lo);
     return exp_hilo(hi, lo);
 }
 
-// thread-level online accumulator: m is the running max, s1 = sum e^(x-m),
-// s2 = sum e^(2(x-m))
-struct OnlineLse {
-    double m = -INFINITY;
+constexpr double kNegInf = -INFINITY;
+__device__ __forceinline__ bool is_neg_inf(double x) {
+    return __double_as_longlong(x) == (long long)0xFFF0000000000000ull;
+}
+
+// Element loops take chunks of 8 consecutive doubles per thread and
+// iteration (four 16-byte loads issued before any use), so each SM keeps
+// enough bytes in flight to cover HBM latency; a scalar loop handles the
+// tail and unaligned arrays.
+constexpr int kChunk = 8;
+
+__device__ __forceinline__ bool aligned16(const void* p) {
+    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
+}
+
+__device__ __forceinline__ void load8(const double* __restrict__ p, double (&v)[kChunk]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 t[kChunk / 2];
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j) t[j] = q[j];
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j) { v[2 * j] = t[j].x; v[2 * j + 1] = t[j].y; }
+}
+
+__device__ __forceinline__ void store8(double* __restrict__ p, const double (&v)[kChunk]) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
+}
+
+// Thread-level sums against a slack reference r: e = exp(x - r) may exceed
+// 1 (up to e^32) so the reference moves only when an element exceeds it by
+// more than 32 nats, not at every new maximum.  No FP64 instruction per
+// element: x and r are split into float hi + lo parts by integer operations
+// and x - r is taken as the pair (xh - rh, xl - rl); the hi difference is
+// exact when x and r are within a factor 2 and otherwise rounded once
+// (relative error 2^-24 of the difference), which the exponential turns
+// into a relative error of at most 2^-24 |x - r| in e.
+struct RefSums {
+    double r = kNegInf;
+    float rh = 0.0f, rl = 0.0f;
     float s1 = 0.0f, s2 = 0.0f;
+    bool any = false;
+    long long kmax = LLONG_MIN;               // key of the largest element
     __device__ __forceinline__ void add(double x) {
-        if (dkey(x) > dkey(m)) {
-            float f = (m == -INFINITY) ? 0.0f : expd(m - x);
+        if (is_neg_inf(x)) return;            // zero weight
+        const long long k = dkey(x);
+        kmax = k > kmax ? k : kmax;
+        float xh, xl;
+        split_double(x, xh, xl);
+        if (!any) { r = x; rh = xh; rl = xl; s1 = 1.0f; s2 = 1.0f; any = true; return; }
+        const float dh = xh - rh, dl = xl - rl;
+        if (dh > 32.0f) {                     // move the reference up to x
+            const float f = exp_hilo(-dh, -dl);
             s1 = fmaf(s1, f, 1.0f);
             s2 = fmaf(s2, f * f, 1.0f);
-            m = x;
-        } else if (x != -INFINITY) {
-            float e = expd(x - m);
+            r = x; rh = xh; rl = xl;
+        } else {
+            const float e = exp_hilo(dh, dl);
             s1 += e;
             s2 = fmaf(e, e, s2);
         }
     }
 };
 
-// block / grid level: FP64 sums
+// block / grid level: FP64 sums relative to a reference m
 struct Lse {
     double m, s1, s2;
 };
 
-__device__ __forceinline__ Lse lse_merge(Lse a, Lse b) {
-    if (b.m == -INFINITY) return a;
-    if (a.m == -INFINITY) return b;
-    if (dkey(b.m) > dkey(a.m)) { Lse t = a; a = b; b = t; }
-    double f = (double)expd(b.m - a.m);
-    a.s1 += b.s1 * f;
-    a.s2 += b.s2 * f * f;
-    return a;
+__device__ __forceinline__ double key_to_double(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
 }
 
-__device__ __forceinline__ Lse warp_merge(Lse v) {
+__device__ __forceinline__ long long warp_max_key(long long key) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        Lse w;
-        w.m = __shfl_xor_sync(0xFFFFFFFFu, v.m, o);
-        w.s1 = __shfl_xor_sync(0xFFFFFFFFu, v.s1, o);
-        w.s2 = __shfl_xor_sync(0xFFFFFFFFu, v.s2, o);
-        v = lse_merge(v, w);
+        const long long k2 = __shfl_xor_sync(0xFFFFFFFFu, key, o);
+        key = k2 > key ? k2 : key;
     }
-    return v;
+    return key;
 }
 
-// merge a value across the block; result valid in every thread
-__device__ __forceinline__ Lse block_merge(Lse v, Lse* sh /* [32] */) {
-    v = warp_merge(v);
-    const int w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-    if ((threadIdx.x & 31) == 0) sh[w] = v;
+// Block combination of thread sums: the block's reference is the largest
+// thread reference (integer comparison of FP64 keys), every thread rescales
+// its FP32 sums to it with one exponential, then FP32 block sums.  Result
+// valid in thread 0.
+__device__ __forceinline__ Lse block_combine(const RefSums& t, long long* s_key, float* s_a,
+                                             float* s_b, double* max_out) {
+    long long key = warp_max_key(t.any ? dkey(t.r) : LLONG_MIN);
+    long long kmx = warp_max_key(t.kmax);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_key[w] = key; s_key[16 + w] = kmx; }
     __syncthreads();
-    if (w == 0) {
-        Lse t = (threadIdx.x < (unsigned)nw) ? sh[threadIdx.x] : Lse{-INFINITY, 0.0, 0.0};
-        t = warp_merge(t);
-        if (threadIdx.x == 0) sh[0] = t;
+    long long bk = LLONG_MIN, bm = LLONG_MIN;
+    for (int i = 0; i < nw; ++i) {
+        bk = s_key[i] > bk ? s_key[i] : bk;
+        bm = s_key[16 + i] > bm ? s_key[16 + i] : bm;
     }
     __syncthreads();
-    Lse r = sh[0];
+    Lse out{kNegInf, 0.0, 0.0};
+    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
+    if (bk == LLONG_MIN) return out;  // every weight zero in this block
+    const double R = key_to_double(bk);
+    float a = 0.0f, b = 0.0f;
+    if (t.any) {
+        const float f = expd(t.r - R);  // <= 1
+        a = t.s1 * f;
+        b = t.s2 * f * f;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) { s_a[w] = a; s_b[w] = b; }
     __syncthreads();
-    return r;
+    if (threadIdx.x == 0) {
+        float A = 0.0f, B = 0.0f;
+        for (int i = 0; i < nw; ++i) { A += s_a[i]; B += s_b[i]; }
+        out = Lse{R, f2d_bits(A), f2d_bits(B)};
+    }
+    __syncthreads();
+    return out;
 }
 
-// partial slot layout (doubles): [b*8 + 0..4] = {m, s1, s2, m_old, s_old}
-// final slot at kMaxPartialBlocks-1: {m, S1, S2, valid, lse, ...}
+// Combine the per-block partials in the last block: the common reference is
+// the largest block reference (integer keys), each partial is scaled to it
+// with one FP32 exponential and the sums are reduced in FP64 as a parallel
+// tree -- no long serial chain of FP64 operations (FP64 latency is long on
+// this part).  Result valid in thread 0; `off` selects {ref, s1, s2} at 0 or
+// {ref_old, s_old} at 3.
+__device__ __forceinline__ Lse combine_partials(const double* partials, int nblocks, int off,
+                                                long long* s_key) {
+    long long k = LLONG_MIN;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double r = __ldcg(partials + (size_t)b * 8 + off);
+        if (!is_neg_inf(r)) { const long long kk = dkey(r); k = kk > k ? kk : k; }
+    }
+    k = warp_max_key(k);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) s_key[w] = k;
+    __syncthreads();
+    long long bk = LLONG_MIN;
+    for (int i = 0; i < nw; ++i) bk = s_key[i] > bk ? s_key[i] : bk;
+    __syncthreads();
+    Lse out{kNegInf, 0.0, 0.0};
+    if (bk == LLONG_MIN) return out;
+    float Rh, Rl;
+    const double R = key_to_double(bk);
+    split_double(R, Rh, Rl);
+    // FP64 accumulation, but only short dependent chains: a few partials per
+    // thread, then a 5-level shuffle tree and 8 warp totals
+    double a = 0.0, bsum = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double* P = partials + (size_t)b * 8 + off;
+        const double r = __ldcg(P);
+        if (is_neg_inf(r)) continue;
+        float h, l;
+        split_double(r, h, l);
+        const float f = exp_hilo(h - Rh, l - Rl);  // <= 1
+        a = fma(__ldcg(P + 1), f2d_bits(f), a);
+        if (off == 0) bsum = fma(__ldcg(P + 2), f2d_bits(f * f), bsum);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
+        bsum += __shfl_xor_sync(0xFFFFFFFFu, bsum, o);
+    }
+    __shared__ double s_da[32], s_db[32];
+    if ((threadIdx.x & 31) == 0) { s_da[w] = a; s_db[w] = bsum; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0;
+        for (int i = 0; i < nw; ++i) { A += s_da[i]; B += s_db[i]; }
+        out = Lse{R, A, B};
+    }
+    __syncthreads();
+    return out;
+}
+
+__device__ __forceinline__ double max_partials(const double* partials, int nblocks, long long* sk) {
+    long long k = LLONG_MIN;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double v = __ldcg(partials + (size_t)b * 8 + 5);
+        if (!is_neg_inf(v)) { const long long kk = dkey(v); k = kk > k ? kk : k; }
+    }
+    k = warp_max_key(k);
+    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = k;
+    __syncthreads();
+    long long m = LLONG_MIN;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = sk[i] > m ? sk[i] : m;
+    __syncthreads();
+    return m == LLONG_MIN ? kNegInf : key_to_double(m);
+}
+
+// ln of a positive float sum, as lg2 * ln 2 (absolute error ~2^-22)
+__device__ __forceinline__ double ln_sum(double s) {
+    return (double)(lg2((float)s) * 0.69314718055994531f);
+}
+
+// partial slot layout (doubles): [b*8 + 0..5] = {ref, s1, s2, ref_old, s_old, max}
+// final slot: {max, S1, S2, valid, lse, (float) 1/S1 in the low word of [5]},
+// S1 and S2 relative to the true maximum
 __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restrict__ ll,
                                                          double dbeta, double* __restrict__ lw,
                                                          int64_t M, int has_inc,
@@ -99,61 +240,89 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
                                                          int32_t* __restrict__ flag,
                                                          double ess_frac, int final_slot,
                                                          uint32_t* status) {
-    __shared__ Lse sh[32];
+    __shared__ long long s_key[48];
+    __shared__ float s_a[32], s_b[32];
     __shared__ bool last;
-    OnlineLse cur, old;
+    RefSums cur, old;
     bool nan_seen = false;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
-        double x = lw[i];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool vec = aligned16(lw) && (!has_inc || aligned16(ll));
+    const int64_t nchunk = vec ? M / kChunk : 0;
+    for (int64_t ch = t0; ch < nchunk; ch += G) {
+        double x[kChunk];
+        load8(lw + ch * kChunk, x);
         if (has_inc) {
-            double v = ll[i];
-            nan_seen |= disnan(x) | disnan(v);
-            old.add(x);
-            x = fma(dbeta, v, x);
-            lw[i] = x;
+            double v[kChunk], n[kChunk];
+            load8(ll + ch * kChunk, v);
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) {
+                nan_seen |= disnan(x[j]) | disnan(v[j]);
+                n[j] = fma(dbeta, v[j], x[j]);
+                nan_seen |= disnan(n[j]);
+            }
+            store8(lw + ch * kChunk, n);
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) { old.add(x[j]); cur.add(n[j]); }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kChunk; ++j) { nan_seen |= disnan(x[j]); cur.add(x[j]); }
         }
+    }
+    for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {  // tail / unaligned
+        const double x = lw[i];
         nan_seen |= disnan(x);
-        cur.add(x);
+        if (has_inc) {
+            const double v = ll[i];
+            const double n = fma(dbeta, v, x);
+            nan_seen |= disnan(v) | disnan(n);
+            lw[i] = n;
+            old.add(x);
+            cur.add(n);
+        } else {
+            cur.add(x);
+        }
     }
     if (nan_seen) raise_status(status, ST_NONFINITE);
-    Lse c = block_merge(Lse{cur.m, (double)cur.s1, (double)cur.s2}, sh);
-    Lse o = has_inc ? block_merge(Lse{old.m, (double)old.s1, 0.0}, sh) : Lse{-INFINITY, 0.0, 0.0};
+    double bmax, bmax_old;
+    const Lse c = block_combine(cur, s_key, s_a, s_b, &bmax);
+    const Lse o = has_inc ? block_combine(old, s_key, s_a, s_b, &bmax_old) : Lse{kNegInf, 0.0, 0.0};
     if (threadIdx.x == 0) {
         double* P = partials + (size_t)blockIdx.x * 8;
-        P[0] = c.m; P[1] = c.s1; P[2] = c.s2; P[3] = o.m; P[4] = o.s1;
+        P[0] = c.m; P[1] = c.s1; P[2] = c.s2; P[3] = o.m; P[4] = o.s1; P[5] = bmax;
         __threadfence();
-        unsigned long long t = atomicAdd(ticket, 1ull);
+        const unsigned long long t = atomicAdd(ticket, 1ull);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // last block: combine every partial
-    Lse tc{-INFINITY, 0.0, 0.0}, to{-INFINITY, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        volatile double* P = partials + (size_t)b * 8;
-        tc = lse_merge(tc, Lse{P[0], P[1], P[2]});
-        to = lse_merge(to, Lse{P[3], P[4], 0.0});
-    }
-    tc = block_merge(tc, sh);
-    to = block_merge(to, sh);
+    Lse tc = combine_partials(partials, gridDim.x, 0, s_key);
+    const Lse to = has_inc ? combine_partials(partials, gridDim.x, 3, s_key)
+                           : Lse{kNegInf, 0.0, 0.0};
+    const double mx = max_partials(partials, gridDim.x, s_key);
     if (threadIdx.x == 0) {
         *ticket = 0ull;
         double* F = partials + (size_t)final_slot * 8;
-        bool valid = tc.m != -INFINITY && !disnan(tc.m);
+        const bool valid = !is_neg_inf(tc.m) && !disnan(tc.m);
+        if (valid) {  // express the sums relative to the true maximum
+            const double f = f2d_bits(expd(tc.m - mx));
+            tc = Lse{mx, tc.s1 * f, tc.s2 * f * f};
+        }
         if (!valid) {
             if (!disnan(tc.m)) raise_status(status, ST_ZERO_WEIGHT);
             F[3] = 0.0;
             if (flag) *flag = 0;
             return;
         }
-        double lse = tc.m + log(tc.s1);
-        double ess = tc.s1 * tc.s1 / tc.s2;
+        const double lse = tc.m + ln_sum(tc.s1);
+        const float s1f = (float)tc.s1;
+        const double ess = f2d_bits(s1f * (s1f / (float)tc.s2));  // FP32 division
         F[0] = tc.m; F[1] = tc.s1; F[2] = tc.s2; F[3] = 1.0; F[4] = lse;
+        reinterpret_cast<float*>(F + 5)[0] = 1.0f / s1f;
         if (scalars) {
             double inc = 0.0;
-            if (has_inc) inc = lse - (to.m + log(to.s1));
+            if (has_inc) inc = lse - (to.m + ln_sum(to.s1));
             scalars[0] = inc;
             scalars[1] = ess;
             scalars[2] = tc.m;
@@ -163,19 +332,35 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
     }
 }
 
-// W_i = exp(lw_i - m) / S1, computed in FP32 on the exact FP64 difference;
-// values below 2^-126 are written as 0.
+// W_i = exp(lw_i - m) / S1 with the difference taken on float hi/lo splits
+// as in RefSums (no FP64 instruction per element); values below 2^-126 are
+// written as 0.
 __global__ void __launch_bounds__(256) k_reweight_normalize(const double* __restrict__ lw,
                                                             int64_t M,
                                                             const double* __restrict__ fin,
                                                             double* __restrict__ W) {
     if (fin[3] == 0.0) return;
-    const double m = fin[0];
-    const float inv = (float)(1.0 / fin[1]);
+    float mh, ml;
+    split_double(fin[0], mh, ml);
+    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
-        float e = expd(lw[i] - m);
-        W[i] = f2d_bits(e * inv);
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nchunk = (aligned16(lw) && aligned16(W)) ? M / kChunk : 0;
+    for (int64_t ch = t0; ch < nchunk; ch += G) {
+        double x[kChunk], w[kChunk];
+        load8(lw + ch * kChunk, x);
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            float xh, xl;
+            split_double(x[j], xh, xl);
+            w[j] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
+        }
+        store8(W + ch * kChunk, w);
+    }
+    for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {
+        float xh, xl;
+        split_double(lw[i], xh, xl);
+        W[i] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
     }
 }
 
@@ -184,41 +369,47 @@ __global__ void __launch_bounds__(256) k_ess_reduce(const double* __restrict__ l
                                                     unsigned long long* ticket,
                                                     double* __restrict__ ess_out,
                                                     uint32_t* status) {
-    __shared__ Lse sh[32];
+    __shared__ long long s_key[48];
+    __shared__ float s_a[32], s_b[32];
     __shared__ bool last;
-    OnlineLse cur;
+    RefSums cur;
     bool nan_seen = false;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
-        double x = lw[i];
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nchunk = aligned16(lw) ? M / kChunk : 0;
+    for (int64_t ch = t0; ch < nchunk; ch += G) {
+        double x[kChunk];
+        load8(lw + ch * kChunk, x);
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) { nan_seen |= disnan(x[j]); cur.add(x[j]); }
+    }
+    for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {
+        const double x = lw[i];
         nan_seen |= disnan(x);
         cur.add(x);
     }
     if (nan_seen) raise_status(status, ST_NONFINITE);
-    Lse c = block_merge(Lse{cur.m, (double)cur.s1, (double)cur.s2}, sh);
+    double bmax;
+    const Lse c = block_combine(cur, s_key, s_a, s_b, &bmax);
     if (threadIdx.x == 0) {
         double* P = partials + (size_t)blockIdx.x * 8;
         P[0] = c.m; P[1] = c.s1; P[2] = c.s2;
         __threadfence();
-        unsigned long long t = atomicAdd(ticket, 1ull);
+        const unsigned long long t = atomicAdd(ticket, 1ull);
         last = (t == gridDim.x - 1);
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    Lse tc{-INFINITY, 0.0, 0.0};
-    for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-        volatile double* P = partials + (size_t)b * 8;
-        tc = lse_merge(tc, Lse{P[0], P[1], P[2]});
-    }
-    tc = block_merge(tc, sh);
+    const Lse tc = combine_partials(partials, gridDim.x, 0, s_key);
     if (threadIdx.x == 0) {
         *ticket = 0ull;
-        if (tc.m == -INFINITY) {
+        if (is_neg_inf(tc.m)) {
             raise_status(status, ST_ZERO_WEIGHT);
             return;
         }
-        *ess_out = tc.s1 * tc.s1 / tc.s2;
+        const float s1f = (float)tc.s1;
+        *ess_out = f2d_bits(s1f * (s1f / (float)tc.s2));
     }
 }
 
@@ -253,8 +444,8 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
                                                   ctx->d_status);
     SMC_CUDA(cudaGetLastError());
     if (W_out) {
-        int nb = (int)((M + 255) / 256);
-        int cap = ctx->num_sms * 16;
+        int nb = (int)((M + 256 * 8 - 1) / (256 * 8));
+        int cap = ctx->num_sms * 8;
         if (nb > cap) nb = cap;
         smc::k_reweight_normalize<<<nb, 256, 0, s>>>(logw, M,
                                                      ctx->d_partials + (size_t)final_slot * 8, W_out);
