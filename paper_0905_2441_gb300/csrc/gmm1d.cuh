@@ -248,27 +248,38 @@ struct SliceAccEqW {
         float2 NU[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) NU[k] = make_float2(nu[k], nu[k]);
-#pragma unroll 2
+#pragma unroll 4
         for (int p = lane; p < np; p += L) {
             const float2 Y = ys2[p];
             float2 T[K];
-            float m0 = INFINITY, m1 = INFINITY;
+            float a0[K], a1[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 T[k] = __ffma2_rn(Y, R2, NU[k]);
-                m0 = fminf(m0, fabsf(T[k].x));
-                m1 = fminf(m1, fabsf(T[k].y));
+                a0[k] = fabsf(T[k].x);
+                a1[k] = fabsf(T[k].y);
             }
-            const float2 C = make_float2(-m0 * m0, -m1 * m1);
-            float2 S;
+            // balanced trees keep the dependency chains short (log2 K)
+#pragma unroll
+            for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+                for (int k = 0; k + w < K; k += 2 * w) {
+                    a0[k] = fminf(a0[k], a0[k + w]);
+                    a1[k] = fminf(a1[k], a1[k + w]);
+                }
+            const float2 C = make_float2(-a0[0] * a0[0], -a1[0] * a1[0]);
+            float2 E[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float2 P = __ffma2_rn(T[k], T[k], C);
-                const float2 E = make_float2(ex2_neg(P.x), ex2_neg(P.y));
-                S = k == 0 ? E : __fadd2_rn(S, E);
+                const float2 Pk = __ffma2_rn(T[k], T[k], C);
+                E[k] = make_float2(ex2_neg(Pk.x), ex2_neg(Pk.y));
             }
+#pragma unroll
+            for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+                for (int k = 0; k + w < K; k += 2 * w) E[k] = __fadd2_rn(E[k], E[k + w]);
             ms = __fadd2_rn(ms, C);
-            pr = __fmul2_rn(pr, S);
+            pr = __fmul2_rn(pr, E[0]);
             if (++cnt == 16) flush();
         }
         if ((cnt_total & 1) && lane == 0) one(ys[cnt_total - 1], nu, r);
@@ -280,6 +291,59 @@ struct SliceAccEqW {
         return part * kLn2 + P.cst;
     }
 };
+
+// The random draws of one chain's move, computed once per slice of L lanes
+// instead of redundantly on every lane.  The slice has P + 1 tasks (P =
+// ceil(K/2) Box-Muller pairs; pair p uses Philox block p/2 of the MOVE
+// stream, words 2p, 2p+1; task P is the ACCEPT block), dealt to its lanes
+// in ceil((P+1)/L) rounds; shuffles hand the K normals and the accept word
+// to every lane of the slice.  Every lane of the warp must call this.
+template <int K>
+__device__ __forceinline__ void slice_draws(uint64_t seed, uint64_t step, uint32_t index,
+                                            int lane, int L, int Kreal, float (&z)[K],
+                                            uint32_t& accept_word) {
+    constexpr int PMAX = (K + 1) / 2;
+    const int P = (Kreal + 1) / 2;
+    const int base = (int)(threadIdx.x & 31) - lane;  // warp lane of this slice's lane 0
+    const int R = (P + L) / L;                        // rounds = ceil((P + 1) / L)
+    float z0[PMAX + 1], z1[PMAX + 1];
+    uint32_t wx[PMAX + 1];
+#pragma unroll
+    for (int r = 0; r <= PMAX; ++r) {
+        z0[r] = 0.0f; z1[r] = 0.0f; wx[r] = 0u;
+        if (r < R) {
+            const int t = r * L + lane;              // this lane's task in round r
+            const bool acc = t == P;
+            const int p = t < P ? t : 0;
+            const uint4 w = draw(seed, acc ? RNG_ACCEPT : RNG_MOVE, step, index,
+                                 acc ? 0u : (uint32_t)(p >> 1));
+            if (p & 1) box_muller(w.z, w.w, z0[r], z1[r]);
+            else box_muller(w.x, w.y, z0[r], z1[r]);
+            wx[r] = w.x;
+        }
+    }
+    // task t sits in round t / L on slice lane t % L (warp-uniform for fixed t)
+    {
+        const int r = P / L;
+        uint32_t v = wx[0];
+#pragma unroll
+        for (int rr = 1; rr <= PMAX; ++rr) v = rr == r ? wx[rr] : v;
+        accept_word = __shfl_sync(0xFFFFFFFFu, v, base + P % L);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int t = k >> 1, r = t / L;
+        float a = z0[0], b = z1[0];
+#pragma unroll
+        for (int rr = 1; rr <= PMAX; ++rr) {
+            a = rr == r ? z0[rr] : a;
+            b = rr == r ? z1[rr] : b;
+        }
+        a = __shfl_sync(0xFFFFFFFFu, a, base + t % L);
+        b = __shfl_sync(0xFFFFFFFFu, b, base + t % L);
+        z[k] = k < Kreal ? ((k & 1) ? b : a) : 0.0f;
+    }
+}
 
 // Chunk size of the staged data (floats) and the shared-memory bytes a
 // kernel using the slice evaluator needs: data buffer + mbarrier.

@@ -58,7 +58,9 @@ __global__ void __launch_bounds__(256) k_mh_move(
     double l = 0.0;
     float b = 0.0f;
 #pragma unroll
-    for (int k = 0; k < K; ++k) { mu[k] = 0.0f; g[k] = 0.0f; z[k] = 0.0f; }
+    for (int k = 0; k < K; ++k) { mu[k] = 0.0f; g[k] = 0.0f; }
+    uint32_t aw;
+    slice_draws<K>(seed, step, (uint32_t)(active ? p : 0), lane, L, Kreal, z, aw);
     if (active) {
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -69,7 +71,6 @@ __global__ void __launch_bounds__(256) k_mh_move(
         }
         l = ll_in[src];
         b = beta[p * beta_stride];
-        normals<K>(seed, RNG_MOVE, step, (uint32_t)p, Kreal, z);
     }
     const float hh2 = 0.5f * scale * scale;
     bool in_box = active;
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(256) k_mh_move(
             log_alpha += (fwd - bwd) / (2.0f * scale * scale);
         }
         if (lp != lp) raise_status(status, ST_NONFINITE);
-        acc_ok = accept(draw(seed, RNG_ACCEPT, step, (uint32_t)p, 0u).x, log_alpha);
+        acc_ok = accept(aw, log_alpha);
     }
     if (active && lane == 0) {
 #pragma unroll
@@ -133,12 +134,13 @@ __global__ void __launch_bounds__(256) k_mh_move(
 
 // ------------------------------------------------------------------ population MCMC
 // Work items are chunks of (blockDim / L) consecutive chains of the flat
-// chain array, handed out by a queue, so every item costs the same whatever
-// the population sizes.  After a chain's move, lane 0 of its slice
-// publishes it (fence + atomic count of the population's finished chains);
-// the slice that finishes a population's last chain runs that population's
-// exchange moves at once (reads through L2), so no CTA ever waits on another.
-// The counters and the queue are left at zero for the next sweep.
+// chain array, dealt round-robin to the CTAs, so every item costs the same
+// whatever the population sizes.  After an item's moves, one thread adds
+// the item's chain count to each population it touches (fence + one
+// integer atomic per population); the CTA that completes a population runs
+// that population's exchange moves at once (one warp, reads through L2), so
+// no CTA ever waits on another.  The counters are left at zero for the next
+// sweep.
 __device__ __forceinline__ int pop_of(const int32_t* __restrict__ offsets, int n_pops, int64_t c) {
     int lo = 0, hi = n_pops;  // largest q with offsets[q] <= c
     while (hi - lo > 1) {
@@ -148,6 +150,7 @@ __device__ __forceinline__ int pop_of(const int32_t* __restrict__ offsets, int n
     }
     return lo;
 }
+
 
 template <int K>
 __device__ __forceinline__ void exchange_population(
@@ -189,18 +192,18 @@ template <int K, bool EQW>
 __global__ void __launch_bounds__(256) k_popmcmc_sweep(
     const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
     const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
-    float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats,
-    unsigned long long* queue, unsigned long long* done, uint32_t* pop_done, Gmm1dArgs P, int L,
-    int Kreal, uint32_t* status) {
+    float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
+    Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
     extern __shared__ __align__(16) float ys[];
-    __shared__ long long s_item;
+    __shared__ int s_ex[2][1025];             // populations completed by an item (<= chains + 1)
+    __shared__ int s_nex[2];
     __shared__ uint32_t s_mh, s_sw, s_try;
     init_mbar(ychunk_mbar(ys));
     if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
-    const int slice0 = (int)(threadIdx.x & 31) / L * L;  // warp lane of this slice's lane 0
-    const long long nitems = (Mtot + ppb - 1) / ppb;
+    const int warp = threadIdx.x >> 5;
+    const int64_t nitems = (Mtot + ppb - 1) / ppb;
     uint32_t phase = 0;
     const bool resident = N <= kYChunk;  // all data in shared memory: stage once
     if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys), phase, status);
@@ -208,30 +211,27 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
 #pragma unroll
     for (int k = 0; k < K; ++k) lw2[k] = P.lw2[k];
 
-    while (true) {
-        if (threadIdx.x == 0) {
-            unsigned long long t = atomicAdd(queue, 1ull);
-            s_item = t < (unsigned long long)nitems ? (long long)t : -1ll;
-        }
-        __syncthreads();
-        const long long item = s_item;
-        __syncthreads();
-        if (item < 0) break;
-        const int64_t c = item * ppb + threadIdx.x / L;
+    // items are equal chunks of ppb consecutive chains, dealt round-robin
+    uint32_t iter = 0;
+    for (int64_t item = blockIdx.x; item < nitems; item += gridDim.x) {
+        const int64_t c0 = item * ppb;
+        const int64_t c1 = c0 + ppb < Mtot ? c0 + ppb : Mtot;
+        const int64_t c = c0 + threadIdx.x / L;
         const bool active = c < Mtot;
         // ---- random-walk MH move of chain c
         float mu[K], z[K], prop[K], nu[K];
         double l = 0.0;
         float b = 0.0f;
+        uint32_t aw;
+        slice_draws<K>(seed, sweep, (uint32_t)(active ? c : 0), lane, L, Kreal, z, aw);
 #pragma unroll
-        for (int k = 0; k < K; ++k) { mu[k] = 0.0f; z[k] = 0.0f; }
+        for (int k = 0; k < K; ++k) mu[k] = 0.0f;
         if (active) {
 #pragma unroll
             for (int k = 0; k < K; ++k)
                 if (k < Kreal) mu[k] = theta[(int64_t)k * Mtot + c];
             l = ll[c];
             b = beta[c];
-            normals<K>(seed, RNG_MOVE, sweep, (uint32_t)c, Kreal, z);
         }
         bool in_box = active;
 #pragma unroll
@@ -262,54 +262,84 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
         bool ok = false;
         if (in_box && lane == 0) {
             if (lp != lp) raise_status(status, ST_NONFINITE);
-            ok = accept(draw(seed, RNG_ACCEPT, sweep, (uint32_t)c, 0u).x, tempered_diff(b, lp, l));
+            ok = accept(aw, tempered_diff(b, lp, l));
         }
-        // ---- publish the chain; the population's last chain runs its exchange
-        int q = 0, Mq = 0;
-        int64_t base = 0;
-        bool last = false;
-        if (active && lane == 0) {
-            if (ok) {
+        if (active && lane == 0 && ok) {
 #pragma unroll
-                for (int k = 0; k < K; ++k)
-                    if (k < Kreal) theta[(int64_t)k * Mtot + c] = prop[k];
-                ll[c] = lp;
-            }
-            q = pop_of(offsets, n_pops, c);
-            base = offsets[q];
-            Mq = (int)(offsets[q + 1] - base);
-            __threadfence();
-            const uint32_t old = atomicAdd(pop_done + q, 1u);
-            last = old == (uint32_t)(Mq - 1);
+            for (int k = 0; k < K; ++k)
+                if (k < Kreal) theta[(int64_t)k * Mtot + c] = prop[k];
+            ll[c] = lp;
+            __threadfence();  // the item's moves are visible before it is counted
         }
         const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, ok);
         if ((threadIdx.x & 31) == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
-        last = __shfl_sync(0xFFFFFFFFu, last, slice0);
-        q = __shfl_sync(0xFFFFFFFFu, q, slice0);
-        Mq = __shfl_sync(0xFFFFFFFFu, Mq, slice0);
-        base = __shfl_sync(0xFFFFFFFFu, base, slice0);
-        if (last) {
+        const int buf = (int)(iter & 1);  // double-buffered list: no third barrier
+        if (threadIdx.x == 0) s_nex[buf] = 0;
+        __syncthreads();
+        // ---- count the item's chains per population: warp 0 finds the first
+        // population by a parallel search, then one lane per touched
+        // population adds its count (one integer atomic each)
+        if (warp == 0) {
+            const int l32 = threadIdx.x & 31;
+            int qlo = 0, qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
+            while (qhi - qlo > 1) {
+                // 32 probes split [qlo, qhi) into 33 parts
+                const int span = qhi - qlo;
+                const int probe = qlo + (int)(((int64_t)span * (l32 + 1)) / 33);
+                const bool le = probe > qlo && probe < qhi && (int64_t)offsets[probe] <= c0;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, le);
+                int nlo = qlo, nhi = qhi;
+                if (m) nlo = __shfl_sync(0xFFFFFFFFu, probe, 31 - __clz(m));
+                const unsigned gt = __ballot_sync(0xFFFFFFFFu, probe > qlo && probe < qhi &&
+                                                                   (int64_t)offsets[probe] > c0);
+                if (gt) nhi = __shfl_sync(0xFFFFFFFFu, probe, __ffs(gt) - 1);
+                if (nlo == qlo && nhi == qhi) {  // fewer than 33 candidates left: scan
+                    const int cand = qlo + 1 + l32;
+                    const bool le2 = cand < qhi && (int64_t)offsets[cand] <= c0;
+                    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, le2);
+                    if (m2) nlo = qlo + 1 + (31 - __clz(m2));
+                    nhi = nlo + 1;
+                }
+                qlo = nlo;
+                qhi = nhi;
+            }
+            // populations qlo, qlo+1, ... overlapping [c0, c1)
+            for (int q = qlo + l32;; q += 32) {
+                const bool in = q < n_pops && (int64_t)offsets[q] < c1;
+                if (!__any_sync(0xFFFFFFFFu, in)) break;
+                if (in) {
+                    const int64_t a = (int64_t)offsets[q] > c0 ? (int64_t)offsets[q] : c0;
+                    const int64_t qe = offsets[q + 1];
+                    const int64_t b2 = qe < c1 ? qe : c1;
+                    if (b2 > a) {
+                        const uint32_t cnt = (uint32_t)(b2 - a);
+                        const uint32_t Mq = (uint32_t)(qe - offsets[q]);
+                        const uint32_t old = atomicAdd(pop_done + q, cnt);
+                        if (old + cnt == Mq) s_ex[buf][atomicAdd(&s_nex[buf], 1)] = q;
+                    }
+                }
+            }
             __threadfence();
-            if (Mq >= 2)
-                exchange_population<K>(theta, ll, Mtot, beta, base, Mq, q, lane, L, Kreal, seed,
-                                       sweep, &s_sw, &s_try);
-            if (lane == 0) pop_done[q] = 0u;
         }
+        __syncthreads();
+        // ---- exchange moves of the populations this item completed (one warp each)
+        const int nex = s_nex[buf];
+        for (int e = warp; e < nex; e += (int)(blockDim.x >> 5)) {
+            const int q = s_ex[buf][e];
+            const int64_t base = offsets[q];
+            const int Mq = (int)(offsets[q + 1] - base);
+            if (Mq >= 2)
+                exchange_population<K>(theta, ll, Mtot, beta, base, Mq, q, threadIdx.x & 31, 32,
+                                       Kreal, seed, sweep, &s_sw, &s_try);
+            if ((threadIdx.x & 31) == 0) pop_done[q] = 0u;
+        }
+        ++iter;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        if (stats) {
-            if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
-            if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
-            if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
-        }
-        __threadfence();
-        const unsigned long long d = atomicAdd(done, 1ull);
-        if (d == (unsigned long long)gridDim.x - 1) {
-            *queue = 0ull;
-            __threadfence();
-            *done = 0ull;
-        }
+    if (threadIdx.x == 0 && stats) {
+        if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
+        if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
+        if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
     }
 }
 
@@ -365,8 +395,7 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
     if (grid > items) grid = items;
     kern<<<(unsigned)grid, threads, smc::kYSmemBytes, s>>>(
         y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
-        reinterpret_cast<unsigned long long*>(stats), ctx->d_counters + CNT_POP_QUEUE,
-        ctx->d_counters + CNT_POP_DONE, ctx->d_popdone, P, L, Kr, ctx->d_status);
+        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, P, L, Kr, ctx->d_status);
     return cuda_ok(cudaGetLastError());
 }
 
