@@ -345,26 +345,34 @@ __device__ __forceinline__ void slice_draws(uint64_t seed, uint64_t step, uint32
     }
 }
 
-// Chunk size of the staged data (floats) and the shared-memory bytes a
-// kernel using the slice evaluator needs: data buffer + mbarrier.
+// Largest chunk of staged data (floats).  A launch sizes its buffer to
+// ychunk = min(kYChunk, N rounded up to 4) floats, followed by the mbarrier,
+// so small data sets leave shared memory for more resident CTAs.
 constexpr int kYChunk = 8192;
-constexpr size_t kYSmemBytes = kYChunk * sizeof(float) + 16;
 
-__device__ __forceinline__ uint64_t* ychunk_mbar(float* ys) {
-    return reinterpret_cast<uint64_t*>(ys + kYChunk);
+__host__ __device__ inline int ychunk_for(int64_t N) {
+    int64_t c = N < 4 ? 4 : ((N + 3) / 4) * 4;
+    return (int)(c < kYChunk ? c : kYChunk);
+}
+__host__ __device__ inline size_t ysmem_bytes(int ychunk) {
+    return (size_t)ychunk * sizeof(float) + 16;
+}
+
+__device__ __forceinline__ uint64_t* ychunk_mbar(float* ys, int ychunk) {
+    return reinterpret_cast<uint64_t*>(ys + ychunk);
 }
 
 // Run one slice accumulator over all N data, staging chunk by chunk.  The
 // whole block calls this (it contains barriers); `active` slices compute.
 template <int K, bool GRAD, bool EQW>
-__device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, float* ys,
+__device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, float* ys, int ychunk,
                                                 const float* __restrict__ y, int64_t N,
                                                 bool active, int lane, int L,
                                                 const float (&nu)[K], const float (&lw2)[K],
                                                 float r, uint32_t& phase, uint32_t* status) {
-    uint64_t* mbar = ychunk_mbar(ys);
-    for (int64_t c0 = 0; c0 < N; c0 += kYChunk) {
-        int cnt = (int)((N - c0) < kYChunk ? (N - c0) : kYChunk);
+    uint64_t* mbar = ychunk_mbar(ys, ychunk);
+    for (int64_t c0 = 0; c0 < N; c0 += ychunk) {
+        int cnt = (int)((N - c0) < ychunk ? (N - c0) : ychunk);
         stage_y(ys, y, c0, cnt, mbar, phase, status);
         if (active) acc.run(ys, cnt, lane, L, nu, lw2, r);
         __syncthreads();
@@ -373,14 +381,14 @@ __device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, flo
 
 // The same chunked streaming for the packed equal-weight accumulator.
 template <int K>
-__device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K>& acc, float* ys,
+__device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K>& acc, float* ys, int ychunk,
                                                    const float* __restrict__ y, int64_t N,
                                                    bool active, int lane, int L,
                                                    const float (&nu)[K], float r,
                                                    uint32_t& phase, uint32_t* status) {
-    uint64_t* mbar = ychunk_mbar(ys);
-    for (int64_t c0 = 0; c0 < N; c0 += kYChunk) {
-        int cnt = (int)((N - c0) < kYChunk ? (N - c0) : kYChunk);
+    uint64_t* mbar = ychunk_mbar(ys, ychunk);
+    for (int64_t c0 = 0; c0 < N; c0 += ychunk) {
+        int cnt = (int)((N - c0) < ychunk ? (N - c0) : ychunk);
         stage_y(ys, y, c0, cnt, mbar, phase, status);
         if (active) acc.run(ys, cnt, lane, L, nu, r);
         __syncthreads();

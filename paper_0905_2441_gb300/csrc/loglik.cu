@@ -19,10 +19,10 @@ __global__ void __launch_bounds__(256) k_loglik_gmm1d(const float* __restrict__ 
                                                       const float* __restrict__ theta, int64_t M,
                                                       double* __restrict__ loglik_out,
                                                       float* __restrict__ grad_out,
-                                                      Gmm1dArgs P, int L, int Kreal,
+                                                      Gmm1dArgs P, int L, int Kreal, int ychunk,
                                                       uint32_t* status) {
     extern __shared__ __align__(16) float ys[];
-    init_mbar(ychunk_mbar(ys));
+    init_mbar(ychunk_mbar(ys, ychunk));
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
     const int64_t p = (int64_t)blockIdx.x * ppb + threadIdx.x / L;
@@ -39,11 +39,11 @@ __global__ void __launch_bounds__(256) k_loglik_gmm1d(const float* __restrict__ 
     double ll;
     if constexpr (EQW && !GRAD) {
         SliceAccEqW<K> acc;
-        slice_over_data_eq(acc, ys, y, N, active, lane, L, nu, P.r, phase, status);
+        slice_over_data_eq(acc, ys, ychunk, y, N, active, lane, L, nu, P.r, phase, status);
         ll = acc.finish(L, P);
     } else {
         SliceAcc<K, GRAD, EQW> acc;
-        slice_over_data(acc, ys, y, N, active, lane, L, nu, lw2, P.r, phase, status);
+        slice_over_data(acc, ys, ychunk, y, N, active, lane, L, nu, lw2, P.r, phase, status);
         ll = acc.finish(L, P, g);
     }
     if (active && lane == 0) {
@@ -171,14 +171,9 @@ template <int K, bool GRAD, bool EQW>
 static void launch_1d(int blocks, int threads, cudaStream_t s, const float* y, int64_t N,
                       const float* theta, int64_t M, double* out, float* grad,
                       const smc::Gmm1dArgs& P, int L, int Kreal, uint32_t* st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(smc::k_loglik_gmm1d<K, GRAD, EQW>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc::kYSmemBytes);
-        attr = true;
-    }
-    smc::k_loglik_gmm1d<K, GRAD, EQW><<<blocks, threads, smc::kYSmemBytes, s>>>(
-        y, N, theta, M, out, grad, P, L, Kreal, st);
+    const int yc = smc::ychunk_for(N);
+    smc::k_loglik_gmm1d<K, GRAD, EQW><<<blocks, threads, smc::ysmem_bytes(yc), s>>>(
+        y, N, theta, M, out, grad, P, L, Kreal, yc, st);
 }
 
 template <int K>

@@ -42,11 +42,11 @@ __global__ void __launch_bounds__(256) k_mh_move(
     const float* grad_in, const int32_t* __restrict__ anc, const int32_t* __restrict__ do_flag,
     float* theta_out, double* ll_out, float* grad_out, int64_t M, const float* __restrict__ beta,
     int64_t beta_stride, float scale, uint64_t seed, uint64_t step, uint32_t* accept_count,
-    Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
+    Gmm1dArgs P, int L, int Kreal, int ychunk, uint32_t* status) {
     extern __shared__ __align__(16) float ys[];
     __shared__ uint32_t s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
-    init_mbar(ychunk_mbar(ys));
+    init_mbar(ychunk_mbar(ys, ychunk));
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
     const int64_t p = (int64_t)blockIdx.x * ppb + threadIdx.x / L;
@@ -92,11 +92,11 @@ __global__ void __launch_bounds__(256) k_mh_move(
     double lp;
     if constexpr (EQW && !MALA) {
         SliceAccEqW<K> acc;
-        slice_over_data_eq(acc, ys, y, N, in_box, lane, L, nu, P.r, phase, status);
+        slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status);
         lp = acc.finish(L, P);
     } else {
         SliceAcc<K, MALA, EQW> acc;
-        slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+        slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
         lp = acc.finish(L, P, gp);
     }
 
@@ -193,20 +193,23 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
     const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
     const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
     float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
-    Gmm1dArgs P, int L, int Kreal, uint32_t* status) {
+    Gmm1dArgs P, int L, int Kreal, int ychunk, uint32_t* status) {
+    // dynamic shared memory: staged data, mbarrier, then two lists of the
+    // populations an item completed (at most chains-per-item + 1 each)
     extern __shared__ __align__(16) float ys[];
-    __shared__ int s_ex[2][1025];             // populations completed by an item (<= chains + 1)
+    const int lcap = blockDim.x / L + 1;
+    int* s_exb = reinterpret_cast<int*>(ys + ychunk + 4);
     __shared__ int s_nex[2];
     __shared__ uint32_t s_mh, s_sw, s_try;
-    init_mbar(ychunk_mbar(ys));
+    init_mbar(ychunk_mbar(ys, ychunk));
     if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
     const int warp = threadIdx.x >> 5;
     const int64_t nitems = (Mtot + ppb - 1) / ppb;
     uint32_t phase = 0;
-    const bool resident = N <= kYChunk;  // all data in shared memory: stage once
-    if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys), phase, status);
+    const bool resident = N <= ychunk;  // all data in shared memory: stage once
+    if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys, ychunk), phase, status);
     float lw2[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) lw2[k] = P.lw2[k];
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
             if (resident) {
                 if (in_box) acc.run(ys, (int)N, lane, L, nu, P.r);
             } else {
-                slice_over_data_eq(acc, ys, y, N, in_box, lane, L, nu, P.r, phase, status);
+                slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status);
             }
             lp = acc.finish(L, P);
         } else {
@@ -254,7 +257,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
             if (resident) {
                 if (in_box) acc.run(ys, (int)N, lane, L, nu, lw2, P.r);
             } else {
-                slice_over_data(acc, ys, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+                slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
             }
             float gd[K];
             lp = acc.finish(L, P, gd);
@@ -315,7 +318,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
                         const uint32_t cnt = (uint32_t)(b2 - a);
                         const uint32_t Mq = (uint32_t)(qe - offsets[q]);
                         const uint32_t old = atomicAdd(pop_done + q, cnt);
-                        if (old + cnt == Mq) s_ex[buf][atomicAdd(&s_nex[buf], 1)] = q;
+                        if (old + cnt == Mq) s_exb[buf * lcap + atomicAdd(&s_nex[buf], 1)] = q;
                     }
                 }
             }
@@ -325,7 +328,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
         // ---- exchange moves of the populations this item completed (one warp each)
         const int nex = s_nex[buf];
         for (int e = warp; e < nex; e += (int)(blockDim.x >> 5)) {
-            const int q = s_ex[buf][e];
+            const int q = s_exb[buf * lcap + e];
             const int64_t base = offsets[q];
             const int Mq = (int)(offsets[q + 1] - base);
             if (Mq >= 2)
@@ -357,8 +360,10 @@ static smc_status launch_move(int blocks, int threads, cudaStream_t s, const flo
                               const float* beta, int64_t bs, float scale, uint64_t seed,
                               uint64_t step, uint32_t* acc, const smc::Gmm1dArgs& P, int L, int Kr,
                               uint32_t* st) {
-    smc::k_mh_move<K, MALA, EQW><<<blocks, threads, smc::kYSmemBytes, s>>>(
-        y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs, scale, seed, step, acc, P, L, Kr, st);
+    const int yc = smc::ychunk_for(N);
+    smc::k_mh_move<K, MALA, EQW><<<blocks, threads, smc::ysmem_bytes(yc), s>>>(
+        y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs, scale, seed, step, acc, P, L, Kr, yc,
+        st);
     return cuda_ok(cudaGetLastError());
 }
 
@@ -385,17 +390,21 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
                              uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P, int L,
                              int Kr) {
     auto kern = smc::k_popmcmc_sweep<K, EQW>;
+    const int yc = smc::ychunk_for(N);
+    const size_t smem = smc::ysmem_bytes(yc) + 2 * (size_t)(threads / L + 1) * sizeof(int);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smc::kYSmemBytes) !=
-            cudaSuccess || occ < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess ||
+        occ < 1)
         occ = 1;
     const int ppb = threads / L;
     int64_t items = (Mt + ppb - 1) / ppb;
     int64_t grid = (int64_t)ctx->num_sms * occ;
     if (grid > items) grid = items;
-    kern<<<(unsigned)grid, threads, smc::kYSmemBytes, s>>>(
+    kern<<<(unsigned)grid, threads, smem, s>>>(
         y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
-        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, P, L, Kr, ctx->d_status);
+        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, P, L, Kr, yc, ctx->d_status);
     return cuda_ok(cudaGetLastError());
 }
 
