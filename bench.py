@@ -116,7 +116,11 @@ def profile_traffic(kernel: str):
     if not e:
         return None
     from paper_0905_2441_gb300 import build as b
-    if e.get("source_digest") != b.source_digest():
+    try:
+        now = b.source_digest(e.get("sources"))
+    except FileNotFoundError:
+        return None
+    if e.get("source_digest") != now:
         return None  # the kernel changed since the counters were taken
     return e.get("bytes_per_launch")
 

@@ -81,7 +81,7 @@ const char* smc_status_string(smc_status s);
 /* Launch-shape override used by the autotuner.  `op` is one of SMC_OP_*;
  * `lanes` = threads cooperating on one particle's likelihood (1,2,4,8,16,32;
  * Section 4.1.3 splits one likelihood over threads when N is large),
- * `threads` = threads per block (64..1024, multiple of 32).  lanes = 0
+ * `threads` = threads per block (64..256, multiple of 32).  lanes = 0
  * restores the built-in heuristic. */
 enum { SMC_OP_LOGLIK = 0, SMC_OP_MOVE = 1, SMC_OP_POPMCMC = 2, SMC_OP_COUNT = 3 };
 smc_status smc_set_launch(smc_ctx* ctx, int32_t op, int32_t lanes, int32_t threads);

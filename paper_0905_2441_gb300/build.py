@@ -24,11 +24,23 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
          "-Xptxas", "-warn-spills", "-I", INCLUDE, "-I", CSRC]
 
 
-def source_digest() -> str:
-    """Digest of every CUDA source and header (identifies a kernel version)."""
+def source_digest(names=None) -> str:
+    """Digest of CUDA sources and headers (identifies a kernel version).
+
+    With `names` (file names under csrc/, e.g. the translation unit of one
+    kernel and the headers it includes) only those files and the public
+    headers are hashed, so a change elsewhere in the library keeps it.
+    """
     import hashlib
     h = hashlib.sha256()
-    files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
+    if names:
+        own = [os.path.join(CSRC, n) for n in names]
+        missing = [f for f in own if not os.path.exists(f)]
+        if missing:
+            raise FileNotFoundError(missing)
+    else:
+        own = glob.glob(os.path.join(CSRC, "*"))
+    files = sorted(own + glob.glob(os.path.join(INCLUDE, "*.h")))
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())

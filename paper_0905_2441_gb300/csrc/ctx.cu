@@ -60,6 +60,13 @@ void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* 
         return;
     }
     (void)K;
+    if (op == SMC_OP_POPMCMC) {
+        // the sweep's cost is per item of chains: two lanes per chain and
+        // 64 chains per 128-thread block balance items against the SMs
+        *lanes = N >= 128 ? 2 : 1;
+        *threads = 128;
+        return;
+    }
     // enough resident warps to cover the SMs (about 32 warps each), but
     // keep at least 8 observations per lane
     int64_t target = (int64_t)ctx->num_sms * 1024;
@@ -88,6 +95,8 @@ extern "C" smc_status smc_create(smc_ctx** out, int device) {
     if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) { delete c; return SMC_ERR_CUDA; }
     c->num_sms = prop.multiProcessorCount;
     c->max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
+    c->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
+    c->smem_reserved = (int)prop.reservedSharedMemPerBlock;
     bool ok = cudaMalloc(&c->d_status, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&c->d_counters, kCounters * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&c->d_partials, (size_t)kMaxPartialBlocks * 8 * sizeof(double)) ==
@@ -166,7 +175,8 @@ extern "C" smc_status smc_set_launch(smc_ctx* ctx, int32_t op, int32_t lanes, in
         ctx->threads[op] = 0;
         return SMC_OK;
     }
-    if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)) || threads < 64 || threads > 1024 ||
+    // every kernel these shapes launch is compiled for at most 256 threads
+    if (lanes < 1 || lanes > 32 || (lanes & (lanes - 1)) || threads < 64 || threads > 256 ||
         threads % 32 || threads % lanes)
         return SMC_ERR_ARG;
     ctx->lanes[op] = lanes;

@@ -195,32 +195,36 @@ struct SliceAcc {
 
 // Equal component weights, no gradient: the common case, written for the
 // issue rate of sm_103a.  Two data are evaluated at once in packed f32x2
-// registers (one FFMA2 / FADD2 / FMUL2 instruction per pair), and the max
-// shift is folded into the exponent argument:
-//   t_k = y r + nu_k,  tmin = min_k |t_k|,  c = -tmin^2  (= max_k a_k)
-//   2^(a_k - max) = 2^(-(t_k^2 + c)) = ex2(-fma(t_k, t_k, c))
-// which leaves per datum and component one packed FFMA (t), one min, half a
-// packed FFMA (the argument), one MUFU ex2 and half a packed FADD (the sum).
-// Groups of 16 pairs keep per-half products of s_n below 2^80 before lg2.
+// registers (one FFMA2 / FMUL2 / FADD2 instruction per pair):
+//   t_k = y r + nu_k,   s = sum_k 2^(-t_k^2)   (log2 units: a_k = c0 - t_k^2)
+// Unlike the max-shifted form, no shift is computed: s is taken as is
+// whenever s >= 2^-100, where every term ex2 flushes to zero (< 2^-126) is
+// below 2^-23 s, i.e. under the FP32 rounding of s itself.  Only data far
+// from every component (s < 2^-100) take the shifted path, with
+// c = -min_k t_k^2 added to the total exactly as in the scalar path.  Per
+// datum and component this leaves half a packed FFMA (t), half a packed
+// FMUL (t^2), one MUFU ex2 and half a packed FADD (the sum).  The product
+// of the s_n is kept as mantissa in [1, 2) times an integer power of two
+// (exponent bits split off after every pair), so one lg2 per slice lane
+// closes the whole sum instead of one per datum.
 __device__ __forceinline__ float ex2_neg(float p) {
     float y;
     asm("{\n\t.reg .f32 t;\n\tneg.f32 t, %1;\n\tex2.approx.ftz.f32 %0, t;\n\t}" : "=f"(y) : "f"(p));
     return y;
 }
 
+// Pairs of data in flight per loop trip of the packed path (compile-time
+// tuning knob: more pairs give more independent work per warp, and more
+// registers per thread).
+#ifndef SMC_EQW_UNROLL
+#define SMC_EQW_UNROLL 4
+#endif
+constexpr int kEqwUnroll = SMC_EQW_UNROLL;
+
 template <int K>
 struct SliceAccEqW {
-    Kahan ll;
-    float2 ms = make_float2(0.0f, 0.0f);  // sum of c over the current group (two halves)
-    float2 pr = make_float2(1.0f, 1.0f);  // product of s over the current group
-    int cnt = 0;
-
-    __device__ __forceinline__ void flush() {
-        ll.add((ms.x + ms.y) + (lg2(pr.x) + lg2(pr.y)));
-        ms = make_float2(0.0f, 0.0f);
-        pr = make_float2(1.0f, 1.0f);
-        cnt = 0;
-    }
+    Kahan ll;                              // log2 terms: exponents, shifts, scalar data
+    float2 pr = make_float2(1.0f, 1.0f);   // mantissa product of s over pairs, in [1, 2)
 
     // one datum on the scalar path (odd tail of a chunk)
     __device__ __forceinline__ void one(float yv, const float (&nu)[K], float r) {
@@ -238,6 +242,29 @@ struct SliceAccEqW {
         ll.add(c + lg2(s));
     }
 
+    // shifted sums of one pair whose unshifted sum fell below 2^-100
+    // (recomputes t_k, so nothing stays live across the rare branch)
+    __device__ __forceinline__ float2 rescue(float2 Y, float2 R2, const float2 (&NU)[K]) {
+        float2 T[K];
+        float a0 = INFINITY, a1 = INFINITY;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            T[k] = __ffma2_rn(Y, R2, NU[k]);
+            a0 = fminf(a0, fabsf(T[k].x));
+            a1 = fminf(a1, fabsf(T[k].y));
+        }
+        const float c0 = -a0 * a0, c1 = -a1 * a1;
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            s0 += ex2_neg(fmaf(T[k].x, T[k].x, c0));
+            s1 += ex2_neg(fmaf(T[k].y, T[k].y, c1));
+        }
+        ll.add(c0);
+        ll.add(c1);
+        return make_float2(s0, s1);
+    }
+
     // data ys[0, cnt_total): pairs p = lane, lane + L, ...; the odd last
     // datum (if any) goes to lane 0
     __device__ __forceinline__ void run(const float* ys, int cnt_total, int lane, int L,
@@ -248,45 +275,39 @@ struct SliceAccEqW {
         float2 NU[K];
 #pragma unroll
         for (int k = 0; k < K; ++k) NU[k] = make_float2(nu[k], nu[k]);
-#pragma unroll 4
+        int ex = 0;  // biased exponents split off pr in this chunk (< 2^21 in all)
+#pragma unroll kEqwUnroll
         for (int p = lane; p < np; p += L) {
             const float2 Y = ys2[p];
-            float2 T[K];
-            float a0[K], a1[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                T[k] = __ffma2_rn(Y, R2, NU[k]);
-                a0[k] = fabsf(T[k].x);
-                a1[k] = fabsf(T[k].y);
-            }
-            // balanced trees keep the dependency chains short (log2 K)
-#pragma unroll
-            for (int w = 1; w < K; w <<= 1)
-#pragma unroll
-                for (int k = 0; k + w < K; k += 2 * w) {
-                    a0[k] = fminf(a0[k], a0[k + w]);
-                    a1[k] = fminf(a1[k], a1[k + w]);
-                }
-            const float2 C = make_float2(-a0[0] * a0[0], -a1[0] * a1[0]);
             float2 E[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float2 Pk = __ffma2_rn(T[k], T[k], C);
-                E[k] = make_float2(ex2_neg(Pk.x), ex2_neg(Pk.y));
+                const float2 T = __ffma2_rn(Y, R2, NU[k]);
+                const float2 Q = __fmul2_rn(T, T);
+                E[k] = make_float2(ex2_neg(Q.x), ex2_neg(Q.y));
             }
+            // balanced tree keeps the dependency chain short (log2 K)
 #pragma unroll
             for (int w = 1; w < K; w <<= 1)
 #pragma unroll
                 for (int k = 0; k + w < K; k += 2 * w) E[k] = __fadd2_rn(E[k], E[k + w]);
-            ms = __fadd2_rn(ms, C);
-            pr = __fmul2_rn(pr, E[0]);
-            if (++cnt == 16) flush();
+            float2 S = E[0];
+            if (fminf(S.x, S.y) < 0x1p-100f) S = rescue(Y, R2, NU);
+            pr = __fmul2_rn(pr, S);  // in [2^-100, 2^4): normal
+            const uint32_t bx = __float_as_uint(pr.x), by = __float_as_uint(pr.y);
+            ex += (int)(bx >> 23) + (int)(by >> 23);
+            pr = make_float2(__uint_as_float((bx & 0x7FFFFFu) | 0x3F800000u),
+                             __uint_as_float((by & 0x7FFFFFu) | 0x3F800000u));
         }
+        // remove the bias 2 x 127 of each pair; the result, at most
+        // 4096 x 200 in size, is exact in FP32
+        const int npairs = lane < np ? (np - 1 - lane) / L + 1 : 0;
+        ll.add((float)(ex - 254 * npairs));
         if ((cnt_total & 1) && lane == 0) one(ys[cnt_total - 1], nu, r);
     }
 
     __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P) {
-        if (cnt) flush();
+        ll.add(lg2(pr.x) + lg2(pr.y));
         const double part = slice_total(ll.s, ll.c, L);
         return part * kLn2 + P.cst;
     }

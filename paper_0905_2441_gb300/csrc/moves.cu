@@ -152,53 +152,89 @@ __device__ __forceinline__ int pop_of(const int32_t* __restrict__ offsets, int n
 }
 
 
+// Pairs of one exchange move (Section 3.3: adjacent temperatures, disjoint
+// pairs chosen by a parity bit): parity 0 pairs (2j, 2j+1); parity 1 pairs
+// (2j+1, 2j+2) and, for an even population, the wrap-around pair (Mq-1, 0).
+__device__ __forceinline__ int exchange_npairs(int Mq, uint32_t par) {
+    return par == 0 ? Mq / 2 : (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
+}
+
+// Exchange move of pair j of population q (chains base..base+Mq-1): the
+// chains' states and log-likelihoods are loaded together (one round trip),
+// then swapped if accepted with log alpha = (beta_a - beta_b)(l_b - l_a).
 template <int K>
-__device__ __forceinline__ void exchange_population(
-    float* theta, double* ll, int64_t Mtot, const float* __restrict__ beta, int64_t base, int Mq,
-    int q, int lane, int L, int Kreal, uint64_t seed, uint64_t sweep, uint32_t* s_sw,
-    uint32_t* s_try) {
-    const uint32_t par = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
-    const int npairs = par == 0 ? Mq / 2 : (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
-    uint32_t swaps = 0;
-    for (int j = lane; j < npairs; j += L) {
-        int ia, ib;
-        if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
-        else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
-        else { ia = Mq - 1; ib = 0; }
-        const int64_t ga = base + ia, gb = base + ib;
-        const double la = __ldcg(ll + ga), lb = __ldcg(ll + gb);
-        const float log_alpha = tempered_diff(beta[ga] - beta[gb], lb, la);
-        const uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
-        if (accept(word_of(w, j & 3), log_alpha)) {
+__device__ __forceinline__ bool exchange_pair(float* theta, double* ll, int64_t Mtot,
+                                              const float* __restrict__ beta, int64_t base,
+                                              int Mq, uint32_t par, int q, int j, int Kreal,
+                                              uint64_t seed, uint64_t sweep) {
+    int ia, ib;
+    if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
+    else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
+    else { ia = Mq - 1; ib = 0; }
+    const int64_t ga = base + ia, gb = base + ib;
+    const double la = __ldcg(ll + ga), lb = __ldcg(ll + gb);
+    float ta[K], tb[K];
 #pragma unroll
-            for (int k = 0; k < K; ++k) {
-                if (k < Kreal) {
-                    const float ta = __ldcg(theta + (int64_t)k * Mtot + ga);
-                    const float tb = __ldcg(theta + (int64_t)k * Mtot + gb);
-                    __stcg(theta + (int64_t)k * Mtot + ga, tb);
-                    __stcg(theta + (int64_t)k * Mtot + gb, ta);
-                }
-            }
-            __stcg(ll + ga, lb);
-            __stcg(ll + gb, la);
-            ++swaps;
+    for (int k = 0; k < K; ++k) {
+        ta[k] = k < Kreal ? __ldcg(theta + (int64_t)k * Mtot + ga) : 0.0f;
+        tb[k] = k < Kreal ? __ldcg(theta + (int64_t)k * Mtot + gb) : 0.0f;
+    }
+    const uint4 w = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 1u + (uint32_t)(j >> 2));
+    const float log_alpha = tempered_diff(beta[ga] - beta[gb], lb, la);
+    if (!accept(word_of(w, j & 3), log_alpha)) return false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (k < Kreal) {
+            __stcg(theta + (int64_t)k * Mtot + ga, tb[k]);
+            __stcg(theta + (int64_t)k * Mtot + gb, ta[k]);
         }
     }
-    if (swaps) atomicAdd(s_sw, swaps);
-    if (lane == 0) atomicAdd(s_try, (uint32_t)npairs);
+    __stcg(ll + ga, lb);
+    __stcg(ll + gb, la);
+    return true;
+}
+
+// Minimum resident 256-thread blocks per SM asked of the register
+// allocator for the sweep (compile-time tuning knob; 1 leaves it free).
+#ifndef SMC_POP_MINB
+#define SMC_POP_MINB 3
+#endif
+
+// add with acquire-release ordering at GPU scope: publishes the writes the
+// calling CTA made before its last barrier, and sees those of every CTA that
+// added before it
+__device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t* p, uint32_t v) {
+    uint32_t old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;"
+                 : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// Programmatic dependent launch: the next sweep in the stream may start its
+// prologue (data staging, random draws, population search: nothing this
+// sweep writes) while this one drains; grid_dep_wait() then holds every
+// thread until the previous grid has finished and its writes are visible.
+// Both are no-ops for a launch without the programmatic attribute.
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 template <int K, bool EQW>
-__global__ void __launch_bounds__(256) k_popmcmc_sweep(
+__global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
     const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
     const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
     float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
     Gmm1dArgs P, int L, int Kreal, int ychunk, uint32_t* status) {
+    grid_dep_launch();
     // dynamic shared memory: staged data, mbarrier, then two lists of the
-    // populations an item completed (at most chains-per-item + 1 each)
+    // populations an item completed (at most chains-per-item + 1 each), an
+    // entry being {population, first chain, chains, parity}
     extern __shared__ __align__(16) float ys[];
     const int lcap = blockDim.x / L + 1;
-    int* s_exb = reinterpret_cast<int*>(ys + ychunk + 4);
+    int4* s_exb = reinterpret_cast<int4*>(ys + ychunk + 4);
     __shared__ int s_nex[2];
     __shared__ uint32_t s_mh, s_sw, s_try;
     init_mbar(ychunk_mbar(ys, ychunk));
@@ -206,6 +242,7 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
     const int warp = threadIdx.x >> 5;
+    const int l32 = threadIdx.x & 31;
     const int64_t nitems = (Mtot + ppb - 1) / ppb;
     uint32_t phase = 0;
     const bool resident = N <= ychunk;  // all data in shared memory: stage once
@@ -221,12 +258,48 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
         const int64_t c1 = c0 + ppb < Mtot ? c0 + ppb : Mtot;
         const int64_t c = c0 + threadIdx.x / L;
         const bool active = c < Mtot;
-        // ---- random-walk MH move of chain c
-        float mu[K], z[K], prop[K], nu[K];
-        double l = 0.0;
-        float b = 0.0f;
+        // ---- work that reads nothing a sweep writes: the move's draws and,
+        // in warp 0, the first population overlapping the item (a 32-way
+        // parallel search) with the bounds of the next 32 populations
+        float z[K];
         uint32_t aw;
         slice_draws<K>(seed, sweep, (uint32_t)(active ? c : 0), lane, L, Kreal, z, aw);
+        const float b = active ? beta[c] : 0.0f;
+        int qlo = 0;
+        int64_t qa = 0, qb = 0;  // bounds of population qlo + l32 (warp 0)
+        if (warp == 0) {
+            int qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
+            while (qhi - qlo > 1) {
+                // 32 probes split [qlo, qhi) into 33 parts
+                const int span = qhi - qlo;
+                const int probe = qlo + (int)(((int64_t)span * (l32 + 1)) / 33);
+                const bool inside = probe > qlo && probe < qhi;
+                const int64_t op = inside ? (int64_t)offsets[probe] : 0;
+                const unsigned m = __ballot_sync(0xFFFFFFFFu, inside && op <= c0);
+                const unsigned gt = __ballot_sync(0xFFFFFFFFu, inside && op > c0);
+                int nlo = qlo, nhi = qhi;
+                if (m) nlo = __shfl_sync(0xFFFFFFFFu, probe, 31 - __clz(m));
+                if (gt) nhi = __shfl_sync(0xFFFFFFFFu, probe, __ffs(gt) - 1);
+                if (nlo == qlo && nhi == qhi) {  // fewer than 33 candidates left: scan
+                    const int cand = qlo + 1 + l32;
+                    const bool le2 = cand < qhi && (int64_t)offsets[cand] <= c0;
+                    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, le2);
+                    if (m2) nlo = qlo + 1 + (31 - __clz(m2));
+                    nhi = nlo + 1;
+                }
+                qlo = nlo;
+                qhi = nhi;
+            }
+            const int q = qlo + l32;
+            if (q < n_pops) {
+                qa = offsets[q];
+                qb = offsets[q + 1];
+            }
+        }
+        // ---- the state of the chains: written by the previous sweep
+        if (iter == 0) grid_dep_wait();
+        float mu[K], prop[K], nu[K];
+        double l = 0.0;
 #pragma unroll
         for (int k = 0; k < K; ++k) mu[k] = 0.0f;
         if (active) {
@@ -234,8 +307,8 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
             for (int k = 0; k < K; ++k)
                 if (k < Kreal) mu[k] = theta[(int64_t)k * Mtot + c];
             l = ll[c];
-            b = beta[c];
         }
+        // ---- random-walk MH move of chain c
         bool in_box = active;
 #pragma unroll
         for (int k = 0; k < K; ++k) {
@@ -272,72 +345,71 @@ __global__ void __launch_bounds__(256) k_popmcmc_sweep(
             for (int k = 0; k < K; ++k)
                 if (k < Kreal) theta[(int64_t)k * Mtot + c] = prop[k];
             ll[c] = lp;
-            __threadfence();  // the item's moves are visible before it is counted
         }
         const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, ok);
-        if ((threadIdx.x & 31) == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
+        if (l32 == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
         const int buf = (int)(iter & 1);  // double-buffered list: no third barrier
         if (threadIdx.x == 0) s_nex[buf] = 0;
-        __syncthreads();
-        // ---- count the item's chains per population: warp 0 finds the first
-        // population by a parallel search, then one lane per touched
-        // population adds its count (one integer atomic each)
+        __syncthreads();  // the item's moves are done (and ordered before warp 0's release)
+        // ---- count the item's chains per population: one lane per touched
+        // population adds its count with release semantics (publishing the
+        // moves above); the lane whose add completes a population acquires
+        // every other CTA's moves of it and lists it for exchange
         if (warp == 0) {
-            const int l32 = threadIdx.x & 31;
-            int qlo = 0, qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
-            while (qhi - qlo > 1) {
-                // 32 probes split [qlo, qhi) into 33 parts
-                const int span = qhi - qlo;
-                const int probe = qlo + (int)(((int64_t)span * (l32 + 1)) / 33);
-                const bool le = probe > qlo && probe < qhi && (int64_t)offsets[probe] <= c0;
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, le);
-                int nlo = qlo, nhi = qhi;
-                if (m) nlo = __shfl_sync(0xFFFFFFFFu, probe, 31 - __clz(m));
-                const unsigned gt = __ballot_sync(0xFFFFFFFFu, probe > qlo && probe < qhi &&
-                                                                   (int64_t)offsets[probe] > c0);
-                if (gt) nhi = __shfl_sync(0xFFFFFFFFu, probe, __ffs(gt) - 1);
-                if (nlo == qlo && nhi == qhi) {  // fewer than 33 candidates left: scan
-                    const int cand = qlo + 1 + l32;
-                    const bool le2 = cand < qhi && (int64_t)offsets[cand] <= c0;
-                    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, le2);
-                    if (m2) nlo = qlo + 1 + (31 - __clz(m2));
-                    nhi = nlo + 1;
-                }
-                qlo = nlo;
-                qhi = nhi;
-            }
-            // populations qlo, qlo+1, ... overlapping [c0, c1)
             for (int q = qlo + l32;; q += 32) {
-                const bool in = q < n_pops && (int64_t)offsets[q] < c1;
+                if (q >= qlo + 32 && q < n_pops) {  // beyond the prefetched 32 (rare)
+                    qa = offsets[q];
+                    qb = offsets[q + 1];
+                }
+                const bool in = q < n_pops && qa < c1;
                 if (!__any_sync(0xFFFFFFFFu, in)) break;
                 if (in) {
-                    const int64_t a = (int64_t)offsets[q] > c0 ? (int64_t)offsets[q] : c0;
-                    const int64_t qe = offsets[q + 1];
-                    const int64_t b2 = qe < c1 ? qe : c1;
+                    const int64_t a = qa > c0 ? qa : c0;
+                    const int64_t b2 = qb < c1 ? qb : c1;
                     if (b2 > a) {
                         const uint32_t cnt = (uint32_t)(b2 - a);
-                        const uint32_t Mq = (uint32_t)(qe - offsets[q]);
-                        const uint32_t old = atomicAdd(pop_done + q, cnt);
-                        if (old + cnt == Mq) s_exb[buf * lcap + atomicAdd(&s_nex[buf], 1)] = q;
+                        const uint32_t Mq = (uint32_t)(qb - qa);
+                        const uint32_t old = atomic_add_acq_rel(pop_done + q, cnt);
+                        if (old + cnt == Mq) {
+                            const uint32_t par =
+                                draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
+                            s_exb[buf * lcap + atomicAdd(&s_nex[buf], 1)] =
+                                make_int4(q, (int)qa, (int)Mq, (int)par);
+                        }
                     }
                 }
             }
-            __threadfence();
         }
         __syncthreads();
-        // ---- exchange moves of the populations this item completed (one warp each)
+        // ---- exchange moves of the populations this item completed: their
+        // pairs are dealt over all threads of the block
         const int nex = s_nex[buf];
-        for (int e = warp; e < nex; e += (int)(blockDim.x >> 5)) {
-            const int q = s_exb[buf * lcap + e];
-            const int64_t base = offsets[q];
-            const int Mq = (int)(offsets[q + 1] - base);
-            if (Mq >= 2)
-                exchange_population<K>(theta, ll, Mtot, beta, base, Mq, q, threadIdx.x & 31, 32,
-                                       Kreal, seed, sweep, &s_sw, &s_try);
-            if ((threadIdx.x & 31) == 0) pop_done[q] = 0u;
+        if (nex) {
+            const int4* ex = s_exb + buf * lcap;
+            int total = 0;
+            for (int e = 0; e < nex; ++e) total += exchange_npairs(ex[e].z, (uint32_t)ex[e].w);
+            uint32_t swaps = 0;
+            for (int t = threadIdx.x; t < total; t += blockDim.x) {
+                int e = 0, j = t;
+                for (;;) {  // entry holding task t (nex is small)
+                    const int np = exchange_npairs(ex[e].z, (uint32_t)ex[e].w);
+                    if (j < np) break;
+                    j -= np;
+                    ++e;
+                }
+                const int4 d = ex[e];
+                swaps += exchange_pair<K>(theta, ll, Mtot, beta, d.y, d.z, (uint32_t)d.w, d.x, j,
+                                          Kreal, seed, sweep);
+            }
+            if (swaps) atomicAdd(&s_sw, swaps);
+            for (int e = threadIdx.x; e < nex; e += blockDim.x) {
+                pop_done[ex[e].x] = 0u;
+                atomicAdd(&s_try, (uint32_t)exchange_npairs(ex[e].z, (uint32_t)ex[e].w));
+            }
         }
         ++iter;
     }
+    if (iter == 0) grid_dep_wait();  // a block without items still orders its stats
     __syncthreads();
     if (threadIdx.x == 0 && stats) {
         if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
@@ -383,6 +455,11 @@ static smc_status dispatch_move(bool mala, bool eqw, int blocks, int threads, cu
 #undef SMC_MV
 }
 
+// Programmatic dependent launch of consecutive sweeps (compile-time knob).
+#ifndef SMC_POP_PDL
+#define SMC_POP_PDL 1
+#endif
+
 template <int K, bool EQW>
 static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const float* y,
                              int64_t N, float* th, double* l, int64_t Mt, const float* beta,
@@ -391,21 +468,52 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
                              int Kr) {
     auto kern = smc::k_popmcmc_sweep<K, EQW>;
     const int yc = smc::ychunk_for(N);
-    const size_t smem = smc::ysmem_bytes(yc) + 2 * (size_t)(threads / L + 1) * sizeof(int);
-    if (smem > 48 * 1024)
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    size_t smem = smc::ysmem_bytes(yc) + 2 * (size_t)(threads / L + 1) * sizeof(int4);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess ||
         occ < 1)
         occ = 1;
     const int ppb = threads / L;
-    int64_t items = (Mt + ppb - 1) / ppb;
+    const int64_t items = (Mt + ppb - 1) / ppb;
+    // Items fewer than the resident slots: hold every SM to k = ceil(items /
+    // SMs) blocks (by asking for more shared memory), so that no SM runs more
+    // than k items whatever order the blocks are placed in.
+    const int64_t k = (items + ctx->num_sms - 1) / ctx->num_sms;
+    if (k < occ && ctx->smem_per_sm > 0) {
+        const size_t pad = (size_t)(ctx->smem_per_sm / (k + 1) - ctx->smem_reserved + 1024) &
+                           ~(size_t)1023;
+        if (pad > smem) {
+            int occ2 = 0;
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)pad) == cudaSuccess &&
+                cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, kern, threads, pad) ==
+                    cudaSuccess &&
+                occ2 == k) {
+                smem = pad;
+                occ = occ2;
+            }
+        }
+    }
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int64_t grid = (int64_t)ctx->num_sms * occ;
     if (grid > items) grid = items;
-    kern<<<(unsigned)grid, threads, smem, s>>>(
-        y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
-        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, P, L, Kr, yc, ctx->d_status);
-    return cuda_ok(cudaGetLastError());
+    // programmatic serialisation: a sweep following a sweep on this stream
+    // runs its prologue while the previous one drains (the kernel waits for
+    // it before touching chain state)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = SMC_POP_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_ok(cudaLaunchKernelEx(&cfg, kern, y, N, th, l, Mt, beta, off, n_pops, scale, seed,
+                                      sweep, reinterpret_cast<unsigned long long*>(stats),
+                                      ctx->d_popdone, P, L, Kr, yc, ctx->d_status));
 }
 
 }  // namespace smc_host
