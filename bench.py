@@ -272,7 +272,10 @@ def bench_popmcmc(args, torch, dist):
             "ops_per_launch": mufu_per_launch,
             "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
                            f"{ex2_ms:.2f} ms microbenchmark",
-            "frac_issued_count": (float(M) * N * (w.K + 1.0 / 16)) / (t_dev / args.steps) / ex2_rate}
+            # the kernel closes each lane's product of sums with one lg2
+            # per sweep, so the ops it issues are the K ex2 alone
+            "issued_count": "K ex2 per particle-datum (lg2 once per lane per sweep)",
+            "frac_issued_count": (float(M) * N * w.K) / (t_dev / args.steps) / ex2_rate}
     out = {
         "metric": "particle-datum loglik evals/s (population MCMC sweeps)",
         "value": value, "unit": "p*d/s", "n_gpus": dist.world, "steps": args.steps,

@@ -17,10 +17,15 @@ CACHE = os.environ.get("SMC_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "smc_gb300_autotune.json"))
 LANES = (1, 2, 4, 8, 16, 32)
 THREADS = (128, 256)
+# the population sweep: few lanes per chain win (its chains are many), and
+# odd block sizes change how items fall on the SMs
+POP_LANES = (1, 2, 4, 8)
+POP_THREADS = (128, 192, 256)
 
 
 def _key(op, K, N, M):
-    return f"{torch.cuda.get_device_name()}|op{op}|K{K}|N{N}|M{M}"
+    from . import build
+    return f"{torch.cuda.get_device_name()}|{build.source_digest()}|op{op}|K{K}|N{N}|M{M}"
 
 
 def _load():
@@ -42,23 +47,26 @@ def _save(d):
         pass
 
 
-def time_call(fn, reps=5):
-    """Median device time (ms) of fn() over reps, CUDA events on the current stream."""
+def time_call(fn, reps=5, inner=1):
+    """Median device time (ms) per call of fn(): CUDA events on the current
+    stream around `inner` back-to-back calls, median over `reps`."""
     fn()
     torch.cuda.synchronize()
     ts = []
     for _ in range(reps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        fn()
+        for _ in range(inner):
+            fn()
         b.record()
         b.synchronize()
-        ts.append(a.elapsed_time(b))
+        ts.append(a.elapsed_time(b) / inner)
     ts.sort()
     return ts[len(ts) // 2]
 
 
-def tune(ctx: api.Context, op: int, K: int, N: int, M: int, fn, use_cache=True, reps=5):
+def tune(ctx: api.Context, op: int, K: int, N: int, M: int, fn, use_cache=True, reps=5,
+         inner=1, lanes_list=LANES, threads_list=THREADS):
     """Pick (lanes, threads) for `op` by timing `fn` (which issues the op with
     the context's current override) over all candidates; apply and cache."""
     key = _key(op, K, N, M)
@@ -68,12 +76,14 @@ def tune(ctx: api.Context, op: int, K: int, N: int, M: int, fn, use_cache=True, 
         ctx.set_launch(op, lanes, threads)
         return lanes, threads, cache[key]
     results = []
-    for lanes in LANES:
+    for lanes in lanes_list:
         if lanes > 1 and N // lanes < 2:
             continue
-        for threads in THREADS:
+        for threads in threads_list:
+            if threads % lanes:
+                continue
             ctx.set_launch(op, lanes, threads)
-            ms = time_call(fn, reps)
+            ms = time_call(fn, reps, inner)
             results.append((ms, lanes, threads))
     results.sort()
     ms, lanes, threads = results[0]
@@ -101,4 +111,7 @@ def tune_popmcmc(ctx, sampler, **kw):
     def fn():
         sampler.sweep(s[0])
         s[0] += 1
-    return tune(ctx, L.OP_POPMCMC, sampler.model.K, sampler.y.numel(), sampler.M, fn, **kw)
+    kw.setdefault("reps", 3)
+    kw.setdefault("inner", 10)
+    return tune(ctx, L.OP_POPMCMC, sampler.model.K, sampler.y.numel(), sampler.M, fn,
+                lanes_list=POP_LANES, threads_list=POP_THREADS, **kw)

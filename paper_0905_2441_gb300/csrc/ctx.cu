@@ -61,10 +61,10 @@ void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* 
     }
     (void)K;
     if (op == SMC_OP_POPMCMC) {
-        // the sweep's cost is per item of chains: two lanes per chain and
-        // 64 chains per 128-thread block balance items against the SMs
+        // two lanes per chain and 128 chains per 256-thread block: few
+        // items, each long enough to hide the block's fixed latencies
         *lanes = N >= 128 ? 2 : 1;
-        *threads = 128;
+        *threads = 256;
         return;
     }
     // enough resident warps to cover the SMs (about 32 warps each), but

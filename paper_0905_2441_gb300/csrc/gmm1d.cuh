@@ -46,11 +46,12 @@ struct Gmm1dArgs {
 };
 
 // Stage y[n0, n0+cnt) into shared memory.  A bulk asynchronous copy moves
-// the 16-byte aligned body (completion on an mbarrier, bounded wait); the
-// unaligned head and tail use plain loads.  Ends with __syncthreads().
-__device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, int64_t n0,
-                                        int cnt, uint64_t* mbar, uint32_t& phase,
-                                        uint32_t* status) {
+// the 16-byte aligned body (completion on an mbarrier); the unaligned head
+// and tail use plain loads.  stage_y_issue starts the copy (every thread of
+// the block calls it; returns whether the bulk copy was used), other work
+// may follow, and stage_y_wait completes it.  stage_y does both.
+__device__ __forceinline__ bool stage_y_issue(float* ys, const float* __restrict__ y, int64_t n0,
+                                              int cnt, uint64_t* mbar) {
     const float* src = y + n0;
     uintptr_t a = reinterpret_cast<uintptr_t>(src);
     int head = (int)(((16u - (uint32_t)(a & 15u)) & 15u) / 4u);
@@ -61,8 +62,7 @@ __device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, 
     bool bulk = body >= 64 && ((reinterpret_cast<uintptr_t>(ys + head) & 15u) == 0);
     if (!bulk) {
         for (int i = threadIdx.x; i < cnt; i += blockDim.x) ys[i] = src[i];
-        __syncthreads();
-        return;
+        return false;
     }
     uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
     if (threadIdx.x == 0) {
@@ -78,7 +78,18 @@ __device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, 
     }
     for (int i = threadIdx.x; i < head; i += blockDim.x) ys[i] = src[i];
     for (int i = head + body + threadIdx.x; i < cnt; i += blockDim.x) ys[i] = src[i];
-    // bounded wait for the copy
+    return true;
+}
+
+// Completes stage_y_issue: every thread of the block calls it.  The wait on
+// the bulk copy is bounded; on timeout the status word gets ST_TIMEOUT.
+__device__ __forceinline__ void stage_y_wait(bool bulk, uint64_t* mbar, uint32_t& phase,
+                                             uint32_t* status) {
+    if (!bulk) {
+        __syncthreads();
+        return;
+    }
+    uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
     uint32_t done = 0;
     for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
         asm volatile(
@@ -102,6 +113,12 @@ __device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, 
     }
     phase ^= 1u;
     __syncthreads();
+}
+
+__device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, int64_t n0,
+                                        int cnt, uint64_t* mbar, uint32_t& phase,
+                                        uint32_t* status) {
+    stage_y_wait(stage_y_issue(ys, y, n0, cnt, mbar), mbar, phase, status);
 }
 
 __device__ __forceinline__ void init_mbar(uint64_t* mbar) {
@@ -213,18 +230,19 @@ __device__ __forceinline__ float ex2_neg(float p) {
     return y;
 }
 
-// Pairs of data in flight per loop trip of the packed path (compile-time
-// tuning knob: more pairs give more independent work per warp, and more
-// registers per thread).
+// Pairs of data evaluated per block of the packed path (compile-time tuning
+// knob: more pairs give more independent work per warp, and more registers
+// per thread).
 #ifndef SMC_EQW_UNROLL
-#define SMC_EQW_UNROLL 4
+#define SMC_EQW_UNROLL 2
 #endif
 constexpr int kEqwUnroll = SMC_EQW_UNROLL;
 
 template <int K>
 struct SliceAccEqW {
     Kahan ll;                              // log2 terms: exponents, shifts, scalar data
-    float2 pr = make_float2(1.0f, 1.0f);   // mantissa product of s over pairs, in [1, 2)
+    float2 pr[2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};  // mantissa products of s (even / odd
+                                                 // pairs of a block), in [1, 2)
 
     // one datum on the scalar path (odd tail of a chunk)
     __device__ __forceinline__ void one(float yv, const float (&nu)[K], float r) {
@@ -265,6 +283,50 @@ struct SliceAccEqW {
         return make_float2(s0, s1);
     }
 
+    // U pairs p, p + L, ..., p + (U-1) L: their sums are computed
+    // independently (straight-line code the scheduler can interleave), with
+    // one test for the rare rescue, then folded into the products
+    template <int U>
+    __device__ __forceinline__ void pairs(const float2* ys2, int p, int L, float2 R2,
+                                          const float2 (&NU)[K], int& ex) {
+        float2 Y[U], S[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) Y[u] = ys2[p + u * L];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float2 E[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float2 T = __ffma2_rn(Y[u], R2, NU[k]);
+                const float2 Q = __fmul2_rn(T, T);
+                E[k] = make_float2(ex2_neg(Q.x), ex2_neg(Q.y));
+            }
+            // balanced tree keeps the dependency chain short (log2 K)
+#pragma unroll
+            for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+                for (int k = 0; k + w < K; k += 2 * w) E[k] = __fadd2_rn(E[k], E[k + w]);
+            S[u] = E[0];
+        }
+        float mn = fminf(S[0].x, S[0].y);
+#pragma unroll
+        for (int u = 1; u < U; ++u) mn = fminf(mn, fminf(S[u].x, S[u].y));
+        if (mn < 0x1p-100f) {
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (fminf(S[u].x, S[u].y) < 0x1p-100f) S[u] = rescue(Y[u], R2, NU);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            float2& acc = pr[u & 1];
+            acc = __fmul2_rn(acc, S[u]);  // in [2^-100, 2^4): normal
+            const uint32_t bx = __float_as_uint(acc.x), by = __float_as_uint(acc.y);
+            ex += (int)(bx >> 23) + (int)(by >> 23);
+            acc = make_float2(__uint_as_float((bx & 0x7FFFFFu) | 0x3F800000u),
+                              __uint_as_float((by & 0x7FFFFFu) | 0x3F800000u));
+        }
+    }
+
     // data ys[0, cnt_total): pairs p = lane, lane + L, ...; the odd last
     // datum (if any) goes to lane 0
     __device__ __forceinline__ void run(const float* ys, int cnt_total, int lane, int L,
@@ -276,29 +338,12 @@ struct SliceAccEqW {
 #pragma unroll
         for (int k = 0; k < K; ++k) NU[k] = make_float2(nu[k], nu[k]);
         int ex = 0;  // biased exponents split off pr in this chunk (< 2^21 in all)
-#pragma unroll kEqwUnroll
-        for (int p = lane; p < np; p += L) {
-            const float2 Y = ys2[p];
-            float2 E[K];
-#pragma unroll
-            for (int k = 0; k < K; ++k) {
-                const float2 T = __ffma2_rn(Y, R2, NU[k]);
-                const float2 Q = __fmul2_rn(T, T);
-                E[k] = make_float2(ex2_neg(Q.x), ex2_neg(Q.y));
-            }
-            // balanced tree keeps the dependency chain short (log2 K)
-#pragma unroll
-            for (int w = 1; w < K; w <<= 1)
-#pragma unroll
-                for (int k = 0; k + w < K; k += 2 * w) E[k] = __fadd2_rn(E[k], E[k + w]);
-            float2 S = E[0];
-            if (fminf(S.x, S.y) < 0x1p-100f) S = rescue(Y, R2, NU);
-            pr = __fmul2_rn(pr, S);  // in [2^-100, 2^4): normal
-            const uint32_t bx = __float_as_uint(pr.x), by = __float_as_uint(pr.y);
-            ex += (int)(bx >> 23) + (int)(by >> 23);
-            pr = make_float2(__uint_as_float((bx & 0x7FFFFFu) | 0x3F800000u),
-                             __uint_as_float((by & 0x7FFFFFu) | 0x3F800000u));
-        }
+        int p = lane;
+#pragma unroll 1
+        for (; p + (kEqwUnroll - 1) * L < np; p += kEqwUnroll * L)
+            pairs<kEqwUnroll>(ys2, p, L, R2, NU, ex);
+#pragma unroll 1
+        for (; p < np; p += L) pairs<1>(ys2, p, L, R2, NU, ex);
         // remove the bias 2 x 127 of each pair; the result, at most
         // 4096 x 200 in size, is exact in FP32
         const int npairs = lane < np ? (np - 1 - lane) / L + 1 : 0;
@@ -307,7 +352,7 @@ struct SliceAccEqW {
     }
 
     __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P) {
-        ll.add(lg2(pr.x) + lg2(pr.y));
+        ll.add((lg2(pr[0].x) + lg2(pr[0].y)) + (lg2(pr[1].x) + lg2(pr[1].y)));
         const double part = slice_total(ll.s, ll.c, L);
         return part * kLn2 + P.cst;
     }

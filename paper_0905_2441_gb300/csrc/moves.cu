@@ -197,7 +197,7 @@ __device__ __forceinline__ bool exchange_pair(float* theta, double* ll, int64_t 
 // Minimum resident 256-thread blocks per SM asked of the register
 // allocator for the sweep (compile-time tuning knob; 1 leaves it free).
 #ifndef SMC_POP_MINB
-#define SMC_POP_MINB 3
+#define SMC_POP_MINB 2
 #endif
 
 // add with acquire-release ordering at GPU scope: publishes the writes the
