@@ -1,9 +1,614 @@
-// diag_tc.cu -- diagonal d-dimensional mixture log-likelihood with the
-// mu . y contraction on the tensor cores (tcgen05, bf16 hi/lo splits).
+// diag_tc.cu -- diagonal d-dimensional mixture log-likelihood (Section 4.1's
+// mixture with components N(mu_k, sigma^2 I_d)) with the mu . y contraction
+// on the tensor cores.
+//
+// In log2 units, with alpha = log2(e) / sigma^2,
+//   a_{n,pk} = log2 w_k - (alpha/2) (|y_n|^2 - 2 y_n . mu_pk + |mu_pk|^2)
+//            = alpha S_{n,pk} + beta_pk - gamma_n,
+//   S = y . mu,  beta_pk = log2 w_k - (alpha/2)|mu_pk|^2,  gamma_n = (alpha/2)|y_n|^2,
+// so  log2 sum_k 2^a = LSE2_k(alpha S + beta) - gamma_n  and the gamma_n sum
+// over the data is one constant for every particle.  S is a GEMM
+// [N x d] . [d x M K] that is never stored: tcgen05.mma forms 128 data x
+// 128 particle-components per instruction group in tensor memory from bf16
+// hi/lo splits of y and mu (hi.hi + hi.lo + lo.hi, FP32 accumulation), and
+// the epilogue warps read it back (tcgen05.ld) for the per-datum
+// log-sum-exp over the K components of each particle and the sum over n.
+//
+// Kernels: k_dtc_prep_y / k_dtc_prep_mu convert y and mu to bf16 hi/lo in
+// the tensor cores' no-swizzle K-major layout (8-row x 16-byte core
+// matrices) and compute beta and the gamma sum; k_dtc_main is persistent,
+// one CTA per SM, warp-specialised: warp 0 moves tiles with bulk async
+// copies (cp.async.bulk, mbarrier completion), warp 1 issues the MMAs from
+// one thread, warps 2..17 are the epilogue; k_dtc_combine adds the units
+// of each particle in a fixed order.  Every wait is bounded; a timeout
+// sets ST_TIMEOUT, drains what is in flight and ends the CTA.
+#include <cmath>
+#include <cstdint>
+
+#include <cuda_bf16.h>
+
 #include "ctx.hpp"
+#include "device.cuh"
+
+using namespace smc_host;
+
+namespace smc {
+namespace dtc {
+
+constexpr int kRows = 128;     // data per tile = MMA M = TMEM lanes
+constexpr int kHalf = 128;     // particle-components per MMA (N) and per TMEM buffer
+constexpr int kBlockCols = 2 * kHalf;  // particle-components per particle block
+constexpr int kStages = 4;     // ring of data tiles
+constexpr int kEpiWarps = 16;  // four warpgroups: (tile parity, half) each
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kTmemCols = 512; // 4 buffers of 128 FP32 columns
+
+// byte offset of element (r, j) of a rows x d bf16 block in the no-swizzle
+// K-major layout: 8-row x 8-element core matrices of 128 contiguous bytes,
+// K-adjacent core matrices 128 B apart, 8-row groups d * 16 B apart
+__host__ __device__ inline uint32_t cm_off(int r, int j, int d) {
+    return (uint32_t)((r >> 3) * (d * 16) + (j >> 3) * 128 + (r & 7) * 16 + (j & 7) * 2);
+}
+
+struct Lw2 {
+    float v[16];  // log2 w_k, k < K (padding components: -inf)
+};
+
+// shared-memory plan (bytes from a 1024-aligned base)
+struct Plan {
+    uint32_t ypart;   // one bf16 part (hi or lo) of a data tile: 128 * d * 2
+    uint32_t bpart;   // one part of a particle block: 256 * d * 2
+    uint32_t y0, b0, beta0, bar0, tmemslot, total;
+};
+
+__host__ __device__ inline Plan plan(int d) {
+    Plan p;
+    p.ypart = (uint32_t)(kRows * d * 2);
+    p.bpart = (uint32_t)(kBlockCols * d * 2);
+    p.y0 = 0;
+    p.b0 = p.y0 + kStages * 2 * p.ypart;
+    p.beta0 = p.b0 + 2 * 2 * p.bpart;
+    p.bar0 = p.beta0 + 2 * kBlockCols * 4;
+    p.tmemslot = p.bar0 + 24 * 8;
+    p.total = p.tmemslot + 16;
+    return p;
+}
+
+// barrier slots
+enum { B_FULL = 0, B_EMPTY = kStages, B_BFULL = 2 * kStages, B_BFREE = B_BFULL + 2,
+       B_TFULL = B_BFREE + 2, B_TEMPTY = B_TFULL + 2, B_DRAIN = B_TEMPTY + 2, B_COUNT };
+static_assert(B_COUNT <= 24, "barrier slots");
+
+// ------------------------------------------------------------------ PTX
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(a) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t a, uint32_t phase) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done) : "r"(a), "r"(phase) : "memory");
+    return done != 0;
+}
+// bounded wait for the phase with parity `phase` to complete; false on
+// timeout, or early once another role has aborted (abort != nullptr)
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t phase, const volatile int* abort) {
+    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+        if (mbar_test(a, phase)) return true;
+        if (it > 256) {
+            if (abort && *abort) return false;
+            __nanosleep(128);
+        }
+    }
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// shared-memory matrix descriptor, no swizzle, K-major: LBO = 128 B between
+// K-adjacent core matrices, SBO = d * 16 B between 8-row groups
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
+}
+// instruction descriptor, kind::f16: bf16 A and B, FP32 D, both K-major,
+// M = 128, N = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHalf >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :: "r"(dtm), "l"(ad), "l"(bd), "r"(kIdesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                 :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------ prep
+// y -> bf16 hi/lo tiles (tile t: hi part then lo part, rows >= N zero) and
+// per-block partial sums of |y_n|^2 (FP64).  One thread per row.
+__global__ void __launch_bounds__(256) k_dtc_prep_y(const float* __restrict__ Y, int64_t N, int d,
+                                                    int64_t ntiles, uint8_t* __restrict__ yt,
+                                                    double* __restrict__ gpart) {
+    __shared__ double red[8];
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    double sq = 0.0;
+    if (row < ntiles * kRows) {
+        const int64_t t = row / kRows;
+        const int r = (int)(row % kRows);
+        uint8_t* hi = yt + (size_t)t * 2 * (kRows * d * 2);
+        uint8_t* lo = hi + kRows * d * 2;
+        for (int j0 = 0; j0 < d; j0 += 8) {
+            uint32_t wh[4], wl[4];
+#pragma unroll
+            for (int e = 0; e < 8; e += 2) {
+                float v0 = 0.0f, v1 = 0.0f;
+                if (row < N) {
+                    v0 = Y[row * d + j0 + e];
+                    v1 = Y[row * d + j0 + e + 1];
+                    sq += (double)v0 * v0 + (double)v1 * v1;
+                }
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+                wh[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) |
+                            ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+                wl[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) |
+                            ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+            }
+            const uint32_t off = cm_off(r, j0, d);
+            *reinterpret_cast<uint4*>(hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+            *reinterpret_cast<uint4*>(lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+        }
+    }
+    sq = warp_sum_d(sq);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sq;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        gpart[blockIdx.x] = s;
+    }
+}
+
+// mu -> bf16 hi/lo particle blocks (block b: rows rho = p_local * KP + k,
+// hi part then lo part) and beta[b][rho] = log2 w_k - (alpha/2)|mu|^2
+// (padding components and particles beyond M: mu = 0, beta = -inf).
+__global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ theta, int64_t M,
+                                                     int K, int KP, int d, int64_t nblocks,
+                                                     float half_alpha, Lw2 lw2,
+                                                     uint8_t* __restrict__ bt,
+                                                     float* __restrict__ beta) {
+    const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= nblocks * kBlockCols) return;
+    const int64_t b = row / kBlockCols;
+    const int rho = (int)(row % kBlockCols);
+    const int64_t p = b * (kBlockCols / KP) + rho / KP;
+    const int k = rho % KP;
+    const bool real = p < M && k < K;
+    const float* mu = theta + ((size_t)p * K + k) * d;
+    uint8_t* hi = bt + (size_t)b * 2 * (kBlockCols * d * 2);
+    uint8_t* lo = hi + kBlockCols * d * 2;
+    float sq = 0.0f;
+    for (int j0 = 0; j0 < d; j0 += 8) {
+        uint32_t wh[4], wl[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            float v0 = 0.0f, v1 = 0.0f;
+            if (real) {
+                v0 = mu[j0 + e];
+                v1 = mu[j0 + e + 1];
+            }
+            sq = fmaf(v0, v0, sq);
+            sq = fmaf(v1, v1, sq);
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
+            wh[e / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            wl[e / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        const uint32_t off = cm_off(rho, j0, d);
+        *reinterpret_cast<uint4*>(hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+        *reinterpret_cast<uint4*>(lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
+    }
+    beta[row] = real ? fmaf(-half_alpha, sq, lw2.v[k]) : -INFINITY;
+}
+
+// ------------------------------------------------------------------ main
+// Work unit u: particle block u / nsplit (256 particle-components), data
+// tiles [split * T / nsplit, (split + 1) * T / nsplit), split = u % nsplit.
+// partial[u][e][i] = sum over the unit's data seen by epilogue warp e of
+// LSE2_k(alpha S + beta) for particle i of the warp's half of the block.
+template <int KP>
+__global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
+    const uint8_t* __restrict__ yt, const uint8_t* __restrict__ bt,
+    const float* __restrict__ beta, int64_t N, int d, int64_t ntiles, int nsplit, int64_t units,
+    float alpha, double* __restrict__ partial, uint32_t* status) {
+    constexpr int PPH = kHalf / KP;       // particles per half
+    constexpr int PPL = 32 / KP;          // particles per 32-column TMEM load
+    extern __shared__ __align__(1024) uint8_t smraw[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
+                                             ~(uintptr_t)1023);
+    const Plan pl = plan(d);
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar = smem_u32(sm + pl.bar0);
+    auto B = [&](int i) { return bar + 8u * (uint32_t)i; };
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + pl.tmemslot);
+    float* sbeta = reinterpret_cast<float*>(sm + pl.beta0);
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(B(B_FULL + s), 1);
+            mbar_init(B(B_EMPTY + s), 1);
+        }
+        for (int j = 0; j < 2; ++j) {
+            mbar_init(B(B_BFULL + j), 1);
+            mbar_init(B(B_BFREE + j), 1 + kEpiWarps);
+            mbar_init(B(B_TFULL + j), 1);
+            mbar_init(B(B_TEMPTY + j), kEpiWarps / 2);
+        }
+        mbar_init(B(B_DRAIN), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {  // tensor memory: 4 accumulator buffers of 128 columns
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = *tslot;
+    volatile int* abort = &s_abort;
+    auto fail = [&]() {
+        raise_status(status, ST_TIMEOUT);
+        *abort = 1;
+    };
+
+    const uint32_t tile_bytes = 2 * pl.ypart;
+    if (warp == 0) {
+        // ---------------------------------------------------------- producer
+        if (lane == 0) {
+            int64_t it = 0;
+            int ui = 0;
+            bool ok = true;
+            for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
+                const int bb = ui & 1;
+                const int64_t pb = u / nsplit, sp = u % nsplit;
+                if (ui >= 2 && !mbar_wait(B(B_BFREE + bb), ((ui >> 1) - 1) & 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                // the buffer was last read through the generic proxy (beta)
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(B(B_BFULL + bb), 2 * pl.bpart + kBlockCols * 4);
+                bulk_g2s(smem_u32(sm + pl.b0 + bb * 2 * pl.bpart), bt + (size_t)pb * 2 * pl.bpart,
+                         2 * pl.bpart, B(B_BFULL + bb));
+                bulk_g2s(smem_u32(sbeta + bb * kBlockCols), beta + (size_t)pb * kBlockCols,
+                         kBlockCols * 4, B(B_BFULL + bb));
+                const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
+                for (int64_t t = t0; t < t1; ++t, ++it) {
+                    const int s = (int)(it % kStages);
+                    if (it >= kStages &&
+                        !mbar_wait(B(B_EMPTY + s), (uint32_t)(((it / kStages) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_expect_tx(B(B_FULL + s), tile_bytes);
+                    bulk_g2s(smem_u32(sm + pl.y0 + s * tile_bytes), yt + (size_t)t * tile_bytes,
+                             tile_bytes, B(B_FULL + s));
+                }
+            }
+            if (!ok) fail();
+            // drain: every copy issued has landed before the CTA ends (fill
+            // number k of a stage or buffer completes phase k)
+            for (int s = 0; s < kStages; ++s)
+                if (it > s) mbar_wait(B(B_FULL + s), (uint32_t)(((it - 1 - s) / kStages) & 1), nullptr);
+            for (int b2 = 0; b2 < 2; ++b2)
+                if (ui > b2) mbar_wait(B(B_BFULL + b2), (uint32_t)(((ui - 1 - b2) / 2) & 1), nullptr);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            int64_t it = 0;
+            int ui = 0;
+            bool ok = true;
+            const uint32_t sbo = (uint32_t)d * 16u;
+            const int ksteps = d / 16;
+            for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
+                const int bb = ui & 1;
+                const int64_t sp = u % nsplit;
+                if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui >> 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t bhi = smem_u32(sm + pl.b0 + bb * 2 * pl.bpart);
+                const uint32_t blo = bhi + pl.bpart;
+                const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
+                for (int64_t t = t0; t < t1; ++t, ++it) {
+                    const int j = (int)(it & 1);
+                    const int s = (int)(it % kStages);
+                    if (it >= 2 &&
+                        !mbar_wait(B(B_TEMPTY + j), (uint32_t)(((it >> 1) - 1) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait(B(B_FULL + s), (uint32_t)((it / kStages) & 1), abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t yhi = smem_u32(sm + pl.y0 + s * tile_bytes);
+                    const uint32_t ylo = yhi + pl.ypart;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t dtm = tbase + (uint32_t)((2 * j + h) * kHalf);
+                        const uint32_t boff = (uint32_t)h * (kHalf / 8) * sbo;
+                        uint32_t acc = 0;
+                        for (int ks = 0; ks < ksteps; ++ks) {
+                            const uint32_t ko = (uint32_t)ks * 256u;
+                            mma_bf16(dtm, smem_desc(yhi + ko, sbo), smem_desc(bhi + boff + ko, sbo), acc);
+                            acc = 1;
+                            mma_bf16(dtm, smem_desc(yhi + ko, sbo), smem_desc(blo + boff + ko, sbo), 1);
+                            mma_bf16(dtm, smem_desc(ylo + ko, sbo), smem_desc(bhi + boff + ko, sbo), 1);
+                        }
+                    }
+                    mma_commit(B(B_EMPTY + s));
+                    mma_commit(B(B_TFULL + j));
+                }
+                mma_commit(B(B_BFREE + bb));
+            }
+            if (!ok) fail();
+            // every MMA issued has completed before tensor memory is freed
+            mma_commit(B(B_DRAIN));
+            mbar_wait(B(B_DRAIN), 0, nullptr);
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int e = warp - 2;
+        const int wg = e >> 2;
+        const int jw = wg >> 1, h = wg & 1;
+        const int q = warp & 3;  // this warp's quarter of the tensor-memory lanes
+        int64_t it = 0;
+        int ui = 0;
+        bool ok = true;
+        for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
+            const int bb = ui & 1;
+            const int64_t sp = u % nsplit;
+            Kahan acc[PPH];
+            if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui >> 1) & 1), abort)) {
+                ok = false;
+                break;
+            }
+            const float* bcol = sbeta + bb * kBlockCols + h * kHalf;
+            const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
+            for (int64_t t = t0; t < t1; ++t, ++it) {
+                const int j = (int)(it & 1);
+                if (j != jw) continue;
+                if (!mbar_wait(B(B_TFULL + j), (uint32_t)((it >> 1) & 1), abort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const bool valid = t * kRows + q * 32 + lane < N;
+#pragma unroll 1
+                for (int c = 0; c < kHalf / 32; ++c) {
+                    float v[32];
+                    tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) +
+                                  (uint32_t)((2 * j + h) * kHalf + c * 32), v);
+#pragma unroll
+                    for (int pi = 0; pi < PPL; ++pi) {
+                        float a[KP];
+                        float m = -INFINITY;
+#pragma unroll
+                        for (int k = 0; k < KP; ++k) {
+                            a[k] = fmaf(alpha, v[pi * KP + k], bcol[c * 32 + pi * KP + k]);
+                            m = fmaxf(m, a[k]);
+                        }
+                        float s = 0.0f;
+#pragma unroll
+                        for (int k = 0; k < KP; ++k) s += ex2(a[k] - m);
+                        if (valid) acc[c * PPL + pi].add(m + lg2(s));
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(B(B_TEMPTY + j));
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(B(B_BFREE + bb));  // done with this unit's beta
+            if (!ok) break;
+            // per-particle sums over the warp's lanes; the 8 warps of each half
+            // are added by k_dtc_combine in a fixed order
+            double* dst = partial + ((size_t)u * kEpiWarps + e) * PPH;
+#pragma unroll
+            for (int i = 0; i < PPH; ++i) {
+                const double vsum = warp_sum_d((double)acc[i].s - (double)acc[i].c);
+                if (lane == 0) dst[i] = vsum;
+            }
+        }
+        if (!ok) fail();
+    }
+    // ---------------------------------------------------------- teardown
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+                     :: "r"(tbase), "r"(kTmemCols) : "memory");
+}
+
+// l_p = ln2 (sum over the units and warps of p - sum_n gamma_n) + N c0,
+// added in a fixed order (splits, then the 8 warps of p's half)
+__global__ void __launch_bounds__(256) k_dtc_combine(const double* __restrict__ partial,
+                                                     int nsplit, int kp, int64_t M,
+                                                     const double* __restrict__ gpart, int ngpart,
+                                                     double half_alpha, double ncst,
+                                                     double* __restrict__ out, uint32_t* status) {
+    __shared__ double red[256];
+    double g = 0.0;
+    for (int i = threadIdx.x; i < ngpart; i += blockDim.x) g += gpart[i];
+    red[threadIdx.x] = g;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double gamma = half_alpha * red[0];
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= M) return;
+    const int ppb = kBlockCols / kp, pph = kHalf / kp;
+    const int64_t pb = p / ppb;
+    const int ib = (int)(p % ppb);
+    const int h = ib / pph, i = ib % pph;
+    double s = 0.0;
+    for (int sp = 0; sp < nsplit; ++sp) {
+        const double* base = partial + ((size_t)(pb * nsplit + sp) * kEpiWarps) * pph;
+        for (int e = 0; e < kEpiWarps; ++e)
+            if (((e >> 2) & 1) == h) s += base[(size_t)e * pph + i];
+    }
+    const double ll = (s - gamma) * kLn2 + ncst;
+    if (ll != ll) raise_status(status, ST_NONFINITE);
+    out[p] = ll;
+}
+
+}  // namespace dtc
+}  // namespace smc
+
+namespace {
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+template <int KP>
+smc_status launch_main(const smc_ctx* ctx, int64_t grid, size_t smem, const uint8_t* yt,
+                       const uint8_t* bt, const float* beta, int64_t N, int d, int64_t ntiles,
+                       int nsplit, int64_t units, float alpha, double* partial, cudaStream_t s) {
+    auto kern = smc::dtc::k_dtc_main<KP>;
+    SMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<(unsigned)grid, smc::dtc::kThreads, smem, s>>>(yt, bt, beta, N, d, ntiles, nsplit, units,
+                                                         alpha, partial, ctx->d_status);
+    return cuda_ok(cudaGetLastError());
+}
+
+}  // namespace
+
+// Workspace bytes of one call (data tiles, particle blocks, beta, partials).
+size_t smc_diag_tc_ws_bytes(int64_t N, int64_t M, int K, int d, int sms) {
+    using namespace smc::dtc;
+    const int KP = K <= 4 ? 4 : (K <= 8 ? 8 : 16);
+    const int64_t ntiles = (N + kRows - 1) / kRows;
+    const int64_t nblocks = (M + kBlockCols / KP - 1) / (kBlockCols / KP);
+    int nsplit = 1;
+    while (nblocks * nsplit < 4 * (int64_t)sms && ntiles / (2 * nsplit) >= 8) nsplit *= 2;
+    const int64_t units = nblocks * nsplit;
+    const int64_t gblocks = (ntiles * kRows + 255) / 256;
+    size_t b = 0;
+    b += align_up((size_t)ntiles * 2 * kRows * d * 2, 1024);
+    b += align_up((size_t)nblocks * 2 * kBlockCols * d * 2, 1024);
+    b += align_up((size_t)nblocks * kBlockCols * 4, 1024);
+    b += align_up((size_t)gblocks * 8, 1024);
+    b += align_up((size_t)units * kEpiWarps * (kHalf / KP) * 8, 1024);
+    return b;
+}
 
 smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y, int64_t N,
                               const float* theta, int64_t M, double* out, cudaStream_t s) {
-    (void)ctx; (void)model; (void)Y; (void)N; (void)theta; (void)M; (void)out; (void)s;
-    return SMC_ERR_UNSUPPORTED;
+    using namespace smc::dtc;
+    const int K = model->K, d = model->d;
+    // tensor-core path: K <= 16 components, d a multiple of 16 up to 32
+    if (K > 16 || (d != 16 && d != 32)) return SMC_ERR_UNSUPPORTED;
+    if (N == 0) return cuda_ok(cudaMemsetAsync(out, 0, (size_t)M * sizeof(double), s));
+    const int KP = K <= 4 ? 4 : (K <= 8 ? 8 : 16);
+    const int64_t ntiles = (N + kRows - 1) / kRows;
+    const int64_t nblocks = (M + kBlockCols / KP - 1) / (kBlockCols / KP);
+    int nsplit = 1;
+    while (nblocks * nsplit < 4 * (int64_t)ctx->num_sms && ntiles / (2 * nsplit) >= 8) nsplit *= 2;
+    const int64_t units = nblocks * nsplit;
+    const int64_t gblocks = (ntiles * kRows + 255) / 256;
+    if (units > 0x7FFFFFFF || gblocks > 0x7FFFFFFF) return SMC_ERR_ARG;
+    smc_status st = ensure_ws(ctx, smc_diag_tc_ws_bytes(N, M, K, d, ctx->num_sms), s);
+    if (st != SMC_OK) return st;
+    uint8_t* w = static_cast<uint8_t*>(ctx->ws);
+    uint8_t* yt = w;
+    w += align_up((size_t)ntiles * 2 * kRows * d * 2, 1024);
+    uint8_t* bt = w;
+    w += align_up((size_t)nblocks * 2 * kBlockCols * d * 2, 1024);
+    float* beta = reinterpret_cast<float*>(w);
+    w += align_up((size_t)nblocks * kBlockCols * 4, 1024);
+    double* gpart = reinterpret_cast<double*>(w);
+    w += align_up((size_t)gblocks * 8, 1024);
+    double* partial = reinterpret_cast<double*>(w);
+
+    const double sg = (double)model->sigma;
+    const double alpha = smc::kLog2e / (sg * sg);
+    Lw2 lw2;
+    for (int k = 0; k < 16; ++k)
+        lw2.v[k] = k < K ? (float)((double)model->log_w[k] * smc::kLog2e) : -INFINITY;
+    k_dtc_prep_y<<<(unsigned)gblocks, 256, 0, s>>>(Y, N, d, ntiles, yt, gpart);
+    SMC_CUDA(cudaGetLastError());
+    k_dtc_prep_mu<<<(unsigned)((nblocks * kBlockCols + 255) / 256), 256, 0, s>>>(
+        theta, M, K, KP, d, nblocks, (float)(0.5 * alpha), lw2, bt, beta);
+    SMC_CUDA(cudaGetLastError());
+    const Plan pl = plan(d);
+    // + alignment slack; at least half an SM's shared memory so that one CTA
+    // (and one 512-column tensor-memory allocation) runs per SM
+    size_t smem = pl.total + 1024;
+    if (ctx->smem_per_sm > 0 && smem < (size_t)ctx->smem_per_sm / 2 + 1024)
+        smem = (size_t)ctx->smem_per_sm / 2 + 1024;
+    int64_t grid = units < ctx->num_sms ? units : ctx->num_sms;
+    switch (KP) {
+        case 4: st = launch_main<4>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
+        case 8: st = launch_main<8>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
+        default: st = launch_main<16>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
+    }
+    if (st != SMC_OK) return st;
+    const double ncst = (double)N * (-0.5 * d * std::log(2.0 * M_PI * sg * sg));
+    k_dtc_combine<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(partial, nsplit, KP, M,
+                                                              gpart, (int)gblocks, 0.5 * alpha,
+                                                              ncst, out, ctx->d_status);
+    return cuda_ok(cudaGetLastError());
 }
