@@ -539,6 +539,93 @@ def bench_resample(args, torch, dist):
     return out
 
 
+def bench_diag(args, torch, dist):
+    """One step = smc_loglik_batch of the diagonal mixture (d=32, K=16,
+    N=65536, M=4096) on the tensor cores (bf16 hi/lo split); the FP32
+    CUDA-core path on the same inputs is timed beside it."""
+    import paper_0905_2441_gb300 as P
+    import synth
+    import oracle
+    w = synth.DIAG32
+    truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
+    Yh = synth.diag_data(w.N, truth, seed=w.data_seed)
+    thh = synth.diag_particles(w.M, truth, seed=w.particle_seed + dist.rank)
+    Y = torch.from_numpy(Yh).cuda()
+    th = torch.from_numpy(thh).cuda()
+    ctx = P.Context()
+    tc = P.DiagGMM(w.K, w.sigma, d=w.d, precision=P.PREC_BF16SPLIT)
+    fp = P.DiagGMM(w.K, w.sigma, d=w.d)
+    out = torch.empty(w.M, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    call = lambda: P.loglik_batch(ctx, tc, Y, th, out=out)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    K = min(args.steps, 200)
+    rec = []
+    dist.barrier(torch)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(K):
+            rec.append(_flush_timed(torch, flush, stream, [call]))
+        torch.cuda.synchronize()
+    ctx.check()
+    per = np.array([e[0].elapsed_time(e[1]) / 1e3 for e in rec])
+    t_dev = float(per.sum())
+    t_max = dist.max(torch, t_dev)
+    pd = float(w.M) * w.N
+    value = dist.sum(torch, pd * K) / t_max
+    got = out.cpu().numpy()
+    # error against the oracle on sampled particles
+    idx = np.array([0, w.M // 2 - 1, w.M // 2, w.M - 1])
+    ref = oracle.gmmdiag_loglik(Yh, w.logw(), w.sigma, thh[idx])
+    err = float(np.max(np.abs(got[idx] - ref) / np.abs(ref)))
+    # the FP32 CUDA-core path on the same inputs
+    outf = torch.empty_like(out)
+    P.loglik_batch(ctx, fp, Y, th, out=outf)
+    torch.cuda.synchronize()
+    recf = [_flush_timed(torch, flush, stream, [lambda: P.loglik_batch(ctx, fp, Y, th, out=outf)])
+            for _ in range(3)]
+    torch.cuda.synchronize()
+    t_fp = float(np.mean([e[0].elapsed_time(e[1]) / 1e3 for e in recf]))
+    # rooflines: issued bf16 MMA flops (3 split products) and MUFU ops
+    t_call = float(per.mean())
+    kp = 16
+    flops = 3 * 2.0 * (-(-w.N // 128) * 128) * (w.M * kp) * w.d
+    mufu = float(w.N) * w.M * (kp + 1)
+    pk = measured_peaks()
+    ex2_rate, _ = measure_peak(P, 0)
+    tens = {"bound": "tensor", "achieved": flops / t_call / 1e12, "peak": pk["bf16_tflops"],
+            "unit": "TFLOP/s", "frac": flops / t_call / 1e12 / pk["bf16_tflops"],
+            "traffic": profile_traffic("k_dtc_main"), "kernel": "k_dtc_main<16> (+ prep, combine)",
+            "flops_per_call": flops,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst (of measured)"}
+    mu = {"achieved": mufu / t_call / 1e9, "peak": ex2_rate / 1e9, "unit": "Gop/s",
+          "frac": mufu / t_call / ex2_rate, "ops_per_call": mufu,
+          "count": "K ex2 + 1 lg2 per particle-datum"}
+    roof = dict(tens)
+    if mu["frac"] > tens["frac"]:
+        roof = {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": mu["achieved"],
+                "peak": mu["peak"], "unit": "Gop/s", "frac": mu["frac"],
+                "traffic": tens["traffic"], "kernel": tens["kernel"], "ops_per_call": mufu}
+    roof["tensor"] = {k: tens[k] for k in ("achieved", "peak", "unit", "frac")}
+    roof["mufu"] = {k: mu[k] for k in ("achieved", "peak", "unit", "frac")}
+    res = {"metric": "particle-datum loglik evals/s (diagonal mixture, tensor cores)",
+           "value": value, "unit": "p*d/s", "n_gpus": dist.world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / K, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
+           "data": "synthetic (seeded mixture data and particles; no dataset)",
+           "config": {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
+                      "l2": "256 MiB buffer written before every timed call, outside its events",
+                      "parallelism": f"independent particle sets per rank x{dist.world}"},
+           "forms": {"tensor_bf16_split": {"ms_per_call": 1e3 * t_call, "max_rel_err": err},
+                     "cuda_core_fp32": {"ms_per_call": 1e3 * t_fp, "value": pd / t_fp}},
+           "roofline": roof, "gpu_launches": 4 * K, "clocks": clk.summary()}
+    ctx.close()
+    return res
+
+
 def all_peaks(torch):
     import paper_0905_2441_gb300 as P
     out = {}
@@ -579,7 +666,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
-                                                              "peaks"])
+                                                              "diag", "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -603,6 +690,8 @@ def main():
         out = bench_pf(args, torch, dist)
     elif args.workload == "resample":
         out = bench_resample(args, torch, dist)
+    elif args.workload == "diag":
+        out = bench_diag(args, torch, dist)
     elif args.workload == "peaks":
         out = {"peaks_ops_per_s": all_peaks(torch)}
     else:

@@ -7,12 +7,14 @@
 //            = alpha S_{n,pk} + beta_pk - gamma_n,
 //   S = y . mu,  beta_pk = log2 w_k - (alpha/2)|mu_pk|^2,  gamma_n = (alpha/2)|y_n|^2,
 // so  log2 sum_k 2^a = LSE2_k(alpha S + beta) - gamma_n  and the gamma_n sum
-// over the data is one constant for every particle.  S is a GEMM
-// [N x d] . [d x M K] that is never stored: tcgen05.mma forms 128 data x
-// 128 particle-components per instruction group in tensor memory from bf16
-// hi/lo splits of y and mu (hi.hi + hi.lo + lo.hi, FP32 accumulation), and
-// the epilogue warps read it back (tcgen05.ld) for the per-datum
-// log-sum-exp over the K components of each particle and the sum over n.
+// over the data is one constant for every particle.  alpha S + beta is a
+// GEMM [N x (d+16)] . [(d+16) x M K] that is never stored: tcgen05.mma
+// forms 128 data x 128 particle-components per instruction group in tensor
+// memory from bf16 hi/lo splits of y and alpha mu (hi.hi + hi.lo + lo.hi,
+// FP32 accumulation) plus one product of a constant ones column with beta
+// split three ways in bf16 (24 bits), and the epilogue warps read the
+// exponents back (tcgen05.ld) for the per-datum log-sum-exp over the K
+// components of each particle and the sum over n.
 //
 // Kernels: k_dtc_prep_y / k_dtc_prep_mu convert y and mu to bf16 hi/lo in
 // the tensor cores' no-swizzle K-major layout (8-row x 16-byte core
@@ -55,20 +57,25 @@ struct Lw2 {
 };
 
 // shared-memory plan (bytes from a 1024-aligned base)
+constexpr uint32_t kOnesBytes = kRows * 16 * 2;       // ones operand: 128 rows x 16 bf16
+constexpr uint32_t kBetaPart = kBlockCols * 16 * 2;   // beta operand: 256 rows x 16 bf16
+
 struct Plan {
     uint32_t ypart;   // one bf16 part (hi or lo) of a data tile: 128 * d * 2
     uint32_t bpart;   // one part of a particle block: 256 * d * 2
-    uint32_t y0, b0, beta0, bar0, tmemslot, total;
+    uint32_t bblock;  // a particle block in memory: hi, lo, beta parts
+    uint32_t y0, b0, ones0, bar0, tmemslot, total;
 };
 
 __host__ __device__ inline Plan plan(int d) {
     Plan p;
     p.ypart = (uint32_t)(kRows * d * 2);
     p.bpart = (uint32_t)(kBlockCols * d * 2);
+    p.bblock = 2 * p.bpart + kBetaPart;
     p.y0 = 0;
     p.b0 = p.y0 + kStages * 2 * p.ypart;
-    p.beta0 = p.b0 + 2 * 2 * p.bpart;
-    p.bar0 = p.beta0 + 2 * kBlockCols * 4;
+    p.ones0 = p.b0 + 2 * p.bblock;
+    p.bar0 = p.ones0 + kOnesBytes;
     p.tmemslot = p.bar0 + 24 * 8;
     p.total = p.tmemslot + 16;
     return p;
@@ -125,6 +132,11 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float r;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+    return r;
 }
 // shared-memory matrix descriptor, no swizzle, K-major: LBO = 128 B between
 // K-adjacent core matrices, SBO = d * 16 B between 8-row groups
@@ -213,14 +225,15 @@ __global__ void __launch_bounds__(256) k_dtc_prep_y(const float* __restrict__ Y,
     }
 }
 
-// mu -> bf16 hi/lo particle blocks (block b: rows rho = p_local * KP + k,
-// hi part then lo part) and beta[b][rho] = log2 w_k - (alpha/2)|mu|^2
-// (padding components and particles beyond M: mu = 0, beta = -inf).
+// alpha mu -> bf16 hi/lo particle blocks (block b: rows rho = p_local * KP
+// + k; hi part, lo part, then the beta part: row rho holds beta_rho split
+// into three bf16 (columns 0..2, rest 0)), beta = log2 w_k - (alpha/2)|mu|^2
+// from the FP32 mu.  Padding components and particles beyond M: mu = 0 and
+// beta = -1e30 (finite, so the splits stay finite; 2^(-1e30 - m) = 0).
 __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ theta, int64_t M,
                                                      int K, int KP, int d, int64_t nblocks,
-                                                     float half_alpha, Lw2 lw2,
-                                                     uint8_t* __restrict__ bt,
-                                                     float* __restrict__ beta) {
+                                                     float alpha, Lw2 lw2,
+                                                     uint8_t* __restrict__ bt) {
     const int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (row >= nblocks * kBlockCols) return;
     const int64_t b = row / kBlockCols;
@@ -229,8 +242,10 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
     const int k = rho % KP;
     const bool real = p < M && k < K;
     const float* mu = theta + ((size_t)p * K + k) * d;
-    uint8_t* hi = bt + (size_t)b * 2 * (kBlockCols * d * 2);
-    uint8_t* lo = hi + kBlockCols * d * 2;
+    const uint32_t bpart = kBlockCols * d * 2;
+    uint8_t* hi = bt + (size_t)b * (2 * bpart + kBetaPart);
+    uint8_t* lo = hi + bpart;
+    uint8_t* bb = lo + bpart;
     float sq = 0.0f;
     for (int j0 = 0; j0 < d; j0 += 8) {
         uint32_t wh[4], wl[4];
@@ -243,6 +258,8 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
             }
             sq = fmaf(v0, v0, sq);
             sq = fmaf(v1, v1, sq);
+            v0 *= alpha;
+            v1 *= alpha;
             const __nv_bfloat16 h0 = __float2bfloat16_rn(v0), h1 = __float2bfloat16_rn(v1);
             const __nv_bfloat16 l0 = __float2bfloat16_rn(v0 - __bfloat162float(h0));
             const __nv_bfloat16 l1 = __float2bfloat16_rn(v1 - __bfloat162float(h1));
@@ -253,7 +270,15 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
         *reinterpret_cast<uint4*>(hi + off) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
         *reinterpret_cast<uint4*>(lo + off) = make_uint4(wl[0], wl[1], wl[2], wl[3]);
     }
-    beta[row] = real ? fmaf(-half_alpha, sq, lw2.v[k]) : -INFINITY;
+    const float beta = real ? fmaf(-0.5f * alpha, sq, lw2.v[k]) : -1e30f;
+    const __nv_bfloat16 b0 = __float2bfloat16_rn(beta);
+    const float r1 = beta - __bfloat162float(b0);
+    const __nv_bfloat16 b1 = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 b2 = __float2bfloat16_rn(r1 - __bfloat162float(b1));
+    const uint32_t w0 = (uint32_t)__bfloat16_as_ushort(b0) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+    const uint32_t w1 = (uint32_t)__bfloat16_as_ushort(b2);
+    *reinterpret_cast<uint4*>(bb + cm_off(rho, 0, 16)) = make_uint4(w0, w1, 0u, 0u);
+    *reinterpret_cast<uint4*>(bb + cm_off(rho, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // ------------------------------------------------------------------ main
@@ -263,9 +288,8 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
 // LSE2_k(alpha S + beta) for particle i of the warp's half of the block.
 template <int KP>
 __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
-    const uint8_t* __restrict__ yt, const uint8_t* __restrict__ bt,
-    const float* __restrict__ beta, int64_t N, int d, int64_t ntiles, int nsplit, int64_t units,
-    float alpha, double* __restrict__ partial, uint32_t* status) {
+    const uint8_t* __restrict__ yt, const uint8_t* __restrict__ bt, int64_t N, int d,
+    int64_t ntiles, int nsplit, int64_t units, double* __restrict__ partial, uint32_t* status) {
     constexpr int PPH = kHalf / KP;       // particles per half
     constexpr int PPL = 32 / KP;          // particles per 32-column TMEM load
     extern __shared__ __align__(1024) uint8_t smraw[];
@@ -277,7 +301,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
     const uint32_t bar = smem_u32(sm + pl.bar0);
     auto B = [&](int i) { return bar + 8u * (uint32_t)i; };
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + pl.tmemslot);
-    float* sbeta = reinterpret_cast<float*>(sm + pl.beta0);
 
     if (threadIdx.x == 0) {
         s_abort = 0;
@@ -294,6 +317,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
         mbar_init(B(B_DRAIN), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // the constant ones operand (columns 0..2 = 1, the rest 0) of the beta product
+    for (int r = threadIdx.x; r < kRows; r += blockDim.x) {
+        const uint32_t one2 = 0x3F803F80u;  // two bf16 ones
+        *reinterpret_cast<uint4*>(sm + pl.ones0 + cm_off(r, 0, 16)) =
+            make_uint4(one2, 0x3F80u, 0u, 0u);
+        *reinterpret_cast<uint4*>(sm + pl.ones0 + cm_off(r, 8, 16)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    // written through the generic proxy, read by the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 1) {  // tensor memory: 4 accumulator buffers of 128 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
                      :: "r"(smem_u32(tslot)), "r"(kTmemCols) : "memory");
@@ -323,13 +355,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                     ok = false;
                     break;
                 }
-                // the buffer was last read through the generic proxy (beta)
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_expect_tx(B(B_BFULL + bb), 2 * pl.bpart + kBlockCols * 4);
-                bulk_g2s(smem_u32(sm + pl.b0 + bb * 2 * pl.bpart), bt + (size_t)pb * 2 * pl.bpart,
-                         2 * pl.bpart, B(B_BFULL + bb));
-                bulk_g2s(smem_u32(sbeta + bb * kBlockCols), beta + (size_t)pb * kBlockCols,
-                         kBlockCols * 4, B(B_BFULL + bb));
+                mbar_expect_tx(B(B_BFULL + bb), pl.bblock);
+                bulk_g2s(smem_u32(sm + pl.b0 + bb * pl.bblock), bt + (size_t)pb * pl.bblock,
+                         pl.bblock, B(B_BFULL + bb));
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
                     const int s = (int)(it % kStages);
@@ -366,8 +394,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                     ok = false;
                     break;
                 }
-                const uint32_t bhi = smem_u32(sm + pl.b0 + bb * 2 * pl.bpart);
+                const uint32_t bhi = smem_u32(sm + pl.b0 + bb * pl.bblock);
                 const uint32_t blo = bhi + pl.bpart;
+                const uint32_t bbeta = blo + pl.bpart;
+                const uint32_t ones = smem_u32(sm + pl.ones0);
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
                     const int j = (int)(it & 1);
@@ -396,6 +426,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                             mma_bf16(dtm, smem_desc(yhi + ko, sbo), smem_desc(blo + boff + ko, sbo), 1);
                             mma_bf16(dtm, smem_desc(ylo + ko, sbo), smem_desc(bhi + boff + ko, sbo), 1);
                         }
+                        // + beta: ones column times the three bf16 parts of beta
+                        mma_bf16(dtm, smem_desc(ones, 256u),
+                                 smem_desc(bbeta + (uint32_t)h * (kHalf / 8) * 256u, 256u), 1);
                     }
                     mma_commit(B(B_EMPTY + s));
                     mma_commit(B(B_TFULL + j));
@@ -420,11 +453,19 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
             const int bb = ui & 1;
             const int64_t sp = u % nsplit;
             Kahan acc[PPH];
+            // per particle (KP = 16): product of the per-datum sums (each in
+            // [1, 16]) and sum of the shifts over up to 16 tiles, then one lg2;
+            // with more particles per thread (KP < 16) one lg2 per datum
+            constexpr bool kProd = KP == 16;
+            constexpr int NPR = kProd ? PPH : 1;
+            float pr[NPR], ms[NPR];
+#pragma unroll
+            for (int i = 0; i < NPR; ++i) { pr[i] = 1.0f; ms[i] = 0.0f; }
+            int ngroup = 0;
             if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui >> 1) & 1), abort)) {
                 ok = false;
                 break;
             }
-            const float* bcol = sbeta + bb * kBlockCols + h * kHalf;
             const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 const int j = (int)(it & 1);
@@ -435,29 +476,57 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                 }
                 tc_fence_after();
                 const bool valid = t * kRows + q * 32 + lane < N;
-#pragma unroll 1
+#pragma unroll
                 for (int c = 0; c < kHalf / 32; ++c) {
-                    float v[32];
+                    float v[32];  // exponents alpha S + beta of 32 / KP particles
                     tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) +
                                   (uint32_t)((2 * j + h) * kHalf + c * 32), v);
 #pragma unroll
                     for (int pi = 0; pi < PPL; ++pi) {
-                        float a[KP];
-                        float m = -INFINITY;
+                        const float* a = v + pi * KP;
+                        float m = max3(a[0], a[1], a[2]);
 #pragma unroll
-                        for (int k = 0; k < KP; ++k) {
-                            a[k] = fmaf(alpha, v[pi * KP + k], bcol[c * 32 + pi * KP + k]);
-                            m = fmaxf(m, a[k]);
+                        for (int k = 3; k + 1 < KP; k += 2) m = max3(m, a[k], a[k + 1]);
+                        if constexpr ((KP - 3) % 2 == 1) m = fmaxf(m, a[KP - 1]);
+                        const float2 NM = make_float2(-m, -m);
+                        float2 E[KP / 2];
+#pragma unroll
+                        for (int k = 0; k < KP / 2; ++k) {
+                            const float2 x = __fadd2_rn(make_float2(a[2 * k], a[2 * k + 1]), NM);
+                            E[k] = make_float2(ex2(x.x), ex2(x.y));
                         }
-                        float s = 0.0f;
 #pragma unroll
-                        for (int k = 0; k < KP; ++k) s += ex2(a[k] - m);
-                        if (valid) acc[c * PPL + pi].add(m + lg2(s));
+                        for (int w2 = 1; w2 < KP / 2; w2 <<= 1)
+#pragma unroll
+                            for (int k = 0; k + w2 < KP / 2; k += 2 * w2)
+                                E[k] = __fadd2_rn(E[k], E[k + w2]);
+                        const int ia = c * PPL + pi;
+                        if (valid) {
+                            if constexpr (kProd) {
+                                pr[ia] *= E[0].x + E[0].y;
+                                ms[ia] += m;
+                            } else {
+                                acc[ia].add(m + lg2(E[0].x + E[0].y));
+                            }
+                        }
                     }
                 }
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(B(B_TEMPTY + j));
+                if (kProd && ++ngroup == 16) {  // 16 sums of at most 16 each: below 2^64
+#pragma unroll
+                    for (int i = 0; i < NPR; ++i) {
+                        acc[i].add(ms[i] + lg2(pr[i]));
+                        pr[i] = 1.0f;
+                        ms[i] = 0.0f;
+                    }
+                    ngroup = 0;
+                }
+            }
+            if constexpr (kProd) {
+#pragma unroll
+                for (int i = 0; i < NPR; ++i) acc[i].add(ms[i] + lg2(pr[i]));
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(B(B_BFREE + bb));  // done with this unit's beta
@@ -525,12 +594,12 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 template <int KP>
 smc_status launch_main(const smc_ctx* ctx, int64_t grid, size_t smem, const uint8_t* yt,
-                       const uint8_t* bt, const float* beta, int64_t N, int d, int64_t ntiles,
-                       int nsplit, int64_t units, float alpha, double* partial, cudaStream_t s) {
+                       const uint8_t* bt, int64_t N, int d, int64_t ntiles, int nsplit,
+                       int64_t units, double* partial, cudaStream_t s) {
     auto kern = smc::dtc::k_dtc_main<KP>;
     SMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<(unsigned)grid, smc::dtc::kThreads, smem, s>>>(yt, bt, beta, N, d, ntiles, nsplit, units,
-                                                         alpha, partial, ctx->d_status);
+    kern<<<(unsigned)grid, smc::dtc::kThreads, smem, s>>>(yt, bt, N, d, ntiles, nsplit, units,
+                                                         partial, ctx->d_status);
     return cuda_ok(cudaGetLastError());
 }
 
@@ -548,8 +617,7 @@ size_t smc_diag_tc_ws_bytes(int64_t N, int64_t M, int K, int d, int sms) {
     const int64_t gblocks = (ntiles * kRows + 255) / 256;
     size_t b = 0;
     b += align_up((size_t)ntiles * 2 * kRows * d * 2, 1024);
-    b += align_up((size_t)nblocks * 2 * kBlockCols * d * 2, 1024);
-    b += align_up((size_t)nblocks * kBlockCols * 4, 1024);
+    b += align_up((size_t)nblocks * (2 * kBlockCols * d * 2 + kBetaPart), 1024);
     b += align_up((size_t)gblocks * 8, 1024);
     b += align_up((size_t)units * kEpiWarps * (kHalf / KP) * 8, 1024);
     return b;
@@ -576,9 +644,7 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
     uint8_t* yt = w;
     w += align_up((size_t)ntiles * 2 * kRows * d * 2, 1024);
     uint8_t* bt = w;
-    w += align_up((size_t)nblocks * 2 * kBlockCols * d * 2, 1024);
-    float* beta = reinterpret_cast<float*>(w);
-    w += align_up((size_t)nblocks * kBlockCols * 4, 1024);
+    w += align_up((size_t)nblocks * (2 * kBlockCols * d * 2 + kBetaPart), 1024);
     double* gpart = reinterpret_cast<double*>(w);
     w += align_up((size_t)gblocks * 8, 1024);
     double* partial = reinterpret_cast<double*>(w);
@@ -591,7 +657,7 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
     k_dtc_prep_y<<<(unsigned)gblocks, 256, 0, s>>>(Y, N, d, ntiles, yt, gpart);
     SMC_CUDA(cudaGetLastError());
     k_dtc_prep_mu<<<(unsigned)((nblocks * kBlockCols + 255) / 256), 256, 0, s>>>(
-        theta, M, K, KP, d, nblocks, (float)(0.5 * alpha), lw2, bt, beta);
+        theta, M, K, KP, d, nblocks, (float)alpha, lw2, bt);
     SMC_CUDA(cudaGetLastError());
     const Plan pl = plan(d);
     // + alignment slack; at least half an SM's shared memory so that one CTA
@@ -601,9 +667,9 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
         smem = (size_t)ctx->smem_per_sm / 2 + 1024;
     int64_t grid = units < ctx->num_sms ? units : ctx->num_sms;
     switch (KP) {
-        case 4: st = launch_main<4>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
-        case 8: st = launch_main<8>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
-        default: st = launch_main<16>(ctx, grid, smem, yt, bt, beta, N, d, ntiles, nsplit, units, (float)alpha, partial, s); break;
+        case 4: st = launch_main<4>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
+        case 8: st = launch_main<8>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
+        default: st = launch_main<16>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
     }
     if (st != SMC_OK) return st;
     const double ncst = (double)N * (-0.5 * d * std::log(2.0 * M_PI * sg * sg));
