@@ -64,10 +64,10 @@ struct Plan {
     uint32_t ypart;   // one bf16 part (hi or lo) of a data tile: 128 * d * 2
     uint32_t bpart;   // one part of a particle block: 256 * d * 2
     uint32_t bblock;  // a particle block in memory: hi, lo, beta parts
-    uint32_t y0, b0, ones0, bar0, tmemslot, total;
+    uint32_t y0, b0, ones0, acc0, bar0, tmemslot, total;
 };
 
-__host__ __device__ inline Plan plan(int d) {
+__host__ __device__ inline Plan plan(int d, int ppw) {
     Plan p;
     p.ypart = (uint32_t)(kRows * d * 2);
     p.bpart = (uint32_t)(kBlockCols * d * 2);
@@ -75,7 +75,8 @@ __host__ __device__ inline Plan plan(int d) {
     p.y0 = 0;
     p.b0 = p.y0 + kStages * 2 * p.ypart;
     p.ones0 = p.b0 + 2 * p.bblock;
-    p.bar0 = p.ones0 + kOnesBytes;
+    p.acc0 = p.ones0 + kOnesBytes;
+    p.bar0 = p.acc0 + (uint32_t)(32 * kEpiWarps * ppw * 4);  // a float per thread and particle
     p.tmemslot = p.bar0 + 24 * 8;
     p.total = p.tmemslot + 16;
     return p;
@@ -145,9 +146,10 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo) {
            ((uint64_t)(sbo >> 4) << 32) | (1ull << 46);
 }
 // instruction descriptor, kind::f16: bf16 A and B, FP32 D, both K-major,
-// M = 128, N = 128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kHalf >> 3) << 17) |
-                            ((uint32_t)(kRows >> 4) << 24);
+// M = 128 data, N = 256 particle-components (one instruction per split
+// product and K step covers the whole particle block)
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(kBlockCols >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
 
 __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t acc) {
     asm volatile(
@@ -159,6 +161,26 @@ __device__ __forceinline__ void mma_bf16(uint32_t dtm, uint64_t ad, uint64_t bd,
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                  :: "r"(mbar) : "memory");
+}
+// 16 columns of this warp's 32 lanes, without waiting: the registers are
+// valid after tmem_wait()
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// waits for every tcgen05.ld of the thread; r (the last load's registers)
+// is passed through so no use of them is scheduled before the wait
+__device__ __forceinline__ void tmem_wait(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+                 :: "memory");
 }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     uint32_t r[32];
@@ -284,18 +306,18 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
 // ------------------------------------------------------------------ main
 // Work unit u: particle block u / nsplit (256 particle-components), data
 // tiles [split * T / nsplit, (split + 1) * T / nsplit), split = u % nsplit.
-// partial[u][e][i] = sum over the unit's data seen by epilogue warp e of
-// LSE2_k(alpha S + beta) for particle i of the warp's half of the block.
+// partial[u][e][i] = sum over the unit's data seen by epilogue warp e (its
+// lane quarter of every tile) of LSE2_k(alpha S + beta) for particle i of
+// the warp's column quarter of the block.
 template <int KP>
 __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
     const uint8_t* __restrict__ yt, const uint8_t* __restrict__ bt, int64_t N, int d,
     int64_t ntiles, int nsplit, int64_t units, double* __restrict__ partial, uint32_t* status) {
-    constexpr int PPH = kHalf / KP;       // particles per half
-    constexpr int PPL = 32 / KP;          // particles per 32-column TMEM load
+    constexpr int PPW = 64 / KP;          // particles per epilogue warp
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                              ~(uintptr_t)1023);
-    const Plan pl = plan(d);
+    const Plan pl = plan(d, PPW);
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar = smem_u32(sm + pl.bar0);
@@ -310,9 +332,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
         }
         for (int j = 0; j < 2; ++j) {
             mbar_init(B(B_BFULL + j), 1);
-            mbar_init(B(B_BFREE + j), 1 + kEpiWarps);
+            mbar_init(B(B_BFREE + j), 1);
             mbar_init(B(B_TFULL + j), 1);
-            mbar_init(B(B_TEMPTY + j), kEpiWarps / 2);
+            mbar_init(B(B_TEMPTY + j), kEpiWarps);
         }
         mbar_init(B(B_DRAIN), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -395,9 +417,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                     break;
                 }
                 const uint32_t bhi = smem_u32(sm + pl.b0 + bb * pl.bblock);
-                const uint32_t blo = bhi + pl.bpart;
-                const uint32_t bbeta = blo + pl.bpart;
-                const uint32_t ones = smem_u32(sm + pl.ones0);
+                const uint64_t dbhi = smem_desc(bhi, sbo);
+                const uint64_t dblo = smem_desc(bhi + pl.bpart, sbo);
+                const uint64_t dbeta = smem_desc(bhi + 2 * pl.bpart, 256u);
+                const uint64_t dones = smem_desc(smem_u32(sm + pl.ones0), 256u);
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
                     const int j = (int)(it & 1);
@@ -412,24 +435,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t yhi = smem_u32(sm + pl.y0 + s * tile_bytes);
-                    const uint32_t ylo = yhi + pl.ypart;
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const uint32_t dtm = tbase + (uint32_t)((2 * j + h) * kHalf);
-                        const uint32_t boff = (uint32_t)h * (kHalf / 8) * sbo;
-                        uint32_t acc = 0;
-                        for (int ks = 0; ks < ksteps; ++ks) {
-                            const uint32_t ko = (uint32_t)ks * 256u;
-                            mma_bf16(dtm, smem_desc(yhi + ko, sbo), smem_desc(bhi + boff + ko, sbo), acc);
-                            acc = 1;
-                            mma_bf16(dtm, smem_desc(yhi + ko, sbo), smem_desc(blo + boff + ko, sbo), 1);
-                            mma_bf16(dtm, smem_desc(ylo + ko, sbo), smem_desc(bhi + boff + ko, sbo), 1);
-                        }
-                        // + beta: ones column times the three bf16 parts of beta
-                        mma_bf16(dtm, smem_desc(ones, 256u),
-                                 smem_desc(bbeta + (uint32_t)h * (kHalf / 8) * 256u, 256u), 1);
+                    // descriptors advance along K by 256 B = 16 address units
+                    const uint64_t ahi = smem_desc(smem_u32(sm + pl.y0 + s * tile_bytes), sbo);
+                    const uint64_t alo = ahi + (pl.ypart >> 4);
+                    const uint32_t dtm = tbase + (uint32_t)(j * kBlockCols);
+                    uint32_t acc = 0;
+                    for (int ks = 0; ks < ksteps; ++ks) {
+                        const uint64_t ko = (uint64_t)ks * 16u;
+                        mma_bf16(dtm, ahi + ko, dbhi + ko, acc);
+                        acc = 1;
+                        mma_bf16(dtm, ahi + ko, dblo + ko, 1);
+                        mma_bf16(dtm, alo + ko, dbhi + ko, 1);
                     }
+                    // + beta: ones column times the three bf16 parts of beta
+                    mma_bf16(dtm, dones, dbeta, 1);
                     mma_commit(B(B_EMPTY + s));
                     mma_commit(B(B_TFULL + j));
                 }
@@ -442,101 +461,94 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
         }
     } else {
         // ---------------------------------------------------------- epilogue
+        // warp e reads lanes 32 q.. (q = its tensor-memory lane quarter) and
+        // columns 64 cq.. (cq = e / 4) of every tile: PPW particles.  It copies
+        // them to registers, releases the buffer at once (so the next MMA
+        // group can start), then reduces.
         const int e = warp - 2;
-        const int wg = e >> 2;
-        const int jw = wg >> 1, h = wg & 1;
-        const int q = warp & 3;  // this warp's quarter of the tensor-memory lanes
+        const int q = warp & 3;
+        const int cq = e >> 2;
         int64_t it = 0;
-        int ui = 0;
         bool ok = true;
-        for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
-            const int bb = ui & 1;
+        float* sacc = reinterpret_cast<float*>(sm + pl.acc0) + (threadIdx.x - 64);
+        for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x) {
             const int64_t sp = u % nsplit;
-            Kahan acc[PPH];
-            // per particle (KP = 16): product of the per-datum sums (each in
-            // [1, 16]) and sum of the shifts over up to 16 tiles, then one lg2;
-            // with more particles per thread (KP < 16) one lg2 per datum
-            constexpr bool kProd = KP == 16;
-            constexpr int NPR = kProd ? PPH : 1;
-            float pr[NPR], ms[NPR];
+            // per-thread sums of this unit in shared memory (registers are the
+            // epilogue's limit), sacc[i * 512 + epilogue thread]: a few
+            // flushes of 16 tiles each, so FP32 holds them to ~1e-7
 #pragma unroll
-            for (int i = 0; i < NPR; ++i) { pr[i] = 1.0f; ms[i] = 0.0f; }
+            for (int i = 0; i < PPW; ++i) sacc[i * 32 * kEpiWarps] = 0.0f;
+            // per particle: product of the per-datum sums (each in [1, KP])
+            // and sum of the shifts over up to 16 tiles, then one lg2
+            float pr[PPW], ms[PPW];
+#pragma unroll
+            for (int i = 0; i < PPW; ++i) { pr[i] = 1.0f; ms[i] = 0.0f; }
             int ngroup = 0;
-            if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui >> 1) & 1), abort)) {
-                ok = false;
-                break;
-            }
             const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
             for (int64_t t = t0; t < t1; ++t, ++it) {
                 const int j = (int)(it & 1);
-                if (j != jw) continue;
                 if (!mbar_wait(B(B_TFULL + j), (uint32_t)((it >> 1) & 1), abort)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const bool valid = t * kRows + q * 32 + lane < N;
+                const uint32_t tcol = tbase + ((uint32_t)(q * 32) << 16) +
+                                      (uint32_t)(j * kBlockCols + cq * 64);
+                uint32_t r[4][16];
 #pragma unroll
-                for (int c = 0; c < kHalf / 32; ++c) {
-                    float v[32];  // exponents alpha S + beta of 32 / KP particles
-                    tmem_ld32(tbase + ((uint32_t)(q * 32) << 16) +
-                                  (uint32_t)((2 * j + h) * kHalf + c * 32), v);
+                for (int c = 0; c < 4; ++c) tmem_ld16_async(tcol + (uint32_t)(c * 16), r[c]);
 #pragma unroll
-                    for (int pi = 0; pi < PPL; ++pi) {
-                        const float* a = v + pi * KP;
-                        float m = max3(a[0], a[1], a[2]);
-#pragma unroll
-                        for (int k = 3; k + 1 < KP; k += 2) m = max3(m, a[k], a[k + 1]);
-                        if constexpr ((KP - 3) % 2 == 1) m = fmaxf(m, a[KP - 1]);
-                        const float2 NM = make_float2(-m, -m);
-                        float2 E[KP / 2];
-#pragma unroll
-                        for (int k = 0; k < KP / 2; ++k) {
-                            const float2 x = __fadd2_rn(make_float2(a[2 * k], a[2 * k + 1]), NM);
-                            E[k] = make_float2(ex2(x.x), ex2(x.y));
-                        }
-#pragma unroll
-                        for (int w2 = 1; w2 < KP / 2; w2 <<= 1)
-#pragma unroll
-                            for (int k = 0; k + w2 < KP / 2; k += 2 * w2)
-                                E[k] = __fadd2_rn(E[k], E[k + w2]);
-                        const int ia = c * PPL + pi;
-                        if (valid) {
-                            if constexpr (kProd) {
-                                pr[ia] *= E[0].x + E[0].y;
-                                ms[ia] += m;
-                            } else {
-                                acc[ia].add(m + lg2(E[0].x + E[0].y));
-                            }
-                        }
-                    }
-                }
+                for (int c = 0; c < 4; ++c) tmem_wait(r[c]);
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(B(B_TEMPTY + j));
-                if (kProd && ++ngroup == 16) {  // 16 sums of at most 16 each: below 2^64
+                const bool valid = t * kRows + q * 32 + lane < N;
 #pragma unroll
-                    for (int i = 0; i < NPR; ++i) {
-                        acc[i].add(ms[i] + lg2(pr[i]));
+                for (int ip = 0; ip < PPW; ++ip) {
+                    float a[KP];  // exponents alpha S + beta of one particle
+#pragma unroll
+                    for (int k = 0; k < KP; ++k)
+                        a[k] = __uint_as_float(r[(ip * KP + k) >> 4][(ip * KP + k) & 15]);
+                    float m = max3(a[0], a[1], a[2]);
+#pragma unroll
+                    for (int k = 3; k + 1 < KP; k += 2) m = max3(m, a[k], a[k + 1]);
+                    if constexpr ((KP - 3) % 2 == 1) m = fmaxf(m, a[KP - 1]);
+                    const float2 NM = make_float2(-m, -m);
+                    float2 E[KP / 2];
+#pragma unroll
+                    for (int k = 0; k < KP / 2; ++k) {
+                        const float2 x = __fadd2_rn(make_float2(a[2 * k], a[2 * k + 1]), NM);
+                        E[k] = make_float2(ex2(x.x), ex2(x.y));
+                    }
+#pragma unroll
+                    for (int w2 = 1; w2 < KP / 2; w2 <<= 1)
+#pragma unroll
+                        for (int k = 0; k + w2 < KP / 2; k += 2 * w2)
+                            E[k] = __fadd2_rn(E[k], E[k + w2]);
+                    if (valid) {
+                        pr[ip] *= E[0].x + E[0].y;
+                        ms[ip] += m;
+                    }
+                }
+                if (++ngroup == 16) {  // 16 sums of at most 16 each: below 2^64
+#pragma unroll
+                    for (int i = 0; i < PPW; ++i) {
+                        sacc[i * 32 * kEpiWarps] += ms[i] + lg2(pr[i]);
                         pr[i] = 1.0f;
                         ms[i] = 0.0f;
                     }
                     ngroup = 0;
                 }
             }
-            if constexpr (kProd) {
-#pragma unroll
-                for (int i = 0; i < NPR; ++i) acc[i].add(ms[i] + lg2(pr[i]));
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(B(B_BFREE + bb));  // done with this unit's beta
             if (!ok) break;
-            // per-particle sums over the warp's lanes; the 8 warps of each half
-            // are added by k_dtc_combine in a fixed order
-            double* dst = partial + ((size_t)u * kEpiWarps + e) * PPH;
 #pragma unroll
-            for (int i = 0; i < PPH; ++i) {
-                const double vsum = warp_sum_d((double)acc[i].s - (double)acc[i].c);
+            for (int i = 0; i < PPW; ++i) sacc[i * 32 * kEpiWarps] += ms[i] + lg2(pr[i]);
+            // per-particle sums over the warp's lanes; the 4 warps of each
+            // column quarter are added by k_dtc_combine in a fixed order
+            double* dst = partial + ((size_t)u * kEpiWarps + e) * PPW;
+#pragma unroll
+            for (int i = 0; i < PPW; ++i) {
+                const double vsum = warp_sum_d((double)sacc[i * 32 * kEpiWarps]);
                 if (lane == 0) dst[i] = vsum;
             }
         }
@@ -552,7 +564,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
 }
 
 // l_p = ln2 (sum over the units and warps of p - sum_n gamma_n) + N c0,
-// added in a fixed order (splits, then the 8 warps of p's half)
+// added in a fixed order (splits, then the 4 warps of p's column quarter)
 __global__ void __launch_bounds__(256) k_dtc_combine(const double* __restrict__ partial,
                                                      int nsplit, int kp, int64_t M,
                                                      const double* __restrict__ gpart, int ngpart,
@@ -570,15 +582,14 @@ __global__ void __launch_bounds__(256) k_dtc_combine(const double* __restrict__ 
     const double gamma = half_alpha * red[0];
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= M) return;
-    const int ppb = kBlockCols / kp, pph = kHalf / kp;
+    const int ppb = kBlockCols / kp, ppw = 64 / kp;
     const int64_t pb = p / ppb;
     const int ib = (int)(p % ppb);
-    const int h = ib / pph, i = ib % pph;
+    const int cq = ib / ppw, i = ib % ppw;
     double s = 0.0;
     for (int sp = 0; sp < nsplit; ++sp) {
-        const double* base = partial + ((size_t)(pb * nsplit + sp) * kEpiWarps) * pph;
-        for (int e = 0; e < kEpiWarps; ++e)
-            if (((e >> 2) & 1) == h) s += base[(size_t)e * pph + i];
+        const double* base = partial + ((size_t)(pb * nsplit + sp) * kEpiWarps) * ppw;
+        for (int w = 0; w < 4; ++w) s += base[(size_t)(4 * cq + w) * ppw + i];
     }
     const double ll = (s - gamma) * kLn2 + ncst;
     if (ll != ll) raise_status(status, ST_NONFINITE);
@@ -597,6 +608,9 @@ smc_status launch_main(const smc_ctx* ctx, int64_t grid, size_t smem, const uint
                        const uint8_t* bt, int64_t N, int d, int64_t ntiles, int nsplit,
                        int64_t units, double* partial, cudaStream_t s) {
     auto kern = smc::dtc::k_dtc_main<KP>;
+    cudaFuncAttributes fa;
+    SMC_CUDA(cudaFuncGetAttributes(&fa, kern));
+    if (fa.maxThreadsPerBlock < smc::dtc::kThreads) return SMC_ERR_UNSUPPORTED;
     SMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)grid, smc::dtc::kThreads, smem, s>>>(yt, bt, N, d, ntiles, nsplit, units,
                                                          partial, ctx->d_status);
@@ -619,7 +633,7 @@ size_t smc_diag_tc_ws_bytes(int64_t N, int64_t M, int K, int d, int sms) {
     b += align_up((size_t)ntiles * 2 * kRows * d * 2, 1024);
     b += align_up((size_t)nblocks * (2 * kBlockCols * d * 2 + kBetaPart), 1024);
     b += align_up((size_t)gblocks * 8, 1024);
-    b += align_up((size_t)units * kEpiWarps * (kHalf / KP) * 8, 1024);
+    b += align_up((size_t)units * kEpiWarps * (64 / KP) * 8, 1024);
     return b;
 }
 
@@ -659,7 +673,7 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
     k_dtc_prep_mu<<<(unsigned)((nblocks * kBlockCols + 255) / 256), 256, 0, s>>>(
         theta, M, K, KP, d, nblocks, (float)alpha, lw2, bt);
     SMC_CUDA(cudaGetLastError());
-    const Plan pl = plan(d);
+    const Plan pl = plan(d, 64 / KP);
     // + alignment slack; at least half an SM's shared memory so that one CTA
     // (and one 512-column tensor-memory allocation) runs per SM
     size_t smem = pl.total + 1024;
