@@ -19,8 +19,11 @@
 
 using namespace smc_host;
 
+// scratch of the context entry point: tile and group sums, the heavy-chunk
+// counter and records, and the inclusive F of heavy tiles' items
 size_t smc_resample_ws_bytes(int64_t M) {
-    return (size_t)smc::rs_words(M) * sizeof(unsigned long long) + 256;
+    return (size_t)(smc::rs_words(M) + 1) * sizeof(unsigned long long) +
+           (size_t)smc::rs_heavy_records(M) * sizeof(uint4) + (size_t)M * sizeof(uint32_t) + 512;
 }
 
 namespace smc {
@@ -47,23 +50,41 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s) {
     const int64_t tiles = smc::rs_tiles(M);
     if (tiles > 0x7FFFFFFF) return SMC_ERR_ARG;
-    // the group sums must start at zero
+    // the group sums (and the heavy-chunk counter right after them) must
+    // start at zero
     SMC_CUDA(cudaMemsetAsync(sc.group_sum, 0,
-                             (size_t)smc::rs_groups(M) * sizeof(unsigned long long), s));
+                             (size_t)(smc::rs_groups(M) + (sc.heavy_count ? 1 : 0)) *
+                                 sizeof(unsigned long long), s));
     int64_t b1 = tiles;
     if (b1 > (int64_t)num_sms * 4) b1 = (int64_t)num_sms * 4;
     smc::k_resample_total<<<(unsigned)b1, smc::kRsThreads, 0, s>>>(W, M, do_flag, sc, status);
     SMC_CUDA(cudaGetLastError());
     smc::k_resample_scan<<<(unsigned)tiles, smc::kRsThreads, 0, s>>>(
         W, M, seed, step, do_flag, sc, anc, counts, lwreset, status);
-    return cuda_ok(cudaGetLastError());
+    SMC_CUDA(cudaGetLastError());
+    if (sc.heavy_list) {
+        smc::k_resample_heavy<<<(unsigned)num_sms * 4, smc::kRsThreads, 0, s>>>(do_flag, sc, M, anc);
+        SMC_CUDA(cudaGetLastError());
+    }
+    return SMC_OK;
 }
 
-// scratch layout inside `base`: tile sums, then group sums
-smc::RsScratch resample_scratch(unsigned long long* base, int64_t M) {
+// scratch layout inside `base`: tile sums, group sums, then (when `heavy`)
+// the heavy-chunk counter, the chunk records and the items' inclusive F
+smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy) {
     smc::RsScratch sc;
     sc.tile_sum = base;
     sc.group_sum = base + smc::rs_tiles(M);
+    sc.heavy_count = nullptr;
+    sc.heavy_list = nullptr;
+    sc.fpos = nullptr;
+    if (heavy) {
+        sc.heavy_count = sc.group_sum + smc::rs_groups(M);
+        uintptr_t p = reinterpret_cast<uintptr_t>(sc.heavy_count + 1);
+        p = (p + 255) & ~(uintptr_t)255;
+        sc.heavy_list = reinterpret_cast<uint4*>(p);
+        sc.fpos = reinterpret_cast<uint32_t*>(sc.heavy_list + smc::rs_heavy_records(M));
+    }
     return sc;
 }
 
@@ -82,7 +103,8 @@ extern "C" smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int
     cudaStream_t s = as_stream(stream);
     st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
     if (st != SMC_OK) return st;
-    const smc::RsScratch sc = resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M);
+    const smc::RsScratch sc =
+        resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
     return resample_launch(ctx->num_sms, W, M, seed, step, ancestors_out, counts_out, do_flag,
                            logw_reset, sc, ctx->d_status, s);
 }
@@ -163,7 +185,8 @@ extern "C" smc_status smc_resample_systematic_noalloc(const double* W, int64_t M
     cudaStream_t s = as_stream(stream);
     // resample_launch clears the group sums before pass 1; pass 1
     // overwrites every tile sum it uses
-    const smc::RsScratch sc = resample_scratch(scratch, M);
+    // no heavy-chunk scratch: a tile with many slots is expanded by its CTA
+    const smc::RsScratch sc = resample_scratch(scratch, M, false);
     return resample_launch(sms, W, M, seed, step, ancestors_out, counts_out, do_flag, logw_reset,
                            sc, status_out, s);
 }

@@ -21,10 +21,16 @@ constexpr int kRsIpt = 8;                      // weights per thread
 constexpr int kRsTile = kRsThreads * kRsIpt;   // weights per tile
 constexpr int kRsGroup = 64;                   // tiles per group sum
 constexpr unsigned long long kMaxTotal = 1ull << 61;   // S must stay below this
+constexpr int kRsStage = 2 * kRsTile;          // output slots of a tile staged in shared memory
 
 struct RsScratch {
     unsigned long long* tile_sum;   // [ntiles]
     unsigned long long* group_sum;  // [ceil(ntiles / kRsGroup)], zero before pass 1
+    // grid-wide expansion of tiles with many output slots (optional: when
+    // null, such a tile is expanded by its own CTA)
+    unsigned long long* heavy_count;  // chunk records written, zero before pass 2
+    uint4* heavy_list;                // {tile, tile's first slot, chunk begin, chunk end}
+    uint32_t* fpos;                   // [M] inclusive F of the items of heavy tiles
 };
 
 __host__ __device__ inline int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1) / kRsTile; }
@@ -33,6 +39,12 @@ __host__ __device__ inline int64_t rs_groups(int64_t M) {
 }
 // words of scratch for M weights: tile sums, group sums
 __host__ __device__ inline int64_t rs_words(int64_t M) { return rs_tiles(M) + rs_groups(M); }
+// output slots of one heavy-expansion chunk, and the most chunk records M
+// weights can produce (a tile's range is split into chunks; ranges add to M)
+constexpr int kRsChunk = 4096;
+__host__ __device__ inline int64_t rs_heavy_records(int64_t M) {
+    return rs_tiles(M) + M / kRsChunk + 1;
+}
 
 // floor(w 2^52) from the bits of w in [0,1]; false if w is outside [0,1] or NaN
 __device__ __forceinline__ bool quantise(double w, unsigned long long& q) {
@@ -133,18 +145,12 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __r
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, ST_BADARG);
 }
 
-// 128-bit unsigned arithmetic for the exact slot test
+// 128-bit unsigned arithmetic for the exact quotient fix-up
 struct U128 {
     unsigned long long lo, hi;
 };
 __device__ __forceinline__ U128 mul64(unsigned long long a, unsigned long long b) {
     return U128{a * b, __umul64hi(a, b)};
-}
-__device__ __forceinline__ U128 add128(U128 a, U128 b) {
-    U128 r;
-    r.lo = a.lo + b.lo;
-    r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
-    return r;
 }
 __device__ __forceinline__ U128 sub128(U128 a, U128 b) {
     U128 r;
@@ -156,93 +162,33 @@ __device__ __forceinline__ bool lt128(U128 a, U128 b) {
     return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
 }
 
-// Slot i lies strictly below the CDF value c iff
-//   A_i = (i 2^32 + u32) S  <  X = c M 2^32.
-// A walker keeps A_i for its current i, so a step to i +- 1 is one 128-bit
-// addition of S 2^32, and F(c) = the first i with A_i >= X (or M).
-struct SlotWalker {
-    U128 step;          // S 2^32
-    uint32_t M;
-    uint32_t i;         // current slot
-    U128 A;             // (i 2^32 + u32) S
-    __device__ __forceinline__ void init(unsigned long long S, uint32_t u32, uint32_t Mv,
-                                         uint32_t i0) {
-        step = U128{S << 32, S >> 32};
-        M = Mv;
-        i = i0;
-        A = mul64(((unsigned long long)i0 << 32) | u32, S);
-    }
-    // move to slot j (a 32 x 128-bit multiply-add)
-    __device__ __forceinline__ void jump(uint32_t j) {
-        if (j >= i) {
-            const U128 d = mul64((unsigned long long)(j - i) << 32, S_of());
-            A = add128(A, d);
-        } else {
-            const U128 d = mul64((unsigned long long)(i - j) << 32, S_of());
-            A = sub128(A, d);
-        }
-        i = j;
-    }
-    __device__ __forceinline__ unsigned long long S_of() const {
-        return (step.lo >> 32) | (step.hi << 32);
-    }
-    // F(X) for X at or above the X of the current slot's F: only steps up
-    // (the merge walk of slots against a non-decreasing CDF)
-    __device__ __forceinline__ uint32_t walk_up(U128 X) {
-        while (i < M && lt128(A, X)) {
-            A = add128(A, step);
-            ++i;
-        }
-        return i;
-    }
-    // F(X): first slot whose A is not below X, starting near the current slot
-    __device__ __forceinline__ uint32_t first_not_below(U128 X) {
-        if (i < M && lt128(A, X)) {                       // walk up
-            for (int it = 0; it < 64; ++it) {
-                A = add128(A, step);
-                ++i;
-                if (i == M || !lt128(A, X)) return i;
-            }
-        } else {                                          // walk down
-            for (int it = 0; it < 64; ++it) {
-                if (i == 0) return 0;
-                const U128 Ap = sub128(A, step);
-                if (lt128(Ap, X)) return i;
-                A = Ap;
-                --i;
-            }
-        }
-        // far from the estimate: bisection on the exact test
-        uint32_t lo = 0, hi = M;
-        while (lo < hi) {
-            const uint32_t mid = lo + (hi - lo) / 2;
-            jump(mid);
-            if (lt128(A, X)) lo = mid + 1;
-            else hi = mid;
-        }
-        jump(lo);
-        return lo;
-    }
-};
+// Slot i lies strictly below the CDF value c iff (i + u) S < c M, with
+// u = u32 / 2^32.  Writing c M = Q S + R (0 <= R < S):
+//   F(c) = #{i >= 0 : (i + u) S < c M} = Q + [R 2^32 > u32 S] = Q + [R > Rth],
+//   Rth = floor(u32 S / 2^32)
+// (R integer: R 2^32 > X  <=>  R > floor(X / 2^32)).  Advancing c by an item's
+// q adds q M to R and carries whole S into Q.
 
-// float -> int by its bits, truncated toward zero, 0 below 1, at most
-// 2^30 (estimates only)
-__device__ __forceinline__ int est_int(float v) {
-    if (!(v >= 1.0f)) return 0;
-    const uint32_t b = __float_as_uint(v);
-    int e = (int)(b >> 23) - 127;
-    if (e > 30) return 1 << 30;
-    const uint32_t m = (b & 0x7FFFFFu) | 0x800000u;
-    return (int)(e >= 23 ? (m << (e - 23)) : (m >> (23 - e)));
-}
-
-// uint64 -> float from 16-bit pieces (exact pieces, a few roundings;
-// estimates only)
-__device__ __forceinline__ float u32_to_f(uint32_t x) {
-    return fmaf(u23_to_f(x >> 16), 65536.0f, u23_to_f(x & 0xFFFFu));
-}
-__device__ __forceinline__ float u64_to_f(unsigned long long v) {
-    return fmaf(u32_to_f((uint32_t)(v >> 32)), 4294967296.0f, u32_to_f((uint32_t)v));
+// c M = Q S + R exactly (c <= S < 2^61, M < 2^31): FP64 estimate of Q,
+// then an exact 128-bit fix-up
+__device__ __forceinline__ void divmod_cm(unsigned long long c, unsigned long long M,
+                                          unsigned long long S, double m_over_s,
+                                          unsigned long long& Q, unsigned long long& R) {
+    const double qe = floor((double)c * m_over_s);
+    unsigned long long q = qe > 0.0 ? (unsigned long long)qe : 0ull;
+    const U128 P = mul64(c, M);
+    U128 QS = mul64(q, S);
+    for (int it = 0; it < 64 && lt128(P, QS); ++it) {  // estimate too high
+        --q;
+        QS = sub128(QS, U128{S, 0ull});
+    }
+    U128 r = sub128(P, QS);
+    for (int it = 0; it < 64 && (r.hi != 0 || r.lo >= S); ++it) {  // too low
+        ++q;
+        r = sub128(r, U128{S, 0ull});
+    }
+    Q = q;
+    R = r.lo;
 }
 
 // Pass 2: one CTA per tile.
@@ -251,10 +197,13 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_scan(
     const int32_t* do_flag, RsScratch sc, int32_t* __restrict__ anc,
     int32_t* __restrict__ counts, double* __restrict__ lwreset, uint32_t* status) {
     __shared__ uint32_t s_hi[kRsTile];            // F at each item's inclusive prefix
+    __shared__ int32_t s_anc[kRsStage];           // the tile's ancestors, staged for coalesced stores
     __shared__ unsigned long long s_warp[kRsThreads / 32];
     __shared__ unsigned long long s_pre[kRsThreads / 32];
     __shared__ unsigned long long s_tot[kRsThreads / 32];
     __shared__ uint32_t s_lo;
+    __shared__ double s_mos;
+    __shared__ unsigned long long s_qh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t tile = blockIdx.x;
     const int64_t base = tile * kRsTile;
@@ -320,50 +269,72 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_scan(
         if (tid == 0 && tile == 0) raise_status(status, S == 0 && !ovf2 ? ST_ZERO_WEIGHT : ST_BADARG);
         return;
     }
-    // ---- F at every prefix of this thread's items (exact, 128-bit walker)
+    // ---- F at every prefix of this thread's items: c M = Q S + R, carried
+    // item by item (items with q M above about 7 S are divided afresh)
     const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
-    const unsigned long long MM = (unsigned long long)M << 32;
+    const unsigned long long MM = (unsigned long long)M;
+    const unsigned long long Rth = __umul64hi((unsigned long long)u32 << 32, S);  // u32 S / 2^32
+    if (tid == 0) {  // FP64 is scarce on this GPU: once per block
+        s_mos = (double)MM / (double)S;
+        // R + q M < 8 S + S < 2^64 while S < 2^60 (else every item is divided)
+        s_qh = S < (1ull << 60) ? (unsigned long long)(7.0 * (double)S / (double)MM) : 0ull;
+    }
+    __syncthreads();
+    const double m_over_s = s_mos;
+    const unsigned long long qheavy = s_qh;
     unsigned long long c = excl + woff + (incl - tsum);  // C before this thread's item 0
-    // M / S in FP32 (S < 2^61): estimate of the slots below c, fixed up exactly
-    const float ms = u64_to_f((unsigned long long)M) / u64_to_f(S);
-    const float u = u32_to_f(u32) * 2.3283064365386963e-10f;
-    U128 X = mul64(c, MM);
-    SlotWalker wk;
-    int e0 = est_int(u64_to_f(c) * ms - u) + 1;
-    if (e0 > (int)M) e0 = (int)M;
-    wk.init(S, u32, (uint32_t)M, (uint32_t)e0);
-    uint32_t F = wk.first_not_below(X);
+    unsigned long long Q, R;
+    divmod_cm(c, MM, S, m_over_s, Q, R);
+    uint32_t F = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
     if (tid == 0) s_lo = F;
-    // items expected to own more than 16 slots jump by an estimate; the
-    // others advance the walker one slot at a time (128-bit add + compare)
-    const float qthr_f = 16.0f / ms;
 #pragma unroll
     for (int j = 0; j < kRsIpt; ++j) {
-        const int64_t g = base + (int64_t)tid * kRsIpt + j;
-        uint32_t Fn = F;
-        if (q[j]) {
-            X = add128(X, mul64(q[j], MM));
-            const float qf = u64_to_f(q[j]);
-            if (qf > qthr_f) {
-                long long e = (long long)F + est_int(qf * ms);
-                if (e > (long long)M) e = M;
-                if ((uint32_t)e != wk.i) wk.jump((uint32_t)e);
-                Fn = wk.first_not_below(X);
-            } else {
-                Fn = wk.walk_up(X);
+        c += q[j];
+        if (q[j] > qheavy) {
+            divmod_cm(c, MM, S, m_over_s, Q, R);
+        } else {
+            R += q[j] * MM;  // q M <= 7 S (+ rounding): no wrap, at most 8 carries
+            for (int it = 0; it < 16 && R >= S; ++it) {
+                R -= S;
+                ++Q;
             }
         }
+        uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+        if (Fn > (uint32_t)M) Fn = (uint32_t)M;
         s_hi[tid * kRsIpt + j] = Fn;
-        if (g < M) {
-            if (counts) counts[g] = (int32_t)(Fn - F);
-            if (lwreset) lwreset[g] = 0.0;
-        }
         F = Fn;
     }
     __syncthreads();
-    // ---- expand the tile's output range [s_lo, s_hi[last]) (blocked per thread)
+    // ---- offspring counts and the log-weight reset, item-major (coalesced)
     const uint32_t lo = s_lo, hi = s_hi[kRsTile - 1];
+    for (int j = tid; j < kRsTile; j += kRsThreads) {
+        const int64_t g = base + j;
+        if (g < M) {
+            if (counts) counts[g] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
+            if (lwreset) lwreset[g] = 0.0;
+        }
+    }
+    // ---- expand the tile's output range [lo, hi): each thread a contiguous
+    // block of slots; staged in shared memory and stored slot-major when the
+    // range fits (the usual case).  A larger range (heavy weights) is split
+    // into chunks for k_resample_heavy, which all CTAs share; without that
+    // scratch the CTA stores it directly.
     const uint32_t range = hi - lo;
+    const bool staged = range <= (uint32_t)kRsStage;
+    if (!staged && sc.heavy_list) {  // uniform over the block
+        for (int j = tid; j < kRsTile; j += kRsThreads)
+            if (base + j < M) sc.fpos[base + j] = s_hi[j];
+        if (tid == 0) {
+            const uint32_t nch = (range + kRsChunk - 1) / kRsChunk;
+            const unsigned long long r0 = atomicAdd(sc.heavy_count, (unsigned long long)nch);
+            for (uint32_t k = 0; k < nch; ++k) {
+                const uint32_t b = lo + k * kRsChunk;
+                const uint32_t e = b + kRsChunk < hi ? b + kRsChunk : hi;
+                sc.heavy_list[r0 + k] = make_uint4((uint32_t)tile, lo, b, e);
+            }
+        }
+        return;
+    }
     const uint32_t per = (range + kRsThreads - 1) / kRsThreads;
     const uint32_t s0 = lo + (uint32_t)tid * per;
     const uint32_t s1 = s0 + per < hi ? s0 + per : hi;
@@ -377,8 +348,49 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_scan(
         int item = a;
         for (uint32_t sl = s0; sl < s1; ++sl) {
             while (s_hi[item] <= sl) ++item;
-            anc[sl] = (int32_t)(base + item);
+            if (staged) s_anc[sl - lo] = (int32_t)(base + item);
+            else anc[sl] = (int32_t)(base + item);
         }
+    }
+    if (staged) {  // uniform over the block
+        __syncthreads();
+        for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
+    }
+}
+
+// Pass 3: the chunks of heavy tiles, shared by all CTAs (grid-stride).  A
+// chunk's first item is found by bisection on the tile's inclusive F
+// values; its slots are staged in shared memory and stored slot-major.
+__global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
+    const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc) {
+    if (do_flag && *do_flag == 0) return;
+    __shared__ int32_t s_anc[kRsChunk];
+    const unsigned long long n = __ldcg(sc.heavy_count);
+    for (unsigned long long r = blockIdx.x; r < n; r += gridDim.x) {
+        const uint4 rec = sc.heavy_list[r];
+        const int64_t base = (int64_t)rec.x * kRsTile;
+        const int nit = (int)(M - base < kRsTile ? M - base : kRsTile);
+        const uint32_t* f = sc.fpos + base;
+        const uint32_t b = rec.z, e = rec.w;
+        const uint32_t per = (e - b + kRsThreads - 1) / kRsThreads;
+        const uint32_t s0 = b + (uint32_t)threadIdx.x * per;
+        const uint32_t s1 = s0 + per < e ? s0 + per : e;
+        if (s0 < s1) {
+            int a = 0, hi = nit - 1;  // first item whose inclusive F exceeds s0
+            while (a < hi) {
+                const int mid = (a + hi) >> 1;
+                if (f[mid] > s0) hi = mid;
+                else a = mid + 1;
+            }
+            int item = a;
+            for (uint32_t sl = s0; sl < s1; ++sl) {
+                while (f[item] <= sl) ++item;
+                s_anc[sl - b] = (int32_t)(base + item);
+            }
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < e - b; k += kRsThreads) anc[b + k] = s_anc[k];
+        __syncthreads();
     }
 }
 
