@@ -50,14 +50,17 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s) {
     const int64_t tiles = smc::rs_tiles(M);
     if (tiles > 0x7FFFFFFF) return SMC_ERR_ARG;
-    // the group sums (and the heavy-chunk counter right after them) must
-    // start at zero
+    // the group sums (and the constants and heavy-chunk counter after them)
+    // must start at zero
     SMC_CUDA(cudaMemsetAsync(sc.group_sum, 0,
-                             (size_t)(smc::rs_groups(M) + (sc.heavy_count ? 1 : 0)) *
+                             (size_t)(smc::rs_groups(M) + smc::kRsConstWords +
+                                      (sc.heavy_count ? 1 : 0)) *
                                  sizeof(unsigned long long), s));
     int64_t b1 = tiles;
     if (b1 > (int64_t)num_sms * 4) b1 = (int64_t)num_sms * 4;
     smc::k_resample_total<<<(unsigned)b1, smc::kRsThreads, 0, s>>>(W, M, do_flag, sc, status);
+    SMC_CUDA(cudaGetLastError());
+    smc::k_resample_finalize<<<1, smc::kRsFinThreads, 0, s>>>(M, seed, step, do_flag, sc, status);
     SMC_CUDA(cudaGetLastError());
     smc::k_resample_scan<<<(unsigned)tiles, smc::kRsThreads, 0, s>>>(
         W, M, seed, step, do_flag, sc, anc, counts, lwreset, status);
@@ -75,11 +78,12 @@ smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy)
     smc::RsScratch sc;
     sc.tile_sum = base;
     sc.group_sum = base + smc::rs_tiles(M);
+    sc.cst = reinterpret_cast<smc::RsConst*>(sc.group_sum + smc::rs_groups(M));
     sc.heavy_count = nullptr;
     sc.heavy_list = nullptr;
     sc.fpos = nullptr;
     if (heavy) {
-        sc.heavy_count = sc.group_sum + smc::rs_groups(M);
+        sc.heavy_count = sc.group_sum + smc::rs_groups(M) + smc::kRsConstWords;
         uintptr_t p = reinterpret_cast<uintptr_t>(sc.heavy_count + 1);
         p = (p + 255) & ~(uintptr_t)255;
         sc.heavy_list = reinterpret_cast<uint4*>(p);
@@ -139,9 +143,12 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 namespace {
 
 constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;   // 16,777,216 weights
-// 8192 tile sums + 128 group sums (+ spare words): about 65 KiB per device
+// 8192 tile sums + 128 group sums + the call constants: about 65 KiB per device
 constexpr int64_t kNoAllocWords = (kNoAllocMaxM / smc::kRsTile) +
-                                  (kNoAllocMaxM / smc::kRsTile / smc::kRsGroup) + 8;
+                                  (kNoAllocMaxM / smc::kRsTile / smc::kRsGroup) +
+                                  smc::kRsConstWords;
+static_assert(sizeof(smc::RsConst) <= smc::kRsConstWords * sizeof(unsigned long long),
+              "constants fit their words");
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
 
 std::mutex g_noalloc_mu;

@@ -23,9 +23,21 @@ constexpr int kRsGroup = 64;                   // tiles per group sum
 constexpr unsigned long long kMaxTotal = 1ull << 61;   // S must stay below this
 constexpr int kRsStage = 2 * kRsTile;          // output slots of a tile staged in shared memory
 
+// constants of one resampling call, formed once by k_resample_finalize
+struct RsConst {
+    unsigned long long S;       // exact total of the quantised weights
+    unsigned long long Rth;     // floor(u32 S / 2^32)
+    unsigned long long qheavy;  // items with q above this are divided afresh
+    double m_over_s;            // M / S (estimates of quotients)
+    float inv_s;                // 1 / S (estimates of carries)
+    uint32_t ok;                // 0: nothing to resample (status already raised)
+};
+constexpr int kRsConstWords = 8;
+
 struct RsScratch {
-    unsigned long long* tile_sum;   // [ntiles]
+    unsigned long long* tile_sum;   // [ntiles]: tile sums, then their exclusive prefixes
     unsigned long long* group_sum;  // [ceil(ntiles / kRsGroup)], zero before pass 1
+    RsConst* cst;                   // after the group sums
     // grid-wide expansion of tiles with many output slots (optional: when
     // null, such a tile is expanded by its own CTA)
     unsigned long long* heavy_count;  // chunk records written, zero before pass 2
@@ -37,8 +49,10 @@ __host__ __device__ inline int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1
 __host__ __device__ inline int64_t rs_groups(int64_t M) {
     return (rs_tiles(M) + kRsGroup - 1) / kRsGroup;
 }
-// words of scratch for M weights: tile sums, group sums
-__host__ __device__ inline int64_t rs_words(int64_t M) { return rs_tiles(M) + rs_groups(M); }
+// words of scratch for M weights: tile sums, group sums, constants
+__host__ __device__ inline int64_t rs_words(int64_t M) {
+    return rs_tiles(M) + rs_groups(M) + kRsConstWords;
+}
 // output slots of one heavy-expansion chunk, and the most chunk records M
 // weights can produce (a tile's range is split into chunks; ranges add to M)
 constexpr int kRsChunk = 4096;
@@ -171,7 +185,7 @@ __device__ __forceinline__ bool lt128(U128 a, U128 b) {
 
 // c M = Q S + R exactly (c <= S < 2^61, M < 2^31): FP64 estimate of Q,
 // then an exact 128-bit fix-up
-__device__ __forceinline__ void divmod_cm(unsigned long long c, unsigned long long M,
+__device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long M,
                                           unsigned long long S, double m_over_s,
                                           unsigned long long& Q, unsigned long long& R) {
     const double qe = floor((double)c * m_over_s);
@@ -191,19 +205,93 @@ __device__ __forceinline__ void divmod_cm(unsigned long long c, unsigned long lo
     R = r.lo;
 }
 
+// Between the passes, one CTA: the exact total S from the group sums, the
+// call's uniform and constants, and every tile's exclusive prefix (the tile
+// sums are replaced in place), so that no tile of pass 2 repeats this work.
+constexpr int kRsFinThreads = 1024;
+__global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
+    int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc,
+    uint32_t* status) {
+    if (do_flag && *do_flag == 0) return;
+    __shared__ unsigned long long s_w[kRsFinThreads / 32];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int64_t ntiles = rs_tiles(M);
+    if (tid == 0) s_bad = 0;
+    __syncthreads();
+    // each thread scans a contiguous run of tile sums
+    const int64_t per = (ntiles + kRsFinThreads - 1) / kRsFinThreads;
+    const int64_t t0 = (int64_t)tid * per;
+    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+    unsigned long long own = 0;
+    bool ovf = false;
+    for (int64_t t = t0; t < t1; ++t) {
+        const unsigned long long n = own + __ldcg(sc.tile_sum + t);
+        ovf |= n < own;
+        own = n;
+    }
+    // block exclusive scan of the runs
+    unsigned long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) {
+            ovf |= incl + v < incl;
+            incl += v;
+        }
+    }
+    if (lane == 31) s_w[wid] = incl;
+    if (ovf) s_bad = 1;
+    __syncthreads();
+    unsigned long long off = 0, S = 0;
+    bool ovf2 = s_bad != 0;
+    for (int w = 0; w < kRsFinThreads / 32; ++w) {
+        if (w < wid) off += s_w[w];
+        const unsigned long long n = S + s_w[w];
+        ovf2 |= n < S;
+        S = n;
+    }
+    unsigned long long run = off + incl - own;
+    for (int64_t t = t0; t < t1; ++t) {
+        const unsigned long long v = __ldcg(sc.tile_sum + t);
+        sc.tile_sum[t] = run;
+        run += v;
+    }
+    if (tid == 0) {
+        RsConst c;
+        c.ok = 0;
+        if (S == 0 || S >= kMaxTotal || ovf2) {
+            raise_status(status, S == 0 && !ovf2 ? ST_ZERO_WEIGHT : ST_BADARG);
+        } else {
+            const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
+            const unsigned long long MM = (unsigned long long)M;
+            c.S = S;
+            c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
+            c.m_over_s = (double)MM / (double)S;
+            // R + q M < 8 S + S < 2^64 while S < 2^60 (else every item is divided)
+            c.qheavy = S < (1ull << 60) ? (unsigned long long)(7.0 * (double)S / (double)MM) : 0ull;
+            c.inv_s = 1.0f / __ull2float_rn(S);
+            c.ok = 1;
+        }
+        *sc.cst = c;
+    }
+}
+
+// Minimum resident blocks per SM asked of the register allocator for the
+// scan (compile-time tuning knob).
+#ifndef SMC_RS_MINB
+#define SMC_RS_MINB 5
+#endif
+
 // Pass 2: one CTA per tile.
-__global__ void __launch_bounds__(kRsThreads) k_resample_scan(
+__global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
     const double* __restrict__ W, int64_t M, uint64_t seed, uint64_t step,
     const int32_t* do_flag, RsScratch sc, int32_t* __restrict__ anc,
     int32_t* __restrict__ counts, double* __restrict__ lwreset, uint32_t* status) {
     __shared__ uint32_t s_hi[kRsTile];            // F at each item's inclusive prefix
     __shared__ int32_t s_anc[kRsStage];           // the tile's ancestors, staged for coalesced stores
     __shared__ unsigned long long s_warp[kRsThreads / 32];
-    __shared__ unsigned long long s_pre[kRsThreads / 32];
-    __shared__ unsigned long long s_tot[kRsThreads / 32];
     __shared__ uint32_t s_lo;
-    __shared__ double s_mos;
-    __shared__ unsigned long long s_qh;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t tile = blockIdx.x;
     const int64_t base = tile * kRsTile;
@@ -218,110 +306,112 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_scan(
         }
         return;
     }
-    // ---- total S and this tile's exclusive prefix from the group / tile sums
-    const int64_t ngroups = rs_groups(M);
-    const int64_t grp = tile / kRsGroup;
-    unsigned long long tot = 0, pre = 0;
-    bool ovf = false;
-    for (int64_t i = tid; i < ngroups; i += kRsThreads) {
-        const unsigned long long v = __ldcg(sc.group_sum + i);
-        const unsigned long long n = tot + v;
-        ovf |= n < tot;
-        tot = n;
-        if (i < grp) pre += v;
-    }
-    for (int64_t i = grp * kRsGroup + tid; i < tile; i += kRsThreads) pre += __ldcg(sc.tile_sum + i);
+    // ---- the call's constants and this tile's exclusive prefix (finalize)
+    const RsConst cst = *sc.cst;
+    if (!cst.ok) return;
+    const unsigned long long S = cst.S;
+    const unsigned long long tpre = __ldcg(sc.tile_sum + tile);
     // ---- this thread's items
     unsigned long long q[kRsIpt];
     load_tile_items(W, M, tile, q);  // pass 1 already reported bad weights
     unsigned long long tsum = 0;
 #pragma unroll
     for (int j = 0; j < kRsIpt; ++j) tsum += q[j];
-    // ---- block scan of the thread sums; block sums of the prefix and total
+    // ---- block exclusive scan of the thread sums
     unsigned long long incl = tsum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
         if (lane >= o) incl += v;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        pre += __shfl_xor_sync(0xFFFFFFFFu, pre, o);
-        const unsigned long long t2 = __shfl_xor_sync(0xFFFFFFFFu, tot, o);
-        const unsigned long long n = tot + t2;
-        ovf |= n < tot;
-        tot = n;
-    }
     if (lane == 31) s_warp[wid] = incl;
-    if (lane == 0) { s_pre[wid] = pre; s_tot[wid] = tot; }
-    const bool any_ovf = __syncthreads_or(ovf);
-    unsigned long long woff = 0, excl = 0, S = 0;
-    bool ovf2 = any_ovf;
+    __syncthreads();
+    unsigned long long woff = 0;
 #pragma unroll
-    for (int w = 0; w < kRsThreads / 32; ++w) {
+    for (int w = 0; w < kRsThreads / 32; ++w)
         if (w < wid) woff += s_warp[w];
-        excl += s_pre[w];
-        const unsigned long long n = S + s_tot[w];
-        ovf2 |= n < S;
-        S = n;
-    }
-    if (S == 0 || S >= kMaxTotal || ovf2) {
-        if (tid == 0 && tile == 0) raise_status(status, S == 0 && !ovf2 ? ST_ZERO_WEIGHT : ST_BADARG);
-        return;
-    }
     // ---- F at every prefix of this thread's items: c M = Q S + R, carried
     // item by item (items with q M above about 7 S are divided afresh)
-    const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
     const unsigned long long MM = (unsigned long long)M;
-    const unsigned long long Rth = __umul64hi((unsigned long long)u32 << 32, S);  // u32 S / 2^32
-    if (tid == 0) {  // FP64 is scarce on this GPU: once per block
-        s_mos = (double)MM / (double)S;
-        // R + q M < 8 S + S < 2^64 while S < 2^60 (else every item is divided)
-        s_qh = S < (1ull << 60) ? (unsigned long long)(7.0 * (double)S / (double)MM) : 0ull;
-    }
-    __syncthreads();
-    const double m_over_s = s_mos;
-    const unsigned long long qheavy = s_qh;
-    unsigned long long c = excl + woff + (incl - tsum);  // C before this thread's item 0
+    const unsigned long long Rth = cst.Rth;
+    const double m_over_s = cst.m_over_s;
+    const unsigned long long qheavy = cst.qheavy;
+    const float inv_s = cst.inv_s;
+    unsigned long long c = tpre + woff + (incl - tsum);  // C before this thread's item 0
     unsigned long long Q, R;
     divmod_cm(c, MM, S, m_over_s, Q, R);
-    uint32_t F = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-    if (tid == 0) s_lo = F;
+    const uint32_t F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+    if (tid == 0) s_lo = F0;
 #pragma unroll
     for (int j = 0; j < kRsIpt; ++j) {
         c += q[j];
-        if (q[j] > qheavy) {
+        if (q[j] > qheavy) {  // rare: a heavy item, divided afresh
             divmod_cm(c, MM, S, m_over_s, Q, R);
         } else {
-            R += q[j] * MM;  // q M <= 7 S (+ rounding): no wrap, at most 8 carries
-            for (int it = 0; it < 16 && R >= S; ++it) {
-                R -= S;
-                ++Q;
-            }
+            // carry R + q M (< 9 S < 2^64) into Q without a data-dependent
+            // loop: n = floor((R + q M) / S) in [0, 8] from an FP32
+            // estimate (off by at most one) and one exact correction each way
+            const unsigned long long R2 = R + q[j] * MM;
+            unsigned long long n = (unsigned long long)(__ull2float_rz(R2) * inv_s);
+            long long r = (long long)(R2 - n * S);
+            const bool lo1 = r < 0;
+            n -= lo1 ? 1ull : 0ull;
+            r += lo1 ? (long long)S : 0ll;
+            const bool hi1 = r >= (long long)S;
+            n += hi1 ? 1ull : 0ull;
+            r -= hi1 ? (long long)S : 0ll;
+            Q += n;
+            R = (unsigned long long)r;
         }
         uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
         if (Fn > (uint32_t)M) Fn = (uint32_t)M;
         s_hi[tid * kRsIpt + j] = Fn;
-        F = Fn;
     }
     __syncthreads();
     // ---- offspring counts and the log-weight reset, item-major (coalesced)
     const uint32_t lo = s_lo, hi = s_hi[kRsTile - 1];
-    for (int j = tid; j < kRsTile; j += kRsThreads) {
-        const int64_t g = base + j;
-        if (g < M) {
-            if (counts) counts[g] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
-            if (lwreset) lwreset[g] = 0.0;
+    if (counts)
+        for (int j = tid; j < kRsTile; j += kRsThreads)
+            if (base + j < M) counts[base + j] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
+    if (lwreset) {
+        if (base + kRsTile <= M && ((reinterpret_cast<uintptr_t>(lwreset + base) & 15u) == 0)) {
+            double2* d2 = reinterpret_cast<double2*>(lwreset + base);
+            for (int j = tid; j < kRsTile / 2; j += kRsThreads) d2[j] = make_double2(0.0, 0.0);
+        } else {
+            for (int j = tid; j < kRsTile; j += kRsThreads)
+                if (base + j < M) lwreset[base + j] = 0.0;
         }
     }
-    // ---- expand the tile's output range [lo, hi): each thread a contiguous
-    // block of slots; staged in shared memory and stored slot-major when the
-    // range fits (the usual case).  A larger range (heavy weights) is split
-    // into chunks for k_resample_heavy, which all CTAs share; without that
-    // scratch the CTA stores it directly.
+    // ---- expand the tile's output range [lo, hi).  Usual case (the range
+    // fits in shared memory): each thread writes its own items' slots there,
+    // then the block stores them slot-major.  A larger range (heavy weights)
+    // is split into chunks for k_resample_heavy, which all CTAs share;
+    // without that scratch the CTA expands it itself (contiguous blocks of
+    // slots per thread, stored directly).
+    if (hi < lo || hi > (uint32_t)M) {  // cannot happen with consistent sums
+        if (tid == 0) raise_status(status, ST_BADARG);
+        return;
+    }
     const uint32_t range = hi - lo;
-    const bool staged = range <= (uint32_t)kRsStage;
-    if (!staged && sc.heavy_list) {  // uniform over the block
+    if (range <= (uint32_t)kRsStage) {  // uniform over the block
+        // each item writes its first 4 slots with predicated stores; the
+        // rare items with more slots finish in a loop
+        uint32_t f = F0;
+        const int32_t i0 = (int32_t)(base + (int64_t)tid * kRsIpt);
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) {
+            const uint32_t e = s_hi[tid * kRsIpt + j];
+#pragma unroll
+            for (uint32_t k = 0; k < 4; ++k)
+                if (f + k < e) s_anc[f + k - lo] = i0 + j;
+            for (uint32_t sl = f + 4; sl < e; ++sl) s_anc[sl - lo] = i0 + j;
+            f = e;
+        }
+        __syncthreads();
+        for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
+        return;
+    }
+    if (sc.heavy_list) {
         for (int j = tid; j < kRsTile; j += kRsThreads)
             if (base + j < M) sc.fpos[base + j] = s_hi[j];
         if (tid == 0) {
@@ -348,13 +438,8 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_scan(
         int item = a;
         for (uint32_t sl = s0; sl < s1; ++sl) {
             while (s_hi[item] <= sl) ++item;
-            if (staged) s_anc[sl - lo] = (int32_t)(base + item);
-            else anc[sl] = (int32_t)(base + item);
+            anc[sl] = (int32_t)(base + item);
         }
-    }
-    if (staged) {  // uniform over the block
-        __syncthreads();
-        for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
     }
 }
 
