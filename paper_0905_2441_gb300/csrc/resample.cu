@@ -62,7 +62,16 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     SMC_CUDA(cudaGetLastError());
     smc::k_resample_finalize<<<1, smc::kRsFinThreads, 0, s>>>(M, seed, step, do_flag, sc, status);
     SMC_CUDA(cudaGetLastError());
-    smc::k_resample_scan<<<(unsigned)tiles, smc::kRsThreads, 0, s>>>(
+    // pass 2 is persistent: as many CTAs as are resident at once
+    static int occ = 0;
+    if (occ == 0 &&
+        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smc::k_resample_scan, smc::kRsThreads,
+                                                       0) != cudaSuccess ||
+         occ < 1))
+        occ = 1;
+    int64_t g2 = (int64_t)num_sms * occ;
+    if (g2 > tiles) g2 = tiles;
+    smc::k_resample_scan<<<(unsigned)g2, smc::kRsThreads, 0, s>>>(
         W, M, seed, step, do_flag, sc, anc, counts, lwreset, status);
     SMC_CUDA(cudaGetLastError());
     if (sc.heavy_list) {

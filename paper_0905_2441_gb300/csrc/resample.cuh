@@ -28,8 +28,9 @@ struct RsConst {
     unsigned long long S;       // exact total of the quantised weights
     unsigned long long Rth;     // floor(u32 S / 2^32)
     unsigned long long qheavy;  // items with q above this are divided afresh
-    double m_over_s;            // M / S (estimates of quotients)
-    float inv_s;                // 1 / S (estimates of carries)
+    unsigned long long mfx;     // floor(M 2^64 / S) when M < S, else 0 (use FP64)
+    unsigned long long ifx;     // floor(2^64 / S) when S > 1, else 0
+    double m_over_s;            // M / S (FP64 estimates, only when M >= S)
     uint32_t ok;                // 0: nothing to resample (status already raised)
 };
 constexpr int kRsConstWords = 8;
@@ -101,6 +102,25 @@ __device__ __forceinline__ bool load_tile_items(const double* __restrict__ W, in
     return bad;
 }
 
+// this thread's kRsIpt raw weights of tile `tile` (0 past M), for loading
+// one tile ahead of its use
+__device__ __forceinline__ void load_tile_raw(const double* __restrict__ W, int64_t M,
+                                              int64_t tile, double (&v)[kRsIpt]) {
+    const int64_t g0 = tile * kRsTile + (int64_t)threadIdx.x * kRsIpt;
+    if (g0 + kRsIpt <= M && ((reinterpret_cast<uintptr_t>(W + g0) & 15u) == 0)) {
+        const double2* p = reinterpret_cast<const double2*>(W + g0);
+#pragma unroll
+        for (int j = 0; j < kRsIpt / 2; ++j) {
+            const double2 d = p[j];
+            v[2 * j] = d.x;
+            v[2 * j + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) v[j] = g0 + j < M ? W[g0 + j] : 0.0;
+    }
+}
+
 // block-wide sum of 64-bit values; result valid in thread 0
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
                                                             unsigned long long* sh) {
@@ -131,9 +151,13 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __r
     bool bad = false;
     unsigned long long gacc = 0;
     int64_t gcur = t0 / kRsGroup;
+    double vn[kRsIpt];
+    if (t0 < t1) load_tile_raw(W, M, t0, vn);
     for (int64_t t = t0; t < t1; ++t) {
         unsigned long long q[kRsIpt];
-        bad |= load_tile_items(W, M, t, q);
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) bad |= !quantise(vn[j], q[j]);
+        if (t + 1 < t1) load_tile_raw(W, M, t + 1, vn);  // next tile in flight
         unsigned long long acc = 0;
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) acc += q[j];  // <= 8 * 2^52: no wrap
@@ -183,13 +207,21 @@ __device__ __forceinline__ bool lt128(U128 a, U128 b) {
 // (R integer: R 2^32 > X  <=>  R > floor(X / 2^32)).  Advancing c by an item's
 // q adds q M to R and carries whole S into Q.
 
-// c M = Q S + R exactly (c <= S < 2^61, M < 2^31): FP64 estimate of Q,
-// then an exact 128-bit fix-up
+// c M = Q S + R exactly (c <= S < 2^61, M < 2^31).  The estimate of Q is
+// c times the fixed-point reciprocal mfx = floor(M 2^64 / S) (integer
+// multiply-high: off by at most one below), fixed up exactly; without it
+// (M >= S, degenerate totals) an FP64 estimate, fixed up the same way.
 __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long M,
-                                          unsigned long long S, double m_over_s,
-                                          unsigned long long& Q, unsigned long long& R) {
-    const double qe = floor((double)c * m_over_s);
-    unsigned long long q = qe > 0.0 ? (unsigned long long)qe : 0ull;
+                                       const RsConst& k, unsigned long long& Q,
+                                       unsigned long long& R) {
+    const unsigned long long S = k.S;
+    unsigned long long q;
+    if (k.mfx) {
+        q = __umul64hi(c, k.mfx);
+    } else {
+        const double qe = floor((double)c * k.m_over_s);
+        q = qe > 0.0 ? (unsigned long long)qe : 0ull;
+    }
     const U128 P = mul64(c, M);
     U128 QS = mul64(q, S);
     for (int it = 0; it < 64 && lt128(P, QS); ++it) {  // estimate too high
@@ -203,6 +235,21 @@ __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long 
     }
     Q = q;
     R = r.lo;
+}
+
+// floor(hi 2^64 / d) for hi < d (restoring long division; once per call)
+__device__ unsigned long long div_shift64(unsigned long long hi, unsigned long long d) {
+    unsigned long long rem = hi, quo = 0;
+    for (int i = 0; i < 64; ++i) {
+        const bool top = (rem >> 63) != 0;
+        rem <<= 1;
+        quo <<= 1;
+        if (top || rem >= d) {
+            rem -= d;
+            quo |= 1ull;
+        }
+    }
+    return quo;
 }
 
 // Between the passes, one CTA: the exact total S from the group sums, the
@@ -219,16 +266,23 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     const int64_t ntiles = rs_tiles(M);
     if (tid == 0) s_bad = 0;
     __syncthreads();
-    // each thread scans a contiguous run of tile sums
+    // each thread scans a contiguous run of tile sums (up to 8 loads in
+    // flight at a time)
     const int64_t per = (ntiles + kRsFinThreads - 1) / kRsFinThreads;
     const int64_t t0 = (int64_t)tid * per;
     const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
     unsigned long long own = 0;
     bool ovf = false;
-    for (int64_t t = t0; t < t1; ++t) {
-        const unsigned long long n = own + __ldcg(sc.tile_sum + t);
-        ovf |= n < own;
-        own = n;
+    for (int64_t t = t0; t < t1; t += 8) {
+        unsigned long long v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const unsigned long long n = own + v[k];
+            ovf |= n < own;
+            own = n;
+        }
     }
     // block exclusive scan of the runs
     unsigned long long incl = own;
@@ -252,10 +306,15 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
         S = n;
     }
     unsigned long long run = off + incl - own;
-    for (int64_t t = t0; t < t1; ++t) {
-        const unsigned long long v = __ldcg(sc.tile_sum + t);
-        sc.tile_sum[t] = run;
-        run += v;
+    for (int64_t t = t0; t < t1; t += 8) {
+        unsigned long long v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (t + k < t1) sc.tile_sum[t + k] = run;
+            run += v[k];
+        }
     }
     if (tid == 0) {
         RsConst c;
@@ -268,9 +327,10 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
             c.S = S;
             c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
             c.m_over_s = (double)MM / (double)S;
+            c.mfx = MM < S ? div_shift64(MM, S) : 0ull;
+            c.ifx = S > 1 ? div_shift64(1ull, S) : 0ull;
             // R + q M < 8 S + S < 2^64 while S < 2^60 (else every item is divided)
-            c.qheavy = S < (1ull << 60) ? (unsigned long long)(7.0 * (double)S / (double)MM) : 0ull;
-            c.inv_s = 1.0f / __ull2float_rn(S);
+            c.qheavy = S < (1ull << 60) && c.ifx ? (7ull * S) / MM : 0ull;
             c.ok = 1;
         }
         *sc.cst = c;
@@ -280,7 +340,7 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
 // Minimum resident blocks per SM asked of the register allocator for the
 // scan (compile-time tuning knob).
 #ifndef SMC_RS_MINB
-#define SMC_RS_MINB 5
+#define SMC_RS_MINB 3
 #endif
 
 // Pass 2: one CTA per tile.
@@ -293,152 +353,163 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
     __shared__ unsigned long long s_warp[kRsThreads / 32];
     __shared__ uint32_t s_lo;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    const int64_t tile = blockIdx.x;
-    const int64_t base = tile * kRsTile;
+    const int64_t ntiles = rs_tiles(M);
+    (void)seed;
+    (void)step;
 
     if (do_flag && *do_flag == 0) {  // no resampling this step: identity
-        for (int j = tid; j < kRsTile; j += kRsThreads) {
-            const int64_t g = base + j;
-            if (g < M) {
-                anc[g] = (int32_t)g;
-                if (counts) counts[g] = 1;
-            }
+        for (int64_t g = (int64_t)blockIdx.x * kRsThreads + tid; g < M;
+             g += (int64_t)gridDim.x * kRsThreads) {
+            anc[g] = (int32_t)g;
+            if (counts) counts[g] = 1;
         }
         return;
     }
-    // ---- the call's constants and this tile's exclusive prefix (finalize)
+    // ---- the call's constants (finalize)
     const RsConst cst = *sc.cst;
     if (!cst.ok) return;
     const unsigned long long S = cst.S;
-    const unsigned long long tpre = __ldcg(sc.tile_sum + tile);
-    // ---- this thread's items
-    unsigned long long q[kRsIpt];
-    load_tile_items(W, M, tile, q);  // pass 1 already reported bad weights
-    unsigned long long tsum = 0;
-#pragma unroll
-    for (int j = 0; j < kRsIpt; ++j) tsum += q[j];
-    // ---- block exclusive scan of the thread sums
-    unsigned long long incl = tsum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    unsigned long long woff = 0;
-#pragma unroll
-    for (int w = 0; w < kRsThreads / 32; ++w)
-        if (w < wid) woff += s_warp[w];
-    // ---- F at every prefix of this thread's items: c M = Q S + R, carried
-    // item by item (items with q M above about 7 S are divided afresh)
     const unsigned long long MM = (unsigned long long)M;
     const unsigned long long Rth = cst.Rth;
-    const double m_over_s = cst.m_over_s;
     const unsigned long long qheavy = cst.qheavy;
-    const float inv_s = cst.inv_s;
-    unsigned long long c = tpre + woff + (incl - tsum);  // C before this thread's item 0
-    unsigned long long Q, R;
-    divmod_cm(c, MM, S, m_over_s, Q, R);
-    const uint32_t F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-    if (tid == 0) s_lo = F0;
+    const unsigned long long ifx = cst.ifx;
+    // persistent over tiles; the next tile's weights and prefix load while
+    // the current one is processed
+    int64_t tile = blockIdx.x;
+    double vn[kRsIpt];
+    unsigned long long pn = 0;
+    if (tile < ntiles) {
+        load_tile_raw(W, M, tile, vn);
+        pn = __ldcg(sc.tile_sum + tile);
+    }
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int64_t base = tile * kRsTile;
+        unsigned long long q[kRsIpt];
 #pragma unroll
-    for (int j = 0; j < kRsIpt; ++j) {
-        c += q[j];
-        if (q[j] > qheavy) {  // rare: a heavy item, divided afresh
-            divmod_cm(c, MM, S, m_over_s, Q, R);
-        } else {
-            // carry R + q M (< 9 S < 2^64) into Q without a data-dependent
-            // loop: n = floor((R + q M) / S) in [0, 8] from an FP32
-            // estimate (off by at most one) and one exact correction each way
-            const unsigned long long R2 = R + q[j] * MM;
-            unsigned long long n = (unsigned long long)(__ull2float_rz(R2) * inv_s);
-            long long r = (long long)(R2 - n * S);
-            const bool lo1 = r < 0;
-            n -= lo1 ? 1ull : 0ull;
-            r += lo1 ? (long long)S : 0ll;
-            const bool hi1 = r >= (long long)S;
-            n += hi1 ? 1ull : 0ull;
-            r -= hi1 ? (long long)S : 0ll;
-            Q += n;
-            R = (unsigned long long)r;
+        for (int j = 0; j < kRsIpt; ++j) quantise(vn[j], q[j]);  // pass 1 reported bad weights
+        const unsigned long long tpre = pn;  // the tile's exclusive prefix (finalize)
+        if (tile + gridDim.x < ntiles) {
+            load_tile_raw(W, M, tile + gridDim.x, vn);
+            pn = __ldcg(sc.tile_sum + tile + gridDim.x);
         }
-        uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-        if (Fn > (uint32_t)M) Fn = (uint32_t)M;
-        s_hi[tid * kRsIpt + j] = Fn;
-    }
-    __syncthreads();
-    // ---- offspring counts and the log-weight reset, item-major (coalesced)
-    const uint32_t lo = s_lo, hi = s_hi[kRsTile - 1];
-    if (counts)
-        for (int j = tid; j < kRsTile; j += kRsThreads)
-            if (base + j < M) counts[base + j] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
-    if (lwreset) {
-        if (base + kRsTile <= M && ((reinterpret_cast<uintptr_t>(lwreset + base) & 15u) == 0)) {
-            double2* d2 = reinterpret_cast<double2*>(lwreset + base);
-            for (int j = tid; j < kRsTile / 2; j += kRsThreads) d2[j] = make_double2(0.0, 0.0);
-        } else {
-            for (int j = tid; j < kRsTile; j += kRsThreads)
-                if (base + j < M) lwreset[base + j] = 0.0;
+        unsigned long long tsum = 0;
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) tsum += q[j];
+        // ---- block exclusive scan of the thread sums
+        unsigned long long incl = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += v;
         }
-    }
-    // ---- expand the tile's output range [lo, hi).  Usual case (the range
-    // fits in shared memory): each thread writes its own items' slots there,
-    // then the block stores them slot-major.  A larger range (heavy weights)
-    // is split into chunks for k_resample_heavy, which all CTAs share;
-    // without that scratch the CTA expands it itself (contiguous blocks of
-    // slots per thread, stored directly).
-    if (hi < lo || hi > (uint32_t)M) {  // cannot happen with consistent sums
-        if (tid == 0) raise_status(status, ST_BADARG);
-        return;
-    }
-    const uint32_t range = hi - lo;
-    if (range <= (uint32_t)kRsStage) {  // uniform over the block
-        // each item writes its first 4 slots with predicated stores; the
-        // rare items with more slots finish in a loop
-        uint32_t f = F0;
-        const int32_t i0 = (int32_t)(base + (int64_t)tid * kRsIpt);
+        __syncthreads();  // the previous tile is done with shared memory
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        unsigned long long woff = 0;
+#pragma unroll
+        for (int w = 0; w < kRsThreads / 32; ++w)
+            if (w < wid) woff += s_warp[w];
+        unsigned long long c = tpre + woff + (incl - tsum);  // C before this thread's item 0
+        unsigned long long Q, R;
+        divmod_cm(c, MM, cst, Q, R);
+        const uint32_t F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+        if (tid == 0) s_lo = F0;
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) {
-            const uint32_t e = s_hi[tid * kRsIpt + j];
-#pragma unroll
-            for (uint32_t k = 0; k < 4; ++k)
-                if (f + k < e) s_anc[f + k - lo] = i0 + j;
-            for (uint32_t sl = f + 4; sl < e; ++sl) s_anc[sl - lo] = i0 + j;
-            f = e;
+            c += q[j];
+            if (q[j] > qheavy) {  // rare: a heavy item, divided afresh
+                divmod_cm(c, MM, cst, Q, R);
+            } else {
+                // carry R + q M (< 9 S < 2^64) into Q without a data-dependent
+                // loop: n = floor((R + q M) / S) in [0, 8] from the
+                // fixed-point reciprocal ifx = floor(2^64 / S) (integer
+                // multiply-high, off by at most one below) and one correction
+                const unsigned long long R2 = R + q[j] * MM;
+                unsigned long long n = __umul64hi(R2, ifx);
+                unsigned long long r = R2 - n * S;
+                const bool hi1 = r >= S;
+                n += hi1 ? 1ull : 0ull;
+                r -= hi1 ? S : 0ull;
+                Q += n;
+                R = r;
+            }
+            uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+            if (Fn > (uint32_t)M) Fn = (uint32_t)M;
+            s_hi[tid * kRsIpt + j] = Fn;
         }
         __syncthreads();
-        for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
-        return;
-    }
-    if (sc.heavy_list) {
-        for (int j = tid; j < kRsTile; j += kRsThreads)
-            if (base + j < M) sc.fpos[base + j] = s_hi[j];
-        if (tid == 0) {
-            const uint32_t nch = (range + kRsChunk - 1) / kRsChunk;
-            const unsigned long long r0 = atomicAdd(sc.heavy_count, (unsigned long long)nch);
-            for (uint32_t k = 0; k < nch; ++k) {
-                const uint32_t b = lo + k * kRsChunk;
-                const uint32_t e = b + kRsChunk < hi ? b + kRsChunk : hi;
-                sc.heavy_list[r0 + k] = make_uint4((uint32_t)tile, lo, b, e);
+        // ---- offspring counts and the log-weight reset, item-major (coalesced)
+        const uint32_t lo = s_lo, hi = s_hi[kRsTile - 1];
+        if (counts)
+            for (int j = tid; j < kRsTile; j += kRsThreads)
+                if (base + j < M) counts[base + j] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
+        if (lwreset) {
+            if (base + kRsTile <= M && ((reinterpret_cast<uintptr_t>(lwreset + base) & 15u) == 0)) {
+                double2* d2 = reinterpret_cast<double2*>(lwreset + base);
+                for (int j = tid; j < kRsTile / 2; j += kRsThreads) d2[j] = make_double2(0.0, 0.0);
+            } else {
+                for (int j = tid; j < kRsTile; j += kRsThreads)
+                    if (base + j < M) lwreset[base + j] = 0.0;
             }
         }
-        return;
-    }
-    const uint32_t per = (range + kRsThreads - 1) / kRsThreads;
-    const uint32_t s0 = lo + (uint32_t)tid * per;
-    const uint32_t s1 = s0 + per < hi ? s0 + per : hi;
-    if (s0 < s1) {
-        int a = 0, b = kRsTile - 1;  // first item whose inclusive F exceeds s0
-        while (a < b) {
-            const int mid = (a + b) >> 1;
-            if (s_hi[mid] > s0) b = mid;
-            else a = mid + 1;
+        // ---- expand the tile's output range [lo, hi).  Usual case (the range
+        // fits in shared memory): each thread writes its own items' slots there,
+        // then the block stores them slot-major.  A larger range (heavy weights)
+        // is split into chunks for k_resample_heavy, which all CTAs share;
+        // without that scratch the CTA expands it itself (contiguous blocks of
+        // slots per thread, stored directly).
+        if (hi < lo || hi > (uint32_t)M) {  // cannot happen with consistent sums
+            if (tid == 0) raise_status(status, ST_BADARG);
+            continue;
         }
-        int item = a;
-        for (uint32_t sl = s0; sl < s1; ++sl) {
-            while (s_hi[item] <= sl) ++item;
-            anc[sl] = (int32_t)(base + item);
+        const uint32_t range = hi - lo;
+        if (range <= (uint32_t)kRsStage) {  // uniform over the block
+            // each item writes its first 4 slots with predicated stores; the
+            // rare items with more slots finish in a loop
+            uint32_t f = F0;
+            const int32_t i0 = (int32_t)(base + (int64_t)tid * kRsIpt);
+#pragma unroll
+            for (int j = 0; j < kRsIpt; ++j) {
+                const uint32_t e = s_hi[tid * kRsIpt + j];
+#pragma unroll
+                for (uint32_t k = 0; k < 4; ++k)
+                    if (f + k < e) s_anc[f + k - lo] = i0 + j;
+                for (uint32_t sl = f + 4; sl < e; ++sl) s_anc[sl - lo] = i0 + j;
+                f = e;
+            }
+            __syncthreads();
+            for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
+            continue;
+        }
+        if (sc.heavy_list) {
+            for (int j = tid; j < kRsTile; j += kRsThreads)
+                if (base + j < M) sc.fpos[base + j] = s_hi[j];
+            if (tid == 0) {
+                const uint32_t nch = (range + kRsChunk - 1) / kRsChunk;
+                const unsigned long long r0 = atomicAdd(sc.heavy_count, (unsigned long long)nch);
+                for (uint32_t k = 0; k < nch; ++k) {
+                    const uint32_t b = lo + k * kRsChunk;
+                    const uint32_t e = b + kRsChunk < hi ? b + kRsChunk : hi;
+                    sc.heavy_list[r0 + k] = make_uint4((uint32_t)tile, lo, b, e);
+                }
+            }
+            continue;
+        }
+        const uint32_t per = (range + kRsThreads - 1) / kRsThreads;
+        const uint32_t s0 = lo + (uint32_t)tid * per;
+        const uint32_t s1 = s0 + per < hi ? s0 + per : hi;
+        if (s0 < s1) {
+            int a = 0, b = kRsTile - 1;  // first item whose inclusive F exceeds s0
+            while (a < b) {
+                const int mid = (a + b) >> 1;
+                if (s_hi[mid] > s0) b = mid;
+                else a = mid + 1;
+            }
+            int item = a;
+            for (uint32_t sl = s0; sl < s1; ++sl) {
+                while (s_hi[item] <= sl) ++item;
+                anc[sl] = (int32_t)(base + item);
+            }
         }
     }
 }
