@@ -402,6 +402,20 @@ def bench_secondary(torch, P):
                               "ms_per_step_graph": 1e3 * t_graph / w.T,
                               "logZ_plain": z_plain, "logZ_graph": z_graph}
     ctx.check()
+    # the diagonal mixture on the tensor cores (d=32, K=16, N=65536, M=4096)
+    w = synth.DIAG32
+    truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
+    Y = torch.from_numpy(synth.diag_data(w.N, truth, seed=w.data_seed)).cuda()
+    th = torch.from_numpy(synth.diag_particles(w.M, truth, seed=w.particle_seed)).cuda()
+    tc = P.DiagGMM(w.K, w.sigma, d=w.d, precision=P.PREC_BF16SPLIT)
+    ll = torch.empty(w.M, dtype=torch.float64, device="cuda")
+    P.loglik_batch(ctx, tc, Y, th, out=ll)
+    reps = 10
+    t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
+    ctx.check()
+    out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
+                               "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
+                               "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}
     ctx.close()
     return out
 
