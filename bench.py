@@ -8,11 +8,14 @@ univariate 8-component mixture, N = 1000 observations.  One step = one sweep
 chain, then the exchange moves).  Metric: particle-datum log-likelihood
 evaluations per second (chains x N per sweep).
 
-Other workloads (--workload): smc (4-component tempered SMC sampler,
-M = 8192, 20 temperatures; step = one SMC step), mala (differentiable
-sampler, M = 65536, K = 8, N = 1000, 50 temperatures), pf (d = 3 MSV
-particle filter, M = 2^20; step = one filter step), resample (reweight +
-systematic resampling bandwidth at M = 2^24).
+Other workloads (--workload): pf (d = 3 MSV particle filter, M = 2^20; step
+= one filter step), resample (reweight + systematic resampling bandwidth at
+M = 2^24), diag (diagonal mixture d = 32, K = 16, N = 65536, M = 4096 on the
+tensor cores; step = one likelihood call), peaks (the MUFU / FMA / FP64 /
+conversion rates used as roofline denominators).  The default run also
+reports, under "secondary", the tempered SMC sampler (M = 8192), the MALA
+sampler (M = 65536), the particle filter and the tensor-core likelihood,
+each in its plain and CUDA-graph forms where both exist.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 Under torchrun each rank runs its own independent copy of the workload
@@ -126,17 +129,31 @@ def profile_traffic(kernel: str):
 
 
 class Dist:
-    def __init__(self):
+    """One process per GPU (torchrun's RANK / WORLD_SIZE / LOCAL_RANK): a
+    barrier and the max / sum of per-rank numbers, over NCCL on the GPUs (or
+    gloo on the CPU, as the multi-process tests run it).  No data-path
+    collective: every rank runs an independent replica of the workload."""
+
+    def __init__(self, backend=None):
         self.rank = int(os.environ.get("RANK", "0"))
         self.world = int(os.environ.get("WORLD_SIZE", "1"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
         self.pg = False
 
     def init(self, torch):
         if self.world > 1:
             import torch.distributed as dist
-            dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            if self.backend is None:
+                self.backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if self.backend == "nccl":
+                dist.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            else:
+                dist.init_process_group(self.backend)
             self.pg = True
+
+    def _dev(self):
+        return "cuda" if self.backend == "nccl" else "cpu"
 
     def barrier(self, torch):
         if self.pg:
@@ -147,7 +164,7 @@ class Dist:
         if not self.pg:
             return v
         import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64, device=self._dev())
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
@@ -155,9 +172,15 @@ class Dist:
         if not self.pg:
             return v
         import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
+        t = torch.tensor([v], dtype=torch.float64, device=self._dev())
         dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
+
+    def throughput(self, torch, units: float, seconds: float):
+        """Whole-job rate: the units every rank processed over the slowest
+        rank's time (weak scaling: each rank keeps its own fixed work)."""
+        t_max = self.max(torch, seconds)
+        return self.sum(torch, units) / t_max, t_max
 
     def close(self):
         if self.pg:

@@ -118,7 +118,11 @@ typedef struct smc_gmm {
  *   grad_out (nullable, 1-D only): float[K][M], d loglik / d mu_k =
  *     sum_n r_nk (y_n - mu_k) / sigma^2 with r the responsibilities.
  * The prior box is not applied here.  Diag with SMC_PREC_BF16SPLIT forms
- * mu.y on the tensor cores from bf16 hi/lo splits.  Errors: SMC_ERR_ARG for
+ * mu.y on the tensor cores from bf16 hi/lo splits of y and mu (products
+ * hi.hi + hi.lo + lo.hi, FP32 accumulation; relative error of loglik well
+ * below 1e-3) and takes d = 16 or 32 and K <= 16 (other shapes:
+ * SMC_ERR_UNSUPPORTED, use SMC_PREC_FP32); it uses context scratch of about
+ * N (4 d + 8 bytes) + M K (4 d + 32 bytes).  Errors: SMC_ERR_ARG for
  * M < 0, N < 0, K/d out of range, sigma <= 0, NULL pointers with M, N > 0;
  * M == 0 is a no-op; N == 0 gives loglik 0. */
 smc_status smc_loglik_batch(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
