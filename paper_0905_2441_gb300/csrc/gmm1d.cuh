@@ -238,14 +238,25 @@ __device__ __forceinline__ float ex2_neg(float p) {
 #endif
 constexpr int kEqwUnroll = SMC_EQW_UNROLL;
 
-template <int K>
+template <int K, bool GRAD = false>
 struct SliceAccEqW {
     Kahan ll;                              // log2 terms: exponents, shifts, scalar data
     float2 pr[2] = {{1.0f, 1.0f}, {1.0f, 1.0f}};  // mantissa products of s (even / odd
                                                  // pairs of a block), in [1, 2)
+    // gradient (GRAD): per component, sum over the data of r_nk t_nk with the
+    // responsibilities r_nk = e_nk / s_n (shift-free, so the unshifted sums
+    // serve), one half per datum of a pair
+    float2 G[GRAD ? K : 1];
 
-    // one datum on the scalar path (odd tail of a chunk)
-    __device__ __forceinline__ void one(float yv, const float (&nu)[K], float r) {
+    __device__ __forceinline__ SliceAccEqW() {
+#pragma unroll
+        for (int k = 0; k < (GRAD ? K : 1); ++k) G[k] = make_float2(0.0f, 0.0f);
+    }
+
+    // one datum on the shifted scalar path; returns s and adds the shift to
+    // the sum, and (GRAD) its responsibilities times t_k to G[k].x or .y
+    __device__ __forceinline__ float one_shifted(float yv, const float (&nu)[K], float r,
+                                                 bool upper_half) {
         float t[K];
         float tm = INFINITY;
 #pragma unroll
@@ -253,68 +264,93 @@ struct SliceAccEqW {
             t[k] = fmaf(yv, r, nu[k]);
             tm = fminf(tm, fabsf(t[k]));
         }
-        float c = -tm * tm;
+        const float c = -tm * tm;
+        float e[K];
         float s = 0.0f;
 #pragma unroll
-        for (int k = 0; k < K; ++k) s += ex2_neg(fmaf(t[k], t[k], c));
-        ll.add(c + lg2(s));
+        for (int k = 0; k < K; ++k) {
+            e[k] = ex2_neg(fmaf(t[k], t[k], c));
+            s += e[k];
+        }
+        ll.add(c);
+        if constexpr (GRAD) {
+            const float inv = rcp(s);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float v = e[k] * t[k] * inv;
+                if (upper_half) G[k].y += v;
+                else G[k].x += v;
+            }
+        }
+        return s;
     }
 
-    // shifted sums of one pair whose unshifted sum fell below 2^-100
-    // (recomputes t_k, so nothing stays live across the rare branch)
-    __device__ __forceinline__ float2 rescue(float2 Y, float2 R2, const float2 (&NU)[K]) {
-        float2 T[K];
-        float a0 = INFINITY, a1 = INFINITY;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            T[k] = __ffma2_rn(Y, R2, NU[k]);
-            a0 = fminf(a0, fabsf(T[k].x));
-            a1 = fminf(a1, fabsf(T[k].y));
-        }
-        const float c0 = -a0 * a0, c1 = -a1 * a1;
-        float s0 = 0.0f, s1 = 0.0f;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            s0 += ex2_neg(fmaf(T[k].x, T[k].x, c0));
-            s1 += ex2_neg(fmaf(T[k].y, T[k].y, c1));
-        }
-        ll.add(c0);
-        ll.add(c1);
-        return make_float2(s0, s1);
+    // one datum on the scalar path (odd tail of a chunk)
+    __device__ __forceinline__ void one(float yv, const float (&nu)[K], float r) {
+        const float s = one_shifted(yv, nu, r, false);
+        ll.add(lg2(s));
     }
 
     // U pairs p, p + L, ..., p + (U-1) L: their sums are computed
     // independently (straight-line code the scheduler can interleave), with
-    // one test for the rare rescue, then folded into the products
+    // one test for the rare rescue (data whose unshifted sum fell below
+    // 2^-100 take the shifted path), then folded into the products
     template <int U>
     __device__ __forceinline__ void pairs(const float2* ys2, int p, int L, float2 R2,
-                                          const float2 (&NU)[K], int& ex) {
+                                          const float2 (&NU)[K], const float (&nu)[K], float r,
+                                          int& ex) {
         float2 Y[U], S[U];
+        float2 E[GRAD ? U : 1][K];  // the terms, kept for the gradient
 #pragma unroll
         for (int u = 0; u < U; ++u) Y[u] = ys2[p + u * L];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            float2 E[K];
+            float2 e[K];
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 const float2 T = __ffma2_rn(Y[u], R2, NU[k]);
                 const float2 Q = __fmul2_rn(T, T);
-                E[k] = make_float2(ex2_neg(Q.x), ex2_neg(Q.y));
+                e[k] = make_float2(ex2_neg(Q.x), ex2_neg(Q.y));
+                if constexpr (GRAD) E[u][k] = e[k];
             }
             // balanced tree keeps the dependency chain short (log2 K)
 #pragma unroll
             for (int w = 1; w < K; w <<= 1)
 #pragma unroll
-                for (int k = 0; k + w < K; k += 2 * w) E[k] = __fadd2_rn(E[k], E[k + w]);
-            S[u] = E[0];
+                for (int k = 0; k + w < K; k += 2 * w) e[k] = __fadd2_rn(e[k], e[k + w]);
+            S[u] = e[0];
         }
+        bool resc[U][2];
+#pragma unroll
+        for (int u = 0; u < U; ++u) { resc[u][0] = false; resc[u][1] = false; }
         float mn = fminf(S[0].x, S[0].y);
 #pragma unroll
         for (int u = 1; u < U; ++u) mn = fminf(mn, fminf(S[u].x, S[u].y));
         if (mn < 0x1p-100f) {
 #pragma unroll
-            for (int u = 0; u < U; ++u)
-                if (fminf(S[u].x, S[u].y) < 0x1p-100f) S[u] = rescue(Y[u], R2, NU);
+            for (int u = 0; u < U; ++u) {
+                if (S[u].x < 0x1p-100f) {
+                    resc[u][0] = true;
+                    S[u].x = one_shifted(Y[u].x, nu, r, false);
+                }
+                if (S[u].y < 0x1p-100f) {
+                    resc[u][1] = true;
+                    S[u].y = one_shifted(Y[u].y, nu, r, true);
+                }
+            }
+        }
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                // rescued halves added their own (shifted) contribution
+                const float2 INV = make_float2(resc[u][0] ? 0.0f : rcp(S[u].x),
+                                               resc[u][1] ? 0.0f : rcp(S[u].y));
+#pragma unroll
+                for (int k = 0; k < K; ++k) {
+                    const float2 T = __ffma2_rn(Y[u], R2, NU[k]);
+                    G[k] = __ffma2_rn(__fmul2_rn(E[u][k], T), INV, G[k]);
+                }
+            }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
@@ -341,9 +377,9 @@ struct SliceAccEqW {
         int p = lane;
 #pragma unroll 1
         for (; p + (kEqwUnroll - 1) * L < np; p += kEqwUnroll * L)
-            pairs<kEqwUnroll>(ys2, p, L, R2, NU, ex);
+            pairs<kEqwUnroll>(ys2, p, L, R2, NU, nu, r, ex);
 #pragma unroll 1
-        for (; p < np; p += L) pairs<1>(ys2, p, L, R2, NU, ex);
+        for (; p < np; p += L) pairs<1>(ys2, p, L, R2, NU, nu, r, ex);
         // remove the bias 2 x 127 of each pair; the result, at most
         // 4096 x 200 in size, is exact in FP32
         const int npairs = lane < np ? (np - 1 - lane) / L + 1 : 0;
@@ -355,6 +391,19 @@ struct SliceAccEqW {
         ll.add((lg2(pr[0].x) + lg2(pr[0].y)) + (lg2(pr[1].x) + lg2(pr[1].y)));
         const double part = slice_total(ll.s, ll.c, L);
         return part * kLn2 + P.cst;
+    }
+    // with the gradient d l / d mu_k = sum_n r_nk (y_n - mu_k) / sigma^2
+    // = gscale sum_n r_nk t_nk, reduced over the slice's lanes
+    __device__ __forceinline__ double finish(int L, const Gmm1dArgs& P, float (&g)[K]) {
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float v = G[k].x + G[k].y;
+                for (int o = L >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
+                g[k] = v * P.gscale;
+            }
+        }
+        return finish(L, P);
     }
 };
 
@@ -446,8 +495,8 @@ __device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, flo
 }
 
 // The same chunked streaming for the packed equal-weight accumulator.
-template <int K>
-__device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K>& acc, float* ys, int ychunk,
+template <int K, bool GRAD>
+__device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K, GRAD>& acc, float* ys, int ychunk,
                                                    const float* __restrict__ y, int64_t N,
                                                    bool active, int lane, int L,
                                                    const float (&nu)[K], float r,

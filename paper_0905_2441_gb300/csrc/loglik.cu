@@ -37,10 +37,10 @@ __global__ void __launch_bounds__(256) k_loglik_gmm1d(const float* __restrict__ 
     uint32_t phase = 0;
     float g[K];
     double ll;
-    if constexpr (EQW && !GRAD) {
-        SliceAccEqW<K> acc;
+    if constexpr (EQW) {
+        SliceAccEqW<K, GRAD> acc;
         slice_over_data_eq(acc, ys, ychunk, y, N, active, lane, L, nu, P.r, phase, status);
-        ll = acc.finish(L, P);
+        ll = acc.finish(L, P, g);
     } else {
         SliceAcc<K, GRAD, EQW> acc;
         slice_over_data(acc, ys, ychunk, y, N, active, lane, L, nu, lw2, P.r, phase, status);

@@ -90,10 +90,10 @@ __global__ void __launch_bounds__(256) k_mh_move(
     uint32_t phase = 0;
     float gp[K];
     double lp;
-    if constexpr (EQW && !MALA) {
-        SliceAccEqW<K> acc;
+    if constexpr (EQW) {
+        SliceAccEqW<K, MALA> acc;
         slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status);
-        lp = acc.finish(L, P);
+        lp = acc.finish(L, P, gp);
     } else {
         SliceAcc<K, MALA, EQW> acc;
         slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
