@@ -352,6 +352,7 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
     __shared__ int32_t s_anc[kRsStage];           // the tile's ancestors, staged for coalesced stores
     __shared__ unsigned long long s_warp[kRsThreads / 32];
     __shared__ uint32_t s_lo;
+    __shared__ unsigned long long s_qr[2];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
     (void)seed;
@@ -404,14 +405,30 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
         }
         __syncthreads();  // the previous tile is done with shared memory
         if (lane == 31) s_warp[wid] = incl;
+        if (tid == 0) {  // the tile's own c M = Q S + R, divided once
+            unsigned long long Qt, Rt;
+            divmod_cm(tpre, MM, cst, Qt, Rt);
+            s_qr[0] = Qt;
+            s_qr[1] = Rt;
+        }
         __syncthreads();
         unsigned long long woff = 0;
 #pragma unroll
         for (int w = 0; w < kRsThreads / 32; ++w)
             if (w < wid) woff += s_warp[w];
-        unsigned long long c = tpre + woff + (incl - tsum);  // C before this thread's item 0
-        unsigned long long Q, R;
-        divmod_cm(c, MM, cst, Q, R);
+        const unsigned long long off = woff + (incl - tsum);  // this thread's offset in the tile
+        unsigned long long c = tpre + off;                    // C before this thread's item 0
+        unsigned long long Q = s_qr[0], R = s_qr[1];
+        if (off <= qheavy) {  // carry the tile's Q, R by off M (< 8 S)
+            const unsigned long long R2 = R + off * MM;
+            unsigned long long n = __umul64hi(R2, ifx);
+            unsigned long long r = R2 - n * S;
+            const bool hi1 = r >= S;
+            Q += n + (hi1 ? 1ull : 0ull);
+            R = r - (hi1 ? S : 0ull);
+        } else {
+            divmod_cm(c, MM, cst, Q, R);
+        }
         const uint32_t F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
         if (tid == 0) s_lo = F0;
 #pragma unroll
