@@ -92,6 +92,11 @@ def _declare(L):
     L.orc_pf_run.argtypes = [C.c_int, C.c_int, _f64p, _f64p, C.c_double, _f32p, _i64, _i64, _u64,
                              C.POINTER(C.c_double), _vp]
     L.orc_pf_run.restype = C.c_int
+    L.orc_fsv_step.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _f32p, _f32p, _vp,
+                               _f32p, _f64p, _i64, _u64, _u64]
+    L.orc_fsv_run.argtypes = [C.c_int, C.c_int, _f64p, _f64p, _f64p, _f64p, _f32p, _i64, _i64,
+                              _u64, C.POINTER(C.c_double), _vp]
+    L.orc_fsv_run.restype = C.c_int
     L.orc_kalman_lg.argtypes = [C.c_int, _f64p, _f64p, C.c_double, _f32p, _i64, _vp]
     L.orc_kalman_lg.restype = C.c_double
     L.orc_smc_run.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double, C.c_double,
@@ -308,6 +313,36 @@ def pf_run(kind, phi, chol, bscale, y, M, seed, want_means=False):
                           C.byref(z), _ptr(means))
     if rc:
         raise OracleError(f"pf_run status {rc}")
+    return (z.value, means) if want_means else z.value
+
+
+def fsv_step(phi, cholU, B, psi, yt, x_in, anc, seed, t):
+    """Factor stochastic volatility (Section 4.2): propagate x ([K][M]) and
+    weight by log N(y_t; 0, B diag(exp x) B^T + diag(psi)) (plain m x m
+    Cholesky, FP64)."""
+    x_in = _f32(x_in)
+    K, M = x_in.shape
+    B = _f64(B)
+    m = B.shape[0]
+    x_out = np.zeros_like(x_in)
+    lg = np.zeros(M, np.float64)
+    a = None if anc is None else np.ascontiguousarray(anc, np.int32)
+    lib().orc_fsv_step(K, m, _f64(phi), _f64(cholU), B, _f64(psi), _f32(yt), x_in, _ptr(a),
+                       x_out, lg, M, seed, t)
+    return x_out, lg
+
+
+def fsv_run(phi, cholU, B, psi, y, M, seed, want_means=False):
+    """Bootstrap filter on the factor SV model (resampling every step)."""
+    y = _f32(y)
+    T, m = y.shape
+    K = len(phi)
+    z = C.c_double(0.0)
+    means = np.zeros((T, K), np.float64) if want_means else None
+    rc = lib().orc_fsv_run(K, m, _f64(phi), _f64(cholU), _f64(B), _f64(psi), y, T, M, seed,
+                           C.byref(z), _ptr(means))
+    if rc:
+        raise OracleError(f"fsv_run status {rc}")
     return (z.value, means) if want_means else z.value
 
 

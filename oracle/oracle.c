@@ -712,6 +712,93 @@ double orc_kalman_lg(int d, const double* phi, const double* Sigma, double bscal
     return ll;
 }
 
+/* Factor stochastic volatility (Section 4.2): latent x_t in R^K,
+ * observation y_t in R^m (m <= 8, K <= 8):
+ *   x_t = Phi x_{t-1} + L_U z,  z ~ N(0, I_K),
+ *   y_t | x_t ~ N(0, Sigma_t),  Sigma_t = B diag(exp x_t) B^T + diag(psi).
+ * log g(y_t | x_t) by the plain definition: the m x m covariance, its
+ * Cholesky factor, the log-determinant and one triangular solve, in FP64.
+ * B is row-major m x K; x is [K][M]; yt holds m floats.                    */
+static double orc_fsv_logg(int K, int m, const double* B, const double* psi,
+                           const double* x, const float* yt)
+{
+    double S[64], L[64], w[8];
+    for (int i = 0; i < m; ++i)
+        for (int j = 0; j < m; ++j) {
+            double v = (i == j) ? psi[i] : 0.0;
+            for (int k = 0; k < K; ++k) v += B[i * K + k] * exp(x[k]) * B[j * K + k];
+            S[i * m + j] = v;
+        }
+    if (orc_chol(S, m, L)) return NAN;
+    double logdet = 0.0, quad = 0.0;
+    for (int i = 0; i < m; ++i) {
+        double s = (double)yt[i];
+        for (int k = 0; k < i; ++k) s -= L[i * m + k] * w[k];
+        w[i] = s / L[i * m + i];
+        quad += w[i] * w[i];
+        logdet += 2.0 * log(L[i * m + i]);
+    }
+    return -0.5 * ((double)m * log(2.0 * ORC_PI) + logdet + quad);
+}
+
+void orc_fsv_step(int K, int m, const double* phi, const double* cholU, const double* B,
+                  const double* psi, const float* yt, const float* x_in, const int32_t* anc,
+                  float* x_out, double* logg_out, int64_t M, uint64_t seed, uint64_t t)
+{
+    double z[16], xn[8];
+    for (int64_t i = 0; i < M; ++i) {
+        int64_t src = anc ? (int64_t)anc[i] : i;
+        orc_normals(seed, ORC_P_PFNOISE, t, (uint32_t)i, K, z);
+        for (int r = 0; r < K; ++r) {
+            double v = phi[r] * (double)x_in[(int64_t)r * M + src];
+            for (int c = 0; c <= r; ++c) v += cholU[r * K + c] * z[c];
+            xn[r] = (double)(float)v;  /* the state is stored in FP32 */
+        }
+        for (int r = 0; r < K; ++r) x_out[(int64_t)r * M + i] = (float)xn[r];
+        logg_out[i] = orc_fsv_logg(K, m, B, psi, xn, yt);
+    }
+}
+
+/* Bootstrap filter on the factor SV model, resampling every step as in
+ * orc_pf_run; y is [T][m]; means_out [T][K] (nullable). */
+int orc_fsv_run(int K, int m, const double* phi, const double* cholU, const double* B,
+                const double* psi, const float* y, int64_t T, int64_t M, uint64_t seed,
+                double* logZ_out, double* means_out)
+{
+    float* xa = (float*)calloc((size_t)K * M, sizeof(float));
+    float* xb = (float*)calloc((size_t)K * M, sizeof(float));
+    double* lg = (double*)malloc((size_t)M * sizeof(double));
+    double* lw = (double*)malloc((size_t)M * sizeof(double));
+    double* W = (double*)malloc((size_t)M * sizeof(double));
+    int32_t* anc = (int32_t*)malloc((size_t)M * sizeof(int32_t));
+    double sc[4];
+    double logZ = 0.0;
+    int rc = 0;
+    for (int64_t i = 0; i < M; ++i) anc[i] = (int32_t)i;
+    for (int64_t t = 1; t <= T; ++t) {
+        orc_fsv_step(K, m, phi, cholU, B, psi, y + (t - 1) * m, xa, anc, xb, lg, M, seed,
+                     (uint64_t)t);
+        for (int64_t i = 0; i < M; ++i) lw[i] = 0.0;
+        rc = orc_reweight(lg, 1.0, lw, M, W, sc);
+        if (rc) break;
+        logZ += sc[0];
+        if (means_out) {
+            for (int j = 0; j < K; ++j) {
+                double s = 0.0;
+                for (int64_t i = 0; i < M; ++i) s += W[i] * (double)xb[(int64_t)j * M + i];
+                means_out[(t - 1) * K + j] = s;
+            }
+        }
+        uint32_t u32 = orc_word(seed, ORC_P_RESAMPLE, (uint64_t)t, 0, 0);
+        rc = orc_resample_systematic(W, M, u32, anc, NULL);
+        if (rc) break;
+        float* tmp = xa; xa = xb; xb = tmp;
+    }
+    *logZ_out = logZ;
+    free(xa); free(xb); free(lg); free(lw); free(W); free(anc);
+    return rc;
+}
+
 /* SMC sampler with tempering (Section 3.3 and Section 4.1.2): particles
  * start from the uniform prior (theta0, supplied), beta_0 = 0; for
  * t = 1..T: reweight by (beta_t - beta_{t-1}) l, resample (systematic) iff

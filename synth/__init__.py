@@ -139,6 +139,42 @@ def simulate_ssm(kind: str, T: int, phi, Sigma, beta: float, seed: int = 7):
     return xs, ys.astype(np.float32)
 
 
+def fsv_params():
+    """The factor stochastic volatility model of Section 4.2: K = 3 factors,
+    m = 5 series, phi_i = 0.9, psi_i = 0.5, loading matrix B (m x K, zero
+    above the diagonal) and state covariance U as printed there.  Returns
+    (phi [K], U [K][K], B [m][K], psi [m])."""
+    B = np.array([[1.0, 0.0, 0.0],
+                  [0.5, 1.0, 0.0],
+                  [0.5, 0.5, 1.0],
+                  [0.2, 0.6, 0.3],
+                  [0.8, 0.7, 0.5]])
+    U = np.array([[0.5, 0.2, 0.1],
+                  [0.2, 0.5, 0.2],
+                  [0.1, 0.2, 0.5]])
+    return np.full(3, 0.9), U, B, np.full(5, 0.5)
+
+
+def simulate_fsv(T: int, phi, U, B, psi, seed: int = 7):
+    """Simulate x_{1:T} (x_0 = 0) and y_{1:T} of the factor SV model:
+    x_t = phi x_{t-1} + N(0, U), f_t ~ N(0, diag(exp x_t)), y_t = B f_t +
+    N(0, diag(psi)).  Returns (x [T][K] f64, y [T][m] f32)."""
+    phi = np.asarray(phi, np.float64)
+    B = np.asarray(B, np.float64)
+    L = chol(U)
+    K, m = phi.size, B.shape[0]
+    g = rng(seed)
+    x = np.zeros(K)
+    xs = np.zeros((T, K))
+    ys = np.zeros((T, m))
+    for t in range(T):
+        x = phi * x + L @ g.standard_normal(K)
+        f = np.exp(0.5 * x) * g.standard_normal(K)
+        ys[t] = B @ f + np.sqrt(np.asarray(psi, np.float64)) * g.standard_normal(m)
+        xs[t] = x
+    return xs, ys.astype(np.float32)
+
+
 def gaussian_logweights(M: int, scale: float = 1.0, seed: int = 5) -> np.ndarray:
     return scale * rng(seed).standard_normal(M)
 
@@ -198,6 +234,20 @@ class DiagWorkload:
 
 
 DIAG32 = DiagWorkload()
+
+
+@dataclass
+class FSVWorkload:
+    """Section 4.2 / Table 3: the bootstrap filter on the factor SV model,
+    T = 200 steps, particle counts as in the table, resampling every step."""
+    name: str = "fsv-m5-K3-T200"
+    T: int = 200
+    Ns: tuple = (8192, 16384, 32768, 65536, 131072)
+    data_seed: int = 7
+    method_seed: int = 77
+
+
+FSV = FSVWorkload()
 
 
 @dataclass
