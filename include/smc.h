@@ -260,15 +260,19 @@ smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y,
 
 /* ------------------------------------------------------------ particle filter */
 
-enum { SMC_PF_MSV = 0, SMC_PF_LG = 1 };
+enum { SMC_PF_MSV = 0, SMC_PF_LG = 1, SMC_PF_FSV = 2 };
 
 /* State-space model for pf_step, passed by value through a host pointer. */
 typedef struct smc_pf_model {
-    int32_t kind;          /* SMC_PF_MSV or SMC_PF_LG */
-    int32_t d;             /* state dimension, 1..8 */
+    int32_t kind;          /* SMC_PF_MSV, SMC_PF_LG or SMC_PF_FSV */
+    int32_t d;             /* state dimension: 1..8 (FSV: factors K, 1..4) */
     float phi[8];          /* x_t = phi (.) x_{t-1} + L z */
     float chol[64];        /* row-major lower Cholesky factor L of Sigma (d x d) */
-    float beta;            /* observation scale */
+    float beta;            /* observation scale (MSV, LG) */
+    /* factor stochastic volatility only (Section 4.2): */
+    int32_t m;             /* observed series, 1..8 */
+    float B[64];           /* row-major m x d factor loadings */
+    float psi[8];          /* idiosyncratic variances, > 0 */
 } smc_pf_model;
 
 /* One bootstrap particle-filter step (Section 3.2; the model of Section 4.2
@@ -278,7 +282,10 @@ typedef struct smc_pf_model {
  *   logg_out[i] = log g(y_t | x_out[:, i]):
  *     MSV: sum_j [ -1/2 log(2 pi beta^2) - x_j/2 - y_j^2 exp(-x_j) / (2 beta^2) ]
  *     LG:  sum_j [ -1/2 log(2 pi beta^2) - (y_j - x_j)^2 / (2 beta^2) ]
- *   y_t: device float[d];  x_in, x_out: float[d][M] (must not overlap);
+ *     FSV: log N(y_t; 0, B diag(exp x) B^T + diag(psi)), evaluated through the
+ *          Woodbury identity and the matrix determinant lemma (a d x d
+ *          Cholesky factor per particle instead of an m x m one).
+ *   y_t: device float[d] (FSV: float[m]);  x_in, x_out: float[d][M] (must not overlap);
  *   logg_out: double[M].  Feed logg_out to smc_reweight (dbeta = 1) and
  *   the weights to smc_resample_systematic for the next step's anc. */
 smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,

@@ -14,7 +14,7 @@ OP_LOGLIK, OP_MOVE, OP_POPMCMC = 0, 1, 2
 GMM_1D, GMM_DIAG = 0, 1
 PREC_FP32, PREC_BF16SPLIT = 0, 1
 MOVE_RW, MOVE_MALA = 0, 1
-PF_MSV, PF_LG = 0, 1
+PF_MSV, PF_LG, PF_FSV = 0, 1, 2
 
 # every entry point include/smc.h declares
 EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_status_string",
@@ -33,7 +33,8 @@ class SmcGmm(C.Structure):
 
 class SmcPfModel(C.Structure):
     _fields_ = [("kind", C.c_int32), ("d", C.c_int32), ("phi", C.c_float * 8),
-                ("chol", C.c_float * 64), ("beta", C.c_float)]
+                ("chol", C.c_float * 64), ("beta", C.c_float), ("m", C.c_int32),
+                ("B", C.c_float * 64), ("psi", C.c_float * 8)]
 
 
 _vp, _i64, _u64, _i32, _u32 = C.c_void_p, C.c_int64, C.c_uint64, C.c_int32, C.c_uint32

@@ -124,11 +124,27 @@ class DiagGMM(GMM):
 
 @dataclass
 class PFModel:
-    """State-space model for pf_step: MSV (Section 4.2 family) or linear-Gaussian."""
+    """State-space model for pf_step: MSV (Section 4.2 family), linear-Gaussian,
+    or the factor stochastic volatility model of Section 4.2 (kind PF_FSV:
+    state = factors' log-variances, loadings B [m][d], variances psi [m])."""
     kind: int
     phi: np.ndarray
     chol: np.ndarray
-    beta: float
+    beta: float = 1.0
+    B: np.ndarray = None
+    psi: np.ndarray = None
+
+    def cstruct_cached(self) -> L.SmcPfModel:
+        """The C struct, built once (the model's fields are not meant to change)."""
+        c = self.__dict__.get("_c")
+        if c is None:
+            c = self.cstruct()
+            self.__dict__["_c"] = c
+        return c
+
+    @property
+    def obs_dim(self) -> int:
+        return np.asarray(self.B).shape[0] if self.kind == L.PF_FSV else np.asarray(self.phi).size
 
     def cstruct(self) -> L.SmcPfModel:
         phi = np.asarray(self.phi, np.float64)
@@ -142,6 +158,16 @@ class PFModel:
             for j in range(d):
                 m.chol[i * d + j] = float(ch[i, j])
         m.beta = float(self.beta)
+        if self.kind == L.PF_FSV:
+            B = np.asarray(self.B, np.float64)
+            psi = np.asarray(self.psi, np.float64)
+            if B.ndim != 2 or B.shape[1] != d or psi.shape != (B.shape[0],):
+                raise ValueError("FSV model: B must be [m][d] and psi [m]")
+            m.m = B.shape[0]
+            for i in range(m.m):
+                m.psi[i] = float(psi[i])
+                for k in range(d):
+                    m.B[i * d + k] = float(B[i, k])
         return m
 
 
@@ -259,12 +285,12 @@ def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, sca
 def pf_step(ctx: Context, model: PFModel, y_t, x_in, x_out, logg_out, seed: int, t: int,
             anc=None, stream=None):
     d, M = x_in.shape
-    _need(y_t, torch.float32, "y_t", (d,))
+    _need(y_t, torch.float32, "y_t", (model.obs_dim,))
     _need(x_in, torch.float32, "x_in", (d, M))
     _need(x_out, torch.float32, "x_out", (d, M))
     _need(logg_out, torch.float64, "logg_out", (M,))
     _need(anc, torch.int32, "anc", (M,))
-    m = model.cstruct()
+    m = model.cstruct_cached()
     _chk(L.load().pf_step(ctx.handle, C.byref(m), _ptr(y_t), _ptr(x_in), _ptr(anc), _ptr(x_out),
                           _ptr(logg_out), M, int(seed), int(t), _stream(stream)), "pf_step")
 

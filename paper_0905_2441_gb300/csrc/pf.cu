@@ -56,19 +56,153 @@ __global__ void __launch_bounds__(256) k_pf_step(PfArgs A, const float* __restri
     }
 }
 
+// Factor stochastic volatility (Section 4.2): x_t in R^D (factor
+// log-variances), y_t in R^m with y_t | x_t ~ N(0, Sigma), Sigma = Psi +
+// B H B^T, H = diag(exp x).  With the Woodbury identity and the matrix
+// determinant lemma, for A = H^-1 + C, C = B^T Psi^-1 B:
+//   y^T Sigma^-1 y = q - |L_A^-1 v|^2,   v = B^T Psi^-1 y,  q = y^T Psi^-1 y
+//   log det Sigma  = log det Psi + sum_k x_k + log det A
+// so one particle needs a D x D Cholesky factor of A (D = 3 for the paper's
+// model) instead of the m x m one of Sigma.
+struct FsvArgs {
+    float phi[4];
+    float chol[16];    // L_U, row-major D x D
+    float C[16];       // B^T Psi^-1 B
+    float BtPi[32];    // B^T Psi^-1, row-major D x m
+    float inv_psi[8];
+    float cst;         // -(m/2) log 2 pi - 1/2 log det Psi
+    int m;
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_pf_fsv(FsvArgs A, const float* __restrict__ yt,
+                                                const float* __restrict__ x_in,
+                                                const int32_t* __restrict__ anc,
+                                                float* __restrict__ x_out,
+                                                double* __restrict__ logg, int64_t M,
+                                                uint64_t seed, uint64_t t, uint32_t* status) {
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    // the observation's projections, the same for every particle
+    float v[D], q = 0.0f;
+#pragma unroll
+    for (int k = 0; k < D; ++k) v[k] = 0.0f;
+    for (int j = 0; j < A.m; ++j) {
+        const float yj = yt[j];
+        q = fmaf(A.inv_psi[j] * yj, yj, q);
+#pragma unroll
+        for (int k = 0; k < D; ++k) v[k] = fmaf(A.BtPi[k * 8 + j], yj, v[k]);
+    }
+    constexpr float kLog2e = 1.4426950408889634f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
+        const int64_t src = anc ? (int64_t)anc[i] : i;
+        float z[D], x[D];
+        normals<D>(seed, RNG_PFNOISE, t, (uint32_t)i, D, z);
+        float sx = 0.0f;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            float val = A.phi[r] * x_in[(int64_t)r * M + src];
+#pragma unroll
+            for (int c = 0; c <= r; ++c) val = fmaf(A.chol[r * D + c], z[c], val);
+            x[r] = val;
+            x_out[(int64_t)r * M + i] = val;
+            sx += val;
+        }
+        // A = C + diag(exp(-x)); L L^T = A by Cholesky (rsqrt pivots); w = L^-1 v
+        float L[D][D], inv[D], w[D];
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+#pragma unroll
+            for (int c = 0; c <= r; ++c) {
+                float a = A.C[r * D + c];
+                if (c == r) a += ex2(-x[r] * kLog2e);
+#pragma unroll
+                for (int k = 0; k < c; ++k) a = fmaf(-L[r][k], L[c][k], a);
+                if (c == r) {
+                    inv[r] = rsqrtf(a);
+                    L[r][r] = a * inv[r];
+                } else {
+                    L[r][c] = a * inv[c];
+                }
+            }
+            float s = v[r];
+#pragma unroll
+            for (int k = 0; k < r; ++k) s = fmaf(-L[r][k], w[k], s);
+            w[r] = s * inv[r];
+        }
+        float prod = 1.0f, ww = 0.0f;
+#pragma unroll
+        for (int r = 0; r < D; ++r) {
+            prod *= L[r][r];
+            ww = fmaf(w[r], w[r], ww);
+        }
+        // log det A = 2 ln(prod L_rr)
+        const float lg = A.cst - 0.5f * (sx + 2.0f * 0.69314718055994531f * lg2(prod)) -
+                         0.5f * (q - ww);
+        if (lg != lg) raise_status(status, ST_NONFINITE);
+        logg[i] = f2d_bits(lg);
+    }
+}
+
 }  // namespace smc
+
+static smc_status pf_fsv(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
+                         const float* x_in, const int32_t* anc, float* x_out, double* logg_out,
+                         int64_t M, uint64_t seed, uint64_t t, cudaStream_t s) {
+    const int d = model->d, m = model->m;
+    if (d < 1 || d > 4 || m < 1 || m > 8) return SMC_ERR_ARG;
+    for (int j = 0; j < m; ++j)
+        if (!(model->psi[j] > 0.0f) || !std::isfinite(model->psi[j])) return SMC_ERR_ARG;
+    smc::FsvArgs A = {};
+    A.m = m;
+    double logdet_psi = 0.0;
+    for (int j = 0; j < m; ++j) {
+        A.inv_psi[j] = (float)(1.0 / (double)model->psi[j]);
+        logdet_psi += std::log((double)model->psi[j]);
+    }
+    for (int r = 0; r < d; ++r) {
+        A.phi[r] = model->phi[r];
+        for (int c = 0; c <= r; ++c) A.chol[r * d + c] = model->chol[r * d + c];
+        for (int j = 0; j < m; ++j)
+            A.BtPi[r * 8 + j] = (float)((double)model->B[j * d + r] / (double)model->psi[j]);
+        for (int c = 0; c < d; ++c) {
+            double v = 0.0;
+            for (int j = 0; j < m; ++j)
+                v += (double)model->B[j * d + r] * (double)model->B[j * d + c] /
+                     (double)model->psi[j];
+            A.C[r * d + c] = (float)v;
+        }
+    }
+    A.cst = (float)(-0.5 * (double)m * std::log(2.0 * M_PI) - 0.5 * logdet_psi);
+    int64_t blocks = (M + 255) / 256;
+    if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+#define SMC_FSV(DD)                                                                          \
+    smc::k_pf_fsv<DD><<<(unsigned)blocks, 256, 0, s>>>(A, y_t, x_in, anc, x_out, logg_out, M, \
+                                                       seed, t, ctx->d_status)
+    switch (d) {
+        case 1: SMC_FSV(1); break;
+        case 2: SMC_FSV(2); break;
+        case 3: SMC_FSV(3); break;
+        case 4: SMC_FSV(4); break;
+    }
+#undef SMC_FSV
+    return cuda_ok(cudaGetLastError());
+}
 
 extern "C" smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
                               const float* x_in, const int32_t* anc, float* x_out,
                               double* logg_out, int64_t M, uint64_t seed, uint64_t t,
                               void* stream) {
     if (!ctx || !model || M < 0) return SMC_ERR_ARG;
-    if (model->kind != SMC_PF_MSV && model->kind != SMC_PF_LG) return SMC_ERR_ARG;
-    if (model->d < 1 || model->d > 8 || !(model->beta > 0.0f)) return SMC_ERR_ARG;
+    if (model->kind != SMC_PF_MSV && model->kind != SMC_PF_LG && model->kind != SMC_PF_FSV)
+        return SMC_ERR_ARG;
+    if (model->kind != SMC_PF_FSV && (model->d < 1 || model->d > 8 || !(model->beta > 0.0f)))
+        return SMC_ERR_ARG;
     if (M == 0) return SMC_OK;
     if (!y_t || !x_in || !x_out || !logg_out || x_in == x_out) return SMC_ERR_ARG;
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
+    if (model->kind == SMC_PF_FSV)
+        return pf_fsv(ctx, model, y_t, x_in, anc, x_out, logg_out, M, seed, t, as_stream(stream));
     smc::PfArgs A;
     const int d = model->d;
     for (int i = 0; i < 8; ++i) A.phi[i] = i < d ? model->phi[i] : 0.0f;

@@ -156,7 +156,10 @@ class ParticleFilter(_Graphable):
     def __init__(self, ctx: api.Context, model: api.PFModel, y, M: int, seed: int = 77):
         self.ctx, self.model, self.M, self.seed = ctx, model, int(M), int(seed)
         self.y = _dev(y, torch.float32)
-        self.T, self.d = self.y.shape
+        self.T = self.y.shape[0]
+        self.d = int(np.asarray(model.phi).size)  # state dimension (FSV: factors)
+        if self.y.shape[1] != model.obs_dim:
+            raise ValueError("observations do not match the model's dimension")
         self.x = [torch.zeros(self.d, self.M, device="cuda") for _ in range(2)]
         self.logg = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.lw = torch.zeros(self.M, dtype=torch.float64, device="cuda")
