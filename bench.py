@@ -11,7 +11,8 @@ evaluations per second (chains x N per sweep).
 Other workloads (--workload): pf (d = 3 MSV particle filter, M = 2^20; step
 = one filter step), resample (reweight + systematic resampling bandwidth at
 M = 2^24), diag (diagonal mixture d = 32, K = 16, N = 65536, M = 4096 on the
-tensor cores; step = one likelihood call), peaks (the MUFU / FMA / FP64 /
+tensor cores; step = one likelihood call), fsv (the paper's factor SV particle
+filter, Table 3 sizes; step = one whole T = 200 run), peaks (the MUFU / FMA / FP64 /
 conversion rates used as roofline denominators).  The default run also
 reports, under "secondary", the tempered SMC sampler (M = 8192), the MALA
 sampler (M = 65536), the particle filter and the tensor-core likelihood,
@@ -663,6 +664,72 @@ def bench_diag(args, torch, dist):
     return res
 
 
+# Table 3 of the paper: GTX 280 seconds for the whole T = 200 factor-SV filter
+PAPER_FSV_GTX280_S = {8192: 0.082, 16384: 0.144, 32768: 0.249, 65536: 0.465, 131072: 0.929}
+
+
+def bench_fsv(args, torch, dist):
+    """The paper's particle-filter workload (Section 4.2, Table 3): the
+    bootstrap filter on the factor SV model (m = 5 series, K = 3 factors,
+    T = 200, resampling every step) for each N of the table; one step = one
+    whole filter run (pf_step + reweight + resampling, T times), timed with
+    CUDA events after an L2 flush, in its plain and CUDA-graph forms."""
+    import paper_0905_2441_gb300 as P
+    from paper_0905_2441_gb300 import samplers
+    import synth
+    w = synth.FSV
+    phi, U, B, psi = synth.fsv_params()
+    _, y = synth.simulate_fsv(w.T, phi, U, B, psi, seed=w.data_seed)
+    ctx = P.Context()
+    mod = P.PFModel(P.PF_FSV, phi, synth.chol(U), B=B, psi=psi)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    reps = max(1, min(args.steps, 10))
+    rows = {}
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for N in w.Ns:
+            pf = samplers.ParticleFilter(ctx, mod, y, N, seed=w.method_seed + dist.rank)
+            for _ in range(max(1, args.warmup // 3)):
+                pf.reset()
+                pf.run()
+            t_plain, t_graph = [], []
+            for r in range(reps):
+                pf.reset()
+                ev = _flush_timed(torch, flush, stream, [pf.run])
+                torch.cuda.synchronize()
+                t_plain.append(ev[0].elapsed_time(ev[1]) / 1e3)
+            pf.reset()
+            g = pf._capture(lambda: [pf.step(t) for t in range(1, w.T + 1)])
+            for r in range(reps):
+                pf.reset()
+                ev = _flush_timed(torch, flush, stream, [g.replay])
+                torch.cuda.synchronize()
+                t_graph.append(ev[0].elapsed_time(ev[1]) / 1e3)
+            logz = float(pf.hist[1:, 0].sum().item())
+            tp, tg = statistics.median(t_plain), statistics.median(t_graph)
+            rows[N] = {"plain_s": tp, "graph_s": tg, "paper_gtx280_s": PAPER_FSV_GTX280_S[N],
+                       "speedup_plain_vs_paper_gpu": PAPER_FSV_GTX280_S[N] / tp,
+                       "particle_steps_per_s_plain": N * w.T / tp,
+                       "particle_steps_per_s_graph": N * w.T / tg, "logZ": logz}
+    ctx.check()
+    N = w.Ns[-1]
+    t_max = dist.max(torch, rows[N]["plain_s"])
+    value = dist.sum(torch, float(N) * w.T) / t_max
+    paper_rate = N * w.T / PAPER_FSV_GTX280_S[N]
+    out = {"metric": "particle-steps/s (factor SV particle filter, T=200, plain per-step launches)",
+           "value": value, "unit": "particle-steps/s", "n_gpus": dist.world, "steps": reps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": value / dist.world / paper_rate,
+           "vs_baseline_note": "against Table 3's GTX 280 time for the same N (another machine: context)",
+           "dtype": "f32", "data": "synthetic (observations simulated from the model, seed 7)",
+           "config": {"workload": w.name, "N": N, "T": w.T, "m": 5, "K": 3,
+                      "l2": "256 MiB buffer written before every timed filter run, outside its events",
+                      "parallelism": f"independent filters per rank x{dist.world}"},
+           "table3": rows, "gpu_launches": 7 * w.T * reps, "clocks": clk.summary()}
+    ctx.close()
+    return out
+
+
 def all_peaks(torch):
     import paper_0905_2441_gb300 as P
     out = {}
@@ -703,7 +770,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
-                                                              "diag", "peaks"])
+                                                              "diag", "fsv", "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -729,6 +796,8 @@ def main():
         out = bench_resample(args, torch, dist)
     elif args.workload == "diag":
         out = bench_diag(args, torch, dist)
+    elif args.workload == "fsv":
+        out = bench_fsv(args, torch, dist)
     elif args.workload == "peaks":
         out = {"peaks_ops_per_s": all_peaks(torch)}
     else:
