@@ -54,6 +54,25 @@ inline smc_status cuda_ok(cudaError_t e) { return e == cudaSuccess ? SMC_OK : SM
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Launch with programmatic stream serialisation: the kernel may begin
+// launching while the previous kernel on the stream drains; it calls
+// grid_dep_wait() before touching anything that kernel wrote.
+template <typename... KArgs, typename... Args>
+inline smc_status launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                             cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cuda_ok(cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...));
+}
+
 // True while `s` is being captured into a graph.
 bool capturing(cudaStream_t s);
 

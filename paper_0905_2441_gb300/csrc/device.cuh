@@ -160,6 +160,18 @@ __device__ __forceinline__ float exp_hilo(float hi, float lo) {
     return ex2(f) * p2;
 }
 
+// Programmatic dependent launch: kernels of consecutive calls on a stream are
+// launched with programmatic serialisation; grid_dep_wait() holds the thread
+// until the previous grid has finished and its writes are visible, and
+// grid_dep_launch() lets the next grid start launching.  Both are no-ops for
+// a launch without the programmatic attribute.
+__device__ __forceinline__ void grid_dep_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // FP64 -> sortable signed 64-bit key (total order for non-NaN values)
 __device__ __forceinline__ long long dkey(double x) {
     long long b = __double_as_longlong(x);

@@ -43,6 +43,8 @@ __global__ void __launch_bounds__(256) k_mh_move(
     float* theta_out, double* ll_out, float* grad_out, int64_t M, const float* __restrict__ beta,
     int64_t beta_stride, float scale, uint64_t seed, uint64_t step, uint32_t* accept_count,
     Gmm1dArgs P, int L, int Kreal, int ychunk, uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     extern __shared__ __align__(16) float ys[];
     __shared__ uint32_t s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
@@ -210,17 +212,9 @@ __device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t* p, uint32_t v) 
     return old;
 }
 
-// Programmatic dependent launch: the next sweep in the stream may start its
-// prologue (data staging, random draws, population search: nothing this
-// sweep writes) while this one drains; grid_dep_wait() then holds every
-// thread until the previous grid has finished and its writes are visible.
-// Both are no-ops for a launch without the programmatic attribute.
-__device__ __forceinline__ void grid_dep_launch() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void grid_dep_wait() {
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-}
+// Consecutive sweeps use programmatic dependent launch: the next sweep's
+// prologue (data staging, random draws, population search: nothing a sweep
+// writes) overlaps this one's tail; grid_dep_wait() precedes the chain state.
 
 template <int K, bool EQW>
 __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
@@ -433,10 +427,9 @@ static smc_status launch_move(int blocks, int threads, cudaStream_t s, const flo
                               uint64_t step, uint32_t* acc, const smc::Gmm1dArgs& P, int L, int Kr,
                               uint32_t* st) {
     const int yc = smc::ychunk_for(N);
-    smc::k_mh_move<K, MALA, EQW><<<blocks, threads, smc::ysmem_bytes(yc), s>>>(
-        y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs, scale, seed, step, acc, P, L, Kr, yc,
-        st);
-    return cuda_ok(cudaGetLastError());
+    return launch_pdl(smc::k_mh_move<K, MALA, EQW>, dim3(blocks), dim3(threads),
+                      smc::ysmem_bytes(yc), s, y, N, th, l, g, anc, flag, tho, lo, go, M, beta, bs,
+                      scale, seed, step, acc, P, L, Kr, yc, st);
 }
 
 template <int K>

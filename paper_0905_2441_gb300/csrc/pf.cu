@@ -26,6 +26,8 @@ __global__ void __launch_bounds__(256) k_pf_step(PfArgs A, const float* __restri
                                                  float* __restrict__ x_out,
                                                  double* __restrict__ logg, int64_t M,
                                                  uint64_t seed, uint64_t t, uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     float y[D];
 #pragma unroll
@@ -81,6 +83,8 @@ __global__ void __launch_bounds__(256) k_pf_fsv(FsvArgs A, const float* __restri
                                                 float* __restrict__ x_out,
                                                 double* __restrict__ logg, int64_t M,
                                                 uint64_t seed, uint64_t t, uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     // the observation's projections, the same for every particle
     float v[D], q = 0.0f;
@@ -175,17 +179,17 @@ static smc_status pf_fsv(smc_ctx* ctx, const smc_pf_model* model, const float* y
     A.cst = (float)(-0.5 * (double)m * std::log(2.0 * M_PI) - 0.5 * logdet_psi);
     int64_t blocks = (M + 255) / 256;
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
-#define SMC_FSV(DD)                                                                          \
-    smc::k_pf_fsv<DD><<<(unsigned)blocks, 256, 0, s>>>(A, y_t, x_in, anc, x_out, logg_out, M, \
-                                                       seed, t, ctx->d_status)
+#define SMC_FSV(DD)                                                                       \
+    return launch_pdl(smc::k_pf_fsv<DD>, dim3((unsigned)blocks), dim3(256), 0, s, A, y_t, x_in, \
+                      anc, x_out, logg_out, M, seed, t, ctx->d_status)
     switch (d) {
-        case 1: SMC_FSV(1); break;
-        case 2: SMC_FSV(2); break;
-        case 3: SMC_FSV(3); break;
-        case 4: SMC_FSV(4); break;
+        case 1: SMC_FSV(1);
+        case 2: SMC_FSV(2);
+        case 3: SMC_FSV(3);
+        case 4: SMC_FSV(4);
     }
 #undef SMC_FSV
-    return cuda_ok(cudaGetLastError());
+    return SMC_ERR_ARG;
 }
 
 extern "C" smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
@@ -216,25 +220,21 @@ extern "C" smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const flo
     if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
     cudaStream_t s = as_stream(stream);
     bool msv = model->kind == SMC_PF_MSV;
-#define SMC_PF(DD)                                                                          \
-    do {                                                                                    \
-        if (msv)                                                                            \
-            smc::k_pf_step<DD, true><<<(unsigned)blocks, 256, 0, s>>>(                      \
-                A, y_t, x_in, anc, x_out, logg_out, M, seed, t, ctx->d_status);             \
-        else                                                                                \
-            smc::k_pf_step<DD, false><<<(unsigned)blocks, 256, 0, s>>>(                     \
-                A, y_t, x_in, anc, x_out, logg_out, M, seed, t, ctx->d_status);             \
-    } while (0)
+#define SMC_PF(DD)                                                                        \
+    return msv ? launch_pdl(smc::k_pf_step<DD, true>, dim3((unsigned)blocks), dim3(256), 0, s, \
+                            A, y_t, x_in, anc, x_out, logg_out, M, seed, t, ctx->d_status)   \
+               : launch_pdl(smc::k_pf_step<DD, false>, dim3((unsigned)blocks), dim3(256), 0, \
+                            s, A, y_t, x_in, anc, x_out, logg_out, M, seed, t, ctx->d_status)
     switch (d) {
-        case 1: SMC_PF(1); break;
-        case 2: SMC_PF(2); break;
-        case 3: SMC_PF(3); break;
-        case 4: SMC_PF(4); break;
-        case 5: SMC_PF(5); break;
-        case 6: SMC_PF(6); break;
-        case 7: SMC_PF(7); break;
-        case 8: SMC_PF(8); break;
+        case 1: SMC_PF(1);
+        case 2: SMC_PF(2);
+        case 3: SMC_PF(3);
+        case 4: SMC_PF(4);
+        case 5: SMC_PF(5);
+        case 6: SMC_PF(6);
+        case 7: SMC_PF(7);
+        case 8: SMC_PF(8);
     }
 #undef SMC_PF
-    return cuda_ok(cudaGetLastError());
+    return SMC_ERR_ARG;
 }

@@ -7,19 +7,20 @@
 //   C_j = q_0 + ... + q_j,  S = C_{M-1}
 //   F(c) = #{ i in [0,M) : (i 2^32 + u32) S < c M 2^32 }
 //   particle j fills output slots [F(C_{j-1}), F(C_j)).
-// Pass 1 sums q exactly per tile and per group of 64 tiles (integer
-// atomics: order-free).  Pass 2 takes one tile of 2048 weights per CTA: the
-// total and its exclusive prefix are one parallel read of the group and
-// tile sums (no CTA waits on another), then a block scan, F at every prefix
-// by an FP32 estimate and an exact 128-bit fix-up, and a balanced expansion
-// of the tile's contiguous output range through shared memory.
+// Pass 1 sums q exactly per tile of 2048 weights.  One CTA then turns the
+// tile sums into exclusive prefixes and forms the call's constants (S, the
+// draw u, fixed-point reciprocals of S).  Pass 2 is persistent: per tile a
+// block scan, F at every prefix by a fixed-point quotient and an exact
+// 128-bit fix-up, and a balanced expansion of the tile's contiguous output
+// range through shared memory.  The kernels are chained by programmatic
+// dependent launch, so each one's launch overlaps the previous one's tail.
 #include "ctx.hpp"
 #include "device.cuh"
 #include "resample.cuh"
 
 using namespace smc_host;
 
-// scratch of the context entry point: tile and group sums, the heavy-chunk
+// scratch of the context entry point: tile sums, constants, the heavy-chunk
 // counter and records, and the inclusive F of heavy tiles' items
 size_t smc_resample_ws_bytes(int64_t M) {
     return (size_t)(smc::rs_words(M) + 1) * sizeof(unsigned long long) +
@@ -33,6 +34,8 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ anc,
                                                 float* __restrict__ dst,
                                                 const double* __restrict__ src64,
                                                 double* __restrict__ dst64) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
         int64_t a = anc ? (int64_t)anc[i] : i;
@@ -50,18 +53,14 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s) {
     const int64_t tiles = smc::rs_tiles(M);
     if (tiles > 0x7FFFFFFF) return SMC_ERR_ARG;
-    // the group sums (and the constants and heavy-chunk counter after them)
-    // must start at zero
-    SMC_CUDA(cudaMemsetAsync(sc.group_sum, 0,
-                             (size_t)(smc::rs_groups(M) + smc::kRsConstWords +
-                                      (sc.heavy_count ? 1 : 0)) *
-                                 sizeof(unsigned long long), s));
     int64_t b1 = tiles;
     if (b1 > (int64_t)num_sms * 4) b1 = (int64_t)num_sms * 4;
-    smc::k_resample_total<<<(unsigned)b1, smc::kRsThreads, 0, s>>>(W, M, do_flag, sc, status);
-    SMC_CUDA(cudaGetLastError());
-    smc::k_resample_finalize<<<1, smc::kRsFinThreads, 0, s>>>(M, seed, step, do_flag, sc, status);
-    SMC_CUDA(cudaGetLastError());
+    smc_status st = launch_pdl(smc::k_resample_total, dim3((unsigned)b1), dim3(smc::kRsThreads), 0,
+                               s, W, M, do_flag, sc, status);
+    if (st != SMC_OK) return st;
+    st = launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), 0, s, M, seed,
+                    step, do_flag, sc, status);
+    if (st != SMC_OK) return st;
     // pass 2 is persistent: as many CTAs as are resident at once
     static int occ = 0;
     if (occ == 0 &&
@@ -71,28 +70,29 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
         occ = 1;
     int64_t g2 = (int64_t)num_sms * occ;
     if (g2 > tiles) g2 = tiles;
-    smc::k_resample_scan<<<(unsigned)g2, smc::kRsThreads, 0, s>>>(
-        W, M, seed, step, do_flag, sc, anc, counts, lwreset, status);
-    SMC_CUDA(cudaGetLastError());
+    st = launch_pdl(smc::k_resample_scan, dim3((unsigned)g2), dim3(smc::kRsThreads), 0, s, W, M,
+                    seed, step, do_flag, sc, anc, counts, lwreset, status);
+    if (st != SMC_OK) return st;
     if (sc.heavy_list) {
-        smc::k_resample_heavy<<<(unsigned)num_sms * 4, smc::kRsThreads, 0, s>>>(do_flag, sc, M, anc);
-        SMC_CUDA(cudaGetLastError());
+        st = launch_pdl(smc::k_resample_heavy, dim3((unsigned)num_sms * 4), dim3(smc::kRsThreads),
+                        0, s, do_flag, sc, M, anc);
+        if (st != SMC_OK) return st;
     }
     return SMC_OK;
 }
 
-// scratch layout inside `base`: tile sums, group sums, then (when `heavy`)
-// the heavy-chunk counter, the chunk records and the items' inclusive F
+// scratch layout inside `base`: tile sums, the call constants, then (when
+// `heavy`) the heavy-chunk counter, the chunk records and the items'
+// inclusive F
 smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy) {
     smc::RsScratch sc;
     sc.tile_sum = base;
-    sc.group_sum = base + smc::rs_tiles(M);
-    sc.cst = reinterpret_cast<smc::RsConst*>(sc.group_sum + smc::rs_groups(M));
+    sc.cst = reinterpret_cast<smc::RsConst*>(base + smc::rs_tiles(M));
     sc.heavy_count = nullptr;
     sc.heavy_list = nullptr;
     sc.fpos = nullptr;
     if (heavy) {
-        sc.heavy_count = sc.group_sum + smc::rs_groups(M) + smc::kRsConstWords;
+        sc.heavy_count = base + smc::rs_tiles(M) + smc::kRsConstWords;
         uintptr_t p = reinterpret_cast<uintptr_t>(sc.heavy_count + 1);
         p = (p + 255) & ~(uintptr_t)255;
         sc.heavy_list = reinterpret_cast<uint4*>(p);
@@ -133,9 +133,8 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
     if (st != SMC_OK) return st;
     int64_t b = (M + 255) / 256;
     if (b > (int64_t)ctx->num_sms * 16) b = (int64_t)ctx->num_sms * 16;
-    smc::k_gather<<<(unsigned)b, 256, 0, as_stream(stream)>>>(anc, M, rows_f32, src_f32, dst_f32,
-                                                              src_f64, dst_f64);
-    return cuda_ok(cudaGetLastError());
+    return launch_pdl(smc::k_gather, dim3((unsigned)b), dim3(256), 0, as_stream(stream), anc, M,
+                      rows_f32, src_f32, dst_f32, src_f64, dst_f64);
 }
 
 // ------------------------------------------------------------------ no-allocation variant
@@ -144,7 +143,7 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 // they do not own (a framework's caching pool, a serving runtime with a
 // fixed memory budget), and latency-critical loops that cannot afford the
 // implicit device synchronisation of cudaMalloc / cudaFree.  No context is
-// created: the scan's scratch (tile, group and total sums) lives in a
+// created: the scan's scratch (tile sums and constants) lives in a
 // file-scope device array that every GPU loading this library holds until
 // the process exits.
 #include <mutex>
@@ -152,10 +151,8 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 namespace {
 
 constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;   // 16,777,216 weights
-// 8192 tile sums + 128 group sums + the call constants: about 65 KiB per device
-constexpr int64_t kNoAllocWords = (kNoAllocMaxM / smc::kRsTile) +
-                                  (kNoAllocMaxM / smc::kRsTile / smc::kRsGroup) +
-                                  smc::kRsConstWords;
+// 8192 tile sums + the call constants: about 64 KiB per device
+constexpr int64_t kNoAllocWords = (kNoAllocMaxM / smc::kRsTile) + smc::kRsConstWords;
 static_assert(sizeof(smc::RsConst) <= smc::kRsConstWords * sizeof(unsigned long long),
               "constants fit their words");
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];
@@ -199,8 +196,8 @@ extern "C" smc_status smc_resample_systematic_noalloc(const double* W, int64_t M
     SMC_CUDA(cudaGetDevice(&dev));
     SMC_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     cudaStream_t s = as_stream(stream);
-    // resample_launch clears the group sums before pass 1; pass 1
-    // overwrites every tile sum it uses
+    // pass 1 overwrites every tile sum it uses; the constants are formed
+    // anew by each call
     // no heavy-chunk scratch: a tile with many slots is expanded by its CTA
     const smc::RsScratch sc = resample_scratch(scratch, M, false);
     return resample_launch(sms, W, M, seed, step, ancestors_out, counts_out, do_flag, logw_reset,

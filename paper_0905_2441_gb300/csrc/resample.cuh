@@ -19,7 +19,6 @@ namespace smc {
 constexpr int kRsThreads = 256;
 constexpr int kRsIpt = 8;                      // weights per thread
 constexpr int kRsTile = kRsThreads * kRsIpt;   // weights per tile
-constexpr int kRsGroup = 64;                   // tiles per group sum
 constexpr unsigned long long kMaxTotal = 1ull << 61;   // S must stay below this
 constexpr int kRsStage = 2 * kRsTile;          // output slots of a tile staged in shared memory
 
@@ -37,8 +36,7 @@ constexpr int kRsConstWords = 8;
 
 struct RsScratch {
     unsigned long long* tile_sum;   // [ntiles]: tile sums, then their exclusive prefixes
-    unsigned long long* group_sum;  // [ceil(ntiles / kRsGroup)], zero before pass 1
-    RsConst* cst;                   // after the group sums
+    RsConst* cst;                   // after the tile sums
     // grid-wide expansion of tiles with many output slots (optional: when
     // null, such a tile is expanded by its own CTA)
     unsigned long long* heavy_count;  // chunk records written, zero before pass 2
@@ -47,13 +45,8 @@ struct RsScratch {
 };
 
 __host__ __device__ inline int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1) / kRsTile; }
-__host__ __device__ inline int64_t rs_groups(int64_t M) {
-    return (rs_tiles(M) + kRsGroup - 1) / kRsGroup;
-}
-// words of scratch for M weights: tile sums, group sums, constants
-__host__ __device__ inline int64_t rs_words(int64_t M) {
-    return rs_tiles(M) + rs_groups(M) + kRsConstWords;
-}
+// words of scratch for M weights: tile sums, constants
+__host__ __device__ inline int64_t rs_words(int64_t M) { return rs_tiles(M) + kRsConstWords; }
 // output slots of one heavy-expansion chunk, and the most chunk records M
 // weights can produce (a tile's range is split into chunks; ranges add to M)
 constexpr int kRsChunk = 4096;
@@ -135,13 +128,13 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-// Pass 1: tile sums and group sums.  Each CTA takes a contiguous range of
-// tiles and adds to a group sum once per group it touches (integer atomics
-// on distinct words), so no word receives more than a few atomics; the
-// grand total is formed from the group sums in pass 2.
+// Pass 1: the exact integer sum of every tile (each CTA a contiguous range
+// of tiles, the next tile's weights loading while one is reduced).
 __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __restrict__ W,
                                                                int64_t M, const int32_t* do_flag,
                                                                RsScratch sc, uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
     __shared__ unsigned long long sh[kRsThreads / 32];
     const int64_t ntiles = rs_tiles(M);
@@ -149,8 +142,6 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __r
     const int64_t t0 = (int64_t)blockIdx.x * per;
     const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
     bool bad = false;
-    unsigned long long gacc = 0;
-    int64_t gcur = t0 / kRsGroup;
     double vn[kRsIpt];
     if (t0 < t1) load_tile_raw(W, M, t0, vn);
     for (int64_t t = t0; t < t1; ++t) {
@@ -164,21 +155,8 @@ __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __r
         const unsigned long long ts = block_sum_u64(acc, sh);  // <= 2^63: no wrap
         if (threadIdx.x == 0) {
             sc.tile_sum[t] = ts;
-            const int64_t g = t / kRsGroup;
-            if (g != gcur) {
-                const unsigned long long old = atomicAdd(sc.group_sum + gcur, gacc);
-                if (old + gacc < old) bad = true;
-                gacc = 0;
-                gcur = g;
-            }
-            const unsigned long long n = gacc + ts;
-            if (n < gacc || ts >= kMaxTotal) bad = true;  // far from normalised
-            gacc = n;
+            if (ts >= kMaxTotal) bad = true;  // far from normalised
         }
-    }
-    if (threadIdx.x == 0 && t0 < t1) {
-        const unsigned long long old = atomicAdd(sc.group_sum + gcur, gacc);
-        if (old + gacc < old) bad = true;
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) raise_status(status, ST_BADARG);
 }
@@ -259,6 +237,8 @@ constexpr int kRsFinThreads = 1024;
 __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc,
     uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
     __shared__ unsigned long long s_w[kRsFinThreads / 32];
     __shared__ int s_bad;
@@ -316,6 +296,7 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
             run += v[k];
         }
     }
+    if (tid == 0 && sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
     if (tid == 0) {
         RsConst c;
         c.ok = 0;
@@ -348,6 +329,8 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
     const double* __restrict__ W, int64_t M, uint64_t seed, uint64_t step,
     const int32_t* do_flag, RsScratch sc, int32_t* __restrict__ anc,
     int32_t* __restrict__ counts, double* __restrict__ lwreset, uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     __shared__ uint32_t s_hi[kRsTile];            // F at each item's inclusive prefix
     __shared__ int32_t s_anc[kRsStage];           // the tile's ancestors, staged for coalesced stores
     __shared__ unsigned long long s_warp[kRsThreads / 32];
@@ -536,6 +519,8 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
 // values; its slots are staged in shared memory and stored slot-major.
 __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
     const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
     __shared__ int32_t s_anc[kRsChunk];
     const unsigned long long n = __ldcg(sc.heavy_count);

@@ -240,6 +240,8 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
                                                          int32_t* __restrict__ flag,
                                                          double ess_frac, int final_slot,
                                                          uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     __shared__ long long s_key[48];
     __shared__ float s_a[32], s_b[32];
     __shared__ bool last;
@@ -339,6 +341,8 @@ __global__ void __launch_bounds__(256) k_reweight_normalize(const double* __rest
                                                             int64_t M,
                                                             const double* __restrict__ fin,
                                                             double* __restrict__ W) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     if (fin[3] == 0.0) return;
     float mh, ml;
     split_double(fin[0], mh, ml);
@@ -369,6 +373,8 @@ __global__ void __launch_bounds__(256) k_ess_reduce(const double* __restrict__ l
                                                     unsigned long long* ticket,
                                                     double* __restrict__ ess_out,
                                                     uint32_t* status) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
     __shared__ long long s_key[48];
     __shared__ float s_a[32], s_b[32];
     __shared__ bool last;
@@ -438,18 +444,18 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
     int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
     int blocks = reduce_blocks(ctx, M);
     const int final_slot = kMaxPartialBlocks - 1;
-    smc::k_reweight_reduce<<<blocks, 256, 0, s>>>(loglik, dbeta, logw, M, has_inc, ctx->d_partials,
-                                                  ctx->d_counters + CNT_REWEIGHT_TICKET, scalars_out,
-                                                  resample_flag_out, ess_frac, final_slot,
-                                                  ctx->d_status);
-    SMC_CUDA(cudaGetLastError());
+    st = launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw, M,
+                    has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET, scalars_out,
+                    resample_flag_out, ess_frac, final_slot, ctx->d_status);
+    if (st != SMC_OK) return st;
     if (W_out) {
         int nb = (int)((M + 256 * 8 - 1) / (256 * 8));
         int cap = ctx->num_sms * 8;
         if (nb > cap) nb = cap;
-        smc::k_reweight_normalize<<<nb, 256, 0, s>>>(logw, M,
-                                                     ctx->d_partials + (size_t)final_slot * 8, W_out);
-        SMC_CUDA(cudaGetLastError());
+        st = launch_pdl(smc::k_reweight_normalize, dim3(nb), dim3(256), 0, s,
+                        (const double*)logw, M,
+                        (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out);
+        if (st != SMC_OK) return st;
     }
     return SMC_OK;
 }
@@ -461,8 +467,6 @@ extern "C" smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, doubl
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
     int blocks = reduce_blocks(ctx, M);
-    smc::k_ess_reduce<<<blocks, 256, 0, s>>>(logw, M, ctx->d_partials,
-                                             ctx->d_counters + CNT_ESS_TICKET, ess_out,
-                                             ctx->d_status);
-    return cuda_ok(cudaGetLastError());
+    return launch_pdl(smc::k_ess_reduce, dim3(blocks), dim3(256), 0, s, logw, M, ctx->d_partials,
+                      ctx->d_counters + CNT_ESS_TICKET, ess_out, ctx->d_status);
 }
