@@ -12,7 +12,9 @@ Other workloads (--workload): pf (d = 3 MSV particle filter, M = 2^20; step
 = one filter step), resample (reweight + systematic resampling bandwidth at
 M = 2^24), diag (diagonal mixture d = 32, K = 16, N = 65536, M = 4096 on the
 tensor cores; step = one likelihood call), fsv (the paper's factor SV particle
-filter, Table 3 sizes; step = one whole T = 200 run), peaks (the MUFU / FMA / FP64 /
+filter, Table 3 sizes; step = one whole T = 200 run), tables (the paper's
+Tables 1 and 2 configurations, every size; step = one whole run of each),
+peaks (the MUFU / FMA / FP64 /
 conversion rates used as roofline denominators).  The default run also
 reports, under "secondary", the tempered SMC sampler (M = 8192), the MALA
 sampler (M = 65536), the particle filter and the tensor-core likelihood,
@@ -730,6 +732,126 @@ def bench_fsv(args, torch, dist):
     return out
 
 
+# Tables 1 and 2 (Section 4.1): GTX 280 seconds and single-core CPU minutes
+PAPER_T1_GTX280_S = {8: 1.083, 32: 1.098, 128: 1.100, 512: 1.235, 2048: 1.427, 8192: 2.323,
+                     32768: 7.729, 131072: 28.349}
+PAPER_T1_CPU_MIN = {8: 0.0166, 32: 0.0656, 128: 0.262, 512: 1.04, 2048: 4.16, 8192: 16.64,
+                    32768: 66.7, 131072: 270.3}
+PAPER_T2_GTX280_S = {8192: 0.597, 16384: 1.114, 32768: 2.114, 65536: 4.270, 131072: 8.075,
+                     262144: 16.219}
+PAPER_T2_CPU_MIN = {8192: 4.44, 16384: 8.82, 32768: 17.7, 65536: 35.3, 131072: 70.6,
+                    262144: 141.0}
+
+
+def _whole_run(torch, flush, stream, fn):
+    """CUDA-event seconds of one whole run, L2 flushed just before it."""
+    ev = _flush_timed(torch, flush, stream, [fn])
+    torch.cuda.synchronize()
+    return ev[0].elapsed_time(ev[1]) / 1e3
+
+
+def paper_tables(torch, P, ctx, flush, reps=1, rank=0):
+    """Table 1 (population MCMC: one population of M chains, beta_i = (i/M)^2,
+    N(0, I_4) random walk, 8192 sweeps) and Table 2 (SMC sampler: N
+    particles, 200 temperatures beta_t = (t/200)^2, 10 N(0, I_4) moves per
+    temperature, resampling when ESS < N/2), each whole run timed in its
+    plain (one C-ABI call per kernel step) and CUDA-graph forms."""
+    from paper_0905_2441_gb300 import samplers
+    import synth
+    w = synth.PAPER_TABLES
+    y = w.data()
+    model = P.GMM(w.K, w.sigma)
+    stream = torch.cuda.current_stream()
+    t1 = {}
+    for M in w.table1_M:
+        off = np.array([0, M], np.int32)
+        beta = synth.power_betas(M).astype(np.float32)
+        th0 = synth.prior_particles(w.K, M, seed=w.particle_seed + rank)
+        smp = samplers.PopulationMCMC(ctx, model, y, off, beta, th0, scale=w.scale,
+                                      seed=w.method_seed + rank)
+        smp.run(3)  # warm
+        n = w.table1_sweeps
+        tp = min(_whole_run(torch, flush, stream, lambda: smp.run(n, start=3)) for _ in range(reps))
+        g = smp._capture(lambda: [smp.sweep(3 + n + i) for i in range(n)])
+        tg = min(_whole_run(torch, flush, stream, g.replay) for _ in range(reps))
+        del g
+        st = smp.stats.cpu().numpy()
+        split = M > 2 * 256
+        t1[M] = {"plain_s": tp, "graph_s": tg, "paper_gtx280_s": PAPER_T1_GTX280_S[M],
+                 "paper_cpu_min": PAPER_T1_CPU_MIN[M],
+                 "speedup_plain_vs_paper_gpu": PAPER_T1_GTX280_S[M] / tp,
+                 "speedup_graph_vs_paper_gpu": PAPER_T1_GTX280_S[M] / tg,
+                 "pd_per_s_graph": M * w.N * n / tg,
+                 "launches_per_sweep": 2 if split else 1,
+                 "swap_rate": float(st[1]) / max(1.0, float(st[2])),
+                 "mh_accept_rate": float(st[0]) / float(M * (3 + 2 * n * reps))}
+        ctx.check()
+    t2 = {}
+    betas = synth.power_betas(w.table2_T, start=0)
+    for N in w.table2_N:
+        th0 = synth.prior_particles(w.K, N, seed=w.particle_seed + rank)
+        smp = samplers.SMCSampler(ctx, model, y, th0, betas, scale=w.scale,
+                                  seed=w.method_seed + rank, n_moves=w.table2_moves)
+        smp.run()  # warm
+        tps = []
+        for _ in range(reps):
+            smp.reset(th0)
+            tps.append(_whole_run(torch, flush, stream, smp.run))
+        z_plain = smp.log_evidence()
+        smp.reset(th0)
+        g = smp._capture(smp._body)
+        tgs = []
+        for _ in range(reps):
+            smp.reset(th0)
+            tgs.append(_whole_run(torch, flush, stream, g.replay))
+        del g
+        tp, tg = min(tps), min(tgs)
+        t2[N] = {"plain_s": tp, "graph_s": tg, "paper_gtx280_s": PAPER_T2_GTX280_S[N],
+                 "paper_cpu_min": PAPER_T2_CPU_MIN[N],
+                 "speedup_plain_vs_paper_gpu": PAPER_T2_GTX280_S[N] / tp,
+                 "speedup_graph_vs_paper_gpu": PAPER_T2_GTX280_S[N] / tg,
+                 "pd_per_s_plain": N * w.N * w.table2_T * w.table2_moves / tp,
+                 "logZ": z_plain, "resampled_steps": int(smp.flags[1:].sum().item())}
+        ctx.check()
+    return {"workload": w.name, "table1": t1, "table2": t2,
+            "launches_per_table2_step": 6 + w.table2_moves}
+
+
+def bench_tables(args, torch, dist):
+    """The paper's Tables 1 and 2 replicated on this GPU; the JSON line's
+    value is Table 2's largest run (N = 262144) in its plain form."""
+    import paper_0905_2441_gb300 as P
+    import synth
+    w = synth.PAPER_TABLES
+    ctx = P.Context()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    reps = max(1, min(args.steps, 5))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        tab = paper_tables(torch, P, ctx, flush, reps=reps, rank=dist.rank)
+    ctx.close()
+    N = w.table2_N[-1]
+    work = float(N) * w.N * w.table2_T * w.table2_moves
+    t_max = dist.max(torch, tab["table2"][N]["plain_s"])
+    value = dist.sum(torch, work) / t_max
+    paper_rate = work / PAPER_T2_GTX280_S[N]
+    launches = (w.table2_T * tab["launches_per_table2_step"]) * reps * 2
+    return {"metric": "particle-datum loglik evals/s (Table 2 SMC sampler, 200 temperatures x 10 "
+                      "RW moves, plain per-call launches)",
+            "value": value, "unit": "p*d/s", "n_gpus": dist.world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": value / dist.world / paper_rate,
+            "vs_baseline_note": "against Table 2's GTX 280 time for N = 262144 (another machine: "
+                                "context)",
+            "dtype": "f32 likelihood terms, f64 totals and weights",
+            "data": "synthetic (Section 4.1 model, 100 simulated observations, seed 1)",
+            "config": {"workload": w.name, "N": N, "T": w.table2_T, "moves": w.table2_moves,
+                       "m": w.N, "k": w.K,
+                       "l2": "256 MiB buffer written before every timed run, outside its events",
+                       "parallelism": f"independent samplers per rank x{dist.world}"},
+            "table1": tab["table1"], "table2": tab["table2"], "gpu_launches": launches,
+            "clocks": clk.summary()}
+
+
 def all_peaks(torch):
     import paper_0905_2441_gb300 as P
     out = {}
@@ -770,7 +892,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
-                                                              "diag", "fsv", "peaks"])
+                                                              "diag", "fsv", "tables", "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -798,6 +920,8 @@ def main():
         out = bench_diag(args, torch, dist)
     elif args.workload == "fsv":
         out = bench_fsv(args, torch, dist)
+    elif args.workload == "tables":
+        out = bench_tables(args, torch, dist)
     elif args.workload == "peaks":
         out = {"peaks_ops_per_s": all_peaks(torch)}
     else:

@@ -235,7 +235,7 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
                        const float* beta, int64_t beta_stride, float scale, int32_t kind,
                        uint64_t seed, uint64_t step, uint32_t* accept_count, void* stream);
 
-/* One sweep of population MCMC over many independent populations in ONE
+/* One sweep of population MCMC over many independent populations in one
  * persistent launch (Section 3.1; Section 4.1.1).  Population q owns chains
  * pop_offsets[q] .. pop_offsets[q+1]-1 of theta (float[K][M_total]) and
  * loglik (double[M_total]), updated in place; beta is float[M_total].
@@ -248,7 +248,11 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
  *   log u_j < (beta_a - beta_b)(l_b - l_a), u_j from word 4 + j.
  * The CTAs take equal chunks of chains from a work queue; a population's
  * exchange runs as soon as its last chain has moved, so populations of any
- * size mix freely.  pop_offsets must be non-decreasing with
+ * size mix freely.  When the average population holds more than two chains
+ * per thread of a CTA (M_total > 2 * n_pops * threads, e.g. the single
+ * population of Table 1), stage 2 runs instead as a second, grid-wide
+ * launch over all pairs, with the same pairs, draws and result.
+ * pop_offsets must be non-decreasing with
  * pop_offsets[0] = 0 and pop_offsets[n_pops] = M_total.
  * stats (device uint64[3], nullable) accumulates {MH accepts, swaps
  *   accepted, swaps attempted}.  Uses n_pops counters of context scratch

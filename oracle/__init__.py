@@ -100,8 +100,8 @@ def _declare(L):
     L.orc_kalman_lg.argtypes = [C.c_int, _f64p, _f64p, C.c_double, _f32p, _i64, _vp]
     L.orc_kalman_lg.restype = C.c_double
     L.orc_smc_run.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double, C.c_double,
-                              _f32p, _i64, _f64p, _i64, C.c_int, C.c_float, C.c_double, _u64,
-                              C.POINTER(C.c_double), _vp, _vp]
+                              _f32p, _i64, _f64p, _i64, C.c_int, C.c_float, C.c_int, C.c_double,
+                              _u64, C.POINTER(C.c_double), _vp, _vp]
     L.orc_smc_run.restype = C.c_int
 
 
@@ -354,8 +354,9 @@ def kalman_lg(phi, Sigma, bscale, y, want_means=False):
     return (ll, means) if want_means else ll
 
 
-def smc_run(y, logw, sigma, box, theta0, betas, kind, scale, ess_frac, seed):
-    """Tempered SMC sampler (Sections 3.3, 4.1.2); returns (logZ, theta, ess, resampled)."""
+def smc_run(y, logw, sigma, box, theta0, betas, kind, scale, ess_frac, seed, n_moves=1):
+    """Tempered SMC sampler (Sections 3.3, 4.1.2) with n_moves MH / MALA moves per
+    temperature; returns (logZ, theta, ess, resampled)."""
     y, logw = _f32(y), _f64(logw)
     theta = _f32(theta0).copy()
     K, M = theta.shape
@@ -365,7 +366,8 @@ def smc_run(y, logw, sigma, box, theta0, betas, kind, scale, ess_frac, seed):
     ess_out = np.zeros(T, np.float64)
     rs = np.zeros(T, np.int32)
     rc = lib().orc_smc_run(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]), theta,
-                           M, betas, T, int(kind), float(scale), float(ess_frac), seed,
+                           M, betas, T, int(kind), float(scale), int(n_moves), float(ess_frac),
+                           seed,
                            C.byref(z), _ptr(ess_out), _ptr(rs))
     if rc:
         raise OracleError(f"smc_run status {rc}")

@@ -802,14 +802,17 @@ int orc_fsv_run(int K, int m, const double* phi, const double* cholU, const doub
 /* SMC sampler with tempering (Section 3.3 and Section 4.1.2): particles
  * start from the uniform prior (theta0, supplied), beta_0 = 0; for
  * t = 1..T: reweight by (beta_t - beta_{t-1}) l, resample (systematic) iff
- * ESS < ess_frac * M, then one random-walk MH move (kind 0) or MALA move
- * (kind 1) targeting pi_{beta_t}.  log Z = sum_t log Z increment.
+ * ESS < ess_frac * M, then n_moves random-walk MH moves (kind 0) or MALA
+ * moves (kind 1) targeting pi_{beta_t} (Section 4.1.2 uses 10 per
+ * temperature).  Move r of step t draws with step counter t + r 2^32 (so
+ * a single move uses step t); only move 0 starts from the ancestors.
+ * log Z = sum_t log Z increment.
  * theta is [K][M] in/out; ess_out [T] (nullable) records the ESS before
  * resampling, resampled_out [T] (nullable) the decisions. */
 int orc_smc_run(const float* y, int64_t N, int K, const double* logw, double sigma,
                 double lo, double hi, float* theta, int64_t M,
                 const double* betas /* [T+1], betas[0] = 0 */, int64_t T,
-                int kind, float scale, double ess_frac, uint64_t seed,
+                int kind, float scale, int n_moves, double ess_frac, uint64_t seed,
                 double* logZ_out, double* ess_out, int32_t* resampled_out)
 {
     float* th2 = (float*)malloc((size_t)K * M * sizeof(float));
@@ -846,16 +849,20 @@ int orc_smc_run(const float* y, int64_t N, int K, const double* logw, double sig
             for (int64_t i = 0; i < M; ++i) anc[i] = (int32_t)i;
         }
         float bt = (float)betas[t];
-        if (kind == 0) {
-            orc_rwmh_move(y, N, K, logw, sigma, lo, hi, theta, l, anc, th2, l2, M,
-                          &bt, 0, scale, seed, (uint64_t)t, acc);
-        } else {
-            orc_mala_move(y, N, K, logw, sigma, lo, hi, theta, l, g, anc, th2, l2, g2, M,
-                          &bt, 0, scale, seed, (uint64_t)t, acc);
-            memcpy(g, g2, (size_t)K * M * sizeof(float));
+        for (int r = 0; r < n_moves; ++r) {
+            const int32_t* a = r == 0 ? anc : NULL;
+            uint64_t st = (uint64_t)t + ((uint64_t)r << 32);
+            if (kind == 0) {
+                orc_rwmh_move(y, N, K, logw, sigma, lo, hi, theta, l, a, th2, l2, M,
+                              &bt, 0, scale, seed, st, acc);
+            } else {
+                orc_mala_move(y, N, K, logw, sigma, lo, hi, theta, l, g, a, th2, l2, g2, M,
+                              &bt, 0, scale, seed, st, acc);
+                memcpy(g, g2, (size_t)K * M * sizeof(float));
+            }
+            memcpy(theta, th2, (size_t)K * M * sizeof(float));
+            memcpy(l, l2, (size_t)M * sizeof(double));
         }
-        memcpy(theta, th2, (size_t)K * M * sizeof(float));
-        memcpy(l, l2, (size_t)M * sizeof(double));
     }
     *logZ_out = logZ;
     free(th2); free(g); free(g2); free(l); free(l2); free(lw); free(W); free(gd);

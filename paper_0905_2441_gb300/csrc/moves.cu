@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
     const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
     const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
     float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
-    Gmm1dArgs P, int L, int Kreal, int ychunk, uint32_t* status) {
+    Gmm1dArgs P, int L, int Kreal, int ychunk, int inline_ex, uint32_t* status) {
     grid_dep_launch();
     // dynamic shared memory: staged data, mbarrier, then two lists of the
     // populations an item completed (at most chains-per-item + 1 each), an
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
         const float b = active ? beta[c] : 0.0f;
         int qlo = 0;
         int64_t qa = 0, qb = 0;  // bounds of population qlo + l32 (warp 0)
-        if (warp == 0) {
+        if (inline_ex && warp == 0) {
             int qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
             while (qhi - qlo > 1) {
                 // 32 probes split [qlo, qhi) into 33 parts
@@ -342,7 +342,9 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
         }
         const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, ok);
         if (l32 == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
-        const int buf = (int)(iter & 1);  // double-buffered list: no third barrier
+        ++iter;
+        if (!inline_ex) continue;  // the exchanges run in k_popmcmc_exchange
+        const int buf = (int)((iter - 1) & 1);  // double-buffered list: no third barrier
         if (threadIdx.x == 0) s_nex[buf] = 0;
         __syncthreads();  // the item's moves are done (and ordered before warp 0's release)
         // ---- count the item's chains per population: one lane per touched
@@ -401,12 +403,56 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
                 atomicAdd(&s_try, (uint32_t)exchange_npairs(ex[e].z, (uint32_t)ex[e].w));
             }
         }
-        ++iter;
     }
     if (iter == 0) grid_dep_wait();  // a block without items still orders its stats
     __syncthreads();
     if (threadIdx.x == 0 && stats) {
         if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
+        if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
+        if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
+    }
+}
+
+// Exchange stage of a sweep as its own grid-wide launch, for populations
+// too large for one CTA to exchange after its moves: one thread per chain;
+// the thread of a pair's first chain runs that pair (the same pairs, draws
+// and swap rule as the in-sweep exchange, so the result is identical).
+template <int K>
+__global__ void __launch_bounds__(256) k_popmcmc_exchange(
+    float* theta, double* ll, int64_t Mtot, const float* __restrict__ beta,
+    const int32_t* __restrict__ offsets, int32_t n_pops, uint64_t seed, uint64_t sweep,
+    unsigned long long* stats, int Kreal) {
+    grid_dep_wait();  // the sweep's moves are visible from here on
+    grid_dep_launch();
+    __shared__ uint32_t s_sw, s_try;
+    if (threadIdx.x == 0) { s_sw = 0; s_try = 0; }
+    __syncthreads();
+    uint32_t sw = 0, tries = 0;
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < Mtot; c += G) {
+        const int q = pop_of(offsets, n_pops, c);
+        const int64_t base = __ldg(offsets + q);
+        const int Mq = (int)((int64_t)__ldg(offsets + q + 1) - base);
+        const int r = (int)(c - base);
+        if (Mq < 2) continue;
+        const uint32_t par = draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
+        int j = -1;
+        if (r + 1 < Mq && (uint32_t)(r & 1) == par) j = r >> 1;  // (2j, 2j+1) or (2j+1, 2j+2)
+        else if (par == 1u && r == Mq - 1 && (Mq & 1) == 0) j = (Mq - 1) / 2;  // (Mq-1, 0)
+        if (j < 0) continue;
+        ++tries;
+        sw += exchange_pair<K>(theta, ll, Mtot, beta, base, Mq, par, q, j, Kreal, seed, sweep);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
+        tries += __shfl_xor_sync(0xFFFFFFFFu, tries, o);
+    }
+    if ((threadIdx.x & 31) == 0 && (sw | tries)) {
+        atomicAdd(&s_sw, sw);
+        atomicAdd(&s_try, tries);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && stats) {
         if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
         if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
     }
@@ -458,7 +504,7 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
                              int64_t N, float* th, double* l, int64_t Mt, const float* beta,
                              const int32_t* off, int32_t n_pops, float scale, uint64_t seed,
                              uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P, int L,
-                             int Kr) {
+                             int Kr, bool inline_ex) {
     auto kern = smc::k_popmcmc_sweep<K, EQW>;
     const int yc = smc::ychunk_for(N);
     size_t smem = smc::ysmem_bytes(yc) + 2 * (size_t)(threads / L + 1) * sizeof(int4);
@@ -504,9 +550,16 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
     attr[0].val.programmaticStreamSerializationAllowed = SMC_POP_PDL;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cuda_ok(cudaLaunchKernelEx(&cfg, kern, y, N, th, l, Mt, beta, off, n_pops, scale, seed,
-                                      sweep, reinterpret_cast<unsigned long long*>(stats),
-                                      ctx->d_popdone, P, L, Kr, yc, ctx->d_status));
+    smc_status st = cuda_ok(cudaLaunchKernelEx(
+        &cfg, kern, y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
+        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, P, L, Kr, yc,
+        inline_ex ? 1 : 0, ctx->d_status));
+    if (st != SMC_OK || inline_ex) return st;
+    int64_t xb = (Mt + 255) / 256;
+    if (xb > (int64_t)ctx->num_sms * 8) xb = (int64_t)ctx->num_sms * 8;
+    return launch_pdl(smc::k_popmcmc_exchange<K>, dim3((unsigned)xb), dim3(256), 0, s, th, l, Mt,
+                      beta, off, n_pops, seed, sweep, reinterpret_cast<unsigned long long*>(stats),
+                      Kr);
 }
 
 }  // namespace smc_host
@@ -579,12 +632,18 @@ extern "C" smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, cons
     int L, threads;
     launch_shape(ctx, SMC_OP_POPMCMC, M_total, N, model->K, &L, &threads);
     cudaStream_t s = as_stream(stream);
-    st = ensure_popdone(ctx, n_pops, s);
-    if (st != SMC_OK) return st;
+    // Exchanges run inside the sweep (by the CTA that completes a
+    // population) while the average population has at most two pairs per
+    // thread of a CTA; larger populations take a second, grid-wide launch.
+    const bool inline_ex = M_total <= (int64_t)n_pops * 2 * threads;
+    if (inline_ex) {
+        st = ensure_popdone(ctx, n_pops, s);
+        if (st != SMC_OK) return st;
+    }
     const int Kr = model->K;
 #define SMC_PP(KK, EQ)                                                                       \
     launch_pop<KK, EQ>(ctx, threads, s, y, N, theta, loglik, M_total, beta, pop_offsets,      \
-                       n_pops, scale, seed, sweep, stats, P, L, Kr)
+                       n_pops, scale, seed, sweep, stats, P, L, Kr, inline_ex)
     switch (Kp) {
         case 1: return eqw ? SMC_PP(1, true) : SMC_PP(1, false);
         case 2: return eqw ? SMC_PP(2, true) : SMC_PP(2, false);

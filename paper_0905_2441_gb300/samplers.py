@@ -41,12 +41,17 @@ class _Graphable:
 class SMCSampler(_Graphable):
     """Tempered SMC sampler: particles from the uniform prior, beta_0 = 0; per
     step t: reweight by (beta_t - beta_{t-1}) l, resample (systematic) iff
-    ESS < ess_frac * M, one RW-MH or MALA move targeting prior * L^beta_t."""
+    ESS < ess_frac * M, then n_moves RW-MH or MALA moves targeting
+    prior * L^beta_t (Section 4.1.2 uses 10).  Move r of step t draws with the
+    step counter t + r 2^32; only the first move gathers the ancestors."""
 
     def __init__(self, ctx: api.Context, model: api.GMM, y, theta0, betas, kind=L.MOVE_RW,
-                 scale=0.1, seed=1234, ess_frac=0.5):
+                 scale=0.1, seed=1234, ess_frac=0.5, n_moves=1):
         self.ctx, self.model, self.kind = ctx, model, kind
         self.scale, self.seed, self.ess_frac = float(scale), int(seed), float(ess_frac)
+        self.n_moves = int(n_moves)
+        if self.n_moves < 1:
+            raise ValueError("n_moves must be at least 1")
         self.y = _dev(y, torch.float32)
         th = _dev(theta0, torch.float32)
         self.K, self.M = th.shape
@@ -83,11 +88,15 @@ class SMCSampler(_Graphable):
         api.reweight(ctx, self.ll[c], db, self.lw, self.W, self.hist[t], flag, self.ess_frac)
         api.resample_systematic(ctx, self.W, self.seed, t, anc=self.anc, do_flag=flag,
                                 logw_reset=self.lw)
-        api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n], self.ll[n],
-                    self.betas[t:t + 1], self.scale, self.seed, t, kind=self.kind,
-                    grad_in=self.grad[c], grad_out=self.grad[n], anc=self.anc, do_flag=flag,
-                    accept_count=self.accepts[t:t + 1])
-        self.cur = n
+        for r in range(self.n_moves):
+            first = r == 0
+            api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n],
+                        self.ll[n], self.betas[t:t + 1], self.scale, self.seed, t + (r << 32),
+                        kind=self.kind, grad_in=self.grad[c], grad_out=self.grad[n],
+                        anc=self.anc if first else None, do_flag=flag if first else None,
+                        accept_count=self.accepts[t:t + 1])
+            c, n = n, c
+        self.cur = c
 
     def _body(self):
         for t in range(1, self.T + 1):
@@ -102,7 +111,7 @@ class SMCSampler(_Graphable):
             # the capture recorded the buffer swaps; replay from the same state
             self._graph = g
             g.replay()
-            self.cur = (start + self.T) % 2
+            self.cur = (start + self.T * self.n_moves) % 2
         else:
             self._body()
         return self.log_evidence()

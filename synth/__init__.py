@@ -60,6 +60,12 @@ def geometric_betas(T: int, beta_min: float = 1e-3) -> np.ndarray:
     return np.concatenate([[0.0], b])
 
 
+def power_betas(n: int, start: int = 1) -> np.ndarray:
+    """(i/n)^2 for i = start..n: the cooling schedule of Section 4.1.1
+    (chains i = 1..M, start=1) and Section 4.1.2 (beta_0..beta_T, start=0)."""
+    return (np.arange(start, n + 1, dtype=np.float64) / n) ** 2
+
+
 def population_offsets(n_pops: int, lo: int = 8, hi: int = 128, seed: int = 3) -> np.ndarray:
     """CSR offsets [n_pops+1] of populations with chain counts uniform in [lo, hi]."""
     g = rng(seed)
@@ -215,6 +221,39 @@ GMM8_POP = GMMWorkload("gmm8-popmcmc-512pops-K8-N1000", K=8, N=1000, M=0,
                        means=tuple(float(v) for v in range(-7, 8, 2)), n_pops=512, sweeps=1000)
 GMM8_MALA = GMMWorkload("gmm8-mala-smc-M65536-K8-N1000", K=8, N=1000, M=65536,
                         means=tuple(float(v) for v in range(-7, 8, 2)), T=50, scale=0.05)
+
+
+@dataclass
+class PaperTablesWorkload:
+    """Section 4.1 model (m = 100 data, k = 4, sigma = 0.55, means
+    (-3, 0, 3, 6), uniform prior on [-10, 10]^4), run as in Table 1
+    (one population of M chains with beta_i = (i/M)^2, N(0, I_4) random
+    walk, 8192 sweeps) and Table 2 (N particles, 200 temperatures with
+    beta_t = (t/200)^2, 10 N(0, I_4) random-walk moves per temperature,
+    resampling when ESS < N/2)."""
+    name: str = "gmm4-paper-tables-1-2"
+    K: int = 4
+    N: int = 100
+    means: tuple = (-3.0, 0.0, 3.0, 6.0)
+    sigma: float = 0.55
+    scale: float = 1.0
+    table1_M: tuple = (8, 32, 128, 512, 2048, 8192, 32768, 131072)
+    table1_sweeps: int = 8192
+    table2_N: tuple = (8192, 16384, 32768, 65536, 131072, 262144)
+    table2_T: int = 200
+    table2_moves: int = 10
+    data_seed: int = 1
+    particle_seed: int = 2
+    method_seed: int = 1234
+
+    def logw(self) -> np.ndarray:
+        return np.full(self.K, -np.log(self.K))
+
+    def data(self) -> np.ndarray:
+        return gmm1d_data(self.N, self.means, self.sigma, seed=self.data_seed)
+
+
+PAPER_TABLES = PaperTablesWorkload()
 
 
 @dataclass

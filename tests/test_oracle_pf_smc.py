@@ -114,22 +114,22 @@ def _log_int_normal_product(ys, sigma, lo=-10.0, hi=10.0):
             - S / (2 * sigma**2) + np.log(mass))
 
 
-def _smc_logZ(y, K, M, T, kind, scale, seeds):
+def _smc_logZ(y, K, M, T, kind, scale, seeds, n_moves=1):
     betas = synth.geometric_betas(T, 1e-3)
     out = []
     for s in seeds:
         th0 = synth.prior_particles(K, M, seed=1000 + s)
         z, _, ess, rs = oracle.smc_run(y, np.full(K, -np.log(K)), SIG, (-10, 10), th0, betas, kind,
-                                       scale, 0.5, 500 + s)
+                                       scale, 0.5, 500 + s, n_moves=n_moves)
         out.append(z)
     return np.array(out)
 
 
-@pytest.mark.parametrize("kind,scale", [(0, 0.1), (1, 0.05)])
-def test_smc_evidence_one_component_closed_form(kind, scale):
+@pytest.mark.parametrize("kind,scale,n_moves", [(0, 0.1, 1), (1, 0.05, 1), (0, 0.3, 3)])
+def test_smc_evidence_one_component_closed_form(kind, scale, n_moves):
     y = synth.gmm1d_data(30, [1.0], SIG, seed=31)
     exact = _log_int_normal_product(y, SIG)
-    zs = _smc_logZ(y, 1, 2048, 20, kind, scale, range(12))
+    zs = _smc_logZ(y, 1, 2048, 20, kind, scale, range(12), n_moves=n_moves)
     se = zs.std(ddof=1) / np.sqrt(zs.size)
     assert abs(zs.mean() - exact) < 4 * se + 0.02, (zs.mean(), exact, se)
 
@@ -164,3 +164,43 @@ def test_smc_paper_model_covers_symmetric_modes():
     # paper's 200 x 10) still leave many relabelled modes populated
     assert len(perms) >= 12
     assert rs.sum() >= 1
+
+
+def test_smc_several_moves_per_temperature():
+    """Section 4.1.2 runs 10 random-walk moves per temperature.  Move r of
+    step t draws from step counter t + r 2^32 and starts from move r-1's
+    output (identity ancestors): one move reproduces the single-move run,
+    and the second move's proposals are fresh draws."""
+    y = synth.gmm1d_data(20, [-3, 3], SIG, seed=5)
+    logw = np.full(2, -np.log(2))
+    th0 = synth.prior_particles(2, 256, seed=6)
+    betas = synth.power_betas(3, start=0)
+    a = oracle.smc_run(y, logw, SIG, (-10, 10), th0, betas, 0, 1.0, 0.5, 17)
+    b = oracle.smc_run(y, logw, SIG, (-10, 10), th0, betas, 0, 1.0, 0.5, 17, n_moves=1)
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+    # two moves at one (small) temperature, written out from the single-move primitive
+    b2 = np.array([0.0, 1e-5])
+    bt = np.float32(b2[1])
+    l0 = oracle.gmm1d_loglik(y, logw, SIG, th0)
+    z, th, ess, rs = oracle.smc_run(y, logw, SIG, (-10, 10), th0, b2, 0, 1.0, 0.5, 17,
+                                    n_moves=2)
+    assert rs[0] == 0  # one small temperature step: no resampling
+    t1, l1, _ = oracle.rwmh_move(y, logw, SIG, (-10, 10), th0, l0, bt, 1.0, 17, 1)
+    t2, l2, _ = oracle.rwmh_move(y, logw, SIG, (-10, 10), t1, l1, bt, 1.0, 17, 1 + (1 << 32))
+    np.testing.assert_array_equal(th, t2)
+    assert not np.array_equal(t1, t2)
+
+
+def test_smc_paper_table2_schedule_covers_all_modes():
+    """Section 4.1.2 / Table 2 setting at reduced size: beta_t = (t/T)^2,
+    ten N(0, I_4) random-walk moves per temperature.  The sampler then
+    represents all 24 relabelled modes of the four-component posterior."""
+    y = synth.gmm1d_data(100, [-3, 0, 3, 6], SIG, seed=1)
+    betas = synth.power_betas(30, start=0)
+    th0 = synth.prior_particles(4, 1024, seed=2)
+    z, th, ess, rs = oracle.smc_run(y, np.full(4, -np.log(4)), SIG, (-10, 10), th0, betas, 0, 1.0,
+                                    0.5, 4321, n_moves=10)
+    order = np.argsort(th, axis=0)
+    perms = {tuple(o) for o in order.T}
+    assert len(perms) == 24
+    assert 1 <= rs.sum() < 30
