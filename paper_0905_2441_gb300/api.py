@@ -28,25 +28,34 @@ def _chk(st: int, where: str):
         raise SmcError(st, where)
 
 
-def _stream(stream=None) -> C.c_void_p:
-    s = torch.cuda.current_stream() if stream is None else stream
-    return C.c_void_p(s.cuda_stream)
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
+def _stream(stream=None):
+    """The CUDA stream handle to launch on: the given torch stream, else the
+    current stream of the current device (read without building a Stream
+    object: this runs once per call)."""
+    if stream is not None:
+        return stream.cuda_stream
+    if _raw_stream is not None:
+        return _raw_stream(torch.cuda.current_device())
+    return torch.cuda.current_stream().cuda_stream
 
 
 def _ptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    return None if t is None else t.data_ptr()
 
 
 def _need(t, dtype, name, shape=None):
     if t is None:
         return
-    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise TypeError(f"{name} must be a CUDA tensor")
     if t.dtype != dtype:
         raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
     if not t.is_contiguous():
         raise ValueError(f"{name} must be contiguous")
-    if shape is not None and tuple(t.shape) != tuple(shape):
+    if shape is not None and t.shape != shape:
         raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
 
 
@@ -109,7 +118,23 @@ class GMM:
         self.log_w = np.asarray(self.log_w, np.float64)
         self._w = (C.c_float * self.K)(*[float(v) for v in self.log_w])
 
+    def __setattr__(self, name, value):
+        # the C struct is built once per set of field values
+        super().__setattr__(name, value)
+        if name != "_c":
+            self.__dict__.pop("_c", None)
+            if name == "log_w" and "_w" in self.__dict__ and value is not None:
+                w = np.asarray(value, np.float64)
+                super().__setattr__("_w", (C.c_float * w.size)(*[float(v) for v in w]))
+
     def cstruct(self) -> L.SmcGmm:
+        c = self.__dict__.get("_c")
+        if c is None:
+            c = self._build()
+            self.__dict__["_c"] = c
+        return c
+
+    def _build(self) -> L.SmcGmm:
         return L.SmcGmm(L.GMM_1D, self.K, 1, L.PREC_FP32, self._w, self.sigma, self.lo, self.hi)
 
 
@@ -117,7 +142,7 @@ class GMM:
 class DiagGMM(GMM):
     """d-dimensional mixture with N(mu_k, sigma^2 I_d) components."""
 
-    def cstruct(self) -> L.SmcGmm:
+    def _build(self) -> L.SmcGmm:
         return L.SmcGmm(L.GMM_DIAG, self.K, self.d, self.precision, self._w, self.sigma,
                         self.lo, self.hi)
 

@@ -68,6 +68,9 @@ class SMCSampler(_Graphable):
         self.flags = torch.zeros(self.T + 1, dtype=torch.int32, device="cuda")
         self.hist = torch.zeros(self.T + 1, 4, dtype=torch.float64, device="cuda")
         self.accepts = torch.zeros(self.T + 1, dtype=torch.int32, device="cuda")
+        # per-step views, made once (a step issues its calls without building tensors)
+        self._views = [(self.flags[t:t + 1], self.hist[t], self.betas[t:t + 1],
+                        self.accepts[t:t + 1]) for t in range(self.T + 1)]
         ctx.reserve(self.M)
         self.reset(theta0)
 
@@ -84,17 +87,17 @@ class SMCSampler(_Graphable):
         c, n = self.cur, 1 - self.cur
         ctx = self.ctx
         db = float(self.betas_host[t] - self.betas_host[t - 1])
-        flag = self.flags[t:t + 1]
-        api.reweight(ctx, self.ll[c], db, self.lw, self.W, self.hist[t], flag, self.ess_frac)
+        flag, hist, beta, accepts = self._views[t]
+        api.reweight(ctx, self.ll[c], db, self.lw, self.W, hist, flag, self.ess_frac)
         api.resample_systematic(ctx, self.W, self.seed, t, anc=self.anc, do_flag=flag,
                                 logw_reset=self.lw)
         for r in range(self.n_moves):
             first = r == 0
             api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n],
-                        self.ll[n], self.betas[t:t + 1], self.scale, self.seed, t + (r << 32),
+                        self.ll[n], beta, self.scale, self.seed, t + (r << 32),
                         kind=self.kind, grad_in=self.grad[c], grad_out=self.grad[n],
                         anc=self.anc if first else None, do_flag=flag if first else None,
-                        accept_count=self.accepts[t:t + 1])
+                        accept_count=accepts)
             c, n = n, c
         self.cur = c
 
@@ -175,6 +178,7 @@ class ParticleFilter(_Graphable):
         self.W = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.anc = torch.arange(self.M, dtype=torch.int32, device="cuda")
         self.hist = torch.zeros(self.T + 1, 4, dtype=torch.float64, device="cuda")
+        self._views = [(self.y[max(t - 1, 0)], self.hist[t]) for t in range(self.T + 1)]
         ctx.reserve(self.M)
         self.cur = 0
 
@@ -187,9 +191,10 @@ class ParticleFilter(_Graphable):
 
     def step(self, t: int):
         c, n = self.cur, 1 - self.cur
-        api.pf_step(self.ctx, self.model, self.y[t - 1], self.x[c], self.x[n], self.logg,
+        y_t, hist = self._views[t]
+        api.pf_step(self.ctx, self.model, y_t, self.x[c], self.x[n], self.logg,
                     self.seed, t, anc=self.anc)
-        api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, self.hist[t], None, 0.5)
+        api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
         api.resample_systematic(self.ctx, self.W, self.seed, t, anc=self.anc, logw_reset=self.lw)
         self.cur = n
 
