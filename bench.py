@@ -813,7 +813,20 @@ def paper_tables(torch, P, ctx, flush, reps=1, rank=0):
                  "pd_per_s_plain": N * w.N * w.table2_T * w.table2_moves / tp,
                  "logZ": z_plain, "resampled_steps": int(smp.flags[1:].sum().item())}
         ctx.check()
-    return {"workload": w.name, "table1": t1, "table2": t2,
+    # annealed importance sampling: the same sampler with no resampling
+    # (Section 4.1.2 reports its running time as practically identical)
+    N = w.table2_N[-1]
+    th0 = synth.prior_particles(w.K, N, seed=w.particle_seed + rank)
+    smp = samplers.SMCSampler(ctx, model, y, th0, betas, scale=w.scale, seed=w.method_seed + rank,
+                              n_moves=w.table2_moves, ess_frac=0.0)
+    smp.run()
+    smp.reset(th0)
+    t_ais = _whole_run(torch, flush, stream, smp.run)
+    ais = {"N": N, "plain_s": t_ais, "logZ": smp.log_evidence(),
+           "resampled_steps": int(smp.flags[1:].sum().item()),
+           "vs_smc_plain": t_ais / t2[N]["plain_s"]}
+    ctx.check()
+    return {"workload": w.name, "table1": t1, "table2": t2, "table2_ais": ais,
             "launches_per_table2_step": 6 + w.table2_moves}
 
 
@@ -848,7 +861,8 @@ def bench_tables(args, torch, dist):
                        "m": w.N, "k": w.K,
                        "l2": "256 MiB buffer written before every timed run, outside its events",
                        "parallelism": f"independent samplers per rank x{dist.world}"},
-            "table1": tab["table1"], "table2": tab["table2"], "gpu_launches": launches,
+            "table1": tab["table1"], "table2": tab["table2"], "table2_ais": tab["table2_ais"],
+            "gpu_launches": launches,
             "clocks": clk.summary()}
 
 

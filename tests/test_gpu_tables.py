@@ -189,3 +189,28 @@ def test_smc_paper_table2_setting_matches_oracle_statistically(env):
     g, o = np.array(g), np.array(o)
     spread = max(np.std(g, ddof=1), np.std(o, ddof=1), 0.05)
     assert abs(g.mean() - o.mean()) < 4 * spread, (g, o)
+
+
+def test_ais_on_gpu_never_resamples_and_matches_oracle(env):
+    """Annealed importance sampling (Section 4.1.2: the SMC sampler with no
+    resampling): no step resamples, and the GPU and oracle evidence
+    estimates agree across seeds."""
+    P, S, ctx = env
+    w = synth.PAPER_TABLES
+    y = w.data()
+    betas = synth.power_betas(10, start=0)
+    g, o = [], []
+    for s in range(4):
+        th0 = synth.prior_particles(4, 1024, seed=80 + s)
+        smp = S.SMCSampler(ctx, P.GMM(4, SIG), y, th0, betas, scale=w.scale, seed=90 + s,
+                           n_moves=5, ess_frac=0.0)
+        g.append(smp.run())
+        assert int(smp.flags.sum()) == 0
+        zo, _, _, rs = oracle.smc_run(y, w.logw(), SIG, BOX, th0, betas, 0, w.scale, 0.0, 90 + s,
+                                      n_moves=5)
+        assert rs.sum() == 0
+        o.append(zo)
+    ctx.check()
+    g, o = np.array(g), np.array(o)
+    spread = max(np.std(g, ddof=1), np.std(o, ddof=1), 0.1)
+    assert abs(g.mean() - o.mean()) < 4 * spread, (g, o)

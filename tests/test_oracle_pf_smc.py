@@ -204,3 +204,22 @@ def test_smc_paper_table2_schedule_covers_all_modes():
     perms = {tuple(o) for o in order.T}
     assert len(perms) == 24
     assert 1 <= rs.sum() < 30
+
+
+def test_ais_no_resampling_closed_form():
+    """Section 4.1.2: the sampler with no resampling at all is annealed
+    importance sampling; its evidence estimate still targets the closed-form
+    marginal likelihood (one component), and it never resamples."""
+    y = synth.gmm1d_data(30, [1.0], SIG, seed=31)
+    exact = _log_int_normal_product(y, SIG)
+    betas = synth.geometric_betas(20, 1e-3)
+    zs = []
+    for s in range(12):
+        th0 = synth.prior_particles(1, 2048, seed=1000 + s)
+        z, _, ess, rs = oracle.smc_run(y, np.zeros(1), SIG, (-10, 10), th0, betas, 0, 0.3, 0.0,
+                                       500 + s, n_moves=2)
+        assert rs.sum() == 0
+        zs.append(z)
+    zs = np.array(zs)
+    se = zs.std(ddof=1) / np.sqrt(zs.size)
+    assert abs(zs.mean() - exact) < 4 * se + 0.05, (zs.mean(), exact, se)
