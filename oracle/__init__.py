@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-P_MOVE, P_ACCEPT, P_RESAMPLE, P_EXCHANGE, P_PFNOISE = 1, 2, 3, 4, 5
+P_MOVE, P_ACCEPT, P_RESAMPLE, P_EXCHANGE, P_PFNOISE, P_MULTINOMIAL = 1, 2, 3, 4, 5, 6
 
 
 def build(force: bool = False) -> str:
@@ -76,6 +76,11 @@ def _declare(L):
     L.orc_ess.restype = C.c_double
     L.orc_resample_systematic.argtypes = [_f64p, _i64, C.c_uint32, _i32p, _vp]
     L.orc_resample_systematic.restype = C.c_int
+    L.orc_word_array.argtypes = [_u64, C.c_uint32, _u64, _i64, _u32p]
+    L.orc_resample_multinomial.argtypes = [_f64p, _i64, _u32p, _i32p]
+    L.orc_resample_multinomial.restype = C.c_int
+    L.orc_resample_residual.argtypes = [_f64p, _i64, _u32p, _i32p, C.POINTER(C.c_int64)]
+    L.orc_resample_residual.restype = C.c_int
     L.orc_rwmh_move.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double, C.c_double,
                                 _f32p, _f64p, _vp, _f32p, _f64p, _i64, _f32p, _i64, C.c_float,
                                 _u64, _u64, _i32p]
@@ -224,6 +229,43 @@ def resample_systematic(W, u32):
     if rc:
         raise OracleError(f"resample status {rc}")
     return anc, counts
+
+
+def slot_uniforms(seed, step, n) -> np.ndarray:
+    """Word 0 of (seed, MULTINOMIAL, step, index i) for i < n."""
+    out = np.zeros(max(int(n), 1), np.uint32)
+    lib().orc_word_array(seed, P_MULTINOMIAL, step, int(n), out)
+    return out[:n]
+
+
+def resample_multinomial(W, u):
+    """Exact-integer multinomial resampling with slot uniforms u (uint32[M])."""
+    W = _f64(W)
+    M = W.size
+    u = np.ascontiguousarray(u, np.uint32)
+    if u.size < M:
+        raise ValueError("need one uniform per slot")
+    anc = np.zeros(M, np.int32)
+    rc = lib().orc_resample_multinomial(W, M, u, anc)
+    if rc:
+        raise OracleError(f"resample status {rc}")
+    return anc
+
+
+def resample_residual(W, v):
+    """Exact-integer residual resampling; v (uint32, at least M entries) are
+    the residual draws' uniforms.  Returns (ancestors, R)."""
+    W = _f64(W)
+    M = W.size
+    v = np.ascontiguousarray(v, np.uint32)
+    if v.size < M:
+        raise ValueError("need M uniforms")
+    anc = np.zeros(M, np.int32)
+    R = C.c_int64(0)
+    rc = lib().orc_resample_residual(W, M, v, anc, C.byref(R))
+    if rc:
+        raise OracleError(f"resample status {rc}")
+    return anc, R.value
 
 
 # ----------------------------------------------------------------------- moves

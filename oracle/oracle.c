@@ -41,7 +41,7 @@
 
 /* stream purposes (the same numbers on the GPU side) */
 enum { ORC_P_MOVE = 1, ORC_P_ACCEPT = 2, ORC_P_RESAMPLE = 3,
-       ORC_P_EXCHANGE = 4, ORC_P_PFNOISE = 5 };
+       ORC_P_EXCHANGE = 4, ORC_P_PFNOISE = 5, ORC_P_MULTINOMIAL = 6 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al. 2011): ten rounds of the 4x32 S-box          */
@@ -338,6 +338,114 @@ int orc_resample_systematic(const double* W, int64_t M, uint32_t u32,
     }
     free(C);
     return 0;
+}
+
+/* word 0 of block 0 of the streams (seed, purpose, step, index i) for     */
+/* i = 0..n-1: the per-slot uniforms of multinomial and residual draws.     */
+void orc_word_array(uint64_t seed, uint32_t purpose, uint64_t step, int64_t n, uint32_t* out)
+{
+    for (int64_t i = 0; i < n; ++i) out[i] = orc_word(seed, purpose, step, (uint32_t)i, 0);
+}
+
+/* First j in [0, n) with C[j] > T (C non-decreasing; n if none). */
+static int64_t orc_first_above(const uint64_t* C, int64_t n, uint64_t T)
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (C[mid] > T) hi = mid;
+        else lo = mid + 1;
+    }
+    return lo;
+}
+
+/* q_j = floor(W_j 2^52) and C_j = q_0 + ... + q_j (exact); 0, -1 (a weight
+ * outside [0,1], NaN, or a total beyond 64 bits) or -4 (all zero). */
+static int orc_quantised_cdf(const double* W, int64_t M, uint64_t* q, uint64_t* C,
+                             uint64_t* S_out)
+{
+    unsigned __int128 acc = 0;
+    for (int64_t j = 0; j < M; ++j) {
+        double w = W[j];
+        if (!(w >= 0.0 && w <= 1.0)) return -1;
+        q[j] = (uint64_t)floor(w * 4503599627370496.0); /* 2^52 */
+        acc += q[j];
+        if (acc >> 64) return -1;
+        C[j] = (uint64_t)acc;
+    }
+    if (acc == 0) return -4;
+    *S_out = (uint64_t)acc;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multinomial resampling (Section 3.2: M independent draws from the         */
+/* empirical CDF of the weights), on the same exact-integer CDF as the       */
+/* systematic scheme: slot i takes                                           */
+/*   a_i = min { j : C_j > floor((2 u_i + 1) S / 2^33) },                   */
+/* the j whose CDF interval (C_{j-1}/S, C_j/S] contains (u_i + 1/2) / 2^32.  */
+/* u[i] is the slot's 32-bit uniform (the GPU draws word 0 of (seed,         */
+/* MULTINOMIAL, step, index i)).  Returns as orc_resample_systematic.        */
+/* ------------------------------------------------------------------------ */
+int orc_resample_multinomial(const double* W, int64_t M, const uint32_t* u, int32_t* anc)
+{
+    uint64_t* q = (uint64_t*)malloc((size_t)M * sizeof(uint64_t));
+    uint64_t* C = (uint64_t*)malloc((size_t)M * sizeof(uint64_t));
+    uint64_t S = 0;
+    int rc = (q && C) ? orc_quantised_cdf(W, M, q, C, &S) : -2;
+    if (rc == 0) {
+        for (int64_t i = 0; i < M; ++i) {
+            unsigned __int128 x = (unsigned __int128)(2ull * u[i] + 1ull) * S;
+            anc[i] = (int32_t)orc_first_above(C, M, (uint64_t)(x >> 33));
+        }
+    }
+    free(q);
+    free(C);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Residual resampling (a variant of the Section 3.2 resampling step): each  */
+/* particle first receives its integer share of the M slots, the rest are    */
+/* multinomial draws on the remainders, all in exact integers:               */
+/*   n_j = floor(M q_j / S),  r_j = M q_j - n_j S  (0 <= r_j < S),           */
+/*   slots [N_{j-1}, N_j) take j (N the prefix of n), in particle order;     */
+/*   R = M - sum n residual slots [M - R, M) are multinomial draws on the    */
+/*   remainders shifted to 32 bits: rho_j = r_j >> s with                    */
+/*   s = max(0, bitlen(S) - 32), E_j = rho_0 + ... + rho_j, P = E_{M-1};     */
+/*   residual slot k takes min { j : E_j > floor((2 v_k + 1) P / 2^33) }.    */
+/* v[k] (k < R) as u in the multinomial scheme.  R_out (nullable) = R.       */
+/* ------------------------------------------------------------------------ */
+int orc_resample_residual(const double* W, int64_t M, const uint32_t* v, int32_t* anc,
+                          int64_t* R_out)
+{
+    uint64_t* q = (uint64_t*)malloc((size_t)M * sizeof(uint64_t));
+    uint64_t* C = (uint64_t*)malloc((size_t)M * sizeof(uint64_t));
+    uint64_t S = 0;
+    int rc = (q && C) ? orc_quantised_cdf(W, M, q, C, &S) : -2;
+    if (rc == 0) {
+        int bits = 64 - __builtin_clzll(S);
+        int sh = bits > 32 ? bits - 32 : 0;
+        int64_t pos = 0;
+        uint64_t P = 0;
+        for (int64_t j = 0; j < M; ++j) {
+            unsigned __int128 mq = (unsigned __int128)M * q[j];
+            uint64_t n = (uint64_t)(mq / S);
+            uint64_t r = (uint64_t)(mq - (unsigned __int128)n * S);
+            for (uint64_t k = 0; k < n; ++k) anc[pos++] = (int32_t)j;
+            P += r >> sh;
+            C[j] = P; /* reused: E_j */
+        }
+        int64_t R = M - pos;
+        for (int64_t k = 0; k < R; ++k) {
+            unsigned __int128 x = (unsigned __int128)(2ull * v[k] + 1ull) * P;
+            anc[pos + k] = (int32_t)orc_first_above(C, M, (uint64_t)(x >> 33));
+        }
+        if (R_out) *R_out = R;
+    }
+    free(q);
+    free(C);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -154,3 +154,94 @@ def test_resample_degenerate_and_uniform():
         oracle.resample_systematic(np.array([0.5, np.nan]), 0)
     with pytest.raises(oracle.OracleError):
         oracle.resample_systematic(np.array([0.5, 1.5]), 0)
+
+
+# ------------------------------------------------------------------ multinomial / residual
+def _q_cdf(W):
+    q = [int(Fraction(w) * 2**52) for w in W]
+    return q, np.cumsum(q).tolist(), sum(q)
+
+
+def test_multinomial_brute_force_rationals():
+    """Slot i takes the particle whose CDF interval (C_{j-1}/S, C_j/S]
+    contains (u_i + 1/2) / 2^32, evaluated in exact rationals."""
+    g = np.random.default_rng(11)
+    for M in [1, 2, 3, 5, 9, 40]:
+        for _ in range(10):
+            W = g.dirichlet(np.ones(M) * 0.4)
+            u = g.integers(0, 2**32, M, dtype=np.uint64).astype(np.uint32)
+            u[0] = 0
+            u[-1] = 2**32 - 1
+            q, C, S = _q_cdf(W)
+            want = [next(j for j in range(M) if Fraction(C[j], S) > Fraction(2 * int(ui) + 1, 2**33))
+                    for ui in u]
+            assert np.array_equal(oracle.resample_multinomial(W, u), want)
+
+
+def test_multinomial_frequencies_match_weights():
+    """Counts over many independent calls follow Multinomial(M, W)."""
+    W = np.array([0.05, 0.3, 0.0, 0.15, 0.5])
+    M = W.size
+    counts = np.zeros(M)
+    for step in range(4000):
+        a = oracle.resample_multinomial(W, oracle.slot_uniforms(3, step, M))
+        counts += np.bincount(a, minlength=M)
+    assert counts[2] == 0  # zero weight is never drawn
+    keep = W > 0
+    chi2 = np.sum((counts[keep] - counts.sum() * W[keep]) ** 2 / (counts.sum() * W[keep]))
+    assert stats.chi2.sf(chi2, keep.sum() - 1) > 1e-4, (counts, chi2)
+
+
+def test_residual_brute_force_rationals():
+    """Deterministic shares floor(M q_j / S), then the R remaining slots drawn
+    on the remainders shifted to 32 bits, all in exact rationals."""
+    g = np.random.default_rng(12)
+    for M in [1, 2, 3, 7, 16, 50]:
+        for _ in range(8):
+            W = g.dirichlet(np.ones(M) * 0.5)
+            v = g.integers(0, 2**32, M, dtype=np.uint64).astype(np.uint32)
+            q, C, S = _q_cdf(W)
+            n = [(M * qj) // S for qj in q]
+            r = [M * qj - nj * S for qj, nj in zip(q, n)]
+            sh = max(0, S.bit_length() - 32)
+            E = np.cumsum([rj >> sh for rj in r]).tolist()
+            P = E[-1]
+            det = [j for j in range(M) for _ in range(n[j])]
+            R = M - len(det)
+            res = [next(j for j in range(M) if Fraction(E[j], P) > Fraction(2 * int(v[k]) + 1, 2**33))
+                   for k in range(R)]
+            anc, Rg = oracle.resample_residual(W, v)
+            assert Rg == R and np.array_equal(anc, det + res)
+            # every particle keeps at least its integer share floor(M W_j) up to the 2^-52 grid
+            cnt = np.bincount(anc, minlength=M)
+            assert np.all(cnt >= np.floor(M * W - 1e-9)) and cnt.sum() == M
+
+
+def test_residual_special_cases():
+    M = 64
+    # equal weights: every particle keeps exactly one copy, no residual draw
+    anc, R = oracle.resample_residual(np.full(M, 1.0 / M), oracle.slot_uniforms(1, 1, M))
+    assert R == 0 and np.array_equal(anc, np.arange(M))
+    # one-hot: all M slots deterministic
+    W = np.zeros(M)
+    W[17] = 1.0
+    anc, R = oracle.resample_residual(W, oracle.slot_uniforms(1, 2, M))
+    assert R == 0 and np.all(anc == 17)
+    # expected counts over calls: E[count_j] = M W_j
+    W = np.random.default_rng(3).dirichlet(np.ones(M))
+    tot = np.zeros(M)
+    reps = 3000
+    for step in range(reps):
+        anc, R = oracle.resample_residual(W, oracle.slot_uniforms(4, step, M))
+        tot += np.bincount(anc, minlength=M)
+    assert np.max(np.abs(tot / reps - M * W)) < 0.1
+
+
+def test_multinomial_residual_errors():
+    for f in (oracle.resample_multinomial, oracle.resample_residual):
+        with pytest.raises(oracle.OracleError):
+            f(np.array([0.5, np.nan]), np.zeros(2, np.uint32))
+        with pytest.raises(oracle.OracleError):
+            f(np.zeros(3), np.zeros(3, np.uint32))
+        with pytest.raises(oracle.OracleError):
+            f(np.array([0.5, 1.5]), np.zeros(2, np.uint32))
