@@ -528,7 +528,8 @@ def bench_pf(args, torch, dist):
 
 def bench_resample(args, torch, dist):
     """One step = smc_reweight (lw += l, W, scalars) + smc_resample_systematic
-    (exact-integer systematic resampling) at M = 2^24: HBM-bound kernels."""
+    (exact-integer systematic resampling) at M = 2^24: HBM-bound kernels.
+    The multinomial and residual schemes are timed per call beside it."""
     import paper_0905_2441_gb300 as P
     M = 1 << 24
     ctx = P.Context()
@@ -557,6 +558,20 @@ def bench_resample(args, torch, dist):
     ctx.check()
     per = np.array([[e[i].elapsed_time(e[i + 1]) / 1e3 for i in range(2)] for e in rec])
     t_max = dist.max(torch, float(per.sum()))
+    # the other two schemes on the same weights (4 and 6 kernels per call)
+    variants = {}
+    for name, fn in (("multinomial", P.resample_multinomial), ("residual", P.resample_residual)):
+        call = (lambda fn=fn: fn(ctx, W, 9, 1, anc=anc))
+        for _ in range(3):
+            call()
+        ts = []
+        for _ in range(20):
+            e = _flush_timed(torch, flush, stream, [call])
+            torch.cuda.synchronize()
+            ts.append(e[0].elapsed_time(e[1]) / 1e3)
+        ctx.check()
+        t = statistics.median(ts)
+        variants[name] = {"ms_per_call": 1e3 * t, "particles_per_s": M / t}
     hbm = measured_peaks()["hbm_gbs"]
     b_rw, b_rs = 32, 20
     ach_rs = b_rs * M / per[:, 1].mean() / 1e9
@@ -570,11 +585,12 @@ def bench_resample(args, torch, dist):
            "per_call_gbs": {"reweight": b_rw * M / per[:, 0].mean() / 1e9,
                             "resample": ach_rs},
            "per_call_ms": {"reweight": 1e3 * per[:, 0].mean(), "resample": 1e3 * per[:, 1].mean()},
+           "other_schemes": variants,
            "roofline": {"bound": "hbm", "achieved": ach_rs, "peak": hbm, "unit": "GB/s",
                         "frac": ach_rs / hbm, "traffic": None, "kernel": "resample (2 kernels)",
                         "bytes_per_particle": b_rs,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
-           "gpu_launches": 4 * K, "clocks": clk.summary()}
+           "gpu_launches": 6 * K, "clocks": clk.summary()}
     ctx.close()
     return out
 

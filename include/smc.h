@@ -54,7 +54,7 @@ typedef struct smc_ctx smc_ctx;
 
 /* Stream purposes of the Philox counter (the fourth counter word). */
 enum { SMC_RNG_MOVE = 1, SMC_RNG_ACCEPT = 2, SMC_RNG_RESAMPLE = 3,
-       SMC_RNG_EXCHANGE = 4, SMC_RNG_PFNOISE = 5 };
+       SMC_RNG_EXCHANGE = 4, SMC_RNG_PFNOISE = 5, SMC_RNG_MULTINOMIAL = 6 };
 
 /* ------------------------------------------------------------------ context */
 
@@ -165,15 +165,42 @@ smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, double* ess_out,
  *   do_flag (device int32, nullable): when it holds 0 nothing is resampled;
  *     ancestors_out becomes the identity and counts 1.
  *   logw_reset (nullable): double[M] set to 0 when resampling happened.
- * Two passes: exact integer sums per tile of 2048 weights, per group of 64
- * tiles and in total; then one CTA per tile reads its prefix from those
- * sums, scans the tile and expands its output range.  No CTA waits on
- * another.  A weight outside [0,1] or NaN (or weights summing to 2^9 or
- * more) latches SMC_ERR_ARG, S == 0 SMC_ERR_ZERO_WEIGHT; the outputs are
- * then unspecified. */
+ * Exact integer sums per tile of 2048 weights; one CTA turns them into
+ * prefixes and forms the call's constants; then each tile is scanned and
+ * its output range expanded.  No CTA waits on another.  A weight outside
+ * [0,1] or NaN (or weights summing to 2^9 or more) latches SMC_ERR_ARG,
+ * S == 0 SMC_ERR_ZERO_WEIGHT; the outputs are then unspecified. */
 smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uint64_t seed,
                                    uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
                                    const int32_t* do_flag, double* logw_reset, void* stream);
+
+/* Multinomial resampling (Section 3.2's resampling step as M independent
+ * draws from the empirical CDF), on the exact-integer CDF of
+ * smc_resample_systematic (q_j, C_j, S as there):
+ *   ancestors_out[i] = min { j : C_j > floor((2 u_i + 1) S / 2^33) },
+ *   u_i = word 0 of (seed, MULTINOMIAL = 6, step, index i),
+ * i.e. the particle whose CDF interval contains (u_i + 1/2) / 2^32.  The
+ * ancestors are in draw order (not sorted).  W, do_flag, logw_reset and the
+ * errors as for smc_resample_systematic; no offspring counts.  Scratch:
+ * 8 bytes per particle of context workspace on top of the systematic
+ * scheme's (smc_reserve sizes it). */
+smc_status smc_resample_multinomial(smc_ctx* ctx, const double* W, int64_t M, uint64_t seed,
+                                    uint64_t step, int32_t* ancestors_out,
+                                    const int32_t* do_flag, double* logw_reset, void* stream);
+
+/* Residual resampling (the resampling step with each particle's integer
+ * share of the M slots kept deterministically), in exact integers on the
+ * same q_j, S:
+ *   n_j = floor(M q_j / S), r_j = M q_j - n_j S;  particle j fills slots
+ *   [N_{j-1}, N_j) (N the inclusive prefix of n), in particle order;
+ *   the R = M - sum n slots [M - R, M) are multinomial draws (as
+ *   smc_resample_multinomial, uniforms v_k = word 0 of (seed, MULTINOMIAL,
+ *   step, index k), k < R) on the remainders rho_j = r_j >> s,
+ *   s = max(0, bitlen(S) - 32), whose prefix E and total P replace C and S.
+ * Arguments, scratch and errors as smc_resample_multinomial. */
+smc_status smc_resample_residual(smc_ctx* ctx, const double* W, int64_t M, uint64_t seed,
+                                 uint64_t step, int32_t* ancestors_out, const int32_t* do_flag,
+                                 double* logw_reset, void* stream);
 
 /* The same systematic resampling as smc_resample_systematic (identical
  * arguments and results, bit for bit), for callers that cannot allocate

@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(_HERE, "libsmc.so")
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_CUDA, SMC_ERR_NONFINITE = 0, -1, -2, -3
 SMC_ERR_ZERO_WEIGHT, SMC_ERR_TIMEOUT, SMC_ERR_UNSUPPORTED = -4, -5, -6
-RNG_MOVE, RNG_ACCEPT, RNG_RESAMPLE, RNG_EXCHANGE, RNG_PFNOISE = 1, 2, 3, 4, 5
+RNG_MOVE, RNG_ACCEPT, RNG_RESAMPLE, RNG_EXCHANGE, RNG_PFNOISE, RNG_MULTINOMIAL = 1, 2, 3, 4, 5, 6
 OP_LOGLIK, OP_MOVE, OP_POPMCMC = 0, 1, 2
 GMM_1D, GMM_DIAG = 0, 1
 PREC_FP32, PREC_BF16SPLIT = 0, 1
@@ -21,7 +21,8 @@ EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_sta
            "smc_set_launch", "smc_get_launch", "smc_loglik_batch", "smc_reweight", "smc_ess",
            "smc_resample_systematic", "smc_gather", "smc_mh_move", "smc_popmcmc_sweep",
            "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
-           "smc_resample_systematic_noalloc")
+           "smc_resample_systematic_noalloc", "smc_resample_multinomial",
+           "smc_resample_residual")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -56,6 +57,8 @@ def _declare(L):
     L.smc_resample_systematic.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp, _vp]
     L.smc_resample_systematic_noalloc.argtypes = [_vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp, _vp,
                                                   _vp]
+    L.smc_resample_multinomial.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
+    L.smc_resample_residual.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
     L.smc_gather.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp]
     L.smc_mh_move.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                               _vp, _i64, _vp, _i64, C.c_float, _i32, _u64, _u64, _vp, _vp]

@@ -253,6 +253,48 @@ def resample_systematic(ctx: Context, W, seed: int, step: int, anc=None, counts=
     return anc
 
 
+def _resample_var(fn, where, ctx, W, seed, step, anc, do_flag, logw_reset, stream):
+    M = W.numel()
+    anc = torch.empty(M, dtype=torch.int32, device=W.device) if anc is None else anc
+    _need(W, torch.float64, "W", (M,))
+    _need(anc, torch.int32, "ancestors", (M,))
+    _need(do_flag, torch.int32, "do_flag", (1,))
+    _need(logw_reset, torch.float64, "logw_reset", (M,))
+    _chk(fn(ctx.handle, _ptr(W), M, int(seed), int(step), _ptr(anc), _ptr(do_flag),
+            _ptr(logw_reset), _stream(stream)), where)
+    return anc
+
+
+def resample_multinomial(ctx: Context, W, seed: int, step: int, anc=None, do_flag=None,
+                         logw_reset=None, stream=None):
+    """Exact-integer multinomial resampling (ancestors in draw order)."""
+    return _resample_var(L.load().smc_resample_multinomial, "smc_resample_multinomial", ctx, W,
+                         seed, step, anc, do_flag, logw_reset, stream)
+
+
+def resample_residual(ctx: Context, W, seed: int, step: int, anc=None, do_flag=None,
+                      logw_reset=None, stream=None):
+    """Exact-integer residual resampling (deterministic copies, then residual draws)."""
+    return _resample_var(L.load().smc_resample_residual, "smc_resample_residual", ctx, W, seed,
+                         step, anc, do_flag, logw_reset, stream)
+
+
+RESAMPLERS = ("systematic", "multinomial", "residual")
+
+
+def resample(ctx: Context, kind: str, W, seed: int, step: int, anc=None, do_flag=None,
+             logw_reset=None, stream=None):
+    """Dispatch on the scheme name (one of RESAMPLERS)."""
+    if kind == "systematic":
+        return resample_systematic(ctx, W, seed, step, anc=anc, do_flag=do_flag,
+                                   logw_reset=logw_reset, stream=stream)
+    if kind == "multinomial":
+        return resample_multinomial(ctx, W, seed, step, anc, do_flag, logw_reset, stream)
+    if kind == "residual":
+        return resample_residual(ctx, W, seed, step, anc, do_flag, logw_reset, stream)
+    raise ValueError(f"unknown resampling scheme {kind!r}")
+
+
 def gather(ctx: Context, anc, src32=None, dst32=None, src64=None, dst64=None, stream=None):
     M = (dst64 if dst64 is not None else dst32).shape[-1]
     rows = 0 if src32 is None else (src32.shape[0] if src32.dim() == 2 else 1)

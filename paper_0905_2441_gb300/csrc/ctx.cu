@@ -125,8 +125,9 @@ extern "C" smc_status smc_destroy(smc_ctx* ctx) {
     return SMC_OK;
 }
 
-// bytes of growable workspace the resampler needs for M particles
+// bytes of growable workspace the resamplers need for M particles
 size_t smc_resample_ws_bytes(int64_t M);
+size_t smc_resample_var_ws_bytes(int64_t M);
 
 extern "C" smc_status smc_reserve(smc_ctx* ctx, int64_t max_particles, int32_t max_pops) {
     if (!ctx || max_particles < 0 || max_pops < 0) return SMC_ERR_ARG;
@@ -134,7 +135,9 @@ extern "C" smc_status smc_reserve(smc_ctx* ctx, int64_t max_particles, int32_t m
     if (st != SMC_OK) return st;
     st = ensure_popdone(ctx, max_pops, nullptr);
     if (st != SMC_OK) return st;
-    return ensure_ws(ctx, smc_resample_ws_bytes(max_particles), nullptr);
+    const size_t a = smc_resample_ws_bytes(max_particles);
+    const size_t b = smc_resample_var_ws_bytes(max_particles);
+    return ensure_ws(ctx, a > b ? a : b, nullptr);
 }
 
 extern "C" smc_status smc_ctx_check(smc_ctx* ctx, void* stream) {

@@ -25,7 +25,10 @@ __device__ __forceinline__ void raise_status(uint32_t* st, uint32_t bit) {
 constexpr uint32_t kSpinLimit = 4u << 20;
 
 // ---------------------------------------------------------------- Philox
-enum : uint32_t { RNG_MOVE = 1, RNG_ACCEPT = 2, RNG_RESAMPLE = 3, RNG_EXCHANGE = 4, RNG_PFNOISE = 5 };
+enum : uint32_t {
+    RNG_MOVE = 1, RNG_ACCEPT = 2, RNG_RESAMPLE = 3, RNG_EXCHANGE = 4, RNG_PFNOISE = 5,
+    RNG_MULTINOMIAL = 6
+};
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll

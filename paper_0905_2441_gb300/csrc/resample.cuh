@@ -130,7 +130,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 
 // Pass 1: the exact integer sum of every tile (each CTA a contiguous range
 // of tiles, the next tile's weights loading while one is reduced).
-__global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __restrict__ W,
+static __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __restrict__ W,
                                                                int64_t M, const int32_t* do_flag,
                                                                RsScratch sc, uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
@@ -189,7 +189,7 @@ __device__ __forceinline__ bool lt128(U128 a, U128 b) {
 // c times the fixed-point reciprocal mfx = floor(M 2^64 / S) (integer
 // multiply-high: off by at most one below), fixed up exactly; without it
 // (M >= S, degenerate totals) an FP64 estimate, fixed up the same way.
-__device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long M,
+static __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long M,
                                        const RsConst& k, unsigned long long& Q,
                                        unsigned long long& R) {
     const unsigned long long S = k.S;
@@ -216,7 +216,7 @@ __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long 
 }
 
 // floor(hi 2^64 / d) for hi < d (restoring long division; once per call)
-__device__ unsigned long long div_shift64(unsigned long long hi, unsigned long long d) {
+static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned long long d) {
     unsigned long long rem = hi, quo = 0;
     for (int i = 0; i < 64; ++i) {
         const bool top = (rem >> 63) != 0;
@@ -234,7 +234,7 @@ __device__ unsigned long long div_shift64(unsigned long long hi, unsigned long l
 // call's uniform and constants, and every tile's exclusive prefix (the tile
 // sums are replaced in place), so that no tile of pass 2 repeats this work.
 constexpr int kRsFinThreads = 1024;
-__global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
+static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc,
     uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
 #endif
 
 // Pass 2: one CTA per tile.
-__global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
+static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
     const double* __restrict__ W, int64_t M, uint64_t seed, uint64_t step,
     const int32_t* do_flag, RsScratch sc, int32_t* __restrict__ anc,
     int32_t* __restrict__ counts, double* __restrict__ lwreset, uint32_t* status) {
@@ -517,7 +517,7 @@ __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
 // Pass 3: the chunks of heavy tiles, shared by all CTAs (grid-stride).  A
 // chunk's first item is found by bisection on the tile's inclusive F
 // values; its slots are staged in shared memory and stored slot-major.
-__global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
+static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
     const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
