@@ -23,7 +23,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-P_MOVE, P_ACCEPT, P_RESAMPLE, P_EXCHANGE, P_PFNOISE, P_MULTINOMIAL = 1, 2, 3, 4, 5, 6
+P_MOVE, P_ACCEPT, P_RESAMPLE, P_EXCHANGE, P_PFNOISE, P_MULTINOMIAL, P_PROPOSAL = 1, 2, 3, 4, 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +77,8 @@ def _declare(L):
     L.orc_resample_systematic.argtypes = [_f64p, _i64, C.c_uint32, _i32p, _vp]
     L.orc_resample_systematic.restype = C.c_int
     L.orc_word_array.argtypes = [_u64, C.c_uint32, _u64, _i64, _u32p]
+    L.orc_is_moments.argtypes = [C.c_int, _f64p, _f64p, C.c_double, C.c_double, C.c_double, C.c_int,
+                                 _vp, _i64, _u64, _u64, _f64p]
     L.orc_resample_multinomial.argtypes = [_f64p, _i64, _u32p, _i32p]
     L.orc_resample_multinomial.restype = C.c_int
     L.orc_resample_residual.argtypes = [_f64p, _i64, _u32p, _i32p, C.POINTER(C.c_int64)]
@@ -229,6 +231,18 @@ def resample_systematic(W, u32):
     if rc:
         raise OracleError(f"resample status {rc}")
     return anc, counts
+
+
+def is_moments(mu, a, var, prop_mean, prop_sd, power, x=None, N=None, seed=0, step=0):
+    """Importance-sampling sums {sum w, sum w phi, sum w^2} (Section 2.1);
+    x None draws N proposal samples from (seed, PROPOSAL, step)."""
+    mu, a = _f64(mu), _f64(a)
+    xa = None if x is None else _f32(x)
+    n = xa.size if xa is not None else int(N)
+    out = np.zeros(3, np.float64)
+    lib().orc_is_moments(mu.size, mu, a, float(var), float(prop_mean), float(prop_sd), int(power),
+                         _ptr(xa), n, seed, step, out)
+    return out
 
 
 def slot_uniforms(seed, step, n) -> np.ndarray:

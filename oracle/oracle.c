@@ -41,7 +41,7 @@
 
 /* stream purposes (the same numbers on the GPU side) */
 enum { ORC_P_MOVE = 1, ORC_P_ACCEPT = 2, ORC_P_RESAMPLE = 3,
-       ORC_P_EXCHANGE = 4, ORC_P_PFNOISE = 5, ORC_P_MULTINOMIAL = 6 };
+       ORC_P_EXCHANGE = 4, ORC_P_PFNOISE = 5, ORC_P_MULTINOMIAL = 6, ORC_P_PROPOSAL = 7 };
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10 (Salmon et al. 2011): ten rounds of the 4x32 S-box          */
@@ -446,6 +446,47 @@ int orc_resample_residual(const double* W, int64_t M, const uint32_t* v, int32_t
     free(q);
     free(C);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Importance sampling (Section 2.1 and its worked example; Section 3:       */
+/* weights are target over proposal).  Target: sum_k a_k N(mu_k, var);      */
+/* proposal: N(pm, ps^2); test function phi(x) = x^power.  For each draw     */
+/*   w_i = p(x_i) / q(x_i)                                                   */
+/* and out = { sum w_i, sum w_i phi(x_i), sum w_i^2 }.  x == NULL draws      */
+/* x_i = float(pm + ps z_i), z_i = normal 0 of (seed, PROPOSAL, step, i).    */
+/* ------------------------------------------------------------------------ */
+void orc_is_moments(int K, const double* mu, const double* a, double var, double pm, double ps,
+                    int power, const float* x, int64_t N, uint64_t seed, uint64_t step,
+                    double* out)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    for (int64_t i = 0; i < N; ++i) {
+        double xi;
+        if (x) {
+            xi = (double)x[i];
+        } else {
+            double z;
+            orc_normals(seed, ORC_P_PROPOSAL, step, (uint32_t)i, 1, &z);
+            xi = (double)(float)(pm + ps * z);
+        }
+        double p = 0.0;
+        for (int k = 0; k < K; ++k) {
+            double d = xi - mu[k];
+            p += a[k] * exp(-d * d / (2.0 * var)) / sqrt(2.0 * ORC_PI * var);
+        }
+        double dq = (xi - pm) / ps;
+        double q = exp(-0.5 * dq * dq) / (ps * sqrt(2.0 * ORC_PI));
+        double w = p / q;
+        double phi = 1.0;
+        for (int e = 0; e < power; ++e) phi *= xi;
+        s0 += w;
+        s1 += w * phi;
+        s2 += w * w;
+    }
+    out[0] = s0;
+    out[1] = s1;
+    out[2] = s2;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -46,12 +46,15 @@ class SMCSampler(_Graphable):
     step counter t + r 2^32; only the first move gathers the ancestors."""
 
     def __init__(self, ctx: api.Context, model: api.GMM, y, theta0, betas, kind=L.MOVE_RW,
-                 scale=0.1, seed=1234, ess_frac=0.5, n_moves=1):
+                 scale=0.1, seed=1234, ess_frac=0.5, n_moves=1, resampler="systematic"):
         self.ctx, self.model, self.kind = ctx, model, kind
         self.scale, self.seed, self.ess_frac = float(scale), int(seed), float(ess_frac)
         self.n_moves = int(n_moves)
         if self.n_moves < 1:
             raise ValueError("n_moves must be at least 1")
+        if resampler not in api.RESAMPLERS:
+            raise ValueError(f"resampler must be one of {api.RESAMPLERS}")
+        self.resampler = resampler
         self.y = _dev(y, torch.float32)
         th = _dev(theta0, torch.float32)
         self.K, self.M = th.shape
@@ -89,8 +92,8 @@ class SMCSampler(_Graphable):
         db = float(self.betas_host[t] - self.betas_host[t - 1])
         flag, hist, beta, accepts = self._views[t]
         api.reweight(ctx, self.ll[c], db, self.lw, self.W, hist, flag, self.ess_frac)
-        api.resample_systematic(ctx, self.W, self.seed, t, anc=self.anc, do_flag=flag,
-                                logw_reset=self.lw)
+        api.resample(ctx, self.resampler, self.W, self.seed, t, anc=self.anc, do_flag=flag,
+                     logw_reset=self.lw)
         for r in range(self.n_moves):
             first = r == 0
             api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n],
@@ -162,11 +165,16 @@ class PopulationMCMC(_Graphable):
 
 
 class ParticleFilter(_Graphable):
-    """Bootstrap particle filter with systematic resampling after every step;
-    log Z = sum_t [LSE(log g_t) - log M]."""
+    """Bootstrap particle filter resampling after every step (systematic by
+    default; multinomial or residual on request); log Z = sum_t [LSE(log g_t)
+    - log M]."""
 
-    def __init__(self, ctx: api.Context, model: api.PFModel, y, M: int, seed: int = 77):
+    def __init__(self, ctx: api.Context, model: api.PFModel, y, M: int, seed: int = 77,
+                 resampler: str = "systematic"):
         self.ctx, self.model, self.M, self.seed = ctx, model, int(M), int(seed)
+        if resampler not in api.RESAMPLERS:
+            raise ValueError(f"resampler must be one of {api.RESAMPLERS}")
+        self.resampler = resampler
         self.y = _dev(y, torch.float32)
         self.T = self.y.shape[0]
         self.d = int(np.asarray(model.phi).size)  # state dimension (FSV: factors)
@@ -195,7 +203,8 @@ class ParticleFilter(_Graphable):
         api.pf_step(self.ctx, self.model, y_t, self.x[c], self.x[n], self.logg,
                     self.seed, t, anc=self.anc)
         api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
-        api.resample_systematic(self.ctx, self.W, self.seed, t, anc=self.anc, logw_reset=self.lw)
+        api.resample(self.ctx, self.resampler, self.W, self.seed, t, anc=self.anc,
+                     logw_reset=self.lw)
         self.cur = n
 
     def run(self, graph: bool = False, steps: int | None = None):

@@ -128,3 +128,55 @@ def test_residual_keeps_integer_shares(smc):
     assert cnt.sum() == M and np.all(cnt >= share)
     nd = int(share.sum())
     assert np.all(np.diff(anc[:nd]) >= 0)
+
+
+@pytest.mark.parametrize("scheme", ["multinomial", "residual"])
+def test_samplers_with_other_schemes(smc, scheme):
+    """The SMC sampler and the particle filter with the other schemes: graph
+    form equals the plain form bit for bit, and the filter's evidence agrees
+    with the Kalman filter (linear-Gaussian model) within Monte Carlo error."""
+    import synth
+    from paper_0905_2441_gb300 import samplers as S
+    P, ctx = smc
+    y = synth.gmm1d_data(100, [-3, 0, 3, 6], 0.55, seed=1)
+    th0 = synth.prior_particles(4, 4096, seed=3)
+    smp = S.SMCSampler(ctx, P.GMM(4, 0.55), y, th0, synth.power_betas(12, start=0), scale=1.0,
+                       seed=5, n_moves=2, resampler=scheme)
+    z1 = smp.run()
+    th1 = smp.state[0].clone()
+    smp.reset(th0)
+    z2 = smp.run(graph=True)
+    ctx.check()
+    assert z1 == z2 and torch.equal(th1, smp.state[0]) and int(smp.flags.sum()) >= 1
+    phi, Sigma, beta = synth.msv_params()
+    _, yo = synth.simulate_ssm("lg", 40, phi, Sigma, beta, seed=4)
+    exact = oracle.kalman_lg(phi, Sigma, beta, yo)
+    zs = []
+    for s in range(8):
+        pf = S.ParticleFilter(ctx, P.PFModel(P.PF_LG, phi, synth.chol(Sigma), beta), yo, 1 << 14,
+                              seed=100 + s, resampler=scheme)
+        zs.append(pf.run())
+    ctx.check()
+    zs = np.array(zs)
+    se = max(zs.std(ddof=1) / np.sqrt(zs.size), 0.01)
+    assert abs(zs.mean() - exact) < 5 * se + 0.05, (zs.mean(), exact, se)
+
+
+@pytest.mark.parametrize("frac", [0.0, 0.1, 0.5, 0.9, 1.0, 1.5])
+def test_ess_threshold_decision(smc, frac):
+    """The resampling decision is ESS < frac * M, taken on the device for any
+    threshold (0: never, as in annealed importance sampling; >= 1: at every
+    step unless all weights are equal), matching the oracle's ESS."""
+    P, ctx = smc
+    M = 20000
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    sc = torch.empty(4, dtype=torch.float64, device="cuda")
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    for spread in (0.01, 0.5, 2.0, 8.0):
+        g = np.random.default_rng(int(spread * 100))
+        lw0 = g.normal(0, spread, M)
+        P.reweight(ctx, None, 0.0, cu(lw0), W, sc, flag, frac)
+        ctx.check()
+        ess = oracle.ess(lw0)
+        if abs(ess - frac * M) > 1e-6 * M:  # away from the threshold itself
+            assert int(np_(flag)[0]) == int(ess < frac * M), (spread, ess)

@@ -245,3 +245,31 @@ def test_multinomial_residual_errors():
             f(np.zeros(3), np.zeros(3, np.uint32))
         with pytest.raises(oracle.OracleError):
             f(np.array([0.5, 1.5]), np.zeros(2, np.uint32))
+
+
+def test_is_moments_section_2_1_example():
+    """The worked example of Section 2.1: E[x^2] under the two-component
+    target is 1.875 (closed form); both the plain estimate sum w phi / N and
+    the self-normalised one converge to it, and sum w / N to 1 (the target is
+    normalised).  Given draws and device-style draws give the same sums."""
+    c = GOLD["importance_sampling_example_section_2_1"]
+    exact = sum(w * (c["target_var"] + m**2) for w, m in zip(c["target_weights"], c["target_means"]))
+    assert abs(exact - 1.875) < 1e-15
+    N = 400000
+    out = oracle.is_moments(c["target_means"], c["target_weights"], c["target_var"], 0.0, 1.0, 2,
+                            N=N, seed=5, step=1)
+    ess = out[0] ** 2 / out[2]
+    se = 4.0 / np.sqrt(ess)
+    assert abs(out[1] / N - exact) < se and abs(out[1] / out[0] - exact) < se
+    assert abs(out[0] / N - 1.0) < 4.0 / np.sqrt(ess)
+    # the same draws passed in explicitly
+    z = np.array([oracle.normals(5, oracle.P_PROPOSAL, 1, i, 1)[0] for i in range(1000)])
+    x = (0.0 + 1.0 * z).astype(np.float32)
+    a = oracle.is_moments(c["target_means"], c["target_weights"], c["target_var"], 0.0, 1.0, 2, x=x)
+    b = oracle.is_moments(c["target_means"], c["target_weights"], c["target_var"], 0.0, 1.0, 2,
+                          N=1000, seed=5, step=1)
+    np.testing.assert_allclose(a, b, rtol=1e-12)
+    # weights against independent densities: w = p / q with scipy's normal pdf
+    wr = (0.5 * stats.norm.pdf(x, -1.0, 0.5) + 0.5 * stats.norm.pdf(x, 1.5, 0.5)) / stats.norm.pdf(x)
+    np.testing.assert_allclose(a, [wr.sum(), (wr * x.astype(np.float64) ** 2).sum(), (wr ** 2).sum()],
+                               rtol=1e-10)
