@@ -439,6 +439,46 @@ def bench_secondary(torch, P):
     reps = 10
     t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
     ctx.check()
+    # Section 2.1's importance-sampling example at its size (N = 2^24 draws):
+    # draws in device memory (HBM-bound, 4 bytes a draw), drawn on the
+    # device, and end to end from pinned host memory as in the example
+    prob = P.ISProblem()
+    n_is = 1 << 24
+    x_d = torch.randn(n_is, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
+    x_h = x_d.cpu().pin_memory()
+    res = torch.empty(3, dtype=torch.float64, device="cuda")
+    res_h = torch.empty(3, dtype=torch.float64).pin_memory()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        P.is_moments(ctx, prob, x_d, out=res)
+    t_mem, t_dev, t_e2e = [], [], []
+    for _ in range(10):
+        e = _flush_timed(torch, flush, stream, [lambda: P.is_moments(ctx, prob, x_d, out=res)])
+        torch.cuda.synchronize()
+        t_mem.append(e[0].elapsed_time(e[1]) / 1e3)
+        e = _flush_timed(torch, flush, stream,
+                         [lambda: P.is_moments(ctx, prob, N=n_is, seed=1, step=1, out=res)])
+        torch.cuda.synchronize()
+        t_dev.append(e[0].elapsed_time(e[1]) / 1e3)
+
+        def e2e():
+            x_d.copy_(x_h, non_blocking=True)
+            P.is_moments(ctx, prob, x_d, out=res)
+            res_h.copy_(res, non_blocking=True)
+        e = _flush_timed(torch, flush, stream, [e2e])
+        torch.cuda.synchronize()
+        t_e2e.append(e[0].elapsed_time(e[1]) / 1e3)
+    ctx.check()
+    est = res_h.numpy()
+    tm = statistics.median(t_mem)
+    out["is_example"] = {"workload": "is-section2.1-N16777216", "N": n_is,
+                         "ms_draws_in_hbm": 1e3 * tm, "gbs_draws_in_hbm": 4 * n_is / tm / 1e9,
+                         "hbm_frac": 4 * n_is / tm / 1e9 / measured_peaks()["hbm_gbs"],
+                         "ms_draws_on_device": 1e3 * statistics.median(t_dev),
+                         "ms_end_to_end_from_host": 1e3 * statistics.median(t_e2e),
+                         "estimate_plain": float(est[1] / n_is),
+                         "estimate_self_normalised": float(est[1] / est[0]), "exact": 1.875}
     out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
                                "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
                                "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}

@@ -54,7 +54,8 @@ typedef struct smc_ctx smc_ctx;
 
 /* Stream purposes of the Philox counter (the fourth counter word). */
 enum { SMC_RNG_MOVE = 1, SMC_RNG_ACCEPT = 2, SMC_RNG_RESAMPLE = 3,
-       SMC_RNG_EXCHANGE = 4, SMC_RNG_PFNOISE = 5, SMC_RNG_MULTINOMIAL = 6 };
+       SMC_RNG_EXCHANGE = 4, SMC_RNG_PFNOISE = 5, SMC_RNG_MULTINOMIAL = 6,
+       SMC_RNG_PROPOSAL = 7 };
 
 /* ------------------------------------------------------------------ context */
 
@@ -288,6 +289,36 @@ smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y,
                              float* theta, double* loglik, int64_t M_total, const float* beta,
                              const int32_t* pop_offsets, int32_t n_pops, float scale,
                              uint64_t seed, uint64_t sweep, uint64_t* stats, void* stream);
+
+/* ------------------------------------------------------------ importance sampling */
+
+/* Target and proposal of an importance-sampling estimate (Section 2.1's
+ * worked example: target 1/2 N(-1, 0.25) + 1/2 N(1.5, 0.25), proposal
+ * N(0, 1), test function x^2, expectation 1.875).  Passed by host pointer. */
+typedef struct smc_is_problem {
+    int32_t K;             /* target components, 1..8 */
+    float mu[8];           /* component means */
+    float a[8];            /* component weights, > 0 (normalised target: sum 1) */
+    float var;             /* common component variance, > 0 */
+    float prop_mean;       /* proposal N(prop_mean, prop_sd^2) */
+    float prop_sd;         /* > 0 */
+    int32_t power;         /* test function phi(x) = x^power, 0..8 */
+} smc_is_problem;
+
+/* Importance-sampling sums over N proposal draws (Section 2.1; Section 3:
+ * w = target density / proposal density):
+ *   out[0] = sum w_i,  out[1] = sum w_i phi(x_i),  out[2] = sum w_i^2
+ *   (out: device double[3]).  The plain estimate is out[1] / N, the
+ *   self-normalised one out[1] / out[0], the ESS out[0]^2 / out[2].
+ *   x: device float[N] draws from the proposal, or NULL to draw
+ *      x_i = prop_mean + prop_sd z_i on the device, z_i = normal 0 of
+ *      (seed, PROPOSAL = 7, step, index i).
+ * Per draw in FP32 (w = exp2 of the log2 ratio; overflows for draws where
+ * the target exceeds the proposal by more than 2^128), groups of 8 draws
+ * summed in FP32, group sums in FP64 in a fixed order: the same bits on
+ * every run.  N = 0 writes zeros.  Uses the context's reduction scratch. */
+smc_status smc_is_moments(smc_ctx* ctx, const smc_is_problem* prob, const float* x, int64_t N,
+                          uint64_t seed, uint64_t step, double* out, void* stream);
 
 /* ------------------------------------------------------------ particle filter */
 

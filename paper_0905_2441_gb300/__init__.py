@@ -10,11 +10,11 @@ fails loudly if it is missing -- there is no CPU path.
 """
 from ._lib import (GMM_1D, GMM_DIAG, MOVE_MALA, MOVE_RW, OP_LOGLIK, OP_MOVE, OP_POPMCMC, PF_LG,
                    PF_FSV, PF_MSV, PREC_BF16SPLIT, PREC_FP32, RNG_ACCEPT, RNG_EXCHANGE, RNG_MOVE,
-                   RNG_MULTINOMIAL, RNG_PFNOISE, RNG_RESAMPLE)
+                   RNG_MULTINOMIAL, RNG_PFNOISE, RNG_PROPOSAL, RNG_RESAMPLE)
 
 __all__ = ["GMM_1D", "GMM_DIAG", "MOVE_MALA", "MOVE_RW", "OP_LOGLIK", "OP_MOVE", "OP_POPMCMC",
            "PF_FSV", "PF_LG", "PF_MSV", "PREC_BF16SPLIT", "PREC_FP32", "RNG_ACCEPT", "RNG_EXCHANGE",
-           "RNG_MOVE", "RNG_MULTINOMIAL", "RNG_PFNOISE", "RNG_RESAMPLE"]
+           "RNG_MOVE", "RNG_MULTINOMIAL", "RNG_PFNOISE", "RNG_PROPOSAL", "RNG_RESAMPLE"]
 
 
 def __getattr__(name):

@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(_HERE, "libsmc.so")
 SMC_OK, SMC_ERR_ARG, SMC_ERR_CUDA, SMC_ERR_NONFINITE = 0, -1, -2, -3
 SMC_ERR_ZERO_WEIGHT, SMC_ERR_TIMEOUT, SMC_ERR_UNSUPPORTED = -4, -5, -6
 RNG_MOVE, RNG_ACCEPT, RNG_RESAMPLE, RNG_EXCHANGE, RNG_PFNOISE, RNG_MULTINOMIAL = 1, 2, 3, 4, 5, 6
+RNG_PROPOSAL = 7
 OP_LOGLIK, OP_MOVE, OP_POPMCMC = 0, 1, 2
 GMM_1D, GMM_DIAG = 0, 1
 PREC_FP32, PREC_BF16SPLIT = 0, 1
@@ -22,7 +23,7 @@ EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_sta
            "smc_resample_systematic", "smc_gather", "smc_mh_move", "smc_popmcmc_sweep",
            "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
            "smc_resample_systematic_noalloc", "smc_resample_multinomial",
-           "smc_resample_residual")
+           "smc_resample_residual", "smc_is_moments")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -30,6 +31,11 @@ class SmcGmm(C.Structure):
     _fields_ = [("kind", C.c_int32), ("K", C.c_int32), ("d", C.c_int32),
                 ("precision", C.c_int32), ("log_w", C.POINTER(C.c_float)),
                 ("sigma", C.c_float), ("lo", C.c_float), ("hi", C.c_float)]
+
+
+class SmcIsProblem(C.Structure):
+    _fields_ = [("K", C.c_int32), ("mu", C.c_float * 8), ("a", C.c_float * 8), ("var", C.c_float),
+                ("prop_mean", C.c_float), ("prop_sd", C.c_float), ("power", C.c_int32)]
 
 
 class SmcPfModel(C.Structure):
@@ -60,6 +66,7 @@ def _declare(L):
     L.smc_resample_multinomial.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
     L.smc_resample_residual.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
     L.smc_gather.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.smc_is_moments.argtypes = [_vp, C.POINTER(SmcIsProblem), _vp, _i64, _u64, _u64, _vp, _vp]
     L.smc_mh_move.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp,
                               _vp, _i64, _vp, _i64, C.c_float, _i32, _u64, _u64, _vp, _vp]
     L.smc_popmcmc_sweep.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _vp, _i64, _vp, _vp,

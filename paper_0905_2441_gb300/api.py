@@ -362,6 +362,46 @@ def pf_step(ctx: Context, model: PFModel, y_t, x_in, x_out, logg_out, seed: int,
                           _ptr(logg_out), M, int(seed), int(t), _stream(stream)), "pf_step")
 
 
+@dataclass
+class ISProblem:
+    """Gaussian-mixture target sum_k a_k N(mu_k, var), Gaussian proposal, test
+    function x^power (Section 2.1's example by default)."""
+    mu: tuple = (-1.0, 1.5)
+    a: tuple = (0.5, 0.5)
+    var: float = 0.25
+    prop_mean: float = 0.0
+    prop_sd: float = 1.0
+    power: int = 2
+
+    def cstruct(self) -> L.SmcIsProblem:
+        c = L.SmcIsProblem()
+        c.K = len(self.mu)
+        if c.K < 1 or c.K > 8 or len(self.a) != c.K:
+            raise ValueError("1..8 components, one weight each")
+        for k in range(c.K):
+            c.mu[k] = float(self.mu[k])
+            c.a[k] = float(self.a[k])
+        c.var, c.prop_mean, c.prop_sd = float(self.var), float(self.prop_mean), float(self.prop_sd)
+        c.power = int(self.power)
+        return c
+
+
+def is_moments(ctx: Context, prob: ISProblem, x=None, N: int | None = None, seed: int = 0,
+               step: int = 0, out=None, stream=None):
+    """{sum w, sum w phi, sum w^2} over N proposal draws (x, or drawn on the device)."""
+    if x is not None:
+        _need(x, torch.float32, "x")
+        N = x.numel()
+    elif N is None:
+        raise ValueError("give the draws x or their number N")
+    out = torch.empty(3, dtype=torch.float64, device="cuda") if out is None else out
+    _need(out, torch.float64, "out", (3,))
+    c = prob.cstruct()
+    _chk(L.load().smc_is_moments(ctx.handle, C.byref(c), _ptr(x), int(N), int(seed), int(step),
+                                 _ptr(out), _stream(stream)), "smc_is_moments")
+    return out
+
+
 def rng_words(ctx: Context, seed: int, purpose: int, step: int, n_index: int, n_block: int = 1,
               stream=None):
     out = torch.empty(n_index * n_block * 4, dtype=torch.int32, device="cuda")

@@ -39,6 +39,7 @@ enum : int {
     CNT_POP_DONE = 5,
     CNT_DIAG_TICKET = 6,
     CNT_RESAMPLE_DONE = 7,
+    CNT_IS_TICKET = 8,
     kCounters = 16
 };
 constexpr int kMaxPartialBlocks = 2048;

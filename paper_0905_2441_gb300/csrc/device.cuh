@@ -27,7 +27,7 @@ constexpr uint32_t kSpinLimit = 4u << 20;
 // ---------------------------------------------------------------- Philox
 enum : uint32_t {
     RNG_MOVE = 1, RNG_ACCEPT = 2, RNG_RESAMPLE = 3, RNG_EXCHANGE = 4, RNG_PFNOISE = 5,
-    RNG_MULTINOMIAL = 6
+    RNG_MULTINOMIAL = 6, RNG_PROPOSAL = 7
 };
 
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
