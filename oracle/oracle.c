@@ -449,6 +449,66 @@ int orc_resample_residual(const double* W, int64_t M, const uint32_t* v, int32_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* MRG32k3a (L'Ecuyer 1999), the generator Section 2.5 parallelises by       */
+/* skip-ahead.  Two components of order 3:                                   */
+/*   x_n = (1403580 x_{n-2} - 810728 x_{n-3}) mod (2^32 - 209)               */
+/*   y_n = (527612 y_{n-1} - 1370589 y_{n-3}) mod (2^32 - 22853)             */
+/*   u_n = z_n / (m1 + 1), z_n = (x_n - y_n) mod m1 (m1 in place of 0).      */
+/* Writes n numbers starting at position `start` (position 0 = the first     */
+/* number after the seed state) as float(z * (1 / (m1 + 1))).  The state     */
+/* reaches `start` by multiplying with the one-step matrices raised to the   */
+/* power start, by repeated squaring (O(log start) products).                */
+/* ------------------------------------------------------------------------ */
+static void orc_mat3_mul(const uint64_t* A, const uint64_t* B, uint64_t m, uint64_t* C)
+{
+    uint64_t r[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            unsigned __int128 acc = 0;
+            for (int l = 0; l < 3; ++l) acc += (unsigned __int128)A[3 * i + l] * B[3 * l + j];
+            r[3 * i + j] = (uint64_t)(acc % m);
+        }
+    memcpy(C, r, sizeof(r));
+}
+
+void orc_mrg32k3a(const uint32_t seed[6], uint64_t start, int64_t n, float* out)
+{
+    const uint64_t m1 = 4294967087ull, m2 = 4294944443ull;
+    uint64_t A1[9] = {0, 1, 0, 0, 0, 1, m1 - 810728ull, 1403580ull, 0};
+    uint64_t A2[9] = {0, 1, 0, 0, 0, 1, m2 - 1370589ull, 0, 527612ull};
+    uint64_t P1[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, P2[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    for (uint64_t e = start; e; e >>= 1) {   /* P = A^start */
+        if (e & 1ull) {
+            orc_mat3_mul(P1, A1, m1, P1);
+            orc_mat3_mul(P2, A2, m2, P2);
+        }
+        orc_mat3_mul(A1, A1, m1, A1);
+        orc_mat3_mul(A2, A2, m2, A2);
+    }
+    int64_t x[3], y[3];
+    for (int i = 0; i < 3; ++i) {
+        unsigned __int128 ax = 0, ay = 0;
+        for (int k = 0; k < 3; ++k) {
+            ax += (unsigned __int128)P1[3 * i + k] * seed[k];
+            ay += (unsigned __int128)P2[3 * i + k] * seed[3 + k];
+        }
+        x[i] = (int64_t)(ax % m1);
+        y[i] = (int64_t)(ay % m2);
+    }
+    for (int64_t j = 0; j < n; ++j) {
+        int64_t p1 = (1403580LL * x[1] - 810728LL * x[0]) % (int64_t)m1;
+        if (p1 < 0) p1 += (int64_t)m1;
+        x[0] = x[1]; x[1] = x[2]; x[2] = p1;
+        int64_t p2 = (527612LL * y[2] - 1370589LL * y[0]) % (int64_t)m2;
+        if (p2 < 0) p2 += (int64_t)m2;
+        y[0] = y[1]; y[1] = y[2]; y[2] = p2;
+        int64_t z = (p1 - p2) % (int64_t)m1;
+        if (z <= 0) z += (int64_t)m1;
+        out[j] = (float)((double)z * 2.328306549295727688e-10);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Importance sampling (Section 2.1 and its worked example; Section 3:       */
 /* weights are target over proposal).  Target: sum_k a_k N(mu_k, var);      */
 /* proposal: N(pm, ps^2); test function phi(x) = x^power.  For each draw     */

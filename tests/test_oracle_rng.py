@@ -76,3 +76,42 @@ def test_uniform_and_normal_distributions():
     # pairs are uncorrelated
     zz = np.array([oracle.normals(9, 1, 0, i, 2) for i in range(20000)])
     assert abs(np.corrcoef(zz.T)[0, 1]) < 4 / np.sqrt(20000)
+
+
+# ------------------------------------------------------------------ MRG32k3a (Section 2.5)
+SEED6 = [12345] * 6
+
+
+def test_mrg32k3a_skip_ahead_equals_stepping():
+    """Section 2.5: a thread jumps to its block by skip-ahead in O(log n)
+    products; the numbers it then draws are those sequential stepping
+    reaches (repeated squaring against one-step iteration)."""
+    seq = oracle.mrg32k3a(SEED6, 0, 20000)
+    for start in [1, 2, 3, 7, 64, 1000, 12345, 19990]:
+        n = min(10, 20000 - start)
+        assert np.array_equal(oracle.mrg32k3a(SEED6, start, n), seq[start:start + n]), start
+    other = [1, 2, 3, 4, 5, 6]
+    seq2 = oracle.mrg32k3a(other, 0, 3000)
+    assert np.array_equal(oracle.mrg32k3a(other, 2500, 500), seq2[2500:])
+
+
+def test_mrg32k3a_far_jumps_are_consistent():
+    """Jumps far beyond anything steppable: the block at 2^70 + 5 is the block
+    at 2^70 moved by five places, and substreams 2^76 apart differ."""
+    a = oracle.mrg32k3a(SEED6, 2**70, 20)
+    b = oracle.mrg32k3a(SEED6, 2**70 + 5, 15)
+    assert np.array_equal(a[5:], b)
+    s76 = oracle.mrg32k3a(SEED6, 2**63, 8)
+    assert not np.array_equal(s76, oracle.mrg32k3a(SEED6, 0, 8))
+
+
+def test_mrg32k3a_uniform_and_uncorrelated():
+    u = oracle.mrg32k3a(SEED6, 777, 200000).astype(np.float64)
+    assert np.all((u > 0) & (u < 1))
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    r = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(r) < 0.01
+    # pairs fall evenly into a 16 x 16 grid
+    h, _, _ = np.histogram2d(u[:-1:2], u[1::2], bins=16, range=[[0, 1], [0, 1]])
+    chi2 = np.sum((h - h.mean()) ** 2 / h.mean())
+    assert stats.chi2.sf(chi2, 255) > 1e-4
