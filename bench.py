@@ -479,6 +479,26 @@ def bench_secondary(torch, P):
                          "ms_end_to_end_from_host": 1e3 * statistics.median(t_e2e),
                          "estimate_plain": float(est[1] / n_is),
                          "estimate_self_normalised": float(est[1] / est[0]), "exact": 1.875}
+    # MRG32k3a as Section 2.5 runs it: per thread a skip-ahead to its block,
+    # then the block (float32 out, slot-major)
+    nt, per = 152 * 256 * 4, 1024
+    mrg = torch.empty(nt * per, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        P.rng_mrg32k3a(ctx, (12345,) * 6, 0, nt, per, out=mrg)
+    t_blk, t_jump = [], []
+    for _ in range(10):
+        e = _flush_timed(torch, flush, stream,
+                         [lambda: P.rng_mrg32k3a(ctx, (12345,) * 6, 2**40, nt, per, out=mrg),
+                          lambda: P.rng_mrg32k3a(ctx, (12345,) * 6, 2**40, nt, 1,
+                                                 out=mrg[:nt])])
+        torch.cuda.synchronize()
+        t_blk.append(e[0].elapsed_time(e[1]) / 1e3)
+        t_jump.append(e[1].elapsed_time(e[2]) / 1e3)
+    ctx.check()
+    tb = statistics.median(t_blk)
+    out["mrg32k3a"] = {"threads": nt, "per_thread": per, "ms": 1e3 * tb,
+                       "numbers_per_s": nt * per / tb, "gbs_written": 4 * nt * per / tb / 1e9,
+                       "ms_skip_ahead_only": 1e3 * statistics.median(t_jump)}
     out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
                                "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
                                "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}

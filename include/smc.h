@@ -356,6 +356,31 @@ smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
 
 /* ------------------------------------------------------------------- streams */
 
+/* MRG32k3a (L'Ecuyer 1999), the generator Section 2.5 parallelises: thread
+ * t of n_threads computes the contiguous block of per_thread numbers that
+ * starts at position offset + t * per_thread (mod 2^64) of the one stream
+ * that starts at `seed`, reaching it by skip-ahead in O(log n) matrix-vector
+ * products mod m (the context holds A^(2^k), k < 64).
+ *   x_n = (1403580 x_{n-2} - 810728 x_{n-3}) mod m1,  m1 = 4294967087
+ *   y_n = (527612 y_{n-1} - 1370589 y_{n-3}) mod m2,  m2 = 4294944443
+ *   z_n = (x_n - y_n) mod m1, taken in [1, m1] (m1 in place of 0);
+ *   out_f64 (nullable): u_n = z_n / (m1 + 1), the generator's output, as
+ *     (double) z_n * (1 / (m1 + 1));
+ *   out_f32 (nullable): u_n = (2 floor(z_n / 2^9) + 1) / 2^24, the same
+ *     number cut to the 24 bits a float holds, strictly inside (0, 1).
+ *   At least one of the outputs is given.
+ *   seed: host uint32[6] = (x_0, x_1, x_2 | y_0, y_1, y_2), oldest first;
+ *     x-part < m1, y-part < m2, neither part all zero (else SMC_ERR_ARG).
+ *     Position 0 is the first number after the seed state.
+ *   Layout of each output [per_thread][n_threads]:
+ *     out[j * n_threads + t] = u_{offset + t * per_thread + j}
+ *     (slot-major: consecutive threads write consecutive addresses).
+ * The SMC / MCMC kernels themselves draw from Philox; this stream serves
+ * callers that want the paper's generator. */
+smc_status smc_rng_mrg32k3a(smc_ctx* ctx, const uint32_t seed[6], uint64_t offset,
+                            int64_t n_threads, int64_t per_thread, float* out_f32,
+                            double* out_f64, void* stream);
+
 /* Raw Philox words: out[(i*n_block + b)*4 + w] = word w of
  * (seed, purpose, step, index i, block b), i < n_index, b < n_block. */
 smc_status smc_rng_words(smc_ctx* ctx, uint64_t seed, uint32_t purpose, uint64_t step,

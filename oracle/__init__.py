@@ -77,7 +77,7 @@ def _declare(L):
     L.orc_resample_systematic.argtypes = [_f64p, _i64, C.c_uint32, _i32p, _vp]
     L.orc_resample_systematic.restype = C.c_int
     L.orc_word_array.argtypes = [_u64, C.c_uint32, _u64, _i64, _u32p]
-    L.orc_mrg32k3a.argtypes = [_u32p, _u64, _i64, _f32p]
+    L.orc_mrg32k3a.argtypes = [_u32p, _u64, _i64, _vp, _vp]
     L.orc_is_moments.argtypes = [C.c_int, _f64p, _f64p, C.c_double, C.c_double, C.c_double, C.c_int,
                                  _vp, _i64, _u64, _u64, _f64p]
     L.orc_resample_multinomial.argtypes = [_f64p, _i64, _u32p, _i32p]
@@ -246,10 +246,14 @@ def is_moments(mu, a, var, prop_mean, prop_sd, power, x=None, N=None, seed=0, st
     return out
 
 
-def mrg32k3a(seed, start, n) -> np.ndarray:
-    """n MRG32k3a uniforms (float32) from stream position `start`."""
-    out = np.zeros(max(int(n), 1), np.float32)
-    lib().orc_mrg32k3a(np.ascontiguousarray(seed, np.uint32), int(start) & (2**64 - 1), int(n), out)
+def mrg32k3a(seed, start, n, dtype=np.float32) -> np.ndarray:
+    """n MRG32k3a uniforms from stream position `start`: float32 (24-bit
+    uniforms) or float64 (z / (m1 + 1))."""
+    out = np.zeros(max(int(n), 1), dtype)
+    f32 = out if out.dtype == np.float32 else None
+    f64 = out if out.dtype == np.float64 else None
+    lib().orc_mrg32k3a(np.ascontiguousarray(seed, np.uint32), int(start) & (2**64 - 1), int(n),
+                       _ptr(f32), _ptr(f64))
     return out[:n]
 
 

@@ -455,7 +455,9 @@ int orc_resample_residual(const double* W, int64_t M, const uint32_t* v, int32_t
 /*   y_n = (527612 y_{n-1} - 1370589 y_{n-3}) mod (2^32 - 22853)             */
 /*   u_n = z_n / (m1 + 1), z_n = (x_n - y_n) mod m1 (m1 in place of 0).      */
 /* Writes n numbers starting at position `start` (position 0 = the first     */
-/* number after the seed state) as float(z * (1 / (m1 + 1))).  The state     */
+/* number after the seed state): out64 = z / (m1 + 1) as (double) z times   */
+/* 1 / (m1 + 1); out32 = (2 floor(z / 2^9) + 1) / 2^24 (24 bits, inside     */
+/* (0, 1)); either may be NULL.  The state                                   */
 /* reaches `start` by multiplying with the one-step matrices raised to the   */
 /* power start, by repeated squaring (O(log start) products).                */
 /* ------------------------------------------------------------------------ */
@@ -471,7 +473,8 @@ static void orc_mat3_mul(const uint64_t* A, const uint64_t* B, uint64_t m, uint6
     memcpy(C, r, sizeof(r));
 }
 
-void orc_mrg32k3a(const uint32_t seed[6], uint64_t start, int64_t n, float* out)
+void orc_mrg32k3a(const uint32_t seed[6], uint64_t start, int64_t n, float* out32,
+                  double* out64)
 {
     const uint64_t m1 = 4294967087ull, m2 = 4294944443ull;
     uint64_t A1[9] = {0, 1, 0, 0, 0, 1, m1 - 810728ull, 1403580ull, 0};
@@ -504,7 +507,8 @@ void orc_mrg32k3a(const uint32_t seed[6], uint64_t start, int64_t n, float* out)
         y[0] = y[1]; y[1] = y[2]; y[2] = p2;
         int64_t z = (p1 - p2) % (int64_t)m1;
         if (z <= 0) z += (int64_t)m1;
-        out[j] = (float)((double)z * 2.328306549295727688e-10);
+        if (out32) out32[j] = (float)((2.0 * (double)(z >> 9) + 1.0) / 16777216.0);
+        if (out64) out64[j] = (double)z * 2.328306549295727688e-10;
     }
 }
 

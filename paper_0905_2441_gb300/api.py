@@ -402,6 +402,28 @@ def is_moments(ctx: Context, prob: ISProblem, x=None, N: int | None = None, seed
     return out
 
 
+def rng_mrg32k3a(ctx: Context, seed=(12345,) * 6, offset: int = 0, n_threads: int = 1,
+                 per_thread: int = 1, out=None, dtype=torch.float32, stream=None):
+    """MRG32k3a uniforms: thread t's contiguous block of per_thread numbers
+    starting at stream position offset + t * per_thread; returns a
+    [per_thread, n_threads] tensor (float32: 24-bit uniforms; float64: the
+    generator's z / (m1 + 1))."""
+    out = (torch.empty(per_thread * n_threads, dtype=dtype, device="cuda")
+           if out is None else out)
+    if out.dtype not in (torch.float32, torch.float64):
+        raise TypeError("out must be float32 or float64")
+    _need(out, out.dtype, "out")
+    if out.numel() != per_thread * n_threads:
+        raise ValueError("out must hold per_thread * n_threads numbers")
+    sd = (C.c_uint32 * 6)(*[int(v) for v in seed])
+    f32 = out if out.dtype == torch.float32 else None
+    f64 = out if out.dtype == torch.float64 else None
+    _chk(L.load().smc_rng_mrg32k3a(ctx.handle, C.byref(sd), int(offset) & (2**64 - 1),
+                                   int(n_threads), int(per_thread), _ptr(f32), _ptr(f64),
+                                   _stream(stream)), "smc_rng_mrg32k3a")
+    return out.view(per_thread, n_threads)
+
+
 def rng_words(ctx: Context, seed: int, purpose: int, step: int, n_index: int, n_block: int = 1,
               stream=None):
     out = torch.empty(n_index * n_block * 4, dtype=torch.int32, device="cuda")

@@ -80,6 +80,10 @@ void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* 
 
 // ------------------------------------------------------------------ C ABI
 
+namespace smc_host {
+void mrg_power_table(uint32_t* tab);
+}
+
 extern "C" smc_status smc_create(smc_ctx** out, int device) {
     if (!out) return SMC_ERR_ARG;
     *out = nullptr;
@@ -103,7 +107,13 @@ extern "C" smc_status smc_create(smc_ctx** out, int device) {
                   cudaSuccess &&
               cudaMemset(c->d_status, 0, sizeof(uint32_t)) == cudaSuccess &&
               cudaMemset(c->d_counters, 0, kCounters * sizeof(unsigned long long)) == cudaSuccess &&
-              cudaDeviceSynchronize() == cudaSuccess;
+              cudaMalloc(&c->d_mrg_pow, 64 * 18 * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) {
+        uint32_t tab[64 * 18];
+        mrg_power_table(tab);
+        ok = cudaMemcpy(c->d_mrg_pow, tab, sizeof(tab), cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaDeviceSynchronize() == cudaSuccess;
+    }
     if (!ok) {
         smc_destroy(c);
         return SMC_ERR_CUDA;
@@ -121,6 +131,7 @@ extern "C" smc_status smc_destroy(smc_ctx* ctx) {
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_popdone) cudaFree(ctx->d_popdone);
+    if (ctx->d_mrg_pow) cudaFree(ctx->d_mrg_pow);
     delete ctx;
     return SMC_OK;
 }

@@ -23,6 +23,8 @@ struct smc_ctx {
     // per-population completion counters of the population sweep (zeroed)
     uint32_t* d_popdone = nullptr;
     int64_t popdone_cap = 0;
+    // MRG32k3a skip-ahead table: A1^(2^k), A2^(2^k), k < 64 (filled at creation)
+    uint32_t* d_mrg_pow = nullptr;
     int32_t lanes[SMC_OP_COUNT] = {0, 0, 0};
     int32_t threads[SMC_OP_COUNT] = {0, 0, 0};
 };

@@ -105,6 +105,14 @@ def test_mrg32k3a_far_jumps_are_consistent():
     assert not np.array_equal(s76, oracle.mrg32k3a(SEED6, 0, 8))
 
 
+def test_mrg32k3a_float_output_is_the_double_cut_to_24_bits():
+    u64 = oracle.mrg32k3a(SEED6, 0, 50000, np.float64)
+    u32 = oracle.mrg32k3a(SEED6, 0, 50000).astype(np.float64)
+    assert np.all((u32 > 0) & (u32 < 1)) and np.all((u64 > 0) & (u64 < 1))
+    assert np.max(np.abs(u32 - u64)) <= 2.0**-24 + 2.0**-31
+    assert np.array_equal(oracle.mrg32k3a(SEED6, 9000, 100, np.float64), u64[9000:9100])
+
+
 def test_mrg32k3a_uniform_and_uncorrelated():
     u = oracle.mrg32k3a(SEED6, 777, 200000).astype(np.float64)
     assert np.all((u > 0) & (u < 1))
