@@ -215,19 +215,39 @@ static __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned lon
     R = r.lo;
 }
 
-// floor(hi 2^64 / d) for hi < d (restoring long division; once per call)
+// floor(hi 2^64 / d) for hi < d < 2^63 (once per call): an FP64 estimate
+// (53 bits), the exact 128-bit remainder, a second FP64 estimate of the
+// correction from it, then unit steps until 0 <= remainder < d.
 static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned long long d) {
-    unsigned long long rem = hi, quo = 0;
-    for (int i = 0; i < 64; ++i) {
-        const bool top = (rem >> 63) != 0;
-        rem <<= 1;
-        quo <<= 1;
-        if (top || rem >= d) {
-            rem -= d;
-            quo |= 1ull;
+    const double two64 = 18446744073709551616.0;
+    double e = (double)hi / (double)d * two64;  // < 2^64 (hi < d), relative error ~2^-52
+    unsigned long long q = e >= two64 ? ~0ull : (unsigned long long)e;
+    const U128 N{0ull, hi};  // hi 2^64
+    for (int pass = 0; pass < 2; ++pass) {
+        const U128 qd = mul64(q, d);
+        if (lt128(N, qd)) {  // q too large by ceil((qd - N) / d)
+            const U128 r = sub128(qd, N);
+            const double c = ((double)r.hi * two64 + (double)r.lo) / (double)d;
+            q -= (unsigned long long)c + 1ull;
+        } else {
+            const U128 r = sub128(N, qd);
+            if (r.hi == 0 && r.lo < d) return q;
+            const double c = ((double)r.hi * two64 + (double)r.lo) / (double)d;
+            q += c >= 1.0 ? (unsigned long long)c - 1ull : 0ull;
         }
     }
-    return quo;
+    // within a few units now: exact steps
+    U128 qd = mul64(q, d);
+    for (int it = 0; it < 64 && lt128(N, qd); ++it) {
+        --q;
+        qd = sub128(qd, U128{d, 0ull});
+    }
+    U128 r = sub128(N, qd);
+    for (int it = 0; it < 64 && (r.hi != 0 || r.lo >= d); ++it) {
+        ++q;
+        r = sub128(r, U128{d, 0ull});
+    }
+    return q;
 }
 
 // Between the passes, one CTA: the exact total S from the group sums, the

@@ -249,7 +249,9 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
     bool nan_seen = false;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool vec = aligned16(lw) && (!has_inc || aligned16(ll));
+    // chunks of 8 only when every thread gets one (large M); otherwise one
+    // element per thread keeps each thread's dependent chain short
+    const bool vec = aligned16(lw) && (!has_inc || aligned16(ll)) && M >= G * kChunk;
     const int64_t nchunk = vec ? M / kChunk : 0;
     for (int64_t ch = t0; ch < nchunk; ch += G) {
         double x[kChunk];
@@ -423,10 +425,13 @@ __global__ void __launch_bounds__(256) k_ess_reduce(const double* __restrict__ l
 
 namespace smc_host {
 
+// Up to cap * 256 elements: one element per thread (short dependent chains:
+// the reduction is latency-bound there); beyond, chunks of 8 per thread.
 static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
-    int64_t b = (M + 256 * 8 - 1) / (256 * 8);
     int64_t cap = (int64_t)ctx->num_sms * 8;
     if (cap > kMaxPartialBlocks - 2) cap = kMaxPartialBlocks - 2;
+    int64_t b = (M + 255) / 256;
+    if (b > cap) b = (M + 256 * 8 - 1) / (256 * 8);
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
