@@ -14,6 +14,7 @@ M = 2^24), diag (diagonal mixture d = 32, K = 16, N = 65536, M = 4096 on the
 tensor cores; step = one likelihood call), fsv (the paper's factor SV particle
 filter, Table 3 sizes; step = one whole T = 200 run), tables (the paper's
 Tables 1 and 2 configurations, every size; step = one whole run of each),
+mala (the MALA tempered sampler; step = one whole 50-temperature run),
 peaks (the MUFU / FMA / FP64 /
 conversion rates used as roofline denominators).  The default run also
 reports, under "secondary", the tempered SMC sampler (M = 8192), the MALA
@@ -808,6 +809,78 @@ def bench_fsv(args, torch, dist):
     return out
 
 
+def bench_mala(args, torch, dist):
+    """The differentiable sampler: tempered SMC with MALA moves (M = 65536,
+    K = 8, N = 1000, 50 temperatures).  value = whole-run SMC steps/s in the
+    plain per-call form; the roofline is the fused likelihood + gradient
+    move kernel, timed alone per launch after an L2 flush (MUFU ops: K ex2
+    and one reciprocal per particle-datum)."""
+    import paper_0905_2441_gb300 as P
+    from paper_0905_2441_gb300 import samplers
+    import synth
+    w = synth.GMM8_MALA
+    y = w.data()
+    th0 = synth.prior_particles(w.K, w.M, seed=w.particle_seed + dist.rank)
+    betas = synth.geometric_betas(w.T, w.beta_min)
+    ctx = P.Context()
+    model = P.GMM(w.K, w.sigma)
+    smp = samplers.SMCSampler(ctx, model, y, th0, betas, kind=P.MOVE_MALA, scale=w.scale,
+                              seed=w.method_seed + dist.rank)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(max(1, args.warmup // 3)):
+        smp.reset(th0)
+        smp.run()
+    reps = max(1, min(args.steps, 5))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_run = []
+        for _ in range(reps):
+            smp.reset(th0)
+            e = _flush_timed(torch, flush, stream, [smp.run])
+            torch.cuda.synchronize()
+            t_run.append(e[0].elapsed_time(e[1]) / 1e3)
+        # the move kernel alone, from the sampler's final state
+        th, ll = smp.state
+        g = smp.grad[smp.cur]
+        tho, llo, go = torch.empty_like(th), torch.empty_like(ll), torch.empty_like(g)
+        beta = smp.betas[-1:]
+        mv = (lambda: P.mh_move(ctx, model, smp.y, th, ll, tho, llo, beta, w.scale, 99, 1,
+                                kind=P.MOVE_MALA, grad_in=g, grad_out=go))
+        for _ in range(3):
+            mv()
+        t_mv = []
+        for _ in range(20):
+            e = _flush_timed(torch, flush, stream, [mv])
+            torch.cuda.synchronize()
+            t_mv.append(e[0].elapsed_time(e[1]) / 1e3)
+    ctx.check()
+    tr = statistics.median(t_run)
+    t_max = dist.max(torch, tr)
+    value = dist.sum(torch, float(w.T)) / t_max
+    tm = statistics.median(t_mv)
+    ex2_rate, ex2_ms = measure_peak(P, 0)
+    ops = float(w.M) * w.N * (w.K + 1)
+    ctx.close()
+    return {"metric": "SMC steps/s (MALA tempered sampler, plain per-call launches)",
+            "value": value, "unit": "steps/s", "n_gpus": dist.world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / w.T, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 terms, f64 totals",
+            "data": "synthetic (8-component mixture, 1000 simulated data, seed 1)",
+            "config": {"workload": w.name, "M": w.M, "K": w.K, "N": w.N, "T": w.T, "h": w.scale,
+                       "l2": "256 MiB buffer written before every timed run / move, outside "
+                             "its events",
+                       "parallelism": f"independent samplers per rank x{dist.world}"},
+            "move_ms": 1e3 * tm,
+            "roofline": {"bound": "alu", "pipe": "MUFU", "achieved": ops / tm / 1e9,
+                         "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": ops / tm / ex2_rate,
+                         "traffic": None, "kernel": "k_mh_move<8,true,true> (MALA)",
+                         "ops_per_launch": ops,
+                         "issued_count": "K ex2 + 1 reciprocal per particle-datum",
+                         "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
+                                        f"{ex2_ms:.2f} ms microbenchmark"},
+            "gpu_launches": (w.T * 7) * reps + 20, "clocks": clk.summary()}
+
+
 # Tables 1 and 2 (Section 4.1): GTX 280 seconds and single-core CPU minutes
 PAPER_T1_GTX280_S = {8: 1.083, 32: 1.098, 128: 1.100, 512: 1.235, 2048: 1.427, 8192: 2.323,
                      32768: 7.729, 131072: 28.349}
@@ -982,7 +1055,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
-                                                              "diag", "fsv", "tables", "peaks"])
+                                                              "diag", "fsv", "tables", "mala",
+                                                              "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -1012,6 +1086,8 @@ def main():
         out = bench_fsv(args, torch, dist)
     elif args.workload == "tables":
         out = bench_tables(args, torch, dist)
+    elif args.workload == "mala":
+        out = bench_mala(args, torch, dist)
     elif args.workload == "peaks":
         out = {"peaks_ops_per_s": all_peaks(torch)}
     else:

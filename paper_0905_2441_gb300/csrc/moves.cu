@@ -36,8 +36,16 @@ __device__ __forceinline__ void count_accepts(bool a, uint32_t* accept_count, ui
     if (threadIdx.x == 0 && accept_count && *s_cnt) atomicAdd(accept_count, *s_cnt);
 }
 
+// Minimum resident 256-thread blocks per SM asked of the register
+// allocator for the move kernel with K <= 8 (the state of the move is
+// stashed in shared memory across the likelihood loop, so two blocks fit
+// without spilling).
+#ifndef SMC_MOVE_MINB
+#define SMC_MOVE_MINB 2
+#endif
+
 template <int K, bool MALA, bool EQW>
-__global__ void __launch_bounds__(256) k_mh_move(
+__global__ void __launch_bounds__(256, (K <= 8 ? SMC_MOVE_MINB : 1)) k_mh_move(
     const float* __restrict__ y, int64_t N, const float* theta_in, const double* ll_in,
     const float* grad_in, const int32_t* __restrict__ anc, const int32_t* __restrict__ do_flag,
     float* theta_out, double* ll_out, float* grad_out, int64_t M, const float* __restrict__ beta,
@@ -47,11 +55,17 @@ __global__ void __launch_bounds__(256) k_mh_move(
     grid_dep_launch();
     extern __shared__ __align__(16) float ys[];
     __shared__ uint32_t s_cnt;
+    // K <= 8: the particle's current state, gradient and proposal wait out
+    // the likelihood loop here (written and read back by the particle's
+    // lane 0 only), not in registers
+    constexpr bool STASH = K <= 8;
+    __shared__ float s_st[STASH ? 3 * K * 256 : 1];
     if (threadIdx.x == 0) s_cnt = 0;
     init_mbar(ychunk_mbar(ys, ychunk));
     const int lane = threadIdx.x % L;
     const int ppb = blockDim.x / L;
-    const int64_t p = (int64_t)blockIdx.x * ppb + threadIdx.x / L;
+    const int pi = threadIdx.x / L;
+    const int64_t p = (int64_t)blockIdx.x * ppb + pi;
     const bool active = p < M;
 
     int64_t src = p;
@@ -89,6 +103,16 @@ __global__ void __launch_bounds__(256) k_mh_move(
         nu[k] = -prop[k] * P.r;
         lw2[k] = P.lw2[k];
     }
+    if constexpr (STASH) {
+        if (lane == 0) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                s_st[k * 256 + pi] = mu[k];
+                if (MALA) s_st[(K + k) * 256 + pi] = g[k];
+                s_st[(2 * K + k) * 256 + pi] = prop[k];
+            }
+        }
+    }
     uint32_t phase = 0;
     float gp[K];
     double lp;
@@ -102,6 +126,15 @@ __global__ void __launch_bounds__(256) k_mh_move(
         lp = acc.finish(L, P, gp);
     }
 
+    if constexpr (STASH) {  // back from shared memory (lane 0 is the only reader)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            mu[k] = lane == 0 ? s_st[k * 256 + pi] : 0.0f;
+            g[k] = (MALA && lane == 0) ? s_st[(K + k) * 256 + pi] : 0.0f;
+            prop[k] = lane == 0 ? s_st[(2 * K + k) * 256 + pi] : 0.0f;
+            mf[k] = MALA ? fmaf(hh2 * b, g[k], mu[k]) : mu[k];
+        }
+    }
     bool acc_ok = false;
     if (in_box && lane == 0) {
         float log_alpha = tempered_diff(b, lp, l);
