@@ -649,7 +649,8 @@ def bench_resample(args, torch, dist):
            "per_call_ms": {"reweight": 1e3 * per[:, 0].mean(), "resample": 1e3 * per[:, 1].mean()},
            "other_schemes": variants,
            "roofline": {"bound": "hbm", "achieved": ach_rs, "peak": hbm, "unit": "GB/s",
-                        "frac": ach_rs / hbm, "traffic": None, "kernel": "resample (2 kernels)",
+                        "frac": ach_rs / hbm, "traffic": profile_traffic("resample_systematic"),
+                        "kernel": "resample (2 kernels)",
                         "bytes_per_particle": b_rs,
                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"},
            "gpu_launches": 6 * K, "clocks": clk.summary()}
@@ -874,7 +875,8 @@ def bench_mala(args, torch, dist):
             "move_ms": 1e3 * tm,
             "roofline": {"bound": "alu", "pipe": "MUFU", "achieved": ops / tm / 1e9,
                          "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": ops / tm / ex2_rate,
-                         "traffic": None, "kernel": "k_mh_move<8,true,true> (MALA)",
+                         "traffic": profile_traffic("k_mh_move_mala"),
+                         "kernel": "k_mh_move<8,true,true> (MALA)",
                          "ops_per_launch": ops,
                          "issued_count": "K ex2 + 1 reciprocal per particle-datum",
                          "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
