@@ -1,7 +1,7 @@
 """GPU parity: every C-ABI call against the FP64 oracle on identical seeded
 inputs and identical Philox draws.
 
-Tolerances (derived in the design doc from the arithmetic):
+Tolerances, derived from the arithmetic of each kernel:
   * 1-D / diagonal FP32 log-likelihoods: relative 1e-5 per particle.
   * gradient: |g - g_oracle| <= 1e-4 * sum_n |r_nk (y_n - mu_k)| / sigma^2
     (the scale of the summed terms; cancellation makes plain relative error
