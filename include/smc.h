@@ -175,6 +175,23 @@ smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int64_t M, uin
                                    uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
                                    const int32_t* do_flag, double* logw_reset, void* stream);
 
+/* smc_reweight followed by smc_resample_systematic on its weights, in one
+ * call with one pass fewer: the normalisation pass also forms the exact
+ * integer tile sums of the quantised weights, so resampling starts from
+ * them instead of reading W back.  Same arguments and the same results,
+ * bit for bit, as the two calls
+ *   smc_reweight(ctx, loglik, dbeta, logw, M, W_out, scalars_out,
+ *                resample_flag_out, ess_frac, stream);
+ *   smc_resample_systematic(ctx, W_out, M, seed, step, ancestors_out,
+ *                           counts_out, resample_flag_out, logw, stream);
+ * (resample_flag_out NULL: resample unconditionally; logw is reset to 0
+ * when resampling happened).  W_out and ancestors_out are required. */
+smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
+                                 int64_t M, double* W_out, double* scalars_out,
+                                 int32_t* resample_flag_out, double ess_frac, uint64_t seed,
+                                 uint64_t step, int32_t* ancestors_out, int32_t* counts_out,
+                                 void* stream);
+
 /* Multinomial resampling (Section 3.2's resampling step as M independent
  * draws from the empirical CDF), on the exact-integer CDF of
  * smc_resample_systematic (q_j, C_j, S as there):

@@ -23,7 +23,8 @@ EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_sta
            "smc_resample_systematic", "smc_gather", "smc_mh_move", "smc_popmcmc_sweep",
            "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
            "smc_resample_systematic_noalloc", "smc_resample_multinomial",
-           "smc_resample_residual", "smc_is_moments", "smc_rng_mrg32k3a")
+           "smc_resample_residual", "smc_is_moments", "smc_rng_mrg32k3a",
+           "smc_reweight_resample")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -66,6 +67,8 @@ def _declare(L):
     L.smc_resample_multinomial.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
     L.smc_resample_residual.argtypes = [_vp, _vp, _i64, _u64, _u64, _vp, _vp, _vp, _vp]
     L.smc_gather.argtypes = [_vp, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _vp]
+    L.smc_reweight_resample.argtypes = [_vp, _vp, C.c_double, _vp, _i64, _vp, _vp, _vp, C.c_double,
+                                        _u64, _u64, _vp, _vp, _vp]
     L.smc_rng_mrg32k3a.argtypes = [_vp, C.POINTER(C.c_uint32 * 6), _u64, _i64, _i64, _vp, _vp,
                                    _vp]
     L.smc_is_moments.argtypes = [_vp, C.POINTER(SmcIsProblem), _vp, _i64, _u64, _u64, _vp, _vp]

@@ -229,6 +229,27 @@ def reweight(ctx: Context, loglik, dbeta: float, logw, W_out=None, scalars=None,
          "smc_reweight")
 
 
+def reweight_resample(ctx: Context, loglik, dbeta: float, logw, W_out, seed: int, step: int,
+                      scalars=None, flag=None, ess_frac: float = 0.5, anc=None, counts=None,
+                      stream=None):
+    """reweight followed by systematic resampling of its weights (logw reset
+    where resampled), one pass fewer; flag None resamples unconditionally."""
+    M = logw.numel()
+    anc = torch.empty(M, dtype=torch.int32, device=logw.device) if anc is None else anc
+    _need(loglik, torch.float64, "loglik", (M,))
+    _need(logw, torch.float64, "logw", (M,))
+    _need(W_out, torch.float64, "W_out", (M,))
+    _need(scalars, torch.float64, "scalars", (4,))
+    _need(flag, torch.int32, "flag", (1,))
+    _need(anc, torch.int32, "ancestors", (M,))
+    _need(counts, torch.int32, "counts", (M,))
+    _chk(L.load().smc_reweight_resample(ctx.handle, _ptr(loglik), float(dbeta), _ptr(logw), M,
+                                        _ptr(W_out), _ptr(scalars), _ptr(flag), float(ess_frac),
+                                        int(seed), int(step), _ptr(anc), _ptr(counts),
+                                        _stream(stream)), "smc_reweight_resample")
+    return anc
+
+
 def ess(ctx: Context, logw, out=None, stream=None):
     M = logw.numel()
     out = torch.empty(1, dtype=torch.float64, device=logw.device) if out is None else out

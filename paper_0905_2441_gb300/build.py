@@ -27,9 +27,10 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxe
 def source_digest(names=None) -> str:
     """Digest of CUDA sources and headers (identifies a kernel version).
 
-    With `names` (file names under csrc/, e.g. the translation unit of one
-    kernel and the headers it includes) only those files and the public
-    headers are hashed, so a change elsewhere in the library keeps it.
+    With `names` (file names under csrc/: the files that define one kernel
+    and the headers its device code uses) only those files are hashed, so a
+    change elsewhere in the library, public declarations included, keeps it;
+    without, every source and public header.
     """
     import hashlib
     h = hashlib.sha256()
@@ -38,9 +39,9 @@ def source_digest(names=None) -> str:
         missing = [f for f in own if not os.path.exists(f)]
         if missing:
             raise FileNotFoundError(missing)
+        files = sorted(own)
     else:
-        own = glob.glob(os.path.join(CSRC, "*"))
-    files = sorted(own + glob.glob(os.path.join(INCLUDE, "*.h")))
+        files = sorted(glob.glob(os.path.join(CSRC, "*")) + glob.glob(os.path.join(INCLUDE, "*.h")))
     for f in files:
         with open(f, "rb") as fh:
             h.update(os.path.basename(f).encode())

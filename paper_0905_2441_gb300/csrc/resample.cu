@@ -48,16 +48,22 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ anc,
 
 namespace smc_host {
 
+// tiles_ready: the tile sums of pass 1 are already in sc (formed by the
+// normalisation pass of smc_reweight_resample), so pass 1 is skipped
 smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t seed, uint64_t step,
                            int32_t* anc, int32_t* counts, const int32_t* do_flag, double* lwreset,
-                           const smc::RsScratch& sc, uint32_t* status, cudaStream_t s) {
+                           const smc::RsScratch& sc, uint32_t* status, cudaStream_t s,
+                           bool tiles_ready) {
     const int64_t tiles = smc::rs_tiles(M);
     if (tiles > 0x7FFFFFFF) return SMC_ERR_ARG;
     int64_t b1 = tiles;
     if (b1 > (int64_t)num_sms * 4) b1 = (int64_t)num_sms * 4;
-    smc_status st = launch_pdl(smc::k_resample_total, dim3((unsigned)b1), dim3(smc::kRsThreads), 0,
-                               s, W, M, do_flag, sc, status);
-    if (st != SMC_OK) return st;
+    smc_status st = SMC_OK;
+    if (!tiles_ready) {
+        st = launch_pdl(smc::k_resample_total, dim3((unsigned)b1), dim3(smc::kRsThreads), 0, s, W,
+                        M, do_flag, sc, status);
+        if (st != SMC_OK) return st;
+    }
     st = launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), 0, s, M, seed,
                     step, do_flag, sc, status);
     if (st != SMC_OK) return st;
@@ -119,7 +125,7 @@ extern "C" smc_status smc_resample_systematic(smc_ctx* ctx, const double* W, int
     const smc::RsScratch sc =
         resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
     return resample_launch(ctx->num_sms, W, M, seed, step, ancestors_out, counts_out, do_flag,
-                           logw_reset, sc, ctx->d_status, s);
+                           logw_reset, sc, ctx->d_status, s, false);
 }
 
 extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, int32_t rows_f32,
@@ -201,5 +207,5 @@ extern "C" smc_status smc_resample_systematic_noalloc(const double* W, int64_t M
     // no heavy-chunk scratch: a tile with many slots is expanded by its CTA
     const smc::RsScratch sc = resample_scratch(scratch, M, false);
     return resample_launch(sms, W, M, seed, step, ancestors_out, counts_out, do_flag, logw_reset,
-                           sc, status_out, s);
+                           sc, status_out, s, false);
 }

@@ -15,6 +15,7 @@
 
 #include "ctx.hpp"
 #include "device.cuh"
+#include "resample.cuh"
 
 using namespace smc_host;
 
@@ -421,9 +422,64 @@ __global__ void __launch_bounds__(256) k_ess_reduce(const double* __restrict__ l
     }
 }
 
+// Normalisation fused with pass 1 of systematic resampling: every tile of
+// 2048 weights is written as k_reweight_normalize writes it, and the exact
+// integer sum of q = floor(W 2^52) of those same values is stored for the
+// tile (what k_resample_total would form by reading W back).  Invalid
+// weights (the reduction found none positive) leave zero tile sums, so the
+// resampling that follows reports SMC_ERR_ZERO_WEIGHT and writes nothing.
+__global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __restrict__ lw,
+                                                                int64_t M,
+                                                                const double* __restrict__ fin,
+                                                                double* __restrict__ W,
+                                                                RsScratch sc) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
+    __shared__ unsigned long long sh[kRsThreads / 32];
+    const bool valid = fin[3] != 0.0;
+    float mh = 0.0f, ml = 0.0f, inv = 0.0f;
+    if (valid) {
+        split_double(fin[0], mh, ml);
+        inv = reinterpret_cast<const float*>(fin + 5)[0];
+    }
+    const int64_t ntiles = rs_tiles(M);
+    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        unsigned long long acc = 0;
+        if (valid) {
+            double x[kRsIpt], w[kRsIpt];
+            load_tile_raw(lw, M, t, x);
+            const int64_t g0 = t * kRsTile + (int64_t)threadIdx.x * kRsIpt;
+#pragma unroll
+            for (int j = 0; j < kRsIpt; ++j) {
+                float xh, xl;
+                split_double(x[j], xh, xl);
+                w[j] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
+                unsigned long long q;
+                quantise(w[j], q);  // w in [0, 1]
+                acc += g0 + j < M ? q : 0ull;
+            }
+            if (g0 + kRsIpt <= M && aligned16(W + g0)) {
+                store8(W + g0, w);
+            } else {
+#pragma unroll
+                for (int j = 0; j < kRsIpt; ++j)
+                    if (g0 + j < M) W[g0 + j] = w[j];
+            }
+        }
+        const unsigned long long ts = block_sum_u64(acc, sh);
+        if (threadIdx.x == 0) sc.tile_sum[t] = ts;
+    }
+}
+
 }  // namespace smc
 
 namespace smc_host {
+
+smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy);
+smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t seed, uint64_t step,
+                           int32_t* anc, int32_t* counts, const int32_t* do_flag, double* lwreset,
+                           const smc::RsScratch& sc, uint32_t* status, cudaStream_t s,
+                           bool tiles_ready);
 
 // Up to cap * 256 elements: one element per thread (short dependent chains:
 // the reduction is latency-bound there); beyond, chunks of 8 per thread.
@@ -463,6 +519,41 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
         if (st != SMC_OK) return st;
     }
     return SMC_OK;
+}
+
+size_t smc_resample_ws_bytes(int64_t M);
+
+extern "C" smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, double dbeta,
+                                            double* logw, int64_t M, double* W_out,
+                                            double* scalars_out, int32_t* resample_flag_out,
+                                            double ess_frac, uint64_t seed, uint64_t step,
+                                            int32_t* ancestors_out, int32_t* counts_out,
+                                            void* stream) {
+    if (!ctx || M <= 0 || M > 0x7FFFFFFF || !logw || !W_out || !ancestors_out ||
+        std::isnan(dbeta) || std::isnan(ess_frac))
+        return SMC_ERR_ARG;
+    smc_status st = use_device(ctx);
+    if (st != SMC_OK) return st;
+    cudaStream_t s = as_stream(stream);
+    st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
+    if (st != SMC_OK) return st;
+    const smc::RsScratch sc =
+        resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
+    const int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
+    const int blocks = reduce_blocks(ctx, M);
+    const int final_slot = kMaxPartialBlocks - 1;
+    st = launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw, M,
+                    has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET, scalars_out,
+                    resample_flag_out, ess_frac, final_slot, ctx->d_status);
+    if (st != SMC_OK) return st;
+    int64_t nb = smc::rs_tiles(M);
+    if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
+    st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
+                    (const double*)logw, M,
+                    (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out, sc);
+    if (st != SMC_OK) return st;
+    return resample_launch(ctx->num_sms, W_out, M, seed, step, ancestors_out, counts_out,
+                           resample_flag_out, logw, sc, ctx->d_status, s, true);
 }
 
 extern "C" smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, double* ess_out,

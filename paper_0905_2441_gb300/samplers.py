@@ -91,9 +91,13 @@ class SMCSampler(_Graphable):
         ctx = self.ctx
         db = float(self.betas_host[t] - self.betas_host[t - 1])
         flag, hist, beta, accepts = self._views[t]
-        api.reweight(ctx, self.ll[c], db, self.lw, self.W, hist, flag, self.ess_frac)
-        api.resample(ctx, self.resampler, self.W, self.seed, t, anc=self.anc, do_flag=flag,
-                     logw_reset=self.lw)
+        if self.resampler == "systematic":  # one call, one pass fewer
+            api.reweight_resample(ctx, self.ll[c], db, self.lw, self.W, self.seed, t,
+                                  scalars=hist, flag=flag, ess_frac=self.ess_frac, anc=self.anc)
+        else:
+            api.reweight(ctx, self.ll[c], db, self.lw, self.W, hist, flag, self.ess_frac)
+            api.resample(ctx, self.resampler, self.W, self.seed, t, anc=self.anc, do_flag=flag,
+                         logw_reset=self.lw)
         for r in range(self.n_moves):
             first = r == 0
             api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n],
@@ -202,9 +206,13 @@ class ParticleFilter(_Graphable):
         y_t, hist = self._views[t]
         api.pf_step(self.ctx, self.model, y_t, self.x[c], self.x[n], self.logg,
                     self.seed, t, anc=self.anc)
-        api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
-        api.resample(self.ctx, self.resampler, self.W, self.seed, t, anc=self.anc,
-                     logw_reset=self.lw)
+        if self.resampler == "systematic":  # one call, one pass fewer
+            api.reweight_resample(self.ctx, self.logg, 1.0, self.lw, self.W, self.seed, t,
+                                  scalars=hist, anc=self.anc)
+        else:
+            api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
+            api.resample(self.ctx, self.resampler, self.W, self.seed, t, anc=self.anc,
+                         logw_reset=self.lw)
         self.cur = n
 
     def run(self, graph: bool = False, steps: int | None = None):

@@ -489,3 +489,33 @@ def test_pf_step_parity(smc, kind, M):
     rx, rlg = oracle.pf_step(kind, phi, L, beta, yt, x_in, anc, 21, 8)
     np.testing.assert_allclose(np_(xo), rx, rtol=2e-6, atol=2e-6)
     np.testing.assert_allclose(np_(lg), rlg, rtol=1e-5, atol=2e-5)
+
+
+@pytest.mark.parametrize("M", [1, 3, 2047, 2049, 100003, 1 << 20])
+@pytest.mark.parametrize("with_flag", [False, True])
+def test_reweight_resample_equals_the_two_calls(smc, M, with_flag):
+    """smc_reweight_resample gives, bit for bit, the log-weights, weights,
+    scalars, flag, ancestors and counts of smc_reweight followed by
+    smc_resample_systematic."""
+    P, ctx = smc
+    g = np.random.default_rng(M + with_flag)
+    ll = cu(g.normal(-50, 3, M))
+    lw0 = g.normal(0, 1.5, M)
+    out = []
+    for fused in (False, True):
+        lw = cu(lw0)
+        W = torch.empty(M, dtype=torch.float64, device="cuda")
+        sc = torch.empty(4, dtype=torch.float64, device="cuda")
+        flag = torch.zeros(1, dtype=torch.int32, device="cuda") if with_flag else None
+        anc = torch.empty(M, dtype=torch.int32, device="cuda")
+        cnt = torch.empty(M, dtype=torch.int32, device="cuda")
+        if fused:
+            P.reweight_resample(ctx, ll, 0.3, lw, W, 5, 9, scalars=sc, flag=flag, ess_frac=0.9,
+                                anc=anc, counts=cnt)
+        else:
+            P.reweight(ctx, ll, 0.3, lw, W, sc, flag, 0.9)
+            P.resample_systematic(ctx, W, 5, 9, anc=anc, counts=cnt, do_flag=flag, logw_reset=lw)
+        ctx.check()
+        out.append([np_(t) for t in (lw, W, sc, anc, cnt)] + ([np_(flag)] if with_flag else []))
+    for a, b in zip(*out):
+        assert np.array_equal(a, b)
