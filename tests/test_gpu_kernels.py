@@ -165,16 +165,24 @@ def test_gradient_parity(smc, K, N, M):
     np.testing.assert_allclose(np_(out), oracle.gmm1d_loglik(y, logw, SIG, theta), rtol=1e-5)
 
 
-def test_diag_fp32_parity(smc):
+@pytest.mark.parametrize("d,K,N,M", [(32, 16, 700, 10), (1, 1, 5, 3), (3, 2, 100, 17),
+                                     (7, 5, 1000, 33), (64, 64, 50, 5), (16, 3, 1, 7),
+                                     (5, 4, 0, 3)])
+def test_diag_fp32_parity(smc, d, K, N, M):
+    """FP32 CUDA-core path of the diagonal mixture over the accepted shapes
+    (d, K in 1..64), a single datum and no data (the empty sum)."""
     P, ctx = smc
-    w = synth.DIAG32
-    truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
-    Y = synth.diag_data(700, truth, seed=w.data_seed)
-    th = synth.diag_particles(10, truth, seed=w.particle_seed)
-    model = P.DiagGMM(w.K, w.sigma, d=w.d)
+    truth = synth.diag_truth(K, d, seed=d + K)
+    Y = synth.diag_data(max(N, 1), truth, seed=N + 1)[:N]
+    th = synth.diag_particles(M, truth, seed=M)
+    logw = np.log(np.random.default_rng(K).dirichlet(np.ones(K)))
+    model = P.DiagGMM(K, 0.8, d=d, log_w=logw)
     out = np_(P.loglik_batch(ctx, model, cu(Y), cu(th)))
     ctx.check()
-    np.testing.assert_allclose(out, oracle.gmmdiag_loglik(Y, w.logw(), w.sigma, th), rtol=1e-5)
+    if N == 0:
+        assert np.all(out == 0.0)
+    else:
+        np.testing.assert_allclose(out, oracle.gmmdiag_loglik(Y, logw, 0.8, th), rtol=1e-5)
 
 
 # ------------------------------------------------------------------ weights
@@ -494,6 +502,26 @@ def test_pf_step_parity(smc, kind, M):
     P.pf_step(ctx, model, cu(yt), cu(x_in), xo, lg, 21, 8, anc=cu(anc))
     ctx.check()
     rx, rlg = oracle.pf_step(kind, phi, L, beta, yt, x_in, anc, 21, 8)
+    np.testing.assert_allclose(np_(xo), rx, rtol=2e-6, atol=2e-6)
+    np.testing.assert_allclose(np_(lg), rlg, rtol=1e-5, atol=2e-5)
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("d", [1, 2, 5, 8])
+def test_pf_step_state_dimensions(smc, kind, d):
+    """pf_step over the accepted state dimensions (1..8), identity ancestors."""
+    P, ctx = smc
+    phi, Sigma, beta = synth.msv_params(d)
+    L = synth.chol(Sigma)
+    M = 3001
+    g = np.random.default_rng(d)
+    x_in = g.normal(0, 1, (d, M)).astype(np.float32)
+    yt = g.normal(0, 1, d).astype(np.float32)
+    xo = torch.empty(d, M, device="cuda")
+    lg = torch.empty(M, dtype=torch.float64, device="cuda")
+    P.pf_step(ctx, P.PFModel(kind, phi, L, beta), cu(yt), cu(x_in), xo, lg, 4, 2)
+    ctx.check()
+    rx, rlg = oracle.pf_step(kind, phi, L, beta, yt, x_in, None, 4, 2)
     np.testing.assert_allclose(np_(xo), rx, rtol=2e-6, atol=2e-6)
     np.testing.assert_allclose(np_(lg), rlg, rtol=1e-5, atol=2e-5)
 
