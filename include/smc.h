@@ -291,7 +291,7 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
  *   (parity bit 1, the wrap pair only when M_q is even); the bit is
  *   word 0 bit 0 of (seed, EXCHANGE, sweep, index q); pair j swaps iff
  *   log u_j < (beta_a - beta_b)(l_b - l_a), u_j from word 4 + j.
- * The CTAs take equal chunks of chains from a work queue; a population's
+ * The CTAs take equal chunks of chains (dealt round-robin); a population's
  * exchange runs as soon as its last chain has moved, so populations of any
  * size mix freely.  When the average population holds more than two chains
  * per thread of a CTA (M_total > 2 * n_pops * threads, e.g. the single

@@ -1,6 +1,6 @@
 // moves.cu -- smc_mh_move (random-walk MH and MALA with the gather after
 // resampling fused in) and smc_popmcmc_sweep (many independent populations
-// of tempered chains in one persistent launch with a work queue).
+// of tempered chains in one persistent launch, chains dealt in equal items).
 // Sections 3.1, 4.1.1, 4.1.2 of Lee, Yau, Giles, Doucet & Holmes (2009).
 #include <cmath>
 
@@ -170,12 +170,12 @@ __global__ void __launch_bounds__(256, (K <= 8 ? SMC_MOVE_MINB : 1)) k_mh_move(
 // ------------------------------------------------------------------ population MCMC
 // Work items are chunks of (blockDim / L) consecutive chains of the flat
 // chain array, dealt round-robin to the CTAs, so every item costs the same
-// whatever the population sizes.  After an item's moves, one thread adds
-// the item's chain count to each population it touches (fence + one
-// integer atomic per population); the CTA that completes a population runs
-// that population's exchange moves at once (one warp, reads through L2), so
-// no CTA ever waits on another.  The counters are left at zero for the next
-// sweep.
+// whatever the population sizes.  After an item's moves, one lane adds the
+// item's chain count to each population it touches (one acquire-release
+// atomic per population); the CTA that completes a population runs that
+// population's exchange moves at once, its pairs dealt over all the CTA's
+// threads, so no CTA ever waits on another.  The counters are left at zero
+// for the next sweep.
 __device__ __forceinline__ int pop_of(const int32_t* __restrict__ offsets, int n_pops, int64_t c) {
     int lo = 0, hi = n_pops;  // largest q with offsets[q] <= c
     while (hi - lo > 1) {

@@ -4,13 +4,14 @@
 //
 // Pass 1 (k_resample_total): every tile of kRsTile weights is quantised
 // (q = floor(W 2^52) from the FP64 bits) and reduced exactly; the tile's
-// integer sum is stored, and added atomically to its group of 64 tiles and
-// to the grand total S (integer addition: order-free and exact).
-// Pass 2 (k_resample_scan): one CTA per tile obtains its exclusive prefix
-// from the group sums before it and the tile sums before it in its group
-// (one parallel read, no waiting on other CTAs), scans the tile in shared
-// memory, evaluates F at every prefix and expands the tile's contiguous
-// output range.
+// integer sum is stored.
+// Between the passes (k_resample_finalize, one CTA): the tile sums become
+// exclusive prefixes and the call's constants (S, the uniform, fixed-point
+// reciprocals) are formed once.
+// Pass 2 (k_resample_scan, persistent over tiles): each tile reads its
+// prefix (no waiting on other CTAs), is scanned in shared memory, F is
+// evaluated at every prefix and the tile's contiguous output range is
+// expanded; ranges too long for one CTA go to k_resample_heavy.
 #pragma once
 #include "device.cuh"
 
@@ -250,7 +251,7 @@ static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned
     return q;
 }
 
-// Between the passes, one CTA: the exact total S from the group sums, the
+// Between the passes, one CTA: the exact total S from the tile sums, the
 // call's uniform and constants, and every tile's exclusive prefix (the tile
 // sums are replaced in place), so that no tile of pass 2 repeats this work.
 constexpr int kRsFinThreads = 1024;
