@@ -1,7 +1,8 @@
 // pf.cu -- pf_step: one bootstrap particle-filter step (Section 3.2) for
-// the multivariate stochastic-volatility state of Section 4.2 and a
-// linear-Gaussian variant: gather by ancestor, propagate, weight, fused in
-// one pass (one thread per particle; SoA states, coalesced except for the
+// the multivariate stochastic-volatility state of Section 4.2, a
+// linear-Gaussian variant and the factor stochastic-volatility model of
+// Section 4.2 (Table 3): gather by ancestor, propagate, weight, fused in one
+// pass (one thread per particle; SoA states, coalesced except for the
 // ancestor gather, which reads mostly increasing addresses).
 #include <cmath>
 

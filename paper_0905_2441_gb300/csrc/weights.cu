@@ -7,7 +7,9 @@
 // (sum e, sum e^2) of the new log-weights and (sum e) of the old ones
 // against slack references, plus the exact maximum (integer keys); the last
 // block to finish combines the per-block partials in FP64 and writes the
-// scalars.  A second pass writes W = e / S1.  Per element the only FP64
+// scalars.  A second pass writes W = e / S1 (smc_reweight_resample: the
+// same pass also forms the exact tile sums of pass 1 of systematic
+// resampling from the W it writes).  Per element the only FP64
 // instruction is the log-weight update (GB300 issues FP64 at ~1/64 of
 // FP32); differences and exponentials run in FP32 on hi/lo splits.
 #include <climits>
