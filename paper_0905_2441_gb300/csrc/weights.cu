@@ -231,6 +231,119 @@ __device__ __forceinline__ double ln_sum(double s) {
     return (double)(lg2((float)s) * 0.69314718055994531f);
 }
 
+// Both block combinations of the reweight reduction in one pass (the new
+// log-weights' sums with their maximum, and the old ones' sums): the same
+// references, scalings and summation orders as two calls of block_combine,
+// with two barriers instead of eight.  Results valid in thread 0.
+__device__ __forceinline__ void block_combine2(const RefSums& c, const RefSums& o, bool has_old,
+                                               long long* s_key, float* s_f, Lse* outc,
+                                               Lse* outo, double* max_out) {
+    const long long kc = warp_max_key(c.any ? dkey(c.r) : LLONG_MIN);
+    const long long km = warp_max_key(c.kmax);
+    const long long ko = has_old ? warp_max_key(o.any ? dkey(o.r) : LLONG_MIN) : LLONG_MIN;
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_key[w] = kc; s_key[16 + w] = km; s_key[32 + w] = ko; }
+    __syncthreads();
+    long long bc = LLONG_MIN, bm = LLONG_MIN, bo = LLONG_MIN;
+    for (int i = 0; i < nw; ++i) {
+        bc = s_key[i] > bc ? s_key[i] : bc;
+        bm = s_key[16 + i] > bm ? s_key[16 + i] : bm;
+        bo = s_key[32 + i] > bo ? s_key[32 + i] : bo;
+    }
+    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
+    float a = 0.0f, b = 0.0f, ao = 0.0f;
+    if (bc != LLONG_MIN && c.any) {
+        const float f = expd(c.r - key_to_double(bc));  // <= 1
+        a = c.s1 * f;
+        b = c.s2 * f * f;
+    }
+    if (has_old && bo != LLONG_MIN && o.any) ao = o.s1 * expd(o.r - key_to_double(bo));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
+        b += __shfl_xor_sync(0xFFFFFFFFu, b, off);
+        ao += __shfl_xor_sync(0xFFFFFFFFu, ao, off);
+    }
+    if ((threadIdx.x & 31) == 0) { s_f[w] = a; s_f[32 + w] = b; s_f[64 + w] = ao; }
+    __syncthreads();
+    *outc = Lse{kNegInf, 0.0, 0.0};
+    *outo = Lse{kNegInf, 0.0, 0.0};
+    if (threadIdx.x == 0) {
+        float A = 0.0f, B = 0.0f, AO = 0.0f;
+        for (int i = 0; i < nw; ++i) { A += s_f[i]; B += s_f[32 + i]; AO += s_f[64 + i]; }
+        if (bc != LLONG_MIN) *outc = Lse{key_to_double(bc), f2d_bits(A), f2d_bits(B)};
+        if (bo != LLONG_MIN) *outo = Lse{key_to_double(bo), f2d_bits(AO), 0.0};
+    }
+}
+
+// The last block's three passes over the partials (new sums, old sums,
+// maximum) in one: the same references and summation orders as
+// combine_partials(0), combine_partials(3) and max_partials, with two
+// barriers instead of ten.  Results valid in thread 0.
+__device__ __forceinline__ void combine_partials3(const double* partials, int nblocks,
+                                                  bool has_old, long long* s_key, double* s_d,
+                                                  Lse* outc, Lse* outo, double* max_out) {
+    long long kc = LLONG_MIN, ko = LLONG_MIN, km = LLONG_MIN;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double* P = partials + (size_t)b * 8;
+        const double rc = __ldcg(P), ro = __ldcg(P + 3), mx = __ldcg(P + 5);
+        if (!is_neg_inf(rc)) { const long long k = dkey(rc); kc = k > kc ? k : kc; }
+        if (has_old && !is_neg_inf(ro)) { const long long k = dkey(ro); ko = k > ko ? k : ko; }
+        if (!is_neg_inf(mx)) { const long long k = dkey(mx); km = k > km ? k : km; }
+    }
+    kc = warp_max_key(kc);
+    ko = warp_max_key(ko);
+    km = warp_max_key(km);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { s_key[w] = kc; s_key[16 + w] = ko; s_key[32 + w] = km; }
+    __syncthreads();
+    long long bc = LLONG_MIN, bo = LLONG_MIN, bm = LLONG_MIN;
+    for (int i = 0; i < nw; ++i) {
+        bc = s_key[i] > bc ? s_key[i] : bc;
+        bo = s_key[16 + i] > bo ? s_key[16 + i] : bo;
+        bm = s_key[32 + i] > bm ? s_key[32 + i] : bm;
+    }
+    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
+    float Rch = 0.0f, Rcl = 0.0f, Roh = 0.0f, Rol = 0.0f;
+    if (bc != LLONG_MIN) split_double(key_to_double(bc), Rch, Rcl);
+    if (bo != LLONG_MIN) split_double(key_to_double(bo), Roh, Rol);
+    double a = 0.0, bs = 0.0, ao = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const double* P = partials + (size_t)b * 8;
+        const double rc = __ldcg(P);
+        if (bc != LLONG_MIN && !is_neg_inf(rc)) {
+            float h, l;
+            split_double(rc, h, l);
+            const float f = exp_hilo(h - Rch, l - Rcl);  // <= 1
+            a = fma(__ldcg(P + 1), f2d_bits(f), a);
+            bs = fma(__ldcg(P + 2), f2d_bits(f * f), bs);
+        }
+        const double ro = __ldcg(P + 3);
+        if (has_old && bo != LLONG_MIN && !is_neg_inf(ro)) {
+            float h, l;
+            split_double(ro, h, l);
+            const float f = exp_hilo(h - Roh, l - Rol);
+            ao = fma(__ldcg(P + 4), f2d_bits(f), ao);
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
+        bs += __shfl_xor_sync(0xFFFFFFFFu, bs, off);
+        ao += __shfl_xor_sync(0xFFFFFFFFu, ao, off);
+    }
+    if ((threadIdx.x & 31) == 0) { s_d[w] = a; s_d[32 + w] = bs; s_d[64 + w] = ao; }
+    __syncthreads();
+    *outc = Lse{kNegInf, 0.0, 0.0};
+    *outo = Lse{kNegInf, 0.0, 0.0};
+    if (threadIdx.x == 0) {
+        double A = 0.0, B = 0.0, AO = 0.0;
+        for (int i = 0; i < nw; ++i) { A += s_d[i]; B += s_d[32 + i]; AO += s_d[64 + i]; }
+        if (bc != LLONG_MIN) *outc = Lse{key_to_double(bc), A, B};
+        if (bo != LLONG_MIN) *outo = Lse{key_to_double(bo), AO, 0.0};
+    }
+}
+
 // partial slot layout (doubles): [b*8 + 0..5] = {ref, s1, s2, ref_old, s_old, max}
 // final slot: {max, S1, S2, valid, lse, (float) 1/S1 in the low word of [5]},
 // S1 and S2 relative to the true maximum
@@ -246,7 +359,8 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     __shared__ long long s_key[48];
-    __shared__ float s_a[32], s_b[32];
+    __shared__ float s_f[96];
+    __shared__ double s_d[96];
     __shared__ bool last;
     RefSums cur, old;
     bool nan_seen = false;
@@ -291,9 +405,9 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
         }
     }
     if (nan_seen) raise_status(status, ST_NONFINITE);
-    double bmax, bmax_old;
-    const Lse c = block_combine(cur, s_key, s_a, s_b, &bmax);
-    const Lse o = has_inc ? block_combine(old, s_key, s_a, s_b, &bmax_old) : Lse{kNegInf, 0.0, 0.0};
+    double bmax;
+    Lse c, o;
+    block_combine2(cur, old, has_inc != 0, s_key, s_f, &c, &o, &bmax);
     if (threadIdx.x == 0) {
         double* P = partials + (size_t)blockIdx.x * 8;
         P[0] = c.m; P[1] = c.s1; P[2] = c.s2; P[3] = o.m; P[4] = o.s1; P[5] = bmax;
@@ -304,10 +418,9 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
     __syncthreads();
     if (!last) return;
     __threadfence();
-    Lse tc = combine_partials(partials, gridDim.x, 0, s_key);
-    const Lse to = has_inc ? combine_partials(partials, gridDim.x, 3, s_key)
-                           : Lse{kNegInf, 0.0, 0.0};
-    const double mx = max_partials(partials, gridDim.x, s_key);
+    Lse tc, to;
+    double mx;
+    combine_partials3(partials, gridDim.x, has_inc != 0, s_key, s_d, &tc, &to, &mx);
     if (threadIdx.x == 0) {
         *ticket = 0ull;
         double* F = partials + (size_t)final_slot * 8;
