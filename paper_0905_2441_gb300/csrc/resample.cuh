@@ -272,6 +272,10 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     const int64_t per = (ntiles + kRsFinThreads - 1) / kRsFinThreads;
     const int64_t t0 = (int64_t)tid * per;
     const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+    // up to 8 tiles per thread (M <= 2^24): the run stays in registers
+    // between the sum and the prefix writes
+    const bool in_regs = per <= 8;
+    unsigned long long v0[8];
     unsigned long long own = 0;
     bool ovf = false;
     for (int64_t t = t0; t < t1; t += 8) {
@@ -280,6 +284,7 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
         for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
+            v0[k] = v[k];
             const unsigned long long n = own + v[k];
             ovf |= n < own;
             own = n;
@@ -307,14 +312,22 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
         S = n;
     }
     unsigned long long run = off + incl - own;
-    for (int64_t t = t0; t < t1; t += 8) {
-        unsigned long long v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
+    if (in_regs) {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            if (t + k < t1) sc.tile_sum[t + k] = run;
-            run += v[k];
+            if (t0 + k < t1) sc.tile_sum[t0 + k] = run;
+            run += t0 + k < t1 ? v0[k] : 0ull;
+        }
+    } else {
+        for (int64_t t = t0; t < t1; t += 8) {
+            unsigned long long v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                if (t + k < t1) sc.tile_sum[t + k] = run;
+                run += v[k];
+            }
         }
     }
     if (tid == 0 && sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
