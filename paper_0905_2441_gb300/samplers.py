@@ -81,8 +81,11 @@ class SMCSampler(_Graphable):
         if theta0 is not None:
             self.theta[0].copy_(_dev(theta0, torch.float32))
         self.cur = 0
+        self.t_done = 0  # steps completed
         self.lw.zero_()
         self.accepts.zero_()
+        self.flags.zero_()
+        self.hist.zero_()
         api.loglik_batch(self.ctx, self.model, self.y, self.theta[0], out=self.ll[0],
                          grad=self.grad[0])
 
@@ -108,26 +111,52 @@ class SMCSampler(_Graphable):
             c, n = n, c
         self.cur = c
 
-    def _body(self):
-        for t in range(1, self.T + 1):
+    def _body(self, t0: int = 1, t1: int | None = None):
+        for t in range(t0, (self.T if t1 is None else t1) + 1):
             self.step(t)
 
-    def run(self, graph: bool = False):
-        """Run all T steps; returns log Z (sum of the per-step increments)."""
-        if graph:
-            start = self.cur
-            g = self._capture(self._body)
-            self.cur = start
-            # the capture recorded the buffer swaps; replay from the same state
-            self._graph = g
-            g.replay()
-            self.cur = (start + self.T * self.n_moves) % 2
-        else:
-            self._body()
+    def run(self, graph: bool = False, stop: int | None = None):
+        """Run the steps after the last completed one up to `stop` (default
+        T); returns log Z so far (sum of the per-step increments).  Step t
+        draws from counters fixed by (seed, t), so a run split anywhere, or
+        resumed from a saved state, is bitwise the uninterrupted run."""
+        t0, t1 = self.t_done + 1, (self.T if stop is None else int(stop))
+        if t1 >= t0:
+            if graph:
+                start = self.cur
+                g = self._capture(lambda: self._body(t0, t1))
+                self.cur = start
+                # the capture recorded the buffer swaps; replay from the same state
+                self._graph = g
+                g.replay()
+                self.cur = (start + (t1 - t0 + 1) * self.n_moves) % 2
+            else:
+                self._body(t0, t1)
+            self.t_done = t1
         return self.log_evidence()
 
     def log_evidence(self) -> float:
-        return float(self.hist[1:, 0].sum().item())
+        return float(self.hist[1:self.t_done + 1, 0].sum().item())
+
+    def state_dict(self) -> dict:
+        """Everything a resumed run needs (host copies): the particles, their
+        log-likelihoods (and gradients), log-weights, per-step records and
+        the number of completed steps."""
+        c = self.cur
+        return {"theta": self.theta[c].cpu(), "ll": self.ll[c].cpu(),
+                "grad": None if self.grad[c] is None else self.grad[c].cpu(),
+                "lw": self.lw.cpu(), "flags": self.flags.cpu(), "hist": self.hist.cpu(),
+                "accepts": self.accepts.cpu(), "t_done": self.t_done}
+
+    def load_state_dict(self, d: dict):
+        self.cur = 0
+        self.theta[0].copy_(d["theta"])
+        self.ll[0].copy_(d["ll"])
+        if self.grad[0] is not None:
+            self.grad[0].copy_(d["grad"])
+        for name in ("lw", "flags", "hist", "accepts"):
+            getattr(self, name).copy_(d[name])
+        self.t_done = int(d["t_done"])
 
     @property
     def state(self):
@@ -157,6 +186,16 @@ class PopulationMCMC(_Graphable):
     def sweep(self, s: int):
         api.popmcmc_sweep(self.ctx, self.model, self.y, self.theta, self.ll, self.beta,
                           self.offsets, self.scale, self.seed, s, stats=self.stats)
+
+    def state_dict(self) -> dict:
+        """The chains' states, log-likelihoods and the move statistics (host
+        copies); sweep s draws from counters fixed by (seed, s)."""
+        return {"theta": self.theta.cpu(), "ll": self.ll.cpu(), "stats": self.stats.cpu()}
+
+    def load_state_dict(self, d: dict):
+        self.theta.copy_(d["theta"])
+        self.ll.copy_(d["ll"])
+        self.stats.copy_(d["stats"])
 
     def run(self, n_sweeps: int, start: int = 0, graph: bool = False):
         if graph:
@@ -193,13 +232,16 @@ class ParticleFilter(_Graphable):
         self._views = [(self.y[max(t - 1, 0)], self.hist[t]) for t in range(self.T + 1)]
         ctx.reserve(self.M)
         self.cur = 0
+        self.t_done = 0  # steps completed
 
     def reset(self):
         for x in self.x:
             x.zero_()
         self.lw.zero_()
+        self.hist.zero_()
         self.anc.copy_(torch.arange(self.M, dtype=torch.int32, device="cuda"))
         self.cur = 0
+        self.t_done = 0
 
     def step(self, t: int):
         c, n = self.cur, 1 - self.cur
@@ -216,15 +258,34 @@ class ParticleFilter(_Graphable):
         self.cur = n
 
     def run(self, graph: bool = False, steps: int | None = None):
-        T = self.T if steps is None else steps
-        if graph:
-            start = self.cur
-            g = self._capture(lambda: [self.step(t) for t in range(1, T + 1)])
-            self.cur = start
-            g.replay()
-            self._graph = g
-            self.cur = (start + T) % 2
-        else:
-            for t in range(1, T + 1):
-                self.step(t)
-        return float(self.hist[1:T + 1, 0].sum().item())
+        """Run the steps after the last completed one up to step `steps`
+        (default T); returns log Z so far.  Split or resumed runs are bitwise
+        the uninterrupted run (step t's draws are fixed by (seed, t))."""
+        t0, t1 = self.t_done + 1, (self.T if steps is None else int(steps))
+        if t1 >= t0:
+            if graph:
+                start = self.cur
+                g = self._capture(lambda: [self.step(t) for t in range(t0, t1 + 1)])
+                self.cur = start
+                g.replay()
+                self._graph = g
+                self.cur = (start + (t1 - t0 + 1)) % 2
+            else:
+                for t in range(t0, t1 + 1):
+                    self.step(t)
+            self.t_done = t1
+        return float(self.hist[1:self.t_done + 1, 0].sum().item())
+
+    def state_dict(self) -> dict:
+        """The particles, log-weights, ancestors of the last resampling (the
+        next step gathers through them), per-step records and the number of
+        completed steps (host copies)."""
+        return {"x": self.x[self.cur].cpu(), "lw": self.lw.cpu(), "anc": self.anc.cpu(),
+                "hist": self.hist.cpu(), "t_done": self.t_done}
+
+    def load_state_dict(self, d: dict):
+        self.cur = 0
+        self.x[0].copy_(d["x"])
+        for name in ("lw", "anc", "hist"):
+            getattr(self, name).copy_(d[name])
+        self.t_done = int(d["t_done"])

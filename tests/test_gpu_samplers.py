@@ -169,3 +169,58 @@ def test_autotuner_picks_a_valid_shape(env, tmp_path, monkeypatch):
     again = autotune.tune_loglik(ctx, P.GMM(8, SIG), y, th, reps=2)
     assert again[:2] == (lanes, threads)
     ctx.set_launch(P.OP_LOGLIK, 0, 0)
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_resume_is_bitwise_the_uninterrupted_run(env, graph):
+    """Checkpoint / resume: 6 steps, save, a fresh sampler loads the state and
+    runs the rest -- the same particles, log-likelihoods, log-weights and
+    log Z as one uninterrupted run (counter-based draws need no RNG state)."""
+    P, S, ctx = env
+    y = synth.gmm1d_data(100, [-3, 0, 3, 6], SIG, seed=1)
+    th0 = synth.prior_particles(4, 4096, seed=3)
+    betas = synth.power_betas(12, start=0)
+    mk = lambda: S.SMCSampler(ctx, P.GMM(4, SIG), y, th0, betas, scale=1.0, seed=17, n_moves=2)
+    a = mk()
+    za = a.run(graph=graph)
+    b = mk()
+    b.run(graph=graph, stop=6)
+    sd = b.state_dict()
+    c = mk()
+    c.load_state_dict(sd)
+    zc = c.run(graph=graph)
+    ctx.check()
+    assert za == zc
+    for u, v in zip(a.state, c.state):
+        assert torch.equal(u, v)
+    assert torch.equal(a.lw, c.lw) and torch.equal(a.flags, c.flags)
+    # the particle filter and population MCMC resume the same way
+    phi, Sigma, beta = synth.msv_params()
+    _, yo = synth.simulate_ssm("msv", 30, phi, Sigma, beta, seed=4)
+    mkf = lambda: S.ParticleFilter(ctx, P.PFModel(P.PF_MSV, phi, synth.chol(Sigma), beta), yo,
+                                   20000, seed=8)
+    fa = mkf()
+    zfa = fa.run(graph=graph)
+    fb = mkf()
+    fb.run(graph=graph, steps=13)
+    fc = mkf()
+    fc.load_state_dict(fb.state_dict())
+    zfc = fc.run(graph=graph)
+    assert zfa == zfc and torch.equal(fa.x[fa.cur], fc.x[fc.cur])
+    w = synth.GMM8_POP
+    off = synth.population_offsets(64, seed=w.pop_seed)
+    yp = w.data()
+    beta_p = synth.population_betas(off)
+    thp = synth.population_particles(w.K, off)
+    mkp = lambda: S.PopulationMCMC(ctx, P.GMM(w.K, w.sigma), yp, off, beta_p, thp, scale=0.1,
+                                   seed=3)
+    pa = mkp()
+    pa.run(10, graph=graph)
+    pb = mkp()
+    pb.run(4, graph=graph)
+    pc = mkp()
+    pc.load_state_dict(pb.state_dict())
+    pc.run(6, start=4, graph=graph)
+    ctx.check()
+    assert torch.equal(pa.theta, pc.theta) and torch.equal(pa.ll, pc.ll)
+    assert torch.equal(pa.stats, pc.stats)
