@@ -18,6 +18,34 @@ from . import _lib as L
 from . import api
 
 
+def step_records(hist, betas, M, flags=None, accepts=None, n_moves=1):
+    """Per-step metrics of a tempered SMC run as plain dicts (one per step
+    t = 1..len(hist)-1): temperature, log-evidence increment, ESS (before
+    resampling), whether it resampled, the acceptance rate of the moves,
+    and the running log Z.  `hist` rows are the reweight scalars
+    {log Z increment, ESS, max log-weight, log-sum-exp} (host arrays)."""
+    hist = np.asarray(hist, np.float64)
+    out, logz = [], 0.0
+    for t in range(1, hist.shape[0]):
+        logz += float(hist[t, 0])
+        r = {"t": t, "beta": float(betas[t]), "log_z_inc": float(hist[t, 0]),
+             "log_z": logz, "ess": float(hist[t, 1]), "ess_frac": float(hist[t, 1]) / M}
+        if flags is not None:
+            r["resampled"] = bool(flags[t])
+        if accepts is not None:
+            r["accept_rate"] = float(accepts[t]) / (M * n_moves)
+        out.append(r)
+    return out
+
+
+def write_jsonl(records, path):
+    """One JSON object per line."""
+    import json
+    with open(path, "w") as f:
+        for r in records:
+            f.write(json.dumps(r) + "\n")
+
+
 def _dev(a, dtype):
     if isinstance(a, torch.Tensor):
         return a.to(device="cuda", dtype=dtype).contiguous()
@@ -137,6 +165,13 @@ class SMCSampler(_Graphable):
 
     def log_evidence(self) -> float:
         return float(self.hist[1:self.t_done + 1, 0].sum().item())
+
+    def history(self) -> list:
+        """Per-step metrics of the completed steps (see step_records)."""
+        n = self.t_done + 1
+        return step_records(self.hist[:n].cpu().numpy(), self.betas_host[:n], self.M,
+                            self.flags[:n].cpu().numpy(), self.accepts[:n].cpu().numpy(),
+                            self.n_moves)
 
     def state_dict(self) -> dict:
         """Everything a resumed run needs (host copies): the particles, their

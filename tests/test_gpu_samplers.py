@@ -194,6 +194,8 @@ def test_resume_is_bitwise_the_uninterrupted_run(env, graph):
     for u, v in zip(a.state, c.state):
         assert torch.equal(u, v)
     assert torch.equal(a.lw, c.lw) and torch.equal(a.flags, c.flags)
+    hist = a.history()  # per-step metrics, identical for the resumed run
+    assert hist == c.history() and len(hist) == 12 and abs(hist[-1]["log_z"] - za) < 1e-9
     # the particle filter and population MCMC resume the same way
     phi, Sigma, beta = synth.msv_params()
     _, yo = synth.simulate_ssm("msv", 30, phi, Sigma, beta, seed=4)
