@@ -67,13 +67,18 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     st = launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), 0, s, M, seed,
                     step, do_flag, sc, status);
     if (st != SMC_OK) return st;
-    // pass 2 is persistent: as many CTAs as are resident at once
-    static int occ = 0;
-    if (occ == 0 &&
-        (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smc::k_resample_scan, smc::kRsThreads,
-                                                       0) != cudaSuccess ||
-         occ < 1))
-        occ = 1;
+    // pass 2 is persistent: as many CTAs as are resident at once (per device)
+    static int occ_of_dev[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    int occ = occ_of_dev[dev];
+    if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, smc::k_resample_scan,
+                                                          smc::kRsThreads, 0) != cudaSuccess ||
+            occ < 1)
+            occ = 1;
+        occ_of_dev[dev] = occ;
+    }
     int64_t g2 = (int64_t)num_sms * occ;
     if (g2 > tiles) g2 = tiles;
     st = launch_pdl(smc::k_resample_scan, dim3((unsigned)g2), dim3(smc::kRsThreads), 0, s, W, M,
