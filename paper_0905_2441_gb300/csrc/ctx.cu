@@ -61,9 +61,14 @@ void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* 
     }
     (void)K;
     if (op == SMC_OP_POPMCMC) {
-        // two lanes per chain and 128 chains per 256-thread block: few
-        // items, each long enough to hide the block's fixed latencies
-        *lanes = N >= 128 ? 2 : 1;
+        // at least two lanes per chain for long data (few items, each long
+        // enough to hide the block's fixed latencies); more while the chains
+        // do not fill two resident 256-thread blocks per SM, keeping at
+        // least 8 pairs of observations per lane
+        int L = N >= 128 ? 2 : 1;
+        const int64_t slots = (int64_t)ctx->num_sms * 512;
+        while (L < 32 && M * L < slots && N / (4 * L) >= 8) L *= 2;
+        *lanes = L;
         *threads = 256;
         return;
     }
