@@ -19,7 +19,7 @@ LANES = (1, 2, 4, 8, 16, 32)
 THREADS = (128, 256)
 # the population sweep: few lanes per chain win (its chains are many), and
 # odd block sizes change how items fall on the SMs
-POP_LANES = (1, 2, 4, 8)
+POP_LANES = (1, 2, 4, 8, 16)
 POP_THREADS = (128, 192, 256)
 
 

@@ -457,6 +457,29 @@ def test_popmcmc_sweep_parity(smc, N):
     assert s[2] == rst[2] and abs(int(s[0]) - int(rst[0])) <= 2 and abs(int(s[1]) - int(rst[1])) <= 2
 
 
+@pytest.mark.parametrize("lanes,threads", [(1, 256), (8, 128), (16, 128), (32, 256)])
+def test_popmcmc_sweep_launch_shapes(smc, lanes, threads):
+    """Every sweep shape the autotuner may choose gives the oracle's sweep."""
+    P, ctx = smc
+    K, N = 4, 300
+    y = synth.gmm1d_data(N, [-3, 0, 3, 6], SIG, seed=2)
+    logw = np.full(K, -np.log(K))
+    off = np.array([0, 2, 9, 40, 41, 130, 131, 300], np.int32)
+    beta = synth.population_betas(off)
+    th = synth.population_particles(K, off, seed=3)
+    ll = oracle.gmm1d_loglik(y, logw, SIG, th)
+    tt, lt = cu(th), cu(ll)
+    ctx.set_launch(P.OP_POPMCMC, lanes, threads)
+    try:
+        P.popmcmc_sweep(ctx, P.GMM(K, SIG), cu(y), tt, lt, cu(beta), cu(off), 0.3, 66, 1)
+        ctx.check()
+    finally:
+        ctx.set_launch(P.OP_POPMCMC, 0, 0)
+    rt, rl, _ = oracle.popmcmc_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 66, 1)
+    same = np.all(np.isclose(np_(tt), rt, rtol=3e-7, atol=2e-6), axis=0)
+    assert (~same).sum() <= 4
+
+
 def test_popmcmc_full_size_runs_and_reuses_queue(smc):
     P, ctx = smc
     w = synth.GMM8_POP
