@@ -11,11 +11,17 @@ counters, so their outputs are bitwise equal.
 """
 from __future__ import annotations
 
+import ctypes as C
+
 import numpy as np
 import torch
 
 from . import _lib as L
 from . import api
+
+
+def _p(t):
+    return None if t is None else t.data_ptr()
 
 
 def step_records(hist, betas, M, flags=None, accepts=None, n_moves=1):
@@ -85,6 +91,8 @@ class SMCSampler(_Graphable):
         self.resampler = resampler
         self.y = _dev(y, torch.float32)
         th = _dev(theta0, torch.float32)
+        if th.dim() != 2 or self.y.dim() != 1:
+            raise ValueError("theta0 must be [K, M] and y one-dimensional")
         self.K, self.M = th.shape
         self.betas_host = np.asarray(betas, np.float64)
         self.T = self.betas_host.size - 1
@@ -122,20 +130,31 @@ class SMCSampler(_Graphable):
         ctx = self.ctx
         db = float(self.betas_host[t] - self.betas_host[t - 1])
         flag, hist, beta, accepts = self._views[t]
+        # the sampler's own buffers were checked when it was built: the calls
+        # go to the C ABI directly (the api layer's per-call checks cost more
+        # host time than a small step's kernels)
+        lib, h, st = L.load(), ctx.handle, api._stream()
+        fp = flag.data_ptr()
         if self.resampler == "systematic":  # one call, one pass fewer
-            api.reweight_resample(ctx, self.ll[c], db, self.lw, self.W, self.seed, t,
-                                  scalars=hist, flag=flag, ess_frac=self.ess_frac, anc=self.anc)
+            api._chk(lib.smc_reweight_resample(h, self.ll[c].data_ptr(), db, self.lw.data_ptr(),
+                                               self.M, self.W.data_ptr(), hist.data_ptr(), fp,
+                                               self.ess_frac, self.seed, t, self.anc.data_ptr(),
+                                               None, st), "smc_reweight_resample")
         else:
             api.reweight(ctx, self.ll[c], db, self.lw, self.W, hist, flag, self.ess_frac)
             api.resample(ctx, self.resampler, self.W, self.seed, t, anc=self.anc, do_flag=flag,
                          logw_reset=self.lw)
+        m = C.byref(self.model.cstruct())
+        nd, bp, ap = self.y.numel(), beta.data_ptr(), accepts.data_ptr()
         for r in range(self.n_moves):
             first = r == 0
-            api.mh_move(ctx, self.model, self.y, self.theta[c], self.ll[c], self.theta[n],
-                        self.ll[n], beta, self.scale, self.seed, t + (r << 32),
-                        kind=self.kind, grad_in=self.grad[c], grad_out=self.grad[n],
-                        anc=self.anc if first else None, do_flag=flag if first else None,
-                        accept_count=accepts)
+            api._chk(lib.smc_mh_move(h, m, self.y.data_ptr(), nd, self.theta[c].data_ptr(),
+                                     self.ll[c].data_ptr(), _p(self.grad[c]),
+                                     self.anc.data_ptr() if first else None,
+                                     fp if first else None, self.theta[n].data_ptr(),
+                                     self.ll[n].data_ptr(), _p(self.grad[n]), self.M, bp, 0,
+                                     self.scale, self.kind, self.seed, t + (r << 32), ap, st),
+                     "smc_mh_move")
             c, n = n, c
         self.cur = c
 
@@ -212,15 +231,23 @@ class PopulationMCMC(_Graphable):
         self.n_pops = off.size - 1
         self.beta = _dev(betas, torch.float32)
         self.theta = _dev(theta0, torch.float32).clone()
+        if self.theta.dim() != 2 or self.y.dim() != 1:
+            raise ValueError("theta0 must be [K, M] and y one-dimensional")
         self.K, self.M = self.theta.shape
+        if self.beta.numel() != self.M or off[-1] != self.M:
+            raise ValueError("betas and the population offsets must cover the M chains")
         self.ll = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.stats = torch.zeros(3, dtype=torch.int64, device="cuda")
         ctx.reserve(self.M, self.n_pops)
         api.loglik_batch(ctx, model, self.y, self.theta, out=self.ll)
 
     def sweep(self, s: int):
-        api.popmcmc_sweep(self.ctx, self.model, self.y, self.theta, self.ll, self.beta,
-                          self.offsets, self.scale, self.seed, s, stats=self.stats)
+        # buffers checked at construction (shapes fixed): straight to the C ABI
+        api._chk(L.load().smc_popmcmc_sweep(
+            self.ctx.handle, C.byref(self.model.cstruct()), self.y.data_ptr(), self.y.numel(),
+            self.theta.data_ptr(), self.ll.data_ptr(), self.M, self.beta.data_ptr(),
+            self.offsets.data_ptr(), self.n_pops, self.scale, self.seed, s,
+            self.stats.data_ptr(), api._stream()), "smc_popmcmc_sweep")
 
     def state_dict(self) -> dict:
         """The chains' states, log-likelihoods and the move statistics (host
@@ -281,11 +308,16 @@ class ParticleFilter(_Graphable):
     def step(self, t: int):
         c, n = self.cur, 1 - self.cur
         y_t, hist = self._views[t]
-        api.pf_step(self.ctx, self.model, y_t, self.x[c], self.x[n], self.logg,
-                    self.seed, t, anc=self.anc)
+        lib, h, st = L.load(), self.ctx.handle, api._stream()
+        # buffers checked at construction: straight to the C ABI
+        api._chk(lib.pf_step(h, C.byref(self.model.cstruct_cached()), y_t.data_ptr(),
+                             self.x[c].data_ptr(), self.anc.data_ptr(), self.x[n].data_ptr(),
+                             self.logg.data_ptr(), self.M, self.seed, t, st), "pf_step")
         if self.resampler == "systematic":  # one call, one pass fewer
-            api.reweight_resample(self.ctx, self.logg, 1.0, self.lw, self.W, self.seed, t,
-                                  scalars=hist, anc=self.anc)
+            api._chk(lib.smc_reweight_resample(h, self.logg.data_ptr(), 1.0, self.lw.data_ptr(),
+                                               self.M, self.W.data_ptr(), hist.data_ptr(), None,
+                                               0.5, self.seed, t, self.anc.data_ptr(), None, st),
+                     "smc_reweight_resample")
         else:
             api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
             api.resample(self.ctx, self.resampler, self.W, self.seed, t, anc=self.anc,
