@@ -327,7 +327,10 @@ def bench_popmcmc(args, torch, dist):
     t_graph = ga.elapsed_time(gb) / 1e3
     ctx.check()
     # ---- end to end through the public API with host buffers
-    e2e = e2e_popmcmc(args, torch, P, ctx, smp)
+    # two population groups on two streams (four measured slower: the host
+    # then takes longer to issue a step's twelve calls than the GPU to run them)
+    e2e = e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, 2)
+    e2e["single_stream"] = e2e_popmcmc(args, torch, P, ctx, smp)
     # ---- roofline: MUFU ops of the sweep kernel vs the measured ex2 rate
     ex2_rate, ex2_ms = measure_peak(P, 0)
     mufu_per_launch = float(M) * N * (w.K + 1)  # K ex2 + 1 lg2 per particle-datum
@@ -368,8 +371,9 @@ def bench_popmcmc(args, torch, dist):
 
 
 def e2e_popmcmc(args, torch, P, ctx, smp):
-    """Per step: pinned host -> device copy of the chain state, one sweep
-    through the public API, device -> host copy of the new state.  The state
+    """Per step, on one stream: pinned host -> device copy of the chain
+    state, one sweep through the public API, device -> host copy of the new
+    state.  The state
     (log-likelihoods, then the K x M means) sits in one device buffer with a
     pinned host mirror, so each direction is one copy."""
     M, K, N = smp.M, smp.K, smp.y.numel()
@@ -396,6 +400,68 @@ def e2e_popmcmc(args, torch, P, ctx, smp):
     t = a.elapsed_time(b) / 1e3
     return {"value": float(M) * N * steps / t, "unit": "p*d/s", "h2d_bytes_per_step": nb,
             "d2h_bytes_per_step": nb, "steps": steps}
+
+
+def e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, parts=2):
+    """The same step end to end with the populations in `parts` contiguous
+    groups, each a sampler with its own context, device buffer, pinned host
+    mirror and stream, so that one group's copies overlap another group's
+    sweep.  Every population is swept once per step as before; a group keys
+    its draws by its own chain and population indices."""
+    from paper_0905_2441_gb300 import _lib, samplers
+    off = smp.offsets.cpu().numpy().astype(np.int64)
+    n_pops = off.size - 1
+    cuts = [round(i * n_pops / parts) for i in range(parts + 1)]
+    groups = []
+    for i in range(parts):
+        c0, c1 = int(off[cuts[i]]), int(off[cuts[i + 1]])
+        gctx = P.Context()
+        gctx.set_launch(_lib.OP_POPMCMC, lanes, threads)
+        sub = samplers.PopulationMCMC(gctx, smp.model, smp.y, off[cuts[i]:cuts[i + 1] + 1] - c0,
+                                      smp.beta[c0:c1], smp.theta[:, c0:c1], scale=smp.scale,
+                                      seed=smp.seed)
+        M, K = sub.M, sub.K
+        nb = M * 8 + K * M * 4
+        dev = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        host = torch.empty(nb, dtype=torch.uint8).pin_memory()
+        ll_v = dev[: M * 8].view(torch.float64)
+        th_v = dev[M * 8:].view(torch.float32).view(K, M)
+        ll_v.copy_(sub.ll)
+        th_v.copy_(sub.theta)
+        host.copy_(dev)
+        sub.theta, sub.ll = th_v, ll_v
+        groups.append((gctx, sub, dev, host, torch.cuda.Stream(), nb))
+    main = torch.cuda.current_stream()
+    steps = max(3, min(args.steps, 20))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(2):  # warm: each group's first sweep on its stream
+        for gctx, sub, dev, host, st, nb in groups:
+            with torch.cuda.stream(st):
+                dev.copy_(host, non_blocking=True)
+                sub.sweep(40_000 + i)
+                host.copy_(dev, non_blocking=True)
+    torch.cuda.synchronize()
+    a.record(main)
+    for g in groups:
+        g[4].wait_stream(main)
+    for i in range(steps):
+        for gctx, sub, dev, host, st, nb in groups:
+            with torch.cuda.stream(st):
+                dev.copy_(host, non_blocking=True)
+                sub.sweep(50_000 + i)
+                host.copy_(dev, non_blocking=True)
+    for g in groups:
+        main.wait_stream(g[4])
+    b.record(main)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1e3
+    nbytes = sum(g[5] for g in groups)
+    for g in groups:
+        g[0].check()
+        g[0].close()
+    return {"value": float(smp.M) * smp.y.numel() * steps / t, "unit": "p*d/s",
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": steps,
+            "pipeline": f"{parts} population groups on {parts} streams, one context each"}
 
 
 def measure_peak(P, kind):
