@@ -194,30 +194,55 @@ class Dist:
 
 
 # ------------------------------------------------------------------ CPU baseline (oracle)
+def popmcmc_config(w, M):
+    """The population-MCMC workload's description, shared by both arms."""
+    return {"workload": w.name, "n_pops": w.n_pops, "chains": M, "K": w.K, "N": w.N,
+            "pop_sizes": "uniform 8..128", "temperatures": "geometric 1e-3..1 per population",
+            "rw_scale": w.scale}
+
+
+class CpuPopSample:
+    """The FP64 oracle on a bounded sample of the population-MCMC workload
+    (its first `sample_pops` populations), set up once; `run` continues the
+    chains for as many sweeps as fit in ~budget_s (at least one)."""
+
+    def __init__(self, w, sample_pops):
+        import oracle
+        import synth
+        self.w, self.pops = w, sample_pops
+        off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+        self.M_total = int(off[-1])
+        self.y = w.data()
+        th = synth.population_particles(w.K, off)
+        beta = synth.population_betas(off)
+        self.sub = off[: sample_pops + 1].copy()
+        self.m = int(self.sub[-1])
+        self.ths, self.bs = th[:, :self.m].copy(), beta[:self.m].copy()
+        self.ll = oracle.gmm1d_loglik(self.y, w.logw(), w.sigma, self.ths)
+        self.sweep = 0
+
+    def run(self, budget_s, max_sweeps):
+        import oracle
+        w = self.w
+        t0 = time.perf_counter()
+        n = 0
+        while n < max_sweeps and (time.perf_counter() - t0) < budget_s:
+            self.ths, self.ll, _ = oracle.popmcmc_sweep(self.y, w.logw(), w.sigma, (-10, 10),
+                                                        self.ths, self.ll, self.bs, self.sub,
+                                                        w.scale, 3, self.sweep)
+            self.sweep += 1
+            n += 1
+        dt = time.perf_counter() - t0
+        return {"value": self.m * w.N * n / dt, "unit": "p*d/s", "cores": 1, "kind": "oracle",
+                "seconds": dt,
+                "sample": f"{self.pops} of {w.n_pops} populations ({self.m} chains), {n} sweeps, "
+                          f"{dt:.2f} s single-threaded FP64"}
+
+
 def cpu_popmcmc(w, budget_s=10.0, sample_pops=16, max_sweeps=50):
     """The FP64 oracle on a bounded sample: the first `sample_pops`
     populations of the same workload, as many sweeps as fit in ~budget_s."""
-    import oracle
-    import synth
-    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
-    y = w.data()
-    th = synth.population_particles(w.K, off)
-    beta = synth.population_betas(off)
-    sub = off[: sample_pops + 1].copy()
-    m = int(sub[-1])
-    ths, bs = th[:, :m].copy(), beta[:m].copy()
-    ll = oracle.gmm1d_loglik(y, w.logw(), w.sigma, ths)
-    t0 = time.perf_counter()
-    n = 0
-    while n < max_sweeps and (time.perf_counter() - t0) < budget_s:
-        ths, ll, _ = oracle.popmcmc_sweep(y, w.logw(), w.sigma, (-10, 10), ths, ll, bs, sub,
-                                          w.scale, 3, n)
-        n += 1
-    dt = time.perf_counter() - t0
-    pd = m * w.N * n
-    return {"value": pd / dt, "unit": "p*d/s", "cores": 1, "kind": "oracle",
-            "sample": f"{sample_pops} of {w.n_pops} populations ({m} chains), {n} sweeps, "
-                      f"{dt:.1f} s single-threaded FP64"}
+    return CpuPopSample(w, sample_pops).run(budget_s, max_sweeps)
 
 
 def _cpu_worker(job):
@@ -353,9 +378,7 @@ def bench_popmcmc(args, torch, dist):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded mixture data and chain states; no dataset)",
-        "config": {"workload": w.name, "n_pops": w.n_pops, "chains": M, "K": w.K, "N": N,
-                   "pop_sizes": "uniform 8..128", "temperatures": "geometric 1e-3..1 per population",
-                   "rw_scale": w.scale, "lanes_per_chain": lanes, "threads_per_block": threads,
+        "config": {**popmcmc_config(w, M), "lanes_per_chain": lanes, "threads_per_block": threads,
                    "l2": "256 MiB buffer (2x L2) written before every timed sweep, outside its events",
                    "parallelism": f"independent populations per rank x{dist.world}"},
         "forms": {"plain_per_step": {"value": value, "ms_per_sweep": 1e3 * t_dev / args.steps},
@@ -1139,23 +1162,29 @@ def all_peaks(torch):
 
 # ------------------------------------------------------------------ reference arm
 def reference_arm(args):
-    """The oracle timed on the host cores on bounded samples of the same workload."""
+    """The oracle timed on the host cores on bounded samples of the same
+    workload: each step continues four populations' chains for a share of
+    ~ref_total seconds (at least one sweep), so any --steps ends in minutes."""
     import synth
     w = synth.GMM8_POP
-    vals = []
+    smp = CpuPopSample(w, sample_pops=4)
+    budget = min(args.ref_budget, args.ref_total / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
-        cpu_popmcmc(w, budget_s=1.0, sample_pops=2, max_sweeps=1)
-    samples = []
+        smp.run(budget, 1)
+    vals, samples, secs = [], [], []
     for i in range(args.steps):
-        r = cpu_popmcmc(w, budget_s=args.ref_budget, sample_pops=4, max_sweeps=1000)
+        r = smp.run(budget, 1000)
         vals.append(r["value"])
         samples.append(r["sample"])
+        secs.append(r["seconds"])
     v = statistics.median(vals)
     return {"impl": "reference", "metric": "particle-datum loglik evals/s (population MCMC sweeps)",
-            "value": v, "unit": "p*d/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+            "value": v, "unit": "p*d/s", "n_gpus": args.gpus, "devices": "host cores (rank 0)",
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.median(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)",
-            "config": {"workload": w.name, "K": w.K, "N": w.N},
+            "data": "synthetic (seeded mixture data and chain states; no dataset)",
+            "config": popmcmc_config(w, smp.M_total),
             "cpu_baseline": {"value": v, "unit": "p*d/s", "cores": 1, "kind": "oracle",
                              "sample": samples[0] + f"; median of {args.steps} samples"},
             "e2e": {"value": v, "unit": "p*d/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -1174,7 +1203,10 @@ def main():
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-secondary", action="store_true", help="skip the sampler / filter lines")
-    ap.add_argument("--ref-budget", type=float, default=3.0)
+    ap.add_argument("--ref-budget", type=float, default=3.0,
+                    help="reference arm: at most this many seconds of oracle work per step")
+    ap.add_argument("--ref-total", type=float, default=120.0,
+                    help="reference arm: about this many seconds over all steps")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     dist = Dist()
