@@ -248,7 +248,7 @@ class CpuPopSample:
                           f"{dt:.2f} s single-threaded FP64"}
 
 
-def cpu_popmcmc(w, budget_s=10.0, sample_pops=16, max_sweeps=50):
+def cpu_popmcmc(w, budget_s=10.0, sample_pops=16, max_sweeps=200):
     """The FP64 oracle on a bounded sample: the first `sample_pops`
     populations of the same workload, as many sweeps as fit in ~budget_s."""
     return CpuPopSample(w, sample_pops).run(budget_s, max_sweeps)
