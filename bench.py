@@ -419,7 +419,7 @@ def e2e_popmcmc(args, torch, P, ctx, smp):
     host.copy_(dev)
     smp.theta, smp.ll = th_v, ll_v  # the sampler's state now lives in the one buffer
     stream = torch.cuda.current_stream()
-    steps = max(3, min(args.steps, 20))
+    steps = max(3, min(args.steps, 200))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(stream)
@@ -464,7 +464,7 @@ def e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, parts=2):
         sub.theta, sub.ll = th_v, ll_v
         groups.append((gctx, sub, dev, host, torch.cuda.Stream(), nb))
     main = torch.cuda.current_stream()
-    steps = max(3, min(args.steps, 20))
+    steps = max(3, min(args.steps, 200))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     for i in range(2):  # warm: each group's first sweep on its stream
         for gctx, sub, dev, host, st, nb in groups:
