@@ -366,7 +366,8 @@ def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, sca
     _need(stats, torch.int64, "stats", (3,))
     m = model.cstruct()
     _chk(L.load().smc_popmcmc_sweep(ctx.handle, C.byref(m), _ptr(y), y.numel(), _ptr(theta),
-                                    _ptr(loglik), M, _ptr(beta), _ptr(offsets), n_pops, float(scale), int(seed), int(sweep), _ptr(stats),
+                                    _ptr(loglik), M, _ptr(beta), _ptr(offsets), n_pops,
+                                    float(scale), int(seed), int(sweep), _ptr(stats),
                                     _stream(stream)), "smc_popmcmc_sweep")
 
 
