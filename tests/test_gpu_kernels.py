@@ -508,6 +508,45 @@ def test_popmcmc_full_size_runs_and_reuses_queue(smc):
     np.testing.assert_allclose(np_(lt)[sample], ref, rtol=1e-5)
 
 
+@pytest.mark.parametrize("shape", [(4, 256), (0, 0)])  # the benchmark's tuned shape; default
+def test_popmcmc_full_size_parity(smc, shape):
+    """One sweep of the full batched configuration (512 populations, 34,591
+    chains, K = 8, N = 1000: the benchmarked workload and seeds) against the
+    oracle's sweep, population by population, in the launch shape the
+    benchmark times and in the default one.  A population may differ only
+    through an accept decision taken inside the FP32 likelihood's error band."""
+    P, ctx = smc
+    w = synth.GMM8_POP
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    y = w.data()
+    th = synth.population_particles(w.K, off, seed=4)
+    beta = synth.population_betas(off)
+    ll = oracle.gmm1d_loglik(y, w.logw(), w.sigma, th)
+    tt, lt = cu(th), cu(ll)
+    stats = torch.zeros(3, dtype=torch.int64, device="cuda")
+    ctx.set_launch(P.OP_POPMCMC, *shape)
+    try:
+        P.popmcmc_sweep(ctx, P.GMM(w.K, w.sigma), cu(y), tt, lt, cu(beta), cu(off), w.scale, 3, 7,
+                        stats=stats)
+        ctx.check()
+    finally:
+        ctx.set_launch(P.OP_POPMCMC, 0, 0)
+    rt, rl, rst = oracle.popmcmc_sweep(y, w.logw(), w.sigma, BOX, th, ll, beta, off, w.scale, 3,
+                                       7)
+    gt, gl = np_(tt), np_(lt)
+    bad = []
+    for q in range(w.n_pops):
+        a, b = off[q], off[q + 1]
+        if not (np.allclose(gt[:, a:b], rt[:, a:b], rtol=3e-7, atol=2e-6) and
+                np.allclose(gl[a:b], rl[a:b], rtol=1e-5)):
+            bad.append(q)
+    assert len(bad) <= 2, bad
+    s = np_(stats)
+    assert s[2] == rst[2]
+    assert abs(int(s[0]) - int(rst[0])) <= 4 and abs(int(s[1]) - int(rst[1])) <= 4
+    assert rst[0] > 0 and rst[1] > 0  # moves and swaps both happened
+
+
 # ------------------------------------------------------------------ particle filter
 @pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("M", [1, 1000, 1 << 20])
