@@ -583,9 +583,20 @@ def bench_secondary(torch, P):
     reps = 10
     t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
     ctx.check()
-    # Section 2.1's importance-sampling example at its size (N = 2^24 draws):
-    # draws in device memory (HBM-bound, 4 bytes a draw), drawn on the
-    # device, and end to end from pinned host memory as in the example
+    out["is_example"] = is_example(torch, P, ctx)
+    out["mrg32k3a"] = mrg_blocks(torch, P, ctx)
+    out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
+                               "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
+                               "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}
+    ctx.close()
+    return out
+
+
+def is_example(torch, P, ctx, reps=10):
+    """Section 2.1's importance-sampling example at its size (N = 2^24
+    draws): draws in device memory (HBM-bound, 4 bytes a draw), drawn on the
+    device, and end to end from pinned host memory as in the example; L2
+    flushed before each timed call, medians over `reps`."""
     prob = P.ISProblem()
     n_is = 1 << 24
     x_d = torch.randn(n_is, device="cuda", generator=torch.Generator(device="cuda").manual_seed(3))
@@ -597,7 +608,7 @@ def bench_secondary(torch, P):
     for _ in range(3):
         P.is_moments(ctx, prob, x_d, out=res)
     t_mem, t_dev, t_e2e = [], [], []
-    for _ in range(10):
+    for _ in range(reps):
         e = _flush_timed(torch, flush, stream, [lambda: P.is_moments(ctx, prob, x_d, out=res)])
         torch.cuda.synchronize()
         t_mem.append(e[0].elapsed_time(e[1]) / 1e3)
@@ -616,21 +627,27 @@ def bench_secondary(torch, P):
     ctx.check()
     est = res_h.numpy()
     tm = statistics.median(t_mem)
-    out["is_example"] = {"workload": "is-section2.1-N16777216", "N": n_is,
-                         "ms_draws_in_hbm": 1e3 * tm, "gbs_draws_in_hbm": 4 * n_is / tm / 1e9,
-                         "hbm_frac": 4 * n_is / tm / 1e9 / measured_peaks()["hbm_gbs"],
-                         "ms_draws_on_device": 1e3 * statistics.median(t_dev),
-                         "ms_end_to_end_from_host": 1e3 * statistics.median(t_e2e),
-                         "estimate_plain": float(est[1] / n_is),
-                         "estimate_self_normalised": float(est[1] / est[0]), "exact": 1.875}
-    # MRG32k3a as Section 2.5 runs it: per thread a skip-ahead to its block,
-    # then the block (float32 out, slot-major)
+    return {"workload": "is-section2.1-N16777216", "N": n_is,
+            "ms_draws_in_hbm": 1e3 * tm, "gbs_draws_in_hbm": 4 * n_is / tm / 1e9,
+            "hbm_frac": 4 * n_is / tm / 1e9 / measured_peaks()["hbm_gbs"],
+            "ms_draws_on_device": 1e3 * statistics.median(t_dev),
+            "ms_end_to_end_from_host": 1e3 * statistics.median(t_e2e),
+            "estimate_plain": float(est[1] / n_is),
+            "estimate_self_normalised": float(est[1] / est[0]), "exact": 1.875}
+
+
+def mrg_blocks(torch, P, ctx, reps=10):
+    """MRG32k3a as Section 2.5 runs it: per thread a skip-ahead to its block,
+    then the block (float32 out, slot-major); L2 flushed before each timed
+    call, medians over `reps`."""
     nt, per = 152 * 256 * 4, 1024
     mrg = torch.empty(nt * per, dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
     for _ in range(3):
         P.rng_mrg32k3a(ctx, (12345,) * 6, 0, nt, per, out=mrg)
     t_blk, t_jump = [], []
-    for _ in range(10):
+    for _ in range(reps):
         e = _flush_timed(torch, flush, stream,
                          [lambda: P.rng_mrg32k3a(ctx, (12345,) * 6, 2**40, nt, per, out=mrg),
                           lambda: P.rng_mrg32k3a(ctx, (12345,) * 6, 2**40, nt, 1,
@@ -640,14 +657,61 @@ def bench_secondary(torch, P):
         t_jump.append(e[1].elapsed_time(e[2]) / 1e3)
     ctx.check()
     tb = statistics.median(t_blk)
-    out["mrg32k3a"] = {"threads": nt, "per_thread": per, "ms": 1e3 * tb,
-                       "numbers_per_s": nt * per / tb, "gbs_written": 4 * nt * per / tb / 1e9,
-                       "ms_skip_ahead_only": 1e3 * statistics.median(t_jump)}
-    out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
-                               "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
-                               "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}
+    return {"threads": nt, "per_thread": per, "ms": 1e3 * tb,
+            "numbers_per_s": nt * per / tb, "gbs_written": 4 * nt * per / tb / 1e9,
+            "ms_skip_ahead_only": 1e3 * statistics.median(t_jump)}
+
+
+def bench_is(args, torch, dist):
+    """One step = one importance-sampling call over N = 2^24 draws held in
+    HBM (Section 2.1's example); also its on-device-draw and host forms."""
+    import paper_0905_2441_gb300 as P
+    ctx = P.Context()
+    reps = max(3, min(args.steps, 50))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        r = is_example(torch, P, ctx, reps)
     ctx.close()
-    return out
+    t = dist.max(torch, r["ms_draws_in_hbm"] / 1e3)
+    hbm = measured_peaks()["hbm_gbs"]
+    ach = 4 * r["N"] / t / 1e9
+    return {"metric": "importance-sampling draws/s (Section 2.1 example, draws in HBM)",
+            "value": dist.sum(torch, float(r["N"])) / t, "unit": "draws/s", "n_gpus": dist.world,
+            "steps": reps, "warmup": 3, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32 per draw, f64 sums",
+            "data": "synthetic (N(0,1) draws, seed 3)",
+            "config": {"workload": r["workload"], "N": r["N"],
+                       "l2": "256 MiB buffer written before every timed call, outside its events"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": profile_traffic("k_is_moments"),
+                         "bytes_per_draw": 4},
+            "is_example": r, "gpu_launches": reps, "clocks": clk.summary()}
+
+
+def bench_mrg(args, torch, dist):
+    """One step = 155,648 MRG32k3a streams, each skipping ahead to its block
+    and writing 1024 uniforms (Section 2.5's generator, float32 out)."""
+    import paper_0905_2441_gb300 as P
+    ctx = P.Context()
+    reps = max(3, min(args.steps, 50))
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        r = mrg_blocks(torch, P, ctx, reps)
+    ctx.close()
+    t = dist.max(torch, r["ms"] / 1e3)
+    n = r["threads"] * r["per_thread"]
+    hbm = measured_peaks()["hbm_gbs"]
+    ach = 4 * n / t / 1e9
+    return {"metric": "MRG32k3a uniforms/s (per-thread skip-ahead, then a block each)",
+            "value": dist.sum(torch, float(n)) / t, "unit": "numbers/s", "n_gpus": dist.world,
+            "steps": reps, "warmup": 3, "ms_per_step": 1e3 * t, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32 state, f32 out",
+            "data": "synthetic (seed 12345 x 6)",
+            "config": {"workload": "mrg32k3a-155648x1024", "threads": r["threads"],
+                       "per_thread": r["per_thread"],
+                       "l2": "256 MiB buffer written before every timed call, outside its events"},
+            "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                         "frac": ach / hbm, "traffic": profile_traffic("k_mrg32k3a"),
+                         "bytes_per_number": 4},
+            "mrg32k3a": r, "gpu_launches": 2 * reps, "clocks": clk.summary()}
 
 
 def _flush_timed(torch, flush, stream, fns):
@@ -1207,7 +1271,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
                                                               "diag", "fsv", "tables", "mala",
-                                                              "peaks"])
+                                                              "is", "mrg", "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
@@ -1242,6 +1306,10 @@ def main():
         out = bench_tables(args, torch, dist)
     elif args.workload == "mala":
         out = bench_mala(args, torch, dist)
+    elif args.workload == "is":
+        out = bench_is(args, torch, dist)
+    elif args.workload == "mrg":
+        out = bench_mrg(args, torch, dist)
     elif args.workload == "peaks":
         out = {"peaks_ops_per_s": all_peaks(torch)}
     else:
