@@ -15,6 +15,8 @@ tensor cores; step = one likelihood call), fsv (the paper's factor SV particle
 filter, Table 3 sizes; step = one whole T = 200 run), tables (the paper's
 Tables 1 and 2 configurations, every size; step = one whole run of each),
 mala (the MALA tempered sampler; step = one whole 50-temperature run),
+is (Section 2.1's importance-sampling example, N = 2^24 draws; step = one
+call), mrg (MRG32k3a, 155,648 streams x 1024 numbers; step = one call),
 peaks (the MUFU / FMA / FP64 /
 conversion rates used as roofline denominators).  The default run also
 reports, under "secondary", the paper's Tables 1 and 2 replicated, the

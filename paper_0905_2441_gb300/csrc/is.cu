@@ -72,13 +72,26 @@ __global__ void __launch_bounds__(256, 4) k_is_moments(IsArgs A, const float* __
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     const int64_t ngroups = (N + kIsGroup - 1) / kIsGroup;
-    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ngroups; g += G) {
-        float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
-        const int64_t i0 = g * kIsGroup;
-        if (x && i0 + kIsGroup <= N && ((reinterpret_cast<uintptr_t>(x + i0) & 15u) == 0)) {
-            const float4 v0 = reinterpret_cast<const float4*>(x + i0)[0];
-            const float4 v1 = reinterpret_cast<const float4*>(x + i0)[1];
+    int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x && (reinterpret_cast<uintptr_t>(x) & 15u) == 0) {
+        // draws in memory, 16-byte aligned: the whole groups are software
+        // pipelined (the next group's two 16-byte loads are issued before
+        // this group's arithmetic, so a load is always in flight)
+        const int64_t nfull = N / kIsGroup;
+        const float4* xv = reinterpret_cast<const float4*>(x);
+        float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+        if (g < nfull) {
+            n0 = __ldcs(xv + 2 * g);
+            n1 = __ldcs(xv + 2 * g + 1);
+        }
+        for (; g < nfull; g += G) {
+            const float4 v0 = n0, v1 = n1;
+            if (g + G < nfull) {
+                n0 = __ldcs(xv + 2 * (g + G));
+                n1 = __ldcs(xv + 2 * (g + G) + 1);
+            }
             const float xs[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+            float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
 #pragma unroll
             for (int j = 0; j < kIsGroup; ++j) {
                 float w, wp;
@@ -87,14 +100,22 @@ __global__ void __launch_bounds__(256, 4) k_is_moments(IsArgs A, const float* __
                 f1 += wp;
                 f2 = fmaf(w, w, f2);
             }
-        } else {
-            for (int j = 0; j < kIsGroup && i0 + j < N; ++j) {
-                float w, wp;
-                is_term<KP>(is_x(x, i0 + j, A, seed, step, ps), A, w, wp);
-                f0 += w;
-                f1 += wp;
-                f2 = fmaf(w, w, f2);
-            }
+            a0 += (double)f0;
+            a1 += (double)f1;
+            a2 += (double)f2;
+        }
+        // g is now this thread's first group at or past nfull: the partial
+        // last group (N not a multiple of 8) goes to the generic loop below
+    }
+    for (; g < ngroups; g += G) {
+        float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
+        const int64_t i0 = g * kIsGroup;
+        for (int j = 0; j < kIsGroup && i0 + j < N; ++j) {
+            float w, wp;
+            is_term<KP>(is_x(x, i0 + j, A, seed, step, ps), A, w, wp);
+            f0 += w;
+            f1 += wp;
+            f2 = fmaf(w, w, f2);
         }
         a0 += (double)f0;
         a1 += (double)f1;
