@@ -83,6 +83,31 @@ def test_reference_arm_non_zero_rank_does_no_work():
     assert r.stdout.strip() == ""
 
 
+def test_reference_arm_line_matches_the_gpu_arm_contract():
+    # rank 0 prints one JSON line: the oracle's rate on the same workload
+    # config as the GPU arm, within a bounded time for any --steps
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    steps = 400
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                        "--steps", str(steps), "--warmup", "3", "--ref-total", "4"], env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+    w = synth.GMM8_POP
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    assert d["impl"] == "reference" and d["config"] == bench.popmcmc_config(w, int(off[-1]))
+    assert d["metric"] == "particle-datum loglik evals/s (population MCMC sweeps)"
+    assert d["unit"] == "p*d/s" and d["higher_is_better"] is True and d["steps"] == steps
+    assert d["value"] > 0 and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] == 1
+    assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
+    assert d["ms_per_step"] > 0
+
+
 def test_single_process_dist_is_identity():
     import torch
     sys.path.insert(0, ROOT)
