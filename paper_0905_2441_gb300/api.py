@@ -168,6 +168,10 @@ class PFModel:
         return c
 
     @property
+    def state_dim(self) -> int:
+        return np.asarray(self.phi).size  # FSV: the factors' log-variances
+
+    @property
     def obs_dim(self) -> int:
         return np.asarray(self.B).shape[0] if self.kind == L.PF_FSV else np.asarray(self.phi).size
 
@@ -197,8 +201,28 @@ class PFModel:
 
 
 # ------------------------------------------------------------------ calls
+def _match_model(model, y, theta, name="theta"):
+    """The tensors' layout must be the model's (the C ABI takes bare pointers
+    and sizes, so a tensor smaller than the model implies would be read past
+    its end): 1-D y float[N], theta float[K][M]; diagonal y float[N][d],
+    theta float[M][K][d]."""
+    if isinstance(model, DiagGMM):
+        ok = theta.dim() == 3 and theta.shape[1] == model.K and theta.shape[2] == model.d
+        want = f"[M, {model.K}, {model.d}]"
+        if y.dim() != 2 or y.shape[1] != model.d:
+            raise ValueError(f"y must be [N, {model.d}] for this model, got {tuple(y.shape)}")
+    else:
+        ok = theta.dim() == 2 and theta.shape[0] == model.K
+        want = f"[{model.K}, M]"
+        if y.dim() != 1:
+            raise ValueError(f"y must be one-dimensional for this model, got {tuple(y.shape)}")
+    if not ok:
+        raise ValueError(f"{name} must be {want} for this model, got {tuple(theta.shape)}")
+
+
 def loglik_batch(ctx: Context, model: GMM, y, theta, out=None, grad=None, stream=None):
     """Per-particle mixture log-likelihood (and optional gradient)."""
+    _match_model(model, y, theta)
     if isinstance(model, DiagGMM):
         N = y.shape[0]
         M = theta.shape[0]
@@ -331,6 +355,7 @@ def gather(ctx: Context, anc, src32=None, dst32=None, src64=None, dst64=None, st
 def mh_move(ctx: Context, model: GMM, y, theta_in, ll_in, theta_out, ll_out, beta, scale: float,
             seed: int, step: int, kind: int = L.MOVE_RW, grad_in=None, grad_out=None, anc=None,
             do_flag=None, accept_count=None, stream=None):
+    _match_model(model, y, theta_in, "theta_in")
     K, M = theta_in.shape
     _need(y, torch.float32, "y")
     for t, n in ((theta_in, "theta_in"), (theta_out, "theta_out")):
@@ -356,6 +381,7 @@ def mh_move(ctx: Context, model: GMM, y, theta_in, ll_in, theta_out, ll_out, bet
 
 def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, scale: float,
                   seed: int, sweep: int, stats=None, stream=None):
+    _match_model(model, y, theta)
     K, M = theta.shape
     n_pops = offsets.numel() - 1
     _need(y, torch.float32, "y")
@@ -373,6 +399,9 @@ def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, sca
 
 def pf_step(ctx: Context, model: PFModel, y_t, x_in, x_out, logg_out, seed: int, t: int,
             anc=None, stream=None):
+    if x_in.dim() != 2 or x_in.shape[0] != model.state_dim:
+        raise ValueError(f"x_in must be [{model.state_dim}, M] for this model, "
+                         f"got {tuple(x_in.shape)}")
     d, M = x_in.shape
     _need(y_t, torch.float32, "y_t", (model.obs_dim,))
     _need(x_in, torch.float32, "x_in", (d, M))

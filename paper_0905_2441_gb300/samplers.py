@@ -58,8 +58,40 @@ def _dev(a, dtype):
     return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
 
 
+def _check_replacement(name, old, new):
+    """A sampler's steps pass its buffers' pointers and sizes to the C ABI
+    without re-checking them, so a device tensor (or a tuple of them) may
+    only be replaced by one of the same dtype, shape and device, contiguous."""
+    if isinstance(old, tuple):
+        if not isinstance(new, tuple) or len(new) != len(old):
+            raise ValueError(f"{name} must stay a tuple of {len(old)} buffers")
+        for i, (o, n) in enumerate(zip(old, new)):
+            _check_replacement(f"{name}[{i}]", o, n)
+        return
+    if isinstance(old, torch.Tensor):
+        ok = (isinstance(new, torch.Tensor) and new.dtype == old.dtype and
+              new.shape == old.shape and new.device == old.device and new.is_contiguous())
+        if not ok:
+            raise ValueError(f"{name} may only be replaced by a contiguous tensor of dtype "
+                             f"{old.dtype}, shape {tuple(old.shape)} on {old.device}")
+    elif old is None and isinstance(new, torch.Tensor):
+        raise ValueError(f"{name} is not used by this sampler")
+
+
 class _Graphable:
-    """run(graph=True) captures `_body(...)` once and replays it."""
+    """run(graph=True) captures `_body(...)` once and replays it.  Device
+    buffers set at construction may later be replaced only by tensors of the
+    same dtype, shape and device (`_check_replacement`)."""
+
+    _FIXED = ("M", "K", "T", "d", "n_pops")  # sizes the C calls take with the buffers
+
+    def __setattr__(self, name, value):
+        if name in self.__dict__:
+            old = self.__dict__[name]
+            if name in self._FIXED and value != old:
+                raise ValueError(f"{name} is fixed when the sampler is built")
+            _check_replacement(name, old, value)
+        object.__setattr__(self, name, value)
 
     def _capture(self, fn):
         s = torch.cuda.Stream()
@@ -97,10 +129,10 @@ class SMCSampler(_Graphable):
         self.betas_host = np.asarray(betas, np.float64)
         self.T = self.betas_host.size - 1
         self.betas = _dev(self.betas_host.astype(np.float32), torch.float32)
-        self.theta = [th.clone(), torch.empty_like(th)]
-        self.ll = [torch.empty(self.M, dtype=torch.float64, device="cuda") for _ in range(2)]
+        self.theta = (th.clone(), torch.empty_like(th))
+        self.ll = tuple(torch.empty(self.M, dtype=torch.float64, device="cuda") for _ in range(2))
         mala = kind == L.MOVE_MALA
-        self.grad = [torch.empty_like(th) for _ in range(2)] if mala else [None, None]
+        self.grad = tuple(torch.empty_like(th) for _ in range(2)) if mala else (None, None)
         self.lw = torch.zeros(self.M, dtype=torch.float64, device="cuda")
         self.W = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.anc = torch.empty(self.M, dtype=torch.int32, device="cuda")
@@ -285,7 +317,7 @@ class ParticleFilter(_Graphable):
         self.d = int(np.asarray(model.phi).size)  # state dimension (FSV: factors)
         if self.y.shape[1] != model.obs_dim:
             raise ValueError("observations do not match the model's dimension")
-        self.x = [torch.zeros(self.d, self.M, device="cuda") for _ in range(2)]
+        self.x = tuple(torch.zeros(self.d, self.M, device="cuda") for _ in range(2))
         self.logg = torch.empty(self.M, dtype=torch.float64, device="cuda")
         self.lw = torch.zeros(self.M, dtype=torch.float64, device="cuda")
         self.W = torch.empty(self.M, dtype=torch.float64, device="cuda")
