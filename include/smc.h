@@ -298,7 +298,9 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
  * population of Table 1), stage 2 runs instead as a second, grid-wide
  * launch over all pairs, with the same pairs, draws and result.
  * pop_offsets must be non-decreasing with
- * pop_offsets[0] = 0 and pop_offsets[n_pops] = M_total.
+ * pop_offsets[0] = 0 and pop_offsets[n_pops] = M_total (device data: the
+ * library does not read them on the host, so it cannot check them; other
+ * values make the launch access chains outside [0, M_total)).
  * stats (device uint64[3], nullable) accumulates {MH accepts, swaps
  *   accepted, swaps attempted}.  Uses n_pops counters of context scratch
  *   (smc_reserve's max_pops sizes them before graph capture). */

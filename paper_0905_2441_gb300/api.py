@@ -341,10 +341,18 @@ def resample(ctx: Context, kind: str, W, seed: int, step: int, anc=None, do_flag
 
 
 def gather(ctx: Context, anc, src32=None, dst32=None, src64=None, dst64=None, stream=None):
+    """dst[..., i] = src[..., anc[i]]: float32 rows [rows][M] (or [M]) and a
+    float64 vector [M]; sources and destinations come in pairs of one shape."""
+    if (src32 is None) != (dst32 is None) or (src64 is None) != (dst64 is None):
+        raise ValueError("each source needs its destination and vice versa")
+    if dst32 is None and dst64 is None:
+        raise ValueError("nothing to gather")
     M = (dst64 if dst64 is not None else dst32).shape[-1]
-    rows = 0 if src32 is None else (src32.shape[0] if src32.dim() == 2 else 1)
+    if dst32 is not None and (dst32.dim() not in (1, 2) or dst32.shape[-1] != M):
+        raise ValueError(f"dst_f32 must be [rows, {M}] or [{M}], got {tuple(dst32.shape)}")
+    rows = 0 if src32 is None else (dst32.shape[0] if dst32.dim() == 2 else 1)
     _need(anc, torch.int32, "anc", (M,))
-    _need(src32, torch.float32, "src_f32")
+    _need(src32, torch.float32, "src_f32", None if dst32 is None else dst32.shape)
     _need(dst32, torch.float32, "dst_f32")
     _need(src64, torch.float64, "src_f64", (M,))
     _need(dst64, torch.float64, "dst_f64", (M,))
@@ -381,6 +389,9 @@ def mh_move(ctx: Context, model: GMM, y, theta_in, ll_in, theta_out, ll_out, bet
 
 def popmcmc_sweep(ctx: Context, model: GMM, y, theta, loglik, beta, offsets, scale: float,
                   seed: int, sweep: int, stats=None, stream=None):
+    """One population-MCMC sweep in place.  `offsets` (int32, device) must
+    run non-decreasing from 0 to M: its values live on the device and are
+    not checked here (PopulationMCMC checks them once, on the host)."""
     _match_model(model, y, theta)
     K, M = theta.shape
     n_pops = offsets.numel() - 1

@@ -76,3 +76,15 @@ def test_sizes_are_fixed_after_construction():
     f.buf = torch.zeros(5)
     with pytest.raises(ValueError):
         f.buf = torch.zeros(6)
+
+
+def test_gather_pairs_and_shapes():
+    with pytest.raises(ValueError, match="destination"):
+        P.gather(None, None, src32=torch.zeros(3, 5))
+    with pytest.raises(ValueError, match="destination"):
+        P.gather(None, None, src64=torch.zeros(5, dtype=torch.float64))
+    with pytest.raises(ValueError, match="nothing"):
+        P.gather(None, None)
+    with pytest.raises(ValueError, match=r"dst_f32 must be"):
+        P.gather(None, None, torch.zeros(3, 5), torch.zeros(3, 4),
+                 torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.float64))
