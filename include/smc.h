@@ -30,6 +30,10 @@
  *     float[M][K][d]; log-likelihoods, log-weights and normalised weights
  *     are double[M]; ancestors are int32[M]; particle-filter states are
  *     float[d][M].
+ *   - Index arrays passed in device memory (ancestors, population offsets)
+ *     are used as given: their values are not read on the host, so the
+ *     library cannot check them.  Ancestors must lie in [0, M); those this
+ *     library's resampling calls write always do.
  */
 #ifndef SMC_GB300_H
 #define SMC_GB300_H
