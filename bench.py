@@ -365,8 +365,13 @@ def bench_popmcmc(args, torch, dist):
     # ---- end to end through the public API with host buffers
     # two population groups on two streams (four measured slower: the host
     # then takes longer to issue a step's twelve calls than the GPU to run them)
+    dist.barrier(torch)
     e2e = e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, 2)
-    e2e["single_stream"] = e2e_popmcmc(args, torch, P, ctx, smp)
+    dist.barrier(torch)
+    single = e2e_popmcmc(args, torch, P, ctx, smp)
+    for r in (e2e, single):  # whole job: all ranks' units over the slowest rank's time
+        r["value"] = dist.sum(torch, r.pop("_units")) / dist.max(torch, r.pop("_seconds"))
+    e2e["single_stream"] = single
     # ---- roofline: MUFU ops of the sweep kernel vs the measured ex2 rate
     ex2_rate, ex2_ms = measure_peak(P, 0)
     mufu_per_launch = float(M) * N * (w.K + 1)  # K ex2 + 1 lg2 per particle-datum
@@ -433,7 +438,8 @@ def e2e_popmcmc(args, torch, P, ctx, smp):
     b.synchronize()
     t = a.elapsed_time(b) / 1e3
     return {"value": float(M) * N * steps / t, "unit": "p*d/s", "h2d_bytes_per_step": nb,
-            "d2h_bytes_per_step": nb, "steps": steps}
+            "d2h_bytes_per_step": nb, "steps": steps, "_units": float(M) * N * steps,
+            "_seconds": t}
 
 
 def e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, parts=2):
@@ -493,9 +499,11 @@ def e2e_popmcmc_pipelined(args, torch, P, smp, lanes, threads, parts=2):
     for g in groups:
         g[0].check()
         g[0].close()
-    return {"value": float(smp.M) * smp.y.numel() * steps / t, "unit": "p*d/s",
+    units = float(smp.M) * smp.y.numel() * steps
+    return {"value": units / t, "unit": "p*d/s",
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": steps,
-            "pipeline": f"{parts} population groups on {parts} streams, one context each"}
+            "pipeline": f"{parts} population groups on {parts} streams, one context each",
+            "_units": units, "_seconds": t}
 
 
 def measure_peak(P, kind):
