@@ -19,6 +19,9 @@
  *     counters, the status word) lives in the context.  smc_reserve() sizes
  *     it up front; a call that needs more grows it, which is refused with
  *     SMC_ERR_ARG while the stream is being captured into a CUDA graph.
+ *     Calls on one context share that scratch, so they must run one after
+ *     another on the GPU (one stream, or streams ordered by events); work
+ *     meant to overlap on several streams takes one context per stream.
  *   - Random numbers: counter-based Philox4x32-10 (Salmon et al., SC'11)
  *     in place of the MRG32k3a / xorshift skip-ahead streams of Section
  *     2.5.  key = (seed mod 2^32, seed div 2^32); counter = (index, block,
