@@ -61,7 +61,10 @@ def _need(t, dtype, name, shape=None):
 
 # ------------------------------------------------------------------ context
 class Context:
-    """Owns an smc_ctx (status word, scratch, launch overrides) on one device."""
+    """Owns an smc_ctx (status word, scratch, launch overrides) on one device.
+    Calls on one context share its scratch and must follow one another on
+    the GPU (one stream, or streams ordered by events); work meant to
+    overlap on several streams takes one context per stream."""
 
     def __init__(self, device: int | None = None):
         self._lib = L.load()
