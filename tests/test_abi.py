@@ -71,3 +71,31 @@ def test_product_path_has_no_oracle_or_fallback():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "liboracle" not in txt, f
+
+
+# entry points whose first argument is the context (every compute call)
+_CTX_CALLS = ("smc_destroy", "smc_reserve", "smc_ctx_check", "smc_set_launch", "smc_get_launch",
+              "smc_loglik_batch", "smc_reweight", "smc_ess", "smc_resample_systematic",
+              "smc_gather", "smc_mh_move", "smc_popmcmc_sweep", "pf_step", "smc_rng_words",
+              "smc_rng_normals", "smc_resample_multinomial", "smc_resample_residual",
+              "smc_is_moments", "smc_rng_mrg32k3a", "smc_reweight_resample")
+
+
+def test_every_call_refuses_a_null_context_on_host():
+    """Each compute entry point, called through the binding's own ctypes
+    declarations with a NULL context (pointers NULL, sizes 1), returns
+    SMC_ERR_ARG without touching a device."""
+    from paper_0905_2441_gb300 import _lib
+    lib = _lib.load()
+    for name in _CTX_CALLS:
+        fn = getattr(lib, name)
+        args = []
+        for t in fn.argtypes:
+            if t in (ctypes.c_float, ctypes.c_double):
+                args.append(1.0)
+            elif isinstance(t, type) and issubclass(t, ctypes._SimpleCData) and t is not ctypes.c_void_p:
+                args.append(1)
+            else:  # void* and typed pointers
+                args.append(None)
+        assert fn(*args) == -1, name
+    assert lib.smc_create(None, 0) == -1
