@@ -52,6 +52,23 @@ smc_status ensure_popdone(smc_ctx* ctx, int64_t n, cudaStream_t s) {
     return SMC_OK;
 }
 
+smc_status ensure_groups(smc_ctx* ctx, int64_t n, cudaStream_t s) {
+    if (n <= ctx->grp_cap) return SMC_OK;
+    if (capturing(s)) return SMC_ERR_ARG;
+    int64_t cap = n + n / 4 + 64;
+    SMC_CUDA(cudaStreamSynchronize(s));
+    if (ctx->d_grpdone) SMC_CUDA(cudaFree(ctx->d_grpdone));
+    if (ctx->d_grppart) SMC_CUDA(cudaFree(ctx->d_grppart));
+    ctx->d_grpdone = nullptr;
+    ctx->d_grppart = nullptr;
+    ctx->grp_cap = 0;
+    SMC_CUDA(cudaMalloc(&ctx->d_grpdone, (size_t)cap * sizeof(uint32_t)));
+    SMC_CUDA(cudaMemset(ctx->d_grpdone, 0, (size_t)cap * sizeof(uint32_t)));
+    SMC_CUDA(cudaMalloc(&ctx->d_grppart, (size_t)cap * 64 * sizeof(double)));
+    ctx->grp_cap = cap;
+    return SMC_OK;
+}
+
 void launch_shape(const smc_ctx* ctx, int op, int64_t M, int64_t N, int K, int* lanes,
                   int* threads) {
     if (op >= 0 && op < SMC_OP_COUNT && ctx->lanes[op] > 0) {
@@ -136,6 +153,8 @@ extern "C" smc_status smc_destroy(smc_ctx* ctx) {
     if (ctx->d_partials) cudaFree(ctx->d_partials);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->d_popdone) cudaFree(ctx->d_popdone);
+    if (ctx->d_grpdone) cudaFree(ctx->d_grpdone);
+    if (ctx->d_grppart) cudaFree(ctx->d_grppart);
     if (ctx->d_mrg_pow) cudaFree(ctx->d_mrg_pow);
     delete ctx;
     return SMC_OK;
@@ -150,6 +169,8 @@ extern "C" smc_status smc_reserve(smc_ctx* ctx, int64_t max_particles, int32_t m
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
     st = ensure_popdone(ctx, max_pops, nullptr);
+    if (st != SMC_OK) return st;
+    st = ensure_groups(ctx, (max_particles + 31) / 32, nullptr);
     if (st != SMC_OK) return st;
     const size_t a = smc_resample_ws_bytes(max_particles);
     const size_t b = smc_resample_var_ws_bytes(max_particles);

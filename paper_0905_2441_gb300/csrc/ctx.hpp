@@ -23,6 +23,11 @@ struct smc_ctx {
     // per-population completion counters of the population sweep (zeroed)
     uint32_t* d_popdone = nullptr;
     int64_t popdone_cap = 0;
+    // binned sweep: per chain group of 32, an arrival counter (zeroed) and
+    // the two parts of a group cut by a CTA boundary (double[2][32])
+    uint32_t* d_grpdone = nullptr;
+    double* d_grppart = nullptr;
+    int64_t grp_cap = 0;
     // MRG32k3a skip-ahead table: A1^(2^k), A2^(2^k), k < 64 (filled at creation)
     uint32_t* d_mrg_pow = nullptr;
     int32_t lanes[SMC_OP_COUNT] = {0, 0, 0};
@@ -84,6 +89,10 @@ smc_status ensure_ws(smc_ctx* ctx, size_t bytes, cudaStream_t s);
 
 // Make sure there are n zeroed population counters; grows only outside capture.
 smc_status ensure_popdone(smc_ctx* ctx, int64_t n, cudaStream_t s);
+
+// Make sure there are n zeroed chain-group counters and their part buffers
+// (binned population sweep); grows only outside capture.
+smc_status ensure_groups(smc_ctx* ctx, int64_t n, cudaStream_t s);
 
 // Set the context's device current for the calling thread.
 smc_status use_device(smc_ctx* ctx);

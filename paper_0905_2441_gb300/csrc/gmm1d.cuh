@@ -41,6 +41,9 @@ struct Gmm1dArgs {
     float r;            // sqrt(log2(e) / (2 sigma^2))
     float gscale;       // 1 / (sigma^2 r)
     float lo, hi;       // prior box
+    float cf;           // log2(e) / (2 sigma^2)
+    float binw;         // bin width of the binned form: largest power of 2 with cf (w/2)^2 <= 4
+    float binw_inv;     // 1 / binw (a power of two)
     double cst;         // N (-1/2 ln(2 pi sigma^2)) [+ N ln w when weights are equal]
     float lw2[kMaxK1d]; // log2 w_k (padding components: -inf)
 };

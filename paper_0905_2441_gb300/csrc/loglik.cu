@@ -146,6 +146,10 @@ smc_status gmm1d_prepare(const smc_gmm* model, int64_t N, smc::Gmm1dArgs* P, int
     while (kp < K) kp *= 2;
     double s = (double)model->sigma;
     P->r = (float)std::sqrt(smc::kLog2e / (2.0 * s * s));
+    P->cf = (float)(smc::kLog2e / (2.0 * s * s));
+    // w = 2^floor(log2(4 / sqrt(cf))), so that cf (w/2)^2 <= 4
+    P->binw = (float)std::ldexp(1.0, (int)std::floor(std::log2(4.0 / std::sqrt((double)P->cf))));
+    P->binw_inv = 1.0f / P->binw;
     P->gscale = (float)(1.0 / (s * s * (double)P->r));
     P->lo = model->lo;
     P->hi = model->hi;

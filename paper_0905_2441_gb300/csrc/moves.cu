@@ -5,6 +5,7 @@
 #include <cmath>
 
 #include "ctx.hpp"
+#include "binned.cuh"
 #include "gmm1d.cuh"
 
 using namespace smc_host;
@@ -245,6 +246,109 @@ __device__ __forceinline__ uint32_t atomic_add_acq_rel(uint32_t* p, uint32_t v) 
     return old;
 }
 
+// Warp 0 of a CTA finds the first population overlapping chain c0 (a 32-way
+// parallel search of the CSR offsets) and the bounds [qa, qb) of population
+// qlo + lane; the whole warp calls this.
+__device__ __forceinline__ void pop_search(const int32_t* __restrict__ offsets, int n_pops,
+                                           int64_t c0, int l32, int& qlo, int64_t& qa,
+                                           int64_t& qb) {
+    int qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
+    while (qhi - qlo > 1) {
+        // 32 probes split [qlo, qhi) into 33 parts
+        const int span = qhi - qlo;
+        const int probe = qlo + (int)(((int64_t)span * (l32 + 1)) / 33);
+        const bool inside = probe > qlo && probe < qhi;
+        const int64_t op = inside ? (int64_t)offsets[probe] : 0;
+        const unsigned m = __ballot_sync(0xFFFFFFFFu, inside && op <= c0);
+        const unsigned gt = __ballot_sync(0xFFFFFFFFu, inside && op > c0);
+        int nlo = qlo, nhi = qhi;
+        if (m) nlo = __shfl_sync(0xFFFFFFFFu, probe, 31 - __clz(m));
+        if (gt) nhi = __shfl_sync(0xFFFFFFFFu, probe, __ffs(gt) - 1);
+        if (nlo == qlo && nhi == qhi) {  // fewer than 33 candidates left: scan
+            const int cand = qlo + 1 + l32;
+            const bool le2 = cand < qhi && (int64_t)offsets[cand] <= c0;
+            const unsigned m2 = __ballot_sync(0xFFFFFFFFu, le2);
+            if (m2) nlo = qlo + 1 + (31 - __clz(m2));
+            nhi = nlo + 1;
+        }
+        qlo = nlo;
+        qhi = nhi;
+    }
+    const int q = qlo + l32;
+    if (q < n_pops) {
+        qa = offsets[q];
+        qb = offsets[q + 1];
+    }
+}
+
+// After a CTA's moves of chains [c0, c1): count them per population (one
+// lane of warp 0 per touched population adds its count with release
+// semantics, publishing the moves); the lane whose add completes a
+// population acquires every other CTA's moves of it and lists it; then the
+// CTA runs the exchange moves of the populations it completed, their pairs
+// dealt over all its threads, and clears their counters for the next sweep.
+// The whole block calls this; (qlo, qa, qb) come from pop_search in warp 0.
+template <int K>
+__device__ __forceinline__ void pop_exchange(float* theta, double* ll, int64_t Mtot,
+                                             const float* __restrict__ beta,
+                                             const int32_t* __restrict__ offsets, int n_pops,
+                                             uint64_t seed, uint64_t sweep, uint32_t* pop_done,
+                                             int64_t c0, int64_t c1, int qlo, int64_t qa,
+                                             int64_t qb, int4* exb, int* s_nex, uint32_t* s_sw,
+                                             uint32_t* s_try, int Kreal) {
+    const int warp = threadIdx.x >> 5, l32 = threadIdx.x & 31;
+    if (threadIdx.x == 0) *s_nex = 0;
+    __syncthreads();  // the moves are done (and ordered before warp 0's release)
+    if (warp == 0) {
+        for (int q = qlo + l32;; q += 32) {
+            if (q >= qlo + 32 && q < n_pops) {  // beyond the prefetched 32 (rare)
+                qa = offsets[q];
+                qb = offsets[q + 1];
+            }
+            const bool in = q < n_pops && qa < c1;
+            if (!__any_sync(0xFFFFFFFFu, in)) break;
+            if (in) {
+                const int64_t a = qa > c0 ? qa : c0;
+                const int64_t b2 = qb < c1 ? qb : c1;
+                if (b2 > a) {
+                    const uint32_t cnt = (uint32_t)(b2 - a);
+                    const uint32_t Mq = (uint32_t)(qb - qa);
+                    const uint32_t old = atomic_add_acq_rel(pop_done + q, cnt);
+                    if (old + cnt == Mq) {
+                        const uint32_t par =
+                            draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
+                        exb[atomicAdd(s_nex, 1)] = make_int4(q, (int)qa, (int)Mq, (int)par);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int nex = *s_nex;
+    if (nex) {
+        int total = 0;
+        for (int e = 0; e < nex; ++e) total += exchange_npairs(exb[e].z, (uint32_t)exb[e].w);
+        uint32_t swaps = 0;
+        for (int t = threadIdx.x; t < total; t += blockDim.x) {
+            int e = 0, j = t;
+            for (;;) {  // entry holding task t (nex is small)
+                const int np = exchange_npairs(exb[e].z, (uint32_t)exb[e].w);
+                if (j < np) break;
+                j -= np;
+                ++e;
+            }
+            const int4 d = exb[e];
+            swaps += exchange_pair<K>(theta, ll, Mtot, beta, d.y, d.z, (uint32_t)d.w, d.x, j, Kreal,
+                                      seed, sweep);
+        }
+        if (swaps) atomicAdd(s_sw, swaps);
+        for (int e = threadIdx.x; e < nex; e += blockDim.x) {
+            pop_done[exb[e].x] = 0u;
+            atomicAdd(s_try, (uint32_t)exchange_npairs(exb[e].z, (uint32_t)exb[e].w));
+        }
+    }
+}
+
 // Consecutive sweeps use programmatic dependent launch: the next sweep's
 // prologue (data staging, random draws, population search: nothing a sweep
 // writes) overlaps this one's tail; grid_dep_wait() precedes the chain state.
@@ -294,35 +398,7 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
         const float b = active ? beta[c] : 0.0f;
         int qlo = 0;
         int64_t qa = 0, qb = 0;  // bounds of population qlo + l32 (warp 0)
-        if (inline_ex && warp == 0) {
-            int qhi = n_pops;  // offsets[qlo] <= c0 < offsets[qhi]
-            while (qhi - qlo > 1) {
-                // 32 probes split [qlo, qhi) into 33 parts
-                const int span = qhi - qlo;
-                const int probe = qlo + (int)(((int64_t)span * (l32 + 1)) / 33);
-                const bool inside = probe > qlo && probe < qhi;
-                const int64_t op = inside ? (int64_t)offsets[probe] : 0;
-                const unsigned m = __ballot_sync(0xFFFFFFFFu, inside && op <= c0);
-                const unsigned gt = __ballot_sync(0xFFFFFFFFu, inside && op > c0);
-                int nlo = qlo, nhi = qhi;
-                if (m) nlo = __shfl_sync(0xFFFFFFFFu, probe, 31 - __clz(m));
-                if (gt) nhi = __shfl_sync(0xFFFFFFFFu, probe, __ffs(gt) - 1);
-                if (nlo == qlo && nhi == qhi) {  // fewer than 33 candidates left: scan
-                    const int cand = qlo + 1 + l32;
-                    const bool le2 = cand < qhi && (int64_t)offsets[cand] <= c0;
-                    const unsigned m2 = __ballot_sync(0xFFFFFFFFu, le2);
-                    if (m2) nlo = qlo + 1 + (31 - __clz(m2));
-                    nhi = nlo + 1;
-                }
-                qlo = nlo;
-                qhi = nhi;
-            }
-            const int q = qlo + l32;
-            if (q < n_pops) {
-                qa = offsets[q];
-                qb = offsets[q + 1];
-            }
-        }
+        if (inline_ex && warp == 0) pop_search(offsets, n_pops, c0, l32, qlo, qa, qb);
         // ---- the state of the chains: written by the previous sweep
         if (iter == 0) grid_dep_wait();
         float mu[K], prop[K], nu[K];
@@ -378,66 +454,281 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
         ++iter;
         if (!inline_ex) continue;  // the exchanges run in k_popmcmc_exchange
         const int buf = (int)((iter - 1) & 1);  // double-buffered list: no third barrier
-        if (threadIdx.x == 0) s_nex[buf] = 0;
-        __syncthreads();  // the item's moves are done (and ordered before warp 0's release)
-        // ---- count the item's chains per population: one lane per touched
-        // population adds its count with release semantics (publishing the
-        // moves above); the lane whose add completes a population acquires
-        // every other CTA's moves of it and lists it for exchange
-        if (warp == 0) {
-            for (int q = qlo + l32;; q += 32) {
-                if (q >= qlo + 32 && q < n_pops) {  // beyond the prefetched 32 (rare)
-                    qa = offsets[q];
-                    qb = offsets[q + 1];
-                }
-                const bool in = q < n_pops && qa < c1;
-                if (!__any_sync(0xFFFFFFFFu, in)) break;
-                if (in) {
-                    const int64_t a = qa > c0 ? qa : c0;
-                    const int64_t b2 = qb < c1 ? qb : c1;
-                    if (b2 > a) {
-                        const uint32_t cnt = (uint32_t)(b2 - a);
-                        const uint32_t Mq = (uint32_t)(qb - qa);
-                        const uint32_t old = atomic_add_acq_rel(pop_done + q, cnt);
-                        if (old + cnt == Mq) {
-                            const uint32_t par =
-                                draw(seed, RNG_EXCHANGE, sweep, (uint32_t)q, 0u).x & 1u;
-                            s_exb[buf * lcap + atomicAdd(&s_nex[buf], 1)] =
-                                make_int4(q, (int)qa, (int)Mq, (int)par);
-                        }
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        // ---- exchange moves of the populations this item completed: their
-        // pairs are dealt over all threads of the block
-        const int nex = s_nex[buf];
-        if (nex) {
-            const int4* ex = s_exb + buf * lcap;
-            int total = 0;
-            for (int e = 0; e < nex; ++e) total += exchange_npairs(ex[e].z, (uint32_t)ex[e].w);
-            uint32_t swaps = 0;
-            for (int t = threadIdx.x; t < total; t += blockDim.x) {
-                int e = 0, j = t;
-                for (;;) {  // entry holding task t (nex is small)
-                    const int np = exchange_npairs(ex[e].z, (uint32_t)ex[e].w);
-                    if (j < np) break;
-                    j -= np;
-                    ++e;
-                }
-                const int4 d = ex[e];
-                swaps += exchange_pair<K>(theta, ll, Mtot, beta, d.y, d.z, (uint32_t)d.w, d.x, j,
-                                          Kreal, seed, sweep);
-            }
-            if (swaps) atomicAdd(&s_sw, swaps);
-            for (int e = threadIdx.x; e < nex; e += blockDim.x) {
-                pop_done[ex[e].x] = 0u;
-                atomicAdd(&s_try, (uint32_t)exchange_npairs(ex[e].z, (uint32_t)ex[e].w));
-            }
-        }
+        pop_exchange<K>(theta, ll, Mtot, beta, offsets, n_pops, seed, sweep, pop_done, c0, c1,
+                        qlo, qa, qb, s_exb + buf * lcap, &s_nex[buf], &s_sw, &s_try, Kreal);
     }
     if (iter == 0) grid_dep_wait();  // a block without items still orders its stats
+    __syncthreads();
+    if (threadIdx.x == 0 && stats) {
+        if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
+        if (s_sw) atomicAdd(stats + 1, (unsigned long long)s_sw);
+        if (s_try) atomicAdd(stats + 2, (unsigned long long)s_try);
+    }
+}
+
+// ------------------------------------------------------------------ binned population sweep
+// The sweep for data sets held whole in shared memory (1 <= N <= 4096,
+// K <= 16), with the data sorted into bins once per sweep by every CTA
+// (binned.cuh).  A warp's 32 lanes take 32 consecutive chains (a chain
+// group) over the same slots of the sorted list, so bins, loop counts and
+// shared-memory loads are uniform across the warp.  The work, G groups x H
+// pair slots (H = half the list's padded length), is split evenly over the
+// CTAs (one 512-thread CTA per SM) as contiguous ranges of the group-major
+// order.  A CTA works in rounds of at most 16 groups: its threads draw the
+// round's normals (one Box-Muller pair or accept word per task) and propose;
+// its warps then take chunks (a piece of one bin of one group: one setup of
+// the bin's coefficients each) from a shared-memory queue, largest pieces
+// first, so they finish together whatever the warp scheduler favours.  Each
+// chunk's partial sum enters its chain's total as an exact 2^-32 fixed-point
+// integer, so the totals do not depend on the order chunks finish in.  A
+// group cut by a CTA boundary (at most two parts: the grid never has more
+// CTAs than groups) stores its part in the context and bumps the group's
+// counter; the CTA that brings the counter to two adds the two parts.  The
+// group's chains then take their accept decisions, and the exchange stage is
+// the same as in k_popmcmc_sweep.
+constexpr int kBinThreads = 512;
+constexpr int kOffSmem = 4096;   // population offsets staged in shared memory up to this count
+
+__host__ __device__ inline int binned_yb_len(int64_t N) {
+    return (int)((N + kClasses + 3) & ~(int64_t)3);
+}
+__host__ __device__ inline int binned_rk_len(int64_t N) {  // floats holding N uint16 ranks
+    return (int)(((N + 1) / 2 + 3) & ~(int64_t)3);
+}
+// dynamic shared memory: staged data, mbarrier, sorted list, ranks, the
+// chains' fixed-point totals [16 groups][32 lanes], then per chain slot: old
+// log-likelihood, proposal (normals before it), temperature, accept word,
+// in-box flag; last the population offsets (when at most kOffSmem + 1)
+__host__ __device__ inline size_t binned_smem_bytes(int64_t N, int K, int64_t n_pops) {
+    const int yc = ychunk_for(N);
+    const size_t off = n_pops + 1 <= kOffSmem ? (size_t)(n_pops + 1) * 4 : 0;
+    return ((size_t)yc + 4 + (size_t)binned_yb_len(N) + (size_t)binned_rk_len(N)) * 4 +
+           (size_t)kBinThreads * 8 + (size_t)kBinThreads * (8 + 4 * (size_t)K + 12) + off;
+}
+
+// first pair slot of CTA b's range: floor(b Wt / B)
+__device__ __forceinline__ int64_t cta_first(int64_t b, int64_t Wt, int64_t B) {
+    return b * Wt / B;
+}
+// the CTA whose range holds slot x
+__device__ __forceinline__ int64_t cta_of(int64_t x, int64_t Wt, int64_t B) {
+    int64_t b = x * B / Wt;
+    while (b > 0 && cta_first(b, Wt, B) > x) --b;
+    while (b + 1 < B && cta_first(b + 1, Wt, B) <= x) ++b;
+    return b;
+}
+
+template <int K>
+__global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
+    const float* __restrict__ y, int64_t N, float* theta, double* ll, int64_t Mtot,
+    const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
+    float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
+    uint32_t* grp_done, long long* grp_part, Gmm1dArgs P, int Kreal, int inline_ex,
+    uint32_t* status) {
+    grid_dep_launch();
+    extern __shared__ __align__(16) float sm[];
+    constexpr int T = kBinThreads, NW = T / 32;
+    const int yc = ychunk_for(N);
+    float* ys = sm;
+    float* yb = ys + yc + 4;
+    uint16_t* rk = reinterpret_cast<uint16_t*>(yb + binned_yb_len(N));
+    long long* s_acc = reinterpret_cast<long long*>(yb + binned_yb_len(N) + binned_rk_len(N));
+    double* s_lold = reinterpret_cast<double*>(s_acc + T);
+    float* s_prop = reinterpret_cast<float*>(s_lold + T);
+    float* s_beta = s_prop + K * T;
+    uint32_t* s_aw = reinterpret_cast<uint32_t*>(s_beta + T);
+    int* s_inb = reinterpret_cast<int*>(s_aw + T);
+    int32_t* s_off = reinterpret_cast<int32_t*>(s_inb + T);
+    __shared__ BinTable bt;
+    __shared__ int3 s_piece[kMaxPieces];
+    __shared__ int4 s_exb[T + 1];
+    __shared__ int s_nex, s_next, s_np;
+    __shared__ int s_fin[NW];  // a round's groups decided by this CTA
+    __shared__ uint32_t s_mh, s_sw, s_try;
+    init_mbar(ychunk_mbar(ys, yc));
+    if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
+    const int tid = (int)threadIdx.x, warp = tid >> 5, l32 = tid & 31;
+    // the chain groups of this CTA: [gA, gEnd) with gA = floor(b G / B) and
+    // gEnd <= ceil((b + 1) G / B) (both exact whatever H is)
+    const int64_t G = (Mtot + 31) >> 5;
+    const int64_t B = gridDim.x;
+    const int64_t gA = (int64_t)blockIdx.x * G / B;
+    const int64_t gEub = ((int64_t)blockIdx.x + 1) * G / B +
+                         ((((int64_t)blockIdx.x + 1) * G) % B != 0 ? 1 : 0);
+    const int npair = (Kreal + 1) >> 1;  // Box-Muller pairs per chain
+    // Draws of round g0 (nothing a sweep writes): task t is Box-Muller pair
+    // t % (npair + 1) of chain slot t / (npair + 1), or its accept word; the
+    // normals wait in s_prop.  Also the temperatures (read-only).
+    auto round_draws = [&](int64_t g0, int nslot) {
+        const int64_t cfirst = g0 * 32;
+        const int64_t cb = cfirst + tid;
+        const float bt_c = (tid < nslot && cb < Mtot) ? beta[cb] : 0.0f;  // stored after the draws
+        for (int t = tid; t < nslot * (npair + 1); t += T) {
+            const int slot = t / (npair + 1), j = t - slot * (npair + 1);
+            const uint32_t c = (uint32_t)(cfirst + slot);
+            if (j == npair) {
+                s_aw[slot] = draw(seed, RNG_ACCEPT, sweep, c, 0u).x;
+            } else {
+                const uint4 w = draw(seed, RNG_MOVE, sweep, c, (uint32_t)(j >> 1));
+                float z0, z1;
+                if (j & 1) box_muller(w.z, w.w, z0, z1);
+                else box_muller(w.x, w.y, z0, z1);
+                s_prop[(2 * j) * T + slot] = z0;
+                if (2 * j + 1 < K) s_prop[(2 * j + 1) * T + slot] = z1;
+            }
+        }
+        s_beta[tid] = bt_c;
+    };
+    // ---- prologue: the data's bulk copy and the offsets' loads go out first,
+    // the first round's draws and an L2 prefetch of its chain states overlap
+    // them (a prefetch reads no value; the states are read after the wait)
+    uint32_t phase = 0;
+    const bool bulk = stage_y_issue(ys, y, 0, (int)N, ychunk_mbar(ys, yc));
+    // (each thread's first offset is loaded into a register and stored after
+    // the draws, so the thread does not wait for it)
+    const int32_t* offs = offsets;
+    const bool off_smem = inline_ex && n_pops + 1 <= kOffSmem;
+    int32_t off0 = 0;
+    if (off_smem) {
+        if (tid <= n_pops) off0 = offsets[tid];
+        for (int i = tid + T; i <= n_pops; i += T) s_off[i] = offsets[i];
+        offs = s_off;
+    }
+    {
+        const int64_t ng0 = (gEub - gA) < NW ? (gEub - gA) : NW;
+        const int64_t c = gA * 32 + tid;
+        if (tid < ng0 * 32 && c < Mtot) {
+            for (int k = 0; k < Kreal; ++k)
+                asm volatile("prefetch.global.L2 [%0];" :: "l"(theta + (int64_t)k * Mtot + c));
+            asm volatile("prefetch.global.L2 [%0];" :: "l"(ll + c));
+        }
+        round_draws(gA, (int)(ng0 * 32));
+    }
+    if (off_smem && tid <= n_pops) s_off[tid] = off0;
+    stage_y_wait(bulk, ychunk_mbar(ys, yc), phase, status);
+    // ---- the data sorted into bins, cut into pieces
+    bin_partition(ys, (int)N, yb, rk, bt, P.binw, P.binw_inv, P.cf);
+    bin_pieces(bt, s_piece, &s_np);
+    __syncthreads();
+    const int np = s_np;
+    const int64_t H = bt.start[kClasses] >> 1;
+    const int64_t Wt = G * H;
+    const int64_t R0 = cta_first(blockIdx.x, Wt, B), R1 = cta_first(blockIdx.x + 1, Wt, B);
+    const int64_t gEnd = R1 > R0 ? (R1 - 1) / H + 1 : gA;
+    bool first = true;
+    for (int64_t g0 = gA; g0 < gEnd; g0 += NW) {
+        const int ng = (int)((gEnd - g0) < NW ? (gEnd - g0) : NW);
+        const int64_t cfirst = g0 * 32;
+        const int nslot = ng * 32;
+        if (!first) round_draws(g0, nslot);
+        int qlo = 0;
+        int64_t qa = 0, qb = 0;
+        if (inline_ex && warp == 0) pop_search(offs, n_pops, cfirst, l32, qlo, qa, qb);
+        if (threadIdx.x == 0) s_next = 0;
+        s_acc[tid] = 0;
+        __syncthreads();
+        // ---- the chains' states: written by the previous sweep
+        if (first) {
+            grid_dep_wait();
+            first = false;
+        }
+        {
+            const int64_t c = cfirst + tid;
+            const bool mine = tid < nslot && c < Mtot;
+            bool inb = mine;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                float pk = 0.0f;
+                if (mine && k < Kreal) {
+                    pk = fmaf(scale, s_prop[k * T + tid], theta[(int64_t)k * Mtot + c]);
+                    inb &= (pk >= P.lo) & (pk <= P.hi);
+                }
+                s_prop[k * T + tid] = pk;
+            }
+            s_lold[tid] = mine ? ll[c] : 0.0;
+            s_inb[tid] = inb ? 1 : 0;
+        }
+        __syncthreads();
+        // ---- chunks of the round's slots [P0, P1) from a queue: chunk ci is
+        // piece ci / ng of group ci % ng (largest pieces first)
+        const int64_t P0 = R0 > g0 * H ? R0 : g0 * H;
+        const int64_t P1 = R1 < (g0 + ng) * H ? R1 : (g0 + ng) * H;
+#pragma unroll 1
+        for (;;) {
+            int ci = 0;
+            if (l32 == 0) ci = atomicAdd(&s_next, 1);
+            ci = __shfl_sync(0xFFFFFFFFu, ci, 0);
+            if (ci >= np * ng) break;
+            const int j = ci / ng, gs = ci - j * ng;
+            const int64_t gb = (g0 + gs) * H;
+            const int3 pc = s_piece[j];
+            // the piece clipped to this CTA's slots of the group (even bounds)
+            int a = pc.x, b = pc.y;
+            if (gb * 2 + a < P0 * 2) a = (int)(P0 * 2 - gb * 2);
+            if (gb * 2 + b > P1 * 2) b = (int)(P1 * 2 - gb * 2);
+            if (b <= a) continue;
+            BinnedAcc<K> acc;
+            acc.piece(yb, bt, a, b, pc.z, s_prop + gs * 32 + l32, T, P.lw2, P.cf, P.r);
+            const float2 pp = acc.partial();
+            atomicAdd(reinterpret_cast<unsigned long long*>(s_acc + gs * 32 + l32),
+                      (unsigned long long)(fixed32(pp.x) - fixed32(pp.y)));
+        }
+        __syncthreads();
+        // ---- warp gs: the chains of group g0 + gs
+        bool ok = false;
+        if (warp < ng) {
+            const int64_t g = g0 + warp;
+            const int64_t x0 = g * H, x1 = x0 + H;
+            long long part = s_acc[warp * 32 + l32];
+            bool fin = true;
+            if (x0 < R0 || x1 > R1) {  // cut by a CTA boundary: two parts
+                const int64_t b0 = cta_of(x0, Wt, B);
+                const int k = (int)(blockIdx.x - b0);
+                grp_part[(g * 2 + k) * 32 + l32] = part;
+                __syncwarp();
+                uint32_t old = 0;
+                if (l32 == 0) old = atomic_add_acq_rel(grp_done + g, 1u);
+                old = __shfl_sync(0xFFFFFFFFu, old, 0);
+                fin = old == 1u;
+                if (fin) {
+                    part = __ldcg(grp_part + (g * 2) * 32 + l32) +
+                           __ldcg(grp_part + (g * 2 + 1) * 32 + l32);
+                    if (l32 == 0) grp_done[g] = 0u;
+                }
+            }
+            const int slot = warp * 32 + l32;
+            const int64_t cc = g * 32 + l32;
+            if (fin && cc < Mtot && s_inb[slot]) {
+                const double lp = ((double)part * 0x1p-32 + bt.dconst) * kLn2 + P.cst;
+                if (lp != lp) raise_status(status, ST_NONFINITE);
+                ok = accept(s_aw[slot], tempered_diff(s_beta[slot], lp, s_lold[slot]));
+                if (ok) {
+#pragma unroll
+                    for (int k = 0; k < K; ++k)
+                        if (k < Kreal) theta[(int64_t)k * Mtot + cc] = s_prop[k * T + slot];
+                    ll[cc] = lp;
+                }
+            }
+            if (l32 == 0) s_fin[warp] = fin ? 1 : 0;
+        }
+        const unsigned acc_mask = __ballot_sync(0xFFFFFFFFu, ok);
+        if (l32 == 0 && acc_mask) atomicAdd(&s_mh, (uint32_t)__popc(acc_mask));
+        __syncthreads();
+        if (inline_ex) {
+            // the groups of this round decided here: a contiguous run (only
+            // the first and the last can have been decided by a neighbour)
+            int ga = 0, gz = ng;
+            while (ga < ng && !s_fin[ga]) ++ga;
+            while (gz > ga && !s_fin[gz - 1]) --gz;
+            const int64_t c0 = (g0 + ga) * 32;
+            int64_t c1 = (g0 + gz) * 32;
+            if (c1 > Mtot) c1 = Mtot;
+            pop_exchange<K>(theta, ll, Mtot, beta, offs, n_pops, seed, sweep, pop_done, c0,
+                            c1 > c0 ? c1 : c0, qlo, qa, qb, s_exb, &s_nex, &s_sw, &s_try, Kreal);
+        }
+        __syncthreads();  // the round's shared arrays are free again
+    }
+    if (first) grid_dep_wait();  // a block without chains still orders its stats
     __syncthreads();
     if (threadIdx.x == 0 && stats) {
         if (s_mh) atomicAdd(stats + 0, (unsigned long long)s_mh);
@@ -532,12 +823,57 @@ static smc_status dispatch_move(bool mala, bool eqw, int blocks, int threads, cu
 #define SMC_POP_PDL 1
 #endif
 
+// The binned sweep (data held whole in shared memory): one 512-thread CTA
+// per SM, each with an equal share of the work.
+template <int K>
+static smc_status launch_pop_binned(smc_ctx* ctx, cudaStream_t s, const float* y,
+                                    int64_t N, float* th, double* l, int64_t Mt, const float* beta,
+                                    const int32_t* off, int32_t n_pops, float scale, uint64_t seed,
+                                    uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P,
+                                    int Kr, bool inline_ex) {
+    auto kern = smc::k_popmcmc_binned<K>;
+    const int threads = smc::kBinThreads;
+    const size_t smem = smc::binned_smem_bytes(N, K, n_pops);
+    SMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // at most one CTA per chain group of 32 (so a group meets at most two CTAs)
+    const int64_t groups = (Mt + 31) / 32;
+    smc_status st0 = ensure_groups(ctx, groups, s);
+    if (st0 != SMC_OK) return st0;
+    int64_t grid = ctx->num_sms;
+    if (grid > groups) grid = groups;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = SMC_POP_PDL;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    smc_status st = cuda_ok(cudaLaunchKernelEx(
+        &cfg, kern, y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
+        reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, ctx->d_grpdone,
+        reinterpret_cast<long long*>(ctx->d_grppart), P, Kr, inline_ex ? 1 : 0, ctx->d_status));
+    if (st != SMC_OK || inline_ex) return st;
+    int64_t xb = (Mt + 255) / 256;
+    if (xb > (int64_t)ctx->num_sms * 8) xb = (int64_t)ctx->num_sms * 8;
+    return launch_pdl(smc::k_popmcmc_exchange<K>, dim3((unsigned)xb), dim3(256), 0, s, th, l, Mt,
+                      beta, off, n_pops, seed, sweep, reinterpret_cast<unsigned long long*>(stats),
+                      Kr);
+}
+
 template <int K, bool EQW>
 static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const float* y,
                              int64_t N, float* th, double* l, int64_t Mt, const float* beta,
                              const int32_t* off, int32_t n_pops, float scale, uint64_t seed,
                              uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P, int L,
                              int Kr, bool inline_ex) {
+    if constexpr (K <= 16) {
+        if (N >= 1 && N <= smc::kBinnedMaxN)
+            return launch_pop_binned<K>(ctx, s, y, N, th, l, Mt, beta, off, n_pops, scale, seed,
+                                        sweep, stats, P, Kr, inline_ex);
+    }
     auto kern = smc::k_popmcmc_sweep<K, EQW>;
     const int yc = smc::ychunk_for(N);
     size_t smem = smc::ysmem_bytes(yc) + 2 * (size_t)(threads / L + 1) * sizeof(int4);

@@ -103,7 +103,9 @@ def test_inline_and_split_exchange_agree(env):
     """The same populations swept with the in-sweep exchange (many small
     populations) and with the grid-wide exchange launch (the same chains
     regrouped so the average population is large): chains of populations
-    common to both give identical results."""
+    common to both take the same moves and swaps.  Their log-likelihoods
+    agree to the rounding of the FP32 partial sums, whose split over the
+    data follows the launch geometry (here two different chain counts)."""
     P, S, ctx = env
     w = synth.PAPER_TABLES
     y = w.data()
@@ -124,7 +126,7 @@ def test_inline_and_split_exchange_agree(env):
         res[name] = (np_(tt), np_(lt))
     # population 0 (chains 0..63) is the same population in both layouts
     assert np.array_equal(res["inline"][0][:, :64], res["split"][0][:, :64])
-    assert np.array_equal(res["inline"][1][:64], res["split"][1][:64])
+    np.testing.assert_allclose(res["inline"][1][:64], res["split"][1][:64], rtol=1e-7, atol=0)
 
 
 @pytest.mark.parametrize("kind", [0, 1])
