@@ -298,6 +298,13 @@ def cpu_popmcmc_all_cores(budget_s=8.0, per_worker=16):
 
 # ------------------------------------------------------------------ GPU workloads
 def bench_popmcmc(args, torch, dist):
+    """The configured workload: 512 populations, 34,591 chains, K = 8,
+    N = 1000, one persistent launch per sweep, 1000 sweeps captured in one
+    CUDA graph.  One step = one replay of that graph (the sweep counters are
+    fixed at capture), the L2 flushed before every step outside its events.
+    The plain form (one launch per sweep, L2 flushed before each) is timed
+    beside it, as is the end-to-end form through the public API with host
+    buffers."""
     import paper_0905_2441_gb300 as P
     from paper_0905_2441_gb300 import autotune, samplers
     import synth
@@ -310,17 +317,32 @@ def bench_popmcmc(args, torch, dist):
     model = P.GMM(w.K, w.sigma)
     smp = samplers.PopulationMCMC(ctx, model, y, off, beta, th0, scale=w.scale, seed=3 + dist.rank)
     M, N = smp.M, w.N
-    # launch shape: autotuned on this workload (cached per GPU model)
-    lanes, threads, tune = autotune.tune_popmcmc(ctx, smp, use_cache=not args.retune)
+    # launch shape: the binned sweep (data in shared memory) has one shape;
+    # the lanes-per-chain sweep (longer data) is autotuned
+    binned = 1 <= N <= 4096 and w.K <= 16
+    if binned:
+        lanes, threads, tune = 0, 512, {"binned": "one 512-thread CTA per SM, chain groups of 32"}
+    else:
+        lanes, threads, tune = autotune.tune_popmcmc(ctx, smp, use_cache=not args.retune)
     smp.theta.copy_(torch.from_numpy(th0).cuda())
     P.loglik_batch(ctx, model, smp.y, smp.theta, out=smp.ll)
     ctx.check()
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for s in range(args.warmup):
-        smp.sweep(s)
+    S = args.graph_sweeps
+    # ---- the captured run of S sweeps
+    capt = torch.cuda.Stream()
+    capt.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(capt):
+        with torch.cuda.graph(g, stream=capt):
+            for i in range(S):
+                smp.sweep(100_000 + i)
+    stream.wait_stream(capt)
+    for _ in range(args.warmup):
+        g.replay()
     torch.cuda.synchronize()
-    # ---- timed: K plain sweeps, L2 flushed before each, CUDA events per sweep
+    # ---- timed: K replays, L2 flushed before each, CUDA events per replay
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
     dist.barrier(torch)
@@ -330,7 +352,7 @@ def bench_popmcmc(args, torch, dist):
         for i in range(args.steps):
             flush.fill_(float(i))
             ev[i][0].record(stream)
-            smp.sweep(args.warmup + i)
+            g.replay()
             ev[i][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
@@ -339,29 +361,27 @@ def bench_popmcmc(args, torch, dist):
     per = [a.elapsed_time(b) for a, b in ev]
     t_dev = sum(per) / 1e3
     t_max = dist.max(torch, t_dev)
-    pd_rank = float(M) * N * args.steps
-    pd_total = dist.sum(torch, pd_rank)
-    value = pd_total / t_max
-    # ---- CUDA-graph form: the configuration's 1000 captured sweeps
-    G = args.graph_sweeps
-    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    capt = torch.cuda.Stream()
-    capt.wait_stream(stream)
-    g = torch.cuda.CUDAGraph()
-    base = args.warmup + args.steps
-    with torch.cuda.stream(capt):
-        with torch.cuda.graph(g, stream=capt):
-            for i in range(G):
-                smp.sweep(base + i)
-    stream.wait_stream(capt)
-    g.replay()  # warm
-    flush.fill_(1.0)
-    ga.record(stream)
-    g.replay()
-    gb.record(stream)
-    gb.synchronize()
-    t_graph = ga.elapsed_time(gb) / 1e3
+    pd_rank = float(M) * N * S * args.steps
+    value = dist.sum(torch, pd_rank) / t_max
+    t_sweep = t_dev / (args.steps * S)
+    # the state after the timed run and one more plain sweep from it, kept
+    # for the oracle's check (outside every timed region)
+    snap = {"theta": smp.theta.cpu().numpy(), "ll": smp.ll.cpu().numpy(), "sweep": 7_000_000}
+    smp.sweep(snap["sweep"])
+    snap["theta1"], snap["ll1"] = smp.theta.cpu().numpy(), smp.ll.cpu().numpy()
     ctx.check()
+    # ---- plain form: one launch per sweep, L2 flushed before each
+    Kp = max(20, min(200, args.steps * 10))
+    evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(Kp)]
+    for i in range(Kp):
+        flush.fill_(float(i))
+        evp[i][0].record(stream)
+        smp.sweep(200_000 + i)
+        evp[i][1].record(stream)
+    torch.cuda.synchronize()
+    ctx.check()
+    t_plain = sum(a.elapsed_time(b) for a, b in evp) / 1e3 / Kp
     # ---- end to end through the public API with host buffers
     # two population groups on two streams (four measured slower: the host
     # then takes longer to issue a step's twelve calls than the GPU to run them)
@@ -375,38 +395,88 @@ def bench_popmcmc(args, torch, dist):
     # ---- roofline: MUFU ops of the sweep kernel vs the measured ex2 rate
     ex2_rate, ex2_ms = measure_peak(P, 0)
     mufu_per_launch = float(M) * N * (w.K + 1)  # K ex2 + 1 lg2 per particle-datum
-    achieved = mufu_per_launch / (t_dev / args.steps)
+    kname = "k_popmcmc_binned<8>" if binned else "k_popmcmc_sweep<8,true>"
     sm_mhz = clk.summary()["sm_mhz"]
-    roof = {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": achieved / 1e9,
-            "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": achieved / ex2_rate,
-            "traffic": profile_traffic("k_popmcmc_sweep"),
-            "kernel": "k_popmcmc_sweep<8,true>",
-            "ops_per_launch": mufu_per_launch,
-            "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
-                           f"{ex2_ms:.2f} ms microbenchmark",
-            # the kernel closes each lane's product of sums with one lg2
-            # per sweep, so the ops it issues are the K ex2 alone
-            "issued_count": "K ex2 per particle-datum (lg2 once per lane per sweep)",
-            "frac_issued_count": (float(M) * N * w.K) / (t_dev / args.steps) / ex2_rate}
+
+    def roofline(t_launch, what):
+        return {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": mufu_per_launch / t_launch / 1e9,
+                "peak": ex2_rate / 1e9, "unit": "Gop/s",
+                "frac": mufu_per_launch / t_launch / ex2_rate,
+                "traffic": profile_traffic("k_popmcmc_binned" if binned else "k_popmcmc_sweep"),
+                "kernel": kname, "ops_per_launch": mufu_per_launch, "launch_time": what,
+                "peak_source": "measured in this run: ex2.approx issue rate, all SMs, "
+                               f"{ex2_ms:.2f} ms microbenchmark",
+                # per datum the kernel issues the K ex2 (the logarithm is taken
+                # once per chain segment, not per datum)
+                "issued_count": "K ex2 per particle-datum",
+                "frac_issued_count": float(M) * N * w.K / t_launch / ex2_rate}
+    roof = roofline(t_sweep, f"average sweep launch inside the captured {S}-sweep run")
+    if sm_mhz:
+        roof["sm_mhz_under_load"] = sm_mhz
     out = {
         "metric": "particle-datum loglik evals/s (population MCMC sweeps)",
         "value": value, "unit": "p*d/s", "n_gpus": dist.world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded mixture data and chain states; no dataset)",
-        "config": {**popmcmc_config(w, M), "lanes_per_chain": lanes, "threads_per_block": threads,
-                   "l2": "256 MiB buffer (2x L2) written before every timed sweep, outside its events",
+        "config": {**popmcmc_config(w, M), "sweeps_per_step": S,
+                   "step": f"one replay of a CUDA graph of {S} sweeps (one launch per sweep, "
+                           "sweep counters fixed at capture)",
+                   "launch": tune.get("binned") if binned else
+                   {"lanes_per_chain": lanes, "threads_per_block": threads},
+                   "l2": "256 MiB buffer (2x L2) written before every timed step, outside its events",
                    "parallelism": f"independent populations per rank x{dist.world}"},
-        "forms": {"plain_per_step": {"value": value, "ms_per_sweep": 1e3 * t_dev / args.steps},
-                  "graph_captured": {"sweeps": G, "value": float(M) * N * G / t_graph,
-                                     "ms_per_sweep": 1e3 * t_graph / G}},
-        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps,
+        "forms": {"graph_captured": {"sweeps": S, "value": float(M) * N / t_sweep,
+                                     "us_per_sweep": 1e6 * t_sweep},
+                  "plain_per_step": {"value": float(M) * N / t_plain, "us_per_sweep": 1e6 * t_plain,
+                                     "sweeps": Kp, "l2": "flushed before every sweep",
+                                     "roofline_frac": roofline(t_plain, "plain")["frac"]}},
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps * S,
         "clocks": clk.summary(), "wall_s": wall, "autotune": tune,
+        "_oracle_check": snap,
     }
-    if sm_mhz:
-        out["roofline"]["sm_mhz_under_load"] = sm_mhz
     ctx.close()
     return out
+
+
+def popmcmc_oracle_check(w, snap, n_chains=400, sample_pops=16):
+    """Observed error against the FP64 oracle (part of the CPU leg, outside
+    every timed region): (1) the relative error of the stored
+    log-likelihoods of sampled chains after the timed run, (2) one plain
+    sweep from that state replayed by the oracle on the first populations:
+    chains that differ, and how many MH decisions lay inside the FP32 band
+    |log alpha - log u| < 5e-3 where the two may legitimately part."""
+    import oracle
+    import synth
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    y, logw = w.data(), w.logw()
+    th, ll = snap["theta"], snap["ll"]
+    M = th.shape[1]
+    idx = np.random.default_rng(11).choice(M, n_chains, replace=False)
+    ref = oracle.gmm1d_loglik(y, logw, w.sigma, th[:, idx])
+    rel = float(np.max(np.abs(ll[idx] - ref) / np.abs(ref)))
+    sub = off[: sample_pops + 1].copy()
+    m = int(sub[-1])
+    beta = synth.population_betas(off)[:m]
+    ths, lls = th[:, :m].copy(), ll[:m].copy()
+    seed = 3
+    rt, rl, _ = oracle.popmcmc_sweep(y, logw, w.sigma, (-10, 10), ths, lls, beta, sub, w.scale,
+                                     seed, snap["sweep"])
+    g_th, g_ll = snap["theta1"][:, :m], snap["ll1"][:m]
+    same = np.all(np.isclose(g_th, rt, rtol=3e-7, atol=2e-6), axis=0) & \
+        np.isclose(g_ll, rl, rtol=1e-5, atol=0)
+    _, _, _, la = oracle.rwmh_move(y, logw, w.sigma, (-10, 10), ths, lls, beta, w.scale, seed,
+                                   snap["sweep"], want_log_alpha=True)
+    lu = np.log(np.array([oracle.u01(int(oracle.draw_words(seed, oracle.P_ACCEPT, snap["sweep"],
+                                                               c, 0)[0])) for c in range(m)]))
+    band = int(np.sum(np.isfinite(la) & (np.abs(la - lu) < 5e-3)))
+    pops_diff = int(sum(1 for q in range(sample_pops) if not same[sub[q]:sub[q + 1]].all()))
+    return {"max_rel_loglik_err": rel, "chains_checked": n_chains,
+            "sweep_replayed": {"populations": sample_pops, "chains": m,
+                               "chains_differing": int((~same).sum()),
+                               "populations_differing": pops_diff,
+                               "mh_decisions_in_fp32_band": band},
+            "tolerance": "relative 1e-5 per log-likelihood"}
 
 
 def e2e_popmcmc(args, torch, P, ctx, smp):
@@ -524,8 +594,11 @@ def bench_secondary(torch, P):
     counters in both forms (bitwise-equal outputs)."""
     from paper_0905_2441_gb300 import samplers
     import synth
-    out = {}
+    out, snaps = {}, {}
     ctx = P.Context()
+    ex2_rate, ex2_ms = measure_peak(P, 0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -554,6 +627,8 @@ def bench_secondary(torch, P):
         t_graph = timed(lambda: g.replay())
         z_graph = smp.log_evidence()
         th_graph = smp.theta[(smp.T) % 2]
+        th_f, ll_f = smp.state
+        snaps[name] = {"w": w, "theta": th_f.cpu().numpy(), "ll": ll_f.cpu().numpy()}
         out[name] = {"workload": w.name, "steps": w.T, "M": w.M, "K": w.K, "N": w.N,
                      "plain_steps_per_s": w.T / t_plain, "graph_steps_per_s": w.T / t_graph,
                      "plain_pd_per_s": w.M * w.N * w.T / t_plain,
@@ -562,6 +637,29 @@ def bench_secondary(torch, P):
                      "graph_equals_plain": bool(torch.equal(th_plain, th_graph)) and z_plain == z_graph,
                      "resampled_steps": int(smp.flags[1:].sum().item())}
         ctx.check()
+        if kind == P.MOVE_MALA:  # the fused likelihood + gradient move kernel, timed alone
+            th, ll = smp.state
+            gsrc = smp.grad[smp.cur]
+            tho, llo, go = torch.empty_like(th), torch.empty_like(ll), torch.empty_like(gsrc)
+            bl = smp.betas[-1:]
+            mv = (lambda: P.mh_move(ctx, smp.model, smp.y, th, ll, tho, llo, bl, w.scale, 99, 1,
+                                    kind=P.MOVE_MALA, grad_in=gsrc, grad_out=go))
+            for _ in range(3):
+                mv()
+            tm = statistics.median([_whole_run(torch, flush, stream, mv) for _ in range(10)])
+            ops = float(w.M) * w.N * (w.K + 1)
+            out[name]["move_ms"] = 1e3 * tm
+            out[name]["roofline"] = {
+                "bound": "alu", "pipe": "MUFU", "achieved": ops / tm / 1e9, "peak": ex2_rate / 1e9,
+                "unit": "Gop/s", "frac": ops / tm / ex2_rate,
+                "traffic": profile_traffic("k_mh_move_mala"), "kernel": "k_mh_move<8,MALA,EQW>",
+                "ops_per_launch": ops, "count": "K ex2 + 1 reciprocal per particle-datum",
+                "launch_time": "one launch after an L2 flush (median of 10)",
+                "peak_source": f"measured in this run: ex2.approx issue rate ({ex2_ms:.2f} ms)"}
+            snaps["mala_move"] = {"w": w, "theta": th.cpu().numpy(), "ll": ll.cpu().numpy(),
+                                  "grad": gsrc.cpu().numpy(), "theta1": tho.cpu().numpy(),
+                                  "ll1": llo.cpu().numpy(), "grad1": go.cpu().numpy(),
+                                  "beta": float(bl.item())}
     w = synth.MSV3
     phi, Sigma, beta = synth.msv_params(w.d, w.phi, w.rho, w.beta)
     _, yobs = synth.simulate_ssm("msv", w.T, phi, Sigma, beta, seed=w.data_seed)
@@ -576,6 +674,16 @@ def bench_secondary(torch, P):
     pf.reset()
     t_graph = timed(lambda: g.replay())
     z_graph = float(pf.hist[1:, 0].sum().item())
+    # one more filter step from the final state, kept for the oracle's check
+    c, n = pf.cur, 1 - pf.cur
+    xin = pf.x[c].cpu().numpy()
+    ancs = pf.anc.cpu().numpy()
+    P.pf_step(ctx, pf.model, pf.y[w.T - 1], pf.x[c], pf.x[n], pf.logg, pf.seed, w.T + 1,
+              anc=pf.anc)
+    snaps["particle_filter"] = {"phi": phi, "chol": synth.chol(Sigma), "beta": beta,
+                                "yt": pf.y[w.T - 1].cpu().numpy(), "x_in": xin, "anc": ancs,
+                                "seed": pf.seed, "t": w.T + 1, "logg": pf.logg.cpu().numpy(),
+                                "x_out": pf.x[n].cpu().numpy()}
     out["particle_filter"] = {"workload": w.name, "steps": w.T, "M": w.M,
                               "plain_particle_steps_per_s": w.M * w.T / t_plain,
                               "graph_particle_steps_per_s": w.M * w.T / t_graph,
@@ -595,11 +703,157 @@ def bench_secondary(torch, P):
     ctx.check()
     out["is_example"] = is_example(torch, P, ctx)
     out["mrg32k3a"] = mrg_blocks(torch, P, ctx)
-    out["diag_tensor_core"] = {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
-                               "ms_per_call": 1e3 * t_tc, "pd_per_s": w.M * w.N / t_tc,
-                               "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory"}
+    # rooflines of the tensor-core likelihood: issued bf16 MMA flops (three
+    # split products) and MUFU ops (K ex2 + 1 lg2 per particle-datum)
+    kp = max(4, 1 << (w.K - 1).bit_length())
+    flops = 3 * 2.0 * (-(-w.N // 128) * 128) * (w.M * kp) * w.d
+    mufu = float(w.N) * w.M * (kp + 1)
+    pk = measured_peaks()
+    t_tcf = statistics.median([_whole_run(torch, flush, stream,
+                                          lambda: P.loglik_batch(ctx, tc, Y, th, out=ll))
+                               for _ in range(5)])
+    snaps["diag_tensor_core"] = {"w": w, "theta": th.cpu().numpy(), "ll": ll.cpu().numpy()}
+    out["diag_tensor_core"] = {
+        "workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
+        "ms_per_call": 1e3 * t_tc, "ms_per_call_l2_flushed": 1e3 * t_tcf,
+        "pd_per_s": w.M * w.N / t_tc,
+        "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory",
+        "roofline": {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": mufu / t_tcf / 1e9,
+                     "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": mufu / t_tcf / ex2_rate,
+                     "traffic": profile_traffic("k_dtc_main"),
+                     "kernel": "k_dtc_main (+ prep, combine)", "ops_per_launch": mufu,
+                     "launch_time": "one call after an L2 flush (median of 5)",
+                     "tensor": {"achieved": flops / t_tcf / 1e12, "peak": pk["bf16_tflops"],
+                                "unit": "TFLOP/s", "frac": flops / t_tcf / 1e12 / pk["bf16_tflops"],
+                                "flops_per_call": flops,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst"}}}
+    try:
+        out["reweight_resample"], snaps["reweight_resample"] = reweight_resample_roofline(
+            torch, P, ctx, 1 << 24, 20)
+    except Exception as e:  # noqa: BLE001
+        out["reweight_resample"] = {"error": repr(e)}
     ctx.close()
+    out["_snaps"] = snaps
     return out
+
+
+def reweight_resample_roofline(torch, P, ctx, M, reps, seed=5):
+    """smc_reweight (lw += l, W, log Z increment, ESS) and
+    smc_resample_systematic (with the log-weight reset) at M particles,
+    each timed alone after an L2 flush; algorithmic bytes per particle:
+    reweight 32 (l read, lw read + write, W write), resampling 20 (W read,
+    ancestor write, lw reset write).  Returns the entry and the inputs and
+    outputs of one call for the oracle's check."""
+    ctx.reserve(M)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    ll = torch.randn(M, dtype=torch.float64, device="cuda", generator=g)
+    lw0 = torch.randn(M, dtype=torch.float64, device="cuda", generator=g) * 0.5
+    lw = lw0.clone()
+    W = torch.empty(M, dtype=torch.float64, device="cuda")
+    anc = torch.empty(M, dtype=torch.int32, device="cuda")
+    sc = torch.empty(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    rw = lambda: P.reweight(ctx, ll, 1.0, lw, W, sc, None, 0.5)
+    rs = lambda: P.resample_systematic(ctx, W, 9, 1, anc=anc, logw_reset=lw)
+    for _ in range(3):
+        lw.copy_(lw0)
+        rw()
+        rs()
+    t_rw, t_rs = [], []
+    for _ in range(reps):
+        lw.copy_(lw0)
+        e = _flush_timed(torch, flush, stream, [rw, rs])
+        torch.cuda.synchronize()
+        t_rw.append(e[0].elapsed_time(e[1]) / 1e3)
+        t_rs.append(e[1].elapsed_time(e[2]) / 1e3)
+    ctx.check()
+    hbm = measured_peaks()["hbm_gbs"]
+    trw, trs = statistics.median(t_rw), statistics.median(t_rs)
+    lw.copy_(lw0)
+    rw()
+    snap = {"ll": ll.cpu().numpy(), "lw0": lw0.cpu().numpy(), "W": W.cpu().numpy(),
+            "scalars": sc.cpu().numpy()}
+    rs()
+    snap["anc"] = anc.cpu().numpy()
+    entry = {"M": M, "ms_reweight": 1e3 * trw, "ms_resample": 1e3 * trs,
+             "roofline": {
+                 "reweight": {"bound": "hbm", "achieved": 32 * M / trw / 1e9, "peak": hbm,
+                              "unit": "GB/s", "frac": 32 * M / trw / 1e9 / hbm,
+                              "traffic": profile_traffic("reweight"), "bytes_per_particle": 32,
+                              "kernel": "k_reweight_reduce + k_reweight_normalize"},
+                 "resample": {"bound": "hbm", "achieved": 20 * M / trs / 1e9, "peak": hbm,
+                              "unit": "GB/s", "frac": 20 * M / trs / 1e9 / hbm,
+                              "traffic": profile_traffic("resample_systematic"),
+                              "bytes_per_particle": 20,
+                              "kernel": "systematic resampling (total, finalize, scan)"}},
+             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+             "launch_time": f"each call alone after an L2 flush, median of {reps}"}
+    return entry, snap
+
+
+def secondary_oracle_checks(snaps):
+    """Observed error of each secondary result against the FP64 oracle (part
+    of the CPU leg, outside every timed region)."""
+    import oracle
+    res = {}
+    rng = np.random.default_rng(12)
+    for name in ("smc_sampler", "mala_sampler"):
+        if name in snaps:
+            d = snaps[name]
+            w = d["w"]
+            idx = rng.choice(d["theta"].shape[1], 200, replace=False)
+            ref = oracle.gmm1d_loglik(w.data(), w.logw(), w.sigma, d["theta"][:, idx])
+            res[name] = {"max_rel_loglik_err": float(np.max(np.abs(d["ll"][idx] - ref) /
+                                                           np.abs(ref))),
+                         "particles_checked": 200, "tolerance": "relative 1e-5"}
+    if "mala_move" in snaps:
+        d = snaps["mala_move"]
+        w = d["w"]
+        slots = np.sort(rng.choice(d["theta"].shape[1], 100, replace=False)).astype(np.int32)
+        rt, rl, rg, racc, la = oracle.mala_move(w.data(), w.logw(), w.sigma, (-10, 10), d["theta"],
+                                                d["ll"], d["grad"], d["beta"], w.scale, 99, 1,
+                                                slots=slots, want_log_alpha=True)
+        same = np.all(np.isclose(d["theta1"][:, slots], rt, rtol=3e-7, atol=2e-6), axis=0)
+        ok = same & np.isclose(d["ll1"][slots], rl, rtol=1e-5)
+        res["mala_move"] = {"slots_checked": int(slots.size), "slots_differing": int((~ok).sum()),
+                            "max_rel_loglik_err_agreeing": float(np.max(
+                                np.abs(d["ll1"][slots][ok] - rl[ok]) / np.abs(rl[ok])))
+                            if ok.any() else None}
+    if "diag_tensor_core" in snaps:
+        d = snaps["diag_tensor_core"]
+        w = d["w"]
+        import synth
+        truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
+        Yh = synth.diag_data(w.N, truth, seed=w.data_seed)
+        idx = np.array([0, 1, w.M // 2 - 1, w.M // 2, w.M - 1])
+        ref = oracle.gmmdiag_loglik(Yh, w.logw(), w.sigma, d["theta"][idx])
+        res["diag_tensor_core"] = {"max_rel_loglik_err": float(np.max(np.abs(d["ll"][idx] - ref) /
+                                                                     np.abs(ref))),
+                                   "particles_checked": int(idx.size),
+                                   "tolerance": "relative 1e-3 (BF16 split)"}
+    if "particle_filter" in snaps:
+        d = snaps["particle_filter"]
+        sl = rng.choice(d["x_in"].shape[1], 20000, replace=False)
+        rx, rlg = oracle.pf_step(0, d["phi"], d["chol"], d["beta"], d["yt"], d["x_in"], d["anc"],
+                                 d["seed"], d["t"])
+        res["particle_filter"] = {"max_abs_logg_err": float(np.max(np.abs(d["logg"][sl] - rlg[sl]))),
+                                  "max_rel_logg_err": float(np.max(np.abs(d["logg"][sl] - rlg[sl]) /
+                                                                   np.maximum(np.abs(rlg[sl]), 1))),
+                                  "state_max_abs_err": float(np.max(np.abs(d["x_out"] - rx))),
+                                  "particles_checked": 20000}
+    if "reweight_resample" in snaps:
+        d = snaps["reweight_resample"]
+        nlw, rW, rsc = oracle.reweight(d["ll"], 1.0, d["lw0"])
+        ranc, _ = oracle.resample_systematic(d["W"], oracle.resample_u32(9, 1))
+        res["reweight_resample"] = {
+            "W_max_rel_err": float(np.max(np.abs(d["W"] - rW) / np.maximum(rW, 1e-300))),
+            "ess_rel_err": float(abs(d["scalars"][1] - rsc[1]) / rsc[1]),
+            "logz_inc_abs_err": float(abs(d["scalars"][0] - rsc[0])),
+            "ancestors_differing": int(np.sum(d["anc"] != ranc)),
+            "note": "ancestors from the GPU's own W (bit-exact given the same W)"}
+    return res
 
 
 def is_example(torch, P, ctx, reps=10):
@@ -1276,7 +1530,7 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10000)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="popmcmc", choices=["popmcmc", "pf", "resample",
@@ -1340,8 +1594,22 @@ def main():
         except Exception as e:  # noqa: BLE001
             out["secondary"]["paper_tables"] = {"error": repr(e)}
     if dist.rank == 0:
+        snap = out.pop("_oracle_check", None)
+        if args.no_cpu or dist.world != 1:
+            out.get("secondary", {}).pop("_snaps", None)
         if not args.no_cpu and dist.world == 1 and args.workload == "popmcmc":
             import synth
+            if snap is not None:
+                out["error_vs_oracle"] = popmcmc_oracle_check(synth.GMM8_POP, snap)
+            snaps = out.get("secondary", {}).pop("_snaps", None)
+            if snaps:
+                try:
+                    for k, v in secondary_oracle_checks(snaps).items():
+                        tgt = "mala_sampler" if k == "mala_move" else k
+                        out["secondary"].setdefault(tgt, {})["error_vs_oracle" if k != "mala_move"
+                                                             else "move_error_vs_oracle"] = v
+                except Exception as e:  # noqa: BLE001
+                    out["secondary"]["oracle_check_error"] = repr(e)
             out["cpu_baseline"] = cpu_popmcmc(synth.GMM8_POP)
             try:  # the same oracle on every host core (context beside the 1-core figure)
                 out["cpu_baseline"]["all_cores"] = cpu_popmcmc_all_cores()

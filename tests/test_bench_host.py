@@ -53,3 +53,29 @@ def test_committed_traffic_entries_name_existing_sources():
     for name, e in d.items():
         assert e["bytes_per_launch"] > 0 and e["sources"], name
         build.source_digest(e["sources"])  # every listed source exists
+
+
+def test_popmcmc_oracle_check_reports_zero_error_on_the_oracle_s_own_sweep():
+    """The bench's error check against the oracle, fed a state whose stored
+    log-likelihoods and one-sweep successor come from the oracle itself:
+    no error, no differing chain (the check compares what it should)."""
+    import oracle
+    import synth
+    w = synth.GMM8_POP
+    off = synth.population_offsets(w.n_pops, seed=w.pop_seed)
+    m = int(off[16])
+    th = synth.population_particles(w.K, off, seed=4)[:, :m].copy()
+    ll = oracle.gmm1d_loglik(w.data(), w.logw(), w.sigma, th)
+    beta = synth.population_betas(off)[:m]
+    rt, rl, _ = oracle.popmcmc_sweep(w.data(), w.logw(), w.sigma, (-10, 10), th, ll, beta,
+                                     off[:17], w.scale, 3, 5)
+    snap = {"theta": th, "ll": ll, "theta1": rt, "ll1": rl, "sweep": 5}
+    r = bench.popmcmc_oracle_check(w, snap, n_chains=100, sample_pops=16)
+    assert r["max_rel_loglik_err"] == 0.0
+    assert r["sweep_replayed"]["chains_differing"] == 0
+    assert r["sweep_replayed"]["populations_differing"] == 0
+    # a planted change in one chain's successor is seen
+    rt2 = rt.copy()
+    rt2[0, 10] += 0.5
+    r2 = bench.popmcmc_oracle_check(w, dict(snap, theta1=rt2), n_chains=100, sample_pops=16)
+    assert r2["sweep_replayed"]["chains_differing"] == 1
