@@ -96,6 +96,16 @@ smc_status smc_set_launch(smc_ctx* ctx, int32_t op, int32_t lanes, int32_t threa
 smc_status smc_get_launch(smc_ctx* ctx, int32_t op, int64_t M, int64_t N, int32_t K,
                           int32_t* lanes, int32_t* threads);
 
+/* Test hook for the bounded device waits (no counterpart in the paper):
+ * the number of polls the first wait on a kernel's bulk copy of the data
+ * into shared memory makes before it gives up and latches SMC_ERR_TIMEOUT
+ * in the context (reported by smc_ctx_check).  A wait that gives up is
+ * followed by a second one with the full bound, so no copy is left in
+ * flight and the results stay correct; 0 makes every such wait give up at
+ * once.  Applies to the 1-D likelihood, move and population-sweep calls of
+ * this context.  Default 4,194,304 (seconds of polling). */
+smc_status smc_set_wait_limit(smc_ctx* ctx, uint32_t polls);
+
 /* ------------------------------------------------------------------ models */
 
 enum { SMC_GMM_1D = 0, SMC_GMM_DIAG = 1 };
@@ -242,10 +252,11 @@ smc_status smc_resample_residual(smc_ctx* ctx, const double* W, int64_t M, uint6
  *   from normalised), 2 = all weights zero.
  *   The first call on a device (with that device current) looks up the
  *   array's device address; make that first call before any stream capture.
- *   Every call shares the one array and each call starts by clearing its
- *   sums, so calls whose work overlaps on the GPU (different streams, or
- *   several host threads on one device) race and give wrong results:
- *   serialise them, e.g. on one stream. */
+ *   Every call shares the one array.  Nothing in it needs clearing between
+ *   calls (each call's first pass overwrites every tile sum it uses, and
+ *   its constants are formed anew), but calls whose work overlaps on the
+ *   GPU (different streams, or several host threads on one device) race
+ *   and give wrong results: serialise them, e.g. on one stream. */
 smc_status smc_resample_systematic_noalloc(const double* W, int64_t M, uint64_t seed,
                                            uint64_t step, int32_t* ancestors_out,
                                            int32_t* counts_out, const int32_t* do_flag,

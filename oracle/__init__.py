@@ -95,6 +95,8 @@ def _declare(L):
     L.orc_popmcmc_sweep.argtypes = [_f32p, _i64, C.c_int, _f64p, C.c_double, C.c_double,
                                     C.c_double, _f32p, _f64p, _i64, _f32p, _i32p, C.c_int32,
                                     C.c_float, _u64, _u64, _i64p]
+    L.orc_popmcmc_exchange.argtypes = [C.c_int, _f32p, _f64p, _i64, _f32p, _i32p, C.c_int32,
+                                       C.c_int32, _u64, _u64, _i64p, _vp, _vp]
     L.orc_pf_step.argtypes = [C.c_int, C.c_int, _f64p, _f64p, C.c_double, _f32p, _f32p, _vp,
                               _f32p, _f64p, _i64, _u64, _u64]
     L.orc_pf_run.argtypes = [C.c_int, C.c_int, _f64p, _f64p, C.c_double, _f32p, _i64, _i64, _u64,
@@ -353,6 +355,29 @@ def popmcmc_sweep(y, logw, sigma, box, theta, loglik, beta, offsets, scale, seed
     lib().orc_popmcmc_sweep(y, y.size, K, logw, float(sigma), float(box[0]), float(box[1]),
                             theta, loglik, M, _f32(beta), offsets, offsets.size - 1, float(scale),
                             seed, sweep, stats)
+    return theta, loglik, stats
+
+
+def popmcmc_exchange(theta, loglik, beta, offsets, seed, sweep, q0=0, q1=None, want_la=False,
+                     flip=None):
+    """Stage 2 of a population-MCMC sweep (the exchange moves of Section
+    4.1.1) on populations q0 .. q1-1; returns the new state and stats.
+    want_la: also the log alpha - log u of every pair attempted (populations
+    in order, then pairs); flip: int8 per pair, nonzero takes the opposite
+    decision (test hooks for replaying the stage with chosen decisions)."""
+    theta = _f32(theta).copy()
+    loglik = _f64(loglik).copy()
+    K, M = theta.shape
+    offsets = np.ascontiguousarray(offsets, np.int32)
+    q1 = offsets.size - 1 if q1 is None else int(q1)
+    stats = np.zeros(3, np.int64)
+    npairs = int(sum(int(offsets[q + 1] - offsets[q]) // 2 + 1 for q in range(q0, q1)))
+    la = np.zeros(max(npairs, 1), np.float64) if want_la else None
+    fl = None if flip is None else np.ascontiguousarray(flip, np.int8)
+    lib().orc_popmcmc_exchange(K, theta, loglik, M, _f32(beta), offsets, int(q0), q1, seed, sweep,
+                               stats, _ptr(la), _ptr(fl))
+    if want_la:
+        return theta, loglik, stats, la[: int(stats[2])]
     return theta, loglik, stats
 
 

@@ -714,6 +714,52 @@ void orc_mala_move(const float* y, int64_t N, int K, const double* logw, double 
 /* stats[0] += MH accepts, stats[1] += swaps accepted, stats[2] += swaps     */
 /* attempted.                                                                */
 /* ------------------------------------------------------------------------ */
+/* Stage 2 alone, for populations q0 .. q1-1 (the sweep calls it for all).  */
+/* Test hooks (NULL in the sweep): la_out[p] receives log alpha - log u of   */
+/* the p-th pair attempted (populations in order, then pairs in order,       */
+/* counted from population q0); flip[p] != 0 takes the opposite decision     */
+/* for that pair, so a test can replay the stage with chosen decisions.      */
+void orc_popmcmc_exchange(int K, float* theta, double* loglik, int64_t Mtot,
+                          const float* beta, const int32_t* offsets, int32_t q0, int32_t q1,
+                          uint64_t seed, uint64_t sweep, int64_t* stats, double* la_out,
+                          const int8_t* flip)
+{
+    int64_t p = 0;
+    for (int32_t q = q0; q < q1; ++q) {
+        int64_t base = offsets[q];
+        int64_t Mq = (int64_t)offsets[q + 1] - base;
+        if (Mq < 2) continue;
+        uint32_t b = orc_word(seed, ORC_P_EXCHANGE, sweep, (uint32_t)q, 0) & 1u;
+        int64_t npairs;
+        if (b == 0) npairs = Mq / 2;
+        else npairs = (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
+        for (int64_t j = 0; j < npairs; ++j, ++p) {
+            int64_t ia, ib;
+            if (b == 0) { ia = 2 * j; ib = 2 * j + 1; }
+            else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
+            else { ia = Mq - 1; ib = 0; }
+            int64_t ga = base + ia, gb = base + ib;
+            double la = loglik[ga], lb = loglik[gb];
+            double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
+            double u = orc_u01(orc_word(seed, ORC_P_EXCHANGE, sweep, (uint32_t)q, (uint32_t)(4 + j)));
+            if (la_out) la_out[p] = log_alpha - log(u);
+            int swap = log(u) < log_alpha;
+            if (flip && flip[p]) swap = !swap;
+            stats[2] += 1;
+            if (swap) {
+                stats[1] += 1;
+                for (int k = 0; k < K; ++k) {
+                    float t = theta[(int64_t)k * Mtot + ga];
+                    theta[(int64_t)k * Mtot + ga] = theta[(int64_t)k * Mtot + gb];
+                    theta[(int64_t)k * Mtot + gb] = t;
+                }
+                loglik[ga] = lb;
+                loglik[gb] = la;
+            }
+        }
+    }
+}
+
 void orc_popmcmc_sweep(const float* y, int64_t N, int K, const double* logw, double sigma,
                        double lo, double hi,
                        float* theta, double* loglik, int64_t Mtot,
@@ -728,37 +774,8 @@ void orc_popmcmc_sweep(const float* y, int64_t N, int K, const double* logw, dou
     for (int64_t i = 0; i < Mtot; ++i) stats[0] += acc[i];
     memcpy(theta, th_new, (size_t)Mtot * K * sizeof(float));
     memcpy(loglik, l_new, (size_t)Mtot * sizeof(double));
-
-    for (int32_t q = 0; q < n_pops; ++q) {
-        int64_t base = offsets[q];
-        int64_t Mq = (int64_t)offsets[q + 1] - base;
-        if (Mq < 2) continue;
-        uint32_t b = orc_word(seed, ORC_P_EXCHANGE, sweep, (uint32_t)q, 0) & 1u;
-        int64_t npairs;
-        if (b == 0) npairs = Mq / 2;
-        else npairs = (Mq - 1) / 2 + ((Mq % 2 == 0) ? 1 : 0);
-        for (int64_t j = 0; j < npairs; ++j) {
-            int64_t ia, ib;
-            if (b == 0) { ia = 2 * j; ib = 2 * j + 1; }
-            else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
-            else { ia = Mq - 1; ib = 0; }
-            int64_t ga = base + ia, gb = base + ib;
-            double la = loglik[ga], lb = loglik[gb];
-            double log_alpha = ((double)beta[ga] - (double)beta[gb]) * (lb - la);
-            double u = orc_u01(orc_word(seed, ORC_P_EXCHANGE, sweep, (uint32_t)q, (uint32_t)(4 + j)));
-            stats[2] += 1;
-            if (log(u) < log_alpha) {
-                stats[1] += 1;
-                for (int k = 0; k < K; ++k) {
-                    float t = theta[(int64_t)k * Mtot + ga];
-                    theta[(int64_t)k * Mtot + ga] = theta[(int64_t)k * Mtot + gb];
-                    theta[(int64_t)k * Mtot + gb] = t;
-                }
-                loglik[ga] = lb;
-                loglik[gb] = la;
-            }
-        }
-    }
+    orc_popmcmc_exchange(K, theta, loglik, Mtot, beta, offsets, 0, n_pops, seed, sweep, stats,
+                         NULL, NULL);
     free(th_new); free(l_new); free(acc);
 }
 

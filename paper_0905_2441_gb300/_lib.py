@@ -24,7 +24,7 @@ EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_sta
            "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
            "smc_resample_systematic_noalloc", "smc_resample_multinomial",
            "smc_resample_residual", "smc_is_moments", "smc_rng_mrg32k3a",
-           "smc_reweight_resample")
+           "smc_reweight_resample", "smc_set_wait_limit")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -57,6 +57,7 @@ def _declare(L):
     L.smc_status_string.argtypes = [_st]
     L.smc_status_string.restype = C.c_char_p
     L.smc_set_launch.argtypes = [_vp, _i32, _i32, _i32]
+    L.smc_set_wait_limit.argtypes = [_vp, _u32]
     L.smc_get_launch.argtypes = [_vp, _i32, _i64, _i64, _i32, C.POINTER(_i32), C.POINTER(_i32)]
     L.smc_loglik_batch.argtypes = [_vp, C.POINTER(SmcGmm), _vp, _i64, _vp, _i64, _vp, _vp, _vp]
     L.smc_reweight.argtypes = [_vp, _vp, C.c_double, _vp, _i64, _vp, _vp, _vp, C.c_double, _vp]

@@ -95,6 +95,11 @@ class Context:
     def set_launch(self, op: int, lanes: int, threads: int = 256):
         _chk(self._lib.smc_set_launch(self.handle, op, lanes, threads), "smc_set_launch")
 
+    def set_wait_limit(self, polls: int):
+        """Polls of the first bounded wait on a bulk data copy (a test hook:
+        0 makes every such wait give up and report SMC_ERR_TIMEOUT)."""
+        _chk(self._lib.smc_set_wait_limit(self.handle, int(polls)), "smc_set_wait_limit")
+
     def get_launch(self, op: int, M: int, N: int, K: int):
         l, t = C.c_int32(), C.c_int32()
         _chk(self._lib.smc_get_launch(self.handle, op, M, N, K, C.byref(l), C.byref(t)),

@@ -208,6 +208,12 @@ extern "C" const char* smc_status_string(smc_status s) {
     return "unknown status";
 }
 
+extern "C" smc_status smc_set_wait_limit(smc_ctx* ctx, uint32_t polls) {
+    if (!ctx) return SMC_ERR_ARG;
+    ctx->wait_limit = polls;
+    return SMC_OK;
+}
+
 extern "C" smc_status smc_set_launch(smc_ctx* ctx, int32_t op, int32_t lanes, int32_t threads) {
     if (!ctx || op < 0 || op >= SMC_OP_COUNT) return SMC_ERR_ARG;
     if (lanes == 0) {

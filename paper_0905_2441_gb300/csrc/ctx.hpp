@@ -30,6 +30,9 @@ struct smc_ctx {
     int64_t grp_cap = 0;
     // MRG32k3a skip-ahead table: A1^(2^k), A2^(2^k), k < 64 (filled at creation)
     uint32_t* d_mrg_pow = nullptr;
+    // polls of the first bounded wait on a bulk data copy before it gives up
+    // (ST_TIMEOUT); set by smc_set_wait_limit, a test hook
+    uint32_t wait_limit = 4u << 20;
     int32_t lanes[SMC_OP_COUNT] = {0, 0, 0};
     int32_t threads[SMC_OP_COUNT] = {0, 0, 0};
 };

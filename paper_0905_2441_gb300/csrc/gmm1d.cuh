@@ -46,6 +46,7 @@ struct Gmm1dArgs {
     float binw_inv;     // 1 / binw (a power of two)
     double cst;         // N (-1/2 ln(2 pi sigma^2)) [+ N ln w when weights are equal]
     float lw2[kMaxK1d]; // log2 w_k (padding components: -inf)
+    uint32_t wait_limit;  // polls of the first wait on a bulk data copy (the context's)
 };
 
 // Stage y[n0, n0+cnt) into shared memory.  A bulk asynchronous copy moves
@@ -85,16 +86,18 @@ __device__ __forceinline__ bool stage_y_issue(float* ys, const float* __restrict
 }
 
 // Completes stage_y_issue: every thread of the block calls it.  The wait on
-// the bulk copy is bounded; on timeout the status word gets ST_TIMEOUT.
+// the bulk copy is bounded (`limit` polls, the context's setting); on timeout
+// the status word gets ST_TIMEOUT and a second wait, with the full bound,
+// lets the copy finish, so none is left in flight and the data are complete.
 __device__ __forceinline__ void stage_y_wait(bool bulk, uint64_t* mbar, uint32_t& phase,
-                                             uint32_t* status) {
+                                             uint32_t* status, uint32_t limit = kSpinLimit) {
     if (!bulk) {
         __syncthreads();
         return;
     }
     uint32_t mb = (uint32_t)__cvta_generic_to_shared(mbar);
     uint32_t done = 0;
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    for (uint32_t it = 0; it < limit && !done; ++it) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -120,8 +123,8 @@ __device__ __forceinline__ void stage_y_wait(bool bulk, uint64_t* mbar, uint32_t
 
 __device__ __forceinline__ void stage_y(float* ys, const float* __restrict__ y, int64_t n0,
                                         int cnt, uint64_t* mbar, uint32_t& phase,
-                                        uint32_t* status) {
-    stage_y_wait(stage_y_issue(ys, y, n0, cnt, mbar), mbar, phase, status);
+                                        uint32_t* status, uint32_t limit = kSpinLimit) {
+    stage_y_wait(stage_y_issue(ys, y, n0, cnt, mbar), mbar, phase, status, limit);
 }
 
 __device__ __forceinline__ void init_mbar(uint64_t* mbar) {
@@ -487,11 +490,12 @@ __device__ __forceinline__ void slice_over_data(SliceAcc<K, GRAD, EQW>& acc, flo
                                                 const float* __restrict__ y, int64_t N,
                                                 bool active, int lane, int L,
                                                 const float (&nu)[K], const float (&lw2)[K],
-                                                float r, uint32_t& phase, uint32_t* status) {
+                                                float r, uint32_t& phase, uint32_t* status,
+                                                uint32_t limit = kSpinLimit) {
     uint64_t* mbar = ychunk_mbar(ys, ychunk);
     for (int64_t c0 = 0; c0 < N; c0 += ychunk) {
         int cnt = (int)((N - c0) < ychunk ? (N - c0) : ychunk);
-        stage_y(ys, y, c0, cnt, mbar, phase, status);
+        stage_y(ys, y, c0, cnt, mbar, phase, status, limit);
         if (active) acc.run(ys, cnt, lane, L, nu, lw2, r);
         __syncthreads();
     }
@@ -503,11 +507,12 @@ __device__ __forceinline__ void slice_over_data_eq(SliceAccEqW<K, GRAD>& acc, fl
                                                    const float* __restrict__ y, int64_t N,
                                                    bool active, int lane, int L,
                                                    const float (&nu)[K], float r,
-                                                   uint32_t& phase, uint32_t* status) {
+                                                   uint32_t& phase, uint32_t* status,
+                                                   uint32_t limit = kSpinLimit) {
     uint64_t* mbar = ychunk_mbar(ys, ychunk);
     for (int64_t c0 = 0; c0 < N; c0 += ychunk) {
         int cnt = (int)((N - c0) < ychunk ? (N - c0) : ychunk);
-        stage_y(ys, y, c0, cnt, mbar, phase, status);
+        stage_y(ys, y, c0, cnt, mbar, phase, status, limit);
         if (active) acc.run(ys, cnt, lane, L, nu, r);
         __syncthreads();
     }

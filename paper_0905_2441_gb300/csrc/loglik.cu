@@ -39,11 +39,13 @@ __global__ void __launch_bounds__(256) k_loglik_gmm1d(const float* __restrict__ 
     double ll;
     if constexpr (EQW) {
         SliceAccEqW<K, GRAD> acc;
-        slice_over_data_eq(acc, ys, ychunk, y, N, active, lane, L, nu, P.r, phase, status);
+        slice_over_data_eq(acc, ys, ychunk, y, N, active, lane, L, nu, P.r, phase, status,
+                           P.wait_limit);
         ll = acc.finish(L, P, g);
     } else {
         SliceAcc<K, GRAD, EQW> acc;
-        slice_over_data(acc, ys, ychunk, y, N, active, lane, L, nu, lw2, P.r, phase, status);
+        slice_over_data(acc, ys, ychunk, y, N, active, lane, L, nu, lw2, P.r, phase, status,
+                        P.wait_limit);
         ll = acc.finish(L, P, g);
     }
     if (active && lane == 0) {
@@ -150,6 +152,7 @@ smc_status gmm1d_prepare(const smc_gmm* model, int64_t N, smc::Gmm1dArgs* P, int
     // w = 2^floor(log2(4 / sqrt(cf))), so that cf (w/2)^2 <= 4
     P->binw = (float)std::ldexp(1.0, (int)std::floor(std::log2(4.0 / std::sqrt((double)P->cf))));
     P->binw_inv = 1.0f / P->binw;
+    P->wait_limit = smc::kSpinLimit;
     P->gscale = (float)(1.0 / (s * s * (double)P->r));
     P->lo = model->lo;
     P->hi = model->hi;
@@ -237,6 +240,7 @@ extern "C" smc_status smc_loglik_batch(smc_ctx* ctx, const smc_gmm* model, const
     bool eqw;
     st = gmm1d_prepare(model, N, &P, &Kp, &eqw);
     if (st != SMC_OK) return st;
+    P.wait_limit = ctx->wait_limit;
     if (M == 0) return SMC_OK;
     int L, threads;
     launch_shape(ctx, SMC_OP_LOGLIK, M, N, model->K, &L, &threads);

@@ -119,11 +119,13 @@ __global__ void __launch_bounds__(256, (K <= 8 ? SMC_MOVE_MINB : 1)) k_mh_move(
     double lp;
     if constexpr (EQW) {
         SliceAccEqW<K, MALA> acc;
-        slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status);
+        slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status,
+                           P.wait_limit);
         lp = acc.finish(L, P, gp);
     } else {
         SliceAcc<K, MALA, EQW> acc;
-        slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+        slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status,
+                        P.wait_limit);
         lp = acc.finish(L, P, gp);
     }
 
@@ -377,7 +379,8 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
     const int64_t nitems = (Mtot + ppb - 1) / ppb;
     uint32_t phase = 0;
     const bool resident = N <= ychunk;  // all data in shared memory: stage once
-    if (resident && N > 0) stage_y(ys, y, 0, (int)N, ychunk_mbar(ys, ychunk), phase, status);
+    if (resident && N > 0)
+        stage_y(ys, y, 0, (int)N, ychunk_mbar(ys, ychunk), phase, status, P.wait_limit);
     float lw2[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) lw2[k] = P.lw2[k];
@@ -425,7 +428,8 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
             if (resident) {
                 if (in_box) acc.run(ys, (int)N, lane, L, nu, P.r);
             } else {
-                slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status);
+                slice_over_data_eq(acc, ys, ychunk, y, N, in_box, lane, L, nu, P.r, phase, status,
+                                   P.wait_limit);
             }
             lp = acc.finish(L, P);
         } else {
@@ -433,7 +437,8 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
             if (resident) {
                 if (in_box) acc.run(ys, (int)N, lane, L, nu, lw2, P.r);
             } else {
-                slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status);
+                slice_over_data(acc, ys, ychunk, y, N, in_box, lane, L, nu, lw2, P.r, phase, status,
+                                P.wait_limit);
             }
             float gd[K];
             lp = acc.finish(L, P, gd);
@@ -605,7 +610,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
         round_draws(gA, (int)(ng0 * 32));
     }
     if (off_smem && tid <= n_pops) s_off[tid] = off0;
-    stage_y_wait(bulk, ychunk_mbar(ys, yc), phase, status);
+    stage_y_wait(bulk, ychunk_mbar(ys, yc), phase, status, P.wait_limit);
     // ---- the data sorted into bins, cut into pieces
     bin_partition(ys, (int)N, yb, rk, bt, P.binw, P.binw_inv, P.cf);
     bin_pieces(bt, s_piece, &s_np);
@@ -954,6 +959,7 @@ extern "C" smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const floa
     bool eqw;
     smc_status st = gmm1d_prepare(model, N, &P, &Kp, &eqw);
     if (st != SMC_OK) return st;
+    P.wait_limit = ctx->wait_limit;
     st = use_device(ctx);
     if (st != SMC_OK) return st;
     int L, threads;
@@ -996,6 +1002,7 @@ extern "C" smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, cons
     bool eqw;
     smc_status st = gmm1d_prepare(model, N, &P, &Kp, &eqw);
     if (st != SMC_OK) return st;
+    P.wait_limit = ctx->wait_limit;
     st = use_device(ctx);
     if (st != SMC_OK) return st;
     int L, threads;

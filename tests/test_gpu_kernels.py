@@ -19,6 +19,7 @@ import torch
 
 import oracle
 import synth
+from _popcheck import explain_sweep
 
 pytestmark = pytest.mark.gpu
 
@@ -444,24 +445,19 @@ def test_popmcmc_sweep_parity(smc, N):
                     stats=stats)
     ctx.check()
     rt, rl, rst = oracle.popmcmc_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 55, 0)
-    # a flipped decision changes a whole population; every population must match
-    # except (rarely) one decided inside the FP32 band
-    bad = 0
-    for q in range(off.size - 1):
-        a, b = off[q], off[q + 1]
-        if not (np.allclose(np_(tt)[:, a:b], rt[:, a:b], rtol=3e-7, atol=2e-6) and
-                np.allclose(np_(lt)[a:b], rl[a:b], rtol=1e-5)):
-            bad += 1
-    assert bad <= 1
+    # a population may differ only through decisions inside the FP32 band
+    rep = explain_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 55, 0, np_(tt), np_(lt))
+    assert rep.unexplained == [] and len(rep.differing) <= 1, rep
     s = np_(stats)
     assert s[2] == rst[2] and abs(int(s[0]) - int(rst[0])) <= 2 and abs(int(s[1]) - int(rst[1])) <= 2
 
 
+@pytest.mark.parametrize("N", [300, 5000])  # binned sweep (shape fixed) / lanes-per-chain sweep
 @pytest.mark.parametrize("lanes,threads", [(1, 256), (8, 128), (16, 128), (32, 256)])
-def test_popmcmc_sweep_launch_shapes(smc, lanes, threads):
+def test_popmcmc_sweep_launch_shapes(smc, lanes, threads, N):
     """Every sweep shape the autotuner may choose gives the oracle's sweep."""
     P, ctx = smc
-    K, N = 4, 300
+    K = 4
     y = synth.gmm1d_data(N, [-3, 0, 3, 6], SIG, seed=2)
     logw = np.full(K, -np.log(K))
     off = np.array([0, 2, 9, 40, 41, 130, 131, 300], np.int32)
@@ -475,9 +471,8 @@ def test_popmcmc_sweep_launch_shapes(smc, lanes, threads):
         ctx.check()
     finally:
         ctx.set_launch(P.OP_POPMCMC, 0, 0)
-    rt, rl, _ = oracle.popmcmc_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 66, 1)
-    same = np.all(np.isclose(np_(tt), rt, rtol=3e-7, atol=2e-6), axis=0)
-    assert (~same).sum() <= 4
+    rep = explain_sweep(y, logw, SIG, BOX, th, ll, beta, off, 0.3, 66, 1, np_(tt), np_(lt))
+    assert rep.unexplained == [] and len(rep.differing) <= 1, rep
 
 
 def test_popmcmc_full_size_runs_and_reuses_queue(smc):
@@ -534,13 +529,11 @@ def test_popmcmc_full_size_parity(smc, shape):
     rt, rl, rst = oracle.popmcmc_sweep(y, w.logw(), w.sigma, BOX, th, ll, beta, off, w.scale, 3,
                                        7)
     gt, gl = np_(tt), np_(lt)
-    bad = []
-    for q in range(w.n_pops):
-        a, b = off[q], off[q + 1]
-        if not (np.allclose(gt[:, a:b], rt[:, a:b], rtol=3e-7, atol=2e-6) and
-                np.allclose(gl[a:b], rl[a:b], rtol=1e-5)):
-            bad.append(q)
-    assert len(bad) <= 2, bad
+    # every population that differs is reproduced by the oracle's sweep with
+    # in-band decisions taken the other way; such populations stay rare
+    rep = explain_sweep(y, w.logw(), w.sigma, BOX, th, ll, beta, off, w.scale, 3, 7, gt, gl)
+    assert rep.unexplained == [], rep
+    assert len(rep.differing) <= 3, rep
     s = np_(stats)
     assert s[2] == rst[2]
     assert abs(int(s[0]) - int(rst[0])) <= 4 and abs(int(s[1]) - int(rst[1])) <= 4

@@ -103,3 +103,47 @@ def test_noalloc_identity_flag_and_limits(lib):
     # and the next call is correct again
     r = _both(L, ctx, W, 6, 10)
     assert np.array_equal(r["ctx"][0], r["noalloc"][0]) and r["noalloc"][3] == 0
+
+
+def test_noalloc_at_the_size_limit_matches_the_context_entry_point(lib):
+    """The largest sizes the static array serves (2^24 weights: every tile
+    sum of the array in use, the constants right after them) and one below."""
+    L, ctx = lib
+    for M, seed in [(1 << 24, 21), ((1 << 24) - 1, 22)]:
+        W = torch.from_numpy(_weights(M, seed, 1.0)).cuda()
+        r = _both(L, ctx, W, seed, 3)
+        assert r["noalloc"][3] == 0
+        assert np.array_equal(r["ctx"][0], r["noalloc"][0])
+        assert np.array_equal(r["ctx"][1], r["noalloc"][1])
+
+
+def test_noalloc_one_hot_and_peaked_weights_near_the_limit_match_the_oracle(lib):
+    """Without heavy-chunk scratch a tile whose output range is long is
+    expanded by its own CTA: one-hot weights (one particle takes every slot)
+    and a few heavy particles among light ones, at M = 2^24 - 3, against
+    the oracle's exact-integer resampling (ancestors bit-exact)."""
+    import oracle
+    L, _ = lib
+    M = (1 << 24) - 3
+    onehot = np.zeros(M)
+    onehot[M // 3] = 1.0
+    peaked = np.full(M, 1e-12)
+    peaked[[7, M // 2, M - 2]] = [0.5, 0.3, 0.2]
+    peaked /= peaked.sum()
+    for name, Wh in (("one-hot", onehot), ("peaked", peaked)):
+        W = torch.from_numpy(Wh).cuda()
+        anc = torch.full((M,), -1, dtype=torch.int32, device="cuda")
+        cnt = torch.full((M,), -1, dtype=torch.int32, device="cuda")
+        sw = torch.zeros(1, dtype=torch.int32, device="cuda")
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record()
+        assert L.smc_resample_systematic_noalloc(_p(W), M, 31, 4, _p(anc), _p(cnt), None, None,
+                                                 _p(sw), None) == 0
+        t1.record()
+        torch.cuda.synchronize()
+        assert int(sw.item()) == 0, name
+        ranc, rcnt = oracle.resample_systematic(Wh, oracle.resample_u32(31, 4))
+        assert np.array_equal(anc.cpu().numpy(), ranc), name
+        assert np.array_equal(cnt.cpu().numpy(), rcnt), name
+        print(f"{name}: {t0.elapsed_time(t1):.3f} ms per call (first call of this input)")
