@@ -130,19 +130,21 @@ constexpr double kLog2e = 1.4426950408889634074;
 // and above (and infinities) give +-1e30: the callers only exponentiate
 // non-positive differences, for which both ends are exact enough.
 __device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(d);
-    uint32_t hw = (uint32_t)(b >> 32), lw = (uint32_t)b;
-    int e = (int)((hw >> 20) & 0x7FFu);
-    uint32_t sign = hw & 0x80000000u;
-    if (e < 949) { hi = 0.0f; lo = 0.0f; return; }
-    if (e >= 1023 + 100) { hi = sign ? -1e30f : 1e30f; lo = 0.0f; return; }
-    uint32_t fh = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) | (lw >> 29);
-    hi = __uint_as_float(fh);
+    // branch-free: both ends are formed and selected, so a warp whose
+    // elements span the ranges does not diverge
+    const uint32_t hw = (uint32_t)__double2hiint(d), lw = (uint32_t)__double2loint(d);
+    const int e = (int)((hw >> 20) & 0x7FFu);
+    const uint32_t sign = hw & 0x80000000u;
+    const uint32_t fh = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) |
+                        (lw >> 29);
     // the top 23 of the 29 remaining bits, times 2^(e-1069): the 6 dropped
     // bits lie 2^-46 below hi
     const float r = u23_to_f((lw & 0x1FFFFFFFu) >> 6);
     const float scale = __uint_as_float((uint32_t)(e - 1069 + 127) << 23);
-    lo = sign ? -(r * scale) : r * scale;
+    const float l = sign ? -(r * scale) : r * scale;
+    const bool small = e < 949, big = e >= 1023 + 100;
+    hi = small ? 0.0f : (big ? (sign ? -1e30f : 1e30f) : __uint_as_float(fh));
+    lo = (small || big) ? 0.0f : l;
 }
 
 // exp(d) for an FP64 d <= 0 given as hi + lo floats, in FP32: the argument
@@ -153,14 +155,14 @@ __device__ __forceinline__ float exp_hilo(float hi, float lo) {
     const float L2E_HI = 1.44269502162933349609375f;   // log2(e) rounded to float
     const float L2E_LO = 1.925963033500011e-08f;       // log2(e) - L2E_HI
     const float ph = hi * L2E_HI;
-    if (ph < -127.0f) return 0.0f;                     // below 2^-126 (also -inf, NaN-free)
+    // below 2^-126 (also -inf): 0, selected at the end (no branch)
+    const float phc = fmaxf(ph, -127.5f);
     int ki;
-    const float k = round_magic(ph, ki);               // |ph| < 2^22 here
-    if (ki < -126) return 0.0f;
+    const float k = round_magic(phc, ki);              // |phc| < 2^22 here
     const float pl = fmaf(hi, L2E_HI, -ph);
-    const float f = (ph - k) + (pl + fmaf(hi, L2E_LO, lo * L2E_HI));
+    const float f = (phc - k) + (pl + fmaf(hi, L2E_LO, lo * L2E_HI));
     const float p2 = __uint_as_float((uint32_t)(ki + 127) << 23);
-    return ex2(f) * p2;
+    return (ph < -127.0f || ki < -126) ? 0.0f : ex2(f) * p2;
 }
 
 // Programmatic dependent launch: kernels of consecutive calls on a stream are
@@ -180,9 +182,11 @@ __device__ __forceinline__ long long dkey(double x) {
     long long b = __double_as_longlong(x);
     return b ^ ((b >> 63) & 0x7FFFFFFFFFFFFFFFLL);
 }
+// on the 32-bit halves (an integer test on the whole word may be compiled
+// to an FP64 comparison, and the FP64 pipe is narrow on this part)
 __device__ __forceinline__ bool disnan(double x) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    return (b & 0x7FFFFFFFFFFFFFFFull) > 0x7FF0000000000000ull;
+    const uint32_t h = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
+    return h > 0x7FF00000u || (h == 0x7FF00000u && __double2loint(x) != 0);
 }
 
 // float -> double by integer operations (subnormal floats give 0)

@@ -48,8 +48,28 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ anc,
 
 namespace smc_host {
 
+// The finalize kernel (one CTA, the tile sums staged through 64 KiB of
+// dynamic shared memory); qr: also every tile's (Q_t, R_t) for pass 2.
+smc_status resample_finalize_launch(int64_t M, uint64_t seed, uint64_t step,
+                                    const int32_t* do_flag, const smc::RsScratch& sc, bool qr,
+                                    uint32_t* status, cudaStream_t s) {
+    static bool attr_set[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (!attr_set[dev]) {
+        SMC_CUDA(cudaFuncSetAttribute(smc::k_resample_finalize,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smc::kRsFinSmem));
+        attr_set[dev] = true;
+    }
+    return launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), smc::kRsFinSmem,
+                      s, M, seed, step, do_flag, sc, qr ? 1 : 0, status);
+}
+
 // tiles_ready: the tile sums of pass 1 are already in sc (formed by the
-// normalisation pass of smc_reweight_resample), so pass 1 is skipped
+// normalisation pass of smc_reweight_resample, which writes the weights in
+// descending tile order), so pass 1 is skipped and pass 2 runs ascending;
+// otherwise pass 1 runs ascending and pass 2 descending
 smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t seed, uint64_t step,
                            int32_t* anc, int32_t* counts, const int32_t* do_flag, double* lwreset,
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s,
@@ -64,8 +84,7 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                         M, do_flag, sc, status);
         if (st != SMC_OK) return st;
     }
-    st = launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), 0, s, M, seed,
-                    step, do_flag, sc, status);
+    st = resample_finalize_launch(M, seed, step, do_flag, sc, true, status, s);
     if (st != SMC_OK) return st;
     // pass 2 is persistent: as many CTAs as are resident at once (per device)
     static int occ_of_dev[64] = {};
@@ -82,7 +101,7 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     int64_t g2 = (int64_t)num_sms * occ;
     if (g2 > tiles) g2 = tiles;
     st = launch_pdl(smc::k_resample_scan, dim3((unsigned)g2), dim3(smc::kRsThreads), 0, s, W, M,
-                    seed, step, do_flag, sc, anc, counts, lwreset, status);
+                    tiles_ready ? 0 : 1, do_flag, sc, anc, counts, lwreset, status);
     if (st != SMC_OK) return st;
     if (sc.heavy_list) {
         st = launch_pdl(smc::k_resample_heavy, dim3((unsigned)num_sms * 4), dim3(smc::kRsThreads),
@@ -92,18 +111,21 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     return SMC_OK;
 }
 
-// scratch layout inside `base`: tile sums, the call constants, then (when
-// `heavy`) the heavy-chunk counter, the chunk records and the items'
-// inclusive F
+// scratch layout inside `base`: tile sums, the call constants, the tiles'
+// Q and R, then (when `heavy`) the heavy-chunk counter, the chunk records
+// and the items' inclusive F
 smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy) {
     smc::RsScratch sc;
+    const int64_t nt = smc::rs_tiles(M);
     sc.tile_sum = base;
-    sc.cst = reinterpret_cast<smc::RsConst*>(base + smc::rs_tiles(M));
+    sc.cst = reinterpret_cast<smc::RsConst*>(base + nt);
+    sc.tile_q = base + nt + smc::kRsConstWords;
+    sc.tile_r = sc.tile_q + nt;
     sc.heavy_count = nullptr;
     sc.heavy_list = nullptr;
     sc.fpos = nullptr;
     if (heavy) {
-        sc.heavy_count = base + smc::rs_tiles(M) + smc::kRsConstWords;
+        sc.heavy_count = base + smc::rs_words(M);
         uintptr_t p = reinterpret_cast<uintptr_t>(sc.heavy_count + 1);
         p = (p + 255) & ~(uintptr_t)255;
         sc.heavy_list = reinterpret_cast<uint4*>(p);
@@ -162,8 +184,9 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 namespace {
 
 constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;   // 16,777,216 weights
-// 8192 tile sums + the call constants: about 64 KiB per device
-constexpr int64_t kNoAllocWords = (kNoAllocMaxM / smc::kRsTile) + smc::kRsConstWords;
+// 8192 tile sums, the call constants, 8192 tile quotients and remainders:
+// about 192 KiB per device
+constexpr int64_t kNoAllocWords = smc::rs_words(kNoAllocMaxM);
 static_assert(sizeof(smc::RsConst) <= smc::kRsConstWords * sizeof(unsigned long long),
               "constants fit their words");
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kNoAllocWords];

@@ -1,17 +1,25 @@
 // resample.cuh -- kernels of the exact-integer systematic resampler
-// (included by resample.cu only).  The scratch words they use are passed
-// in explicitly, so any owner of suitable device memory can run them.
+// (included by resample.cu and resample_var.cu).  The scratch words they
+// use are passed in explicitly, so any owner of suitable device memory can
+// run them.
 //
 // Pass 1 (k_resample_total): every tile of kRsTile weights is quantised
 // (q = floor(W 2^52) from the FP64 bits) and reduced exactly; the tile's
 // integer sum is stored.
 // Between the passes (k_resample_finalize, one CTA): the tile sums become
-// exclusive prefixes and the call's constants (S, the uniform, fixed-point
-// reciprocals) are formed once.
+// exclusive prefixes c_t, the call's constants (S, the uniform, fixed-point
+// reciprocals) are formed once, and so is every tile's c_t M = Q_t S + R_t.
 // Pass 2 (k_resample_scan, persistent over tiles): each tile reads its
-// prefix (no waiting on other CTAs), is scanned in shared memory, F is
-// evaluated at every prefix and the tile's contiguous output range is
-// expanded; ranges too long for one CTA go to k_resample_heavy.
+// prefix and (Q_t, R_t) (no waiting on other CTAs), each warp scans its 256
+// items, F is carried item by item from (Q_t, R_t), and each warp expands its
+// own contiguous output range through shared memory; ranges too long for a
+// warp go to k_resample_heavy.
+//
+// The passes alternate direction over the tiles (pass 1 ascending, pass 2
+// descending after it, or ascending after a normalisation that wrote the
+// weights in descending order), so the second read of the weights finds
+// the most recently touched ones still in L2; loads and stores that are a
+// datum's last use carry the streaming (evict-first) hint.
 #pragma once
 #include "device.cuh"
 
@@ -27,7 +35,7 @@ constexpr int kRsStage = 2 * kRsTile;          // output slots of a tile staged 
 struct RsConst {
     unsigned long long S;       // exact total of the quantised weights
     unsigned long long Rth;     // floor(u32 S / 2^32)
-    unsigned long long qheavy;  // items with q above this are divided afresh
+    unsigned long long qheavy;  // items (and offsets) with q above this are divided afresh
     unsigned long long mfx;     // floor(M 2^64 / S) when M < S, else 0 (use FP64)
     unsigned long long ifx;     // floor(2^64 / S) when S > 1, else 0
     double m_over_s;            // M / S (FP64 estimates, only when M >= S)
@@ -37,38 +45,46 @@ constexpr int kRsConstWords = 8;
 
 struct RsScratch {
     unsigned long long* tile_sum;   // [ntiles]: tile sums, then their exclusive prefixes
+    unsigned long long* tile_q;     // [ntiles]: Q_t of c_t M = Q_t S + R_t (finalize)
+    unsigned long long* tile_r;     // [ntiles]: R_t
     RsConst* cst;                   // after the tile sums
     // grid-wide expansion of tiles with many output slots (optional: when
     // null, such a tile is expanded by its own CTA)
     unsigned long long* heavy_count;  // chunk records written, zero before pass 2
-    uint4* heavy_list;                // {tile, tile's first slot, chunk begin, chunk end}
-    uint32_t* fpos;                   // [M] inclusive F of the items of heavy tiles
+    uint4* heavy_list;                // {first item, items, chunk begin, chunk end}
+    uint32_t* fpos;                   // [M] inclusive F of the items of heavy warp segments
 };
 
-__host__ __device__ inline int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1) / kRsTile; }
-// words of scratch for M weights: tile sums, constants
-__host__ __device__ inline int64_t rs_words(int64_t M) { return rs_tiles(M) + kRsConstWords; }
+__host__ __device__ constexpr int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1) / kRsTile; }
+// words of scratch for M weights: tile sums, constants, per-tile Q and R
+__host__ __device__ constexpr int64_t rs_words(int64_t M) {
+    return 3 * rs_tiles(M) + kRsConstWords;
+}
+// items of one warp's segment of a tile in pass 2, and the output slots a
+// warp stages in shared memory
+constexpr int kRsSeg = 32 * kRsIpt;
+constexpr int kRsWarpStage = 2 * kRsSeg;
 // output slots of one heavy-expansion chunk, and the most chunk records M
-// weights can produce (a tile's range is split into chunks; ranges add to M)
+// weights can produce (a segment's range is split into chunks; ranges add to M)
 constexpr int kRsChunk = 4096;
 __host__ __device__ inline int64_t rs_heavy_records(int64_t M) {
-    return rs_tiles(M) + M / kRsChunk + 1;
+    return rs_tiles(M) * (kRsTile / kRsSeg) + M / kRsChunk + 1;
 }
 
-// floor(w 2^52) from the bits of w in [0,1]; false if w is outside [0,1] or NaN
+// floor(w 2^52) from the bits of w in [0,1]; false if w is outside [0,1] or
+// NaN.  On the 32-bit halves of w (an integer test on the whole word may be
+// compiled to an FP64 comparison, and the FP64 pipe is narrow on this part).
 __device__ __forceinline__ bool quantise(double w, unsigned long long& q) {
-    unsigned long long b = (unsigned long long)__double_as_longlong(w);
-    if (b >> 63) {                       // negative (or -0)
-        q = 0;
-        return b == 0x8000000000000000ull;
-    }
-    uint32_t e = (uint32_t)(b >> 52);
-    unsigned long long man = b & 0xFFFFFFFFFFFFFull;
-    if (e > 1023 || (e == 1023 && man != 0)) { q = 0; return false; }  // > 1, inf, NaN
-    uint32_t sh = 1023u - e;
-    q = sh > 52 ? 0ull : (((1ull << 52) | man) >> sh);
-    if (e == 0) q = 0;                   // zero / subnormal
-    return true;
+    const uint32_t hw = (uint32_t)__double2hiint(w), lw = (uint32_t)__double2loint(w);
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    const uint32_t mh = hw & 0xFFFFFu;
+    const bool neg = (hw >> 31) != 0;
+    const bool above = e > 1023u || (e == 1023u && (mh | lw) != 0u);  // > 1, inf, NaN
+    const uint32_t sh = 1023u - e;                                     // w < 2^-sh ... 2^(1-sh)
+    const unsigned long long man = ((unsigned long long)(mh | 0x100000u) << 32) | lw;
+    const unsigned long long v = sh > 52u ? 0ull : (man >> (sh & 63u));
+    q = (neg || above || e == 0u) ? 0ull : v;  // zero / subnormal / negative / invalid: 0
+    return neg ? (hw == 0x80000000u && lw == 0u) : !above;  // -0 is a valid zero
 }
 
 // this thread's kRsIpt weights of tile `tile`, quantised (0 past M)
@@ -115,6 +131,24 @@ __device__ __forceinline__ void load_tile_raw(const double* __restrict__ W, int6
     }
 }
 
+// load_tile_raw with the streaming hint (the weights' last read)
+__device__ __forceinline__ void load_tile_raw_cs(const double* __restrict__ W, int64_t M,
+                                                 int64_t tile, double (&v)[kRsIpt]) {
+    const int64_t g0 = tile * kRsTile + (int64_t)threadIdx.x * kRsIpt;
+    if (g0 + kRsIpt <= M && ((reinterpret_cast<uintptr_t>(W + g0) & 15u) == 0)) {
+        const double2* p = reinterpret_cast<const double2*>(W + g0);
+#pragma unroll
+        for (int j = 0; j < kRsIpt / 2; ++j) {
+            const double2 d = __ldcs(p + j);
+            v[2 * j] = d.x;
+            v[2 * j + 1] = d.y;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) v[j] = g0 + j < M ? __ldcs(W + g0 + j) : 0.0;
+    }
+}
+
 // block-wide sum of 64-bit values; result valid in thread 0
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v,
                                                             unsigned long long* sh) {
@@ -129,33 +163,39 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
     return t;
 }
 
-// Pass 1: the exact integer sum of every tile (each CTA a contiguous range
-// of tiles, the next tile's weights loading while one is reduced).
+// Pass 1: the exact integer sum of every tile; tiles dealt round-robin in
+// ascending order, the next tile's weights loading while one is reduced,
+// one barrier per tile (the warp sums alternate between two arrays).
 static __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __restrict__ W,
                                                                int64_t M, const int32_t* do_flag,
                                                                RsScratch sc, uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
-    __shared__ unsigned long long sh[kRsThreads / 32];
+    __shared__ unsigned long long sh[2][kRsThreads / 32];
     const int64_t ntiles = rs_tiles(M);
-    const int64_t per = (ntiles + gridDim.x - 1) / gridDim.x;
-    const int64_t t0 = (int64_t)blockIdx.x * per;
-    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
+    const int wid = threadIdx.x >> 5;
     bool bad = false;
     double vn[kRsIpt];
-    if (t0 < t1) load_tile_raw(W, M, t0, vn);
-    for (int64_t t = t0; t < t1; ++t) {
+    int64_t tile = blockIdx.x;
+    if (tile < ntiles) load_tile_raw(W, M, tile, vn);
+    for (int buf = 0; tile < ntiles; tile += gridDim.x, buf ^= 1) {
         unsigned long long q[kRsIpt];
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) bad |= !quantise(vn[j], q[j]);
-        if (t + 1 < t1) load_tile_raw(W, M, t + 1, vn);  // next tile in flight
+        if (tile + gridDim.x < ntiles) load_tile_raw(W, M, tile + gridDim.x, vn);
         unsigned long long acc = 0;
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) acc += q[j];  // <= 8 * 2^52: no wrap
-        const unsigned long long ts = block_sum_u64(acc, sh);  // <= 2^63: no wrap
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((threadIdx.x & 31) == 0) sh[buf][wid] = acc;
+        __syncthreads();
         if (threadIdx.x == 0) {
-            sc.tile_sum[t] = ts;
+            unsigned long long ts = 0;  // <= 2^63: no wrap
+#pragma unroll
+            for (int w = 0; w < kRsThreads / 32; ++w) ts += sh[buf][w];
+            sc.tile_sum[tile] = ts;
             if (ts >= kMaxTotal) bad = true;  // far from normalised
         }
     }
@@ -252,90 +292,87 @@ static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned
 }
 
 // Between the passes, one CTA: the exact total S from the tile sums, the
-// call's uniform and constants, and every tile's exclusive prefix (the tile
-// sums are replaced in place), so that no tile of pass 2 repeats this work.
+// call's uniform and constants, every tile's exclusive prefix c_t (the tile
+// sums are replaced in place) and, with `qr`, every tile's c_t M = Q_t S +
+// R_t, so that no tile of pass 2 repeats this work.  The tile sums pass
+// through shared memory kRsFinTiles at a time (coalesced loads and stores);
+// each thread scans eight consecutive ones.
 constexpr int kRsFinThreads = 1024;
+constexpr int kRsFinTiles = 8 * kRsFinThreads;
+constexpr size_t kRsFinSmem = (size_t)kRsFinTiles * sizeof(unsigned long long);
 static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
-    int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc,
+    int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc, int qr,
     uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
+    extern __shared__ unsigned long long s_t[];  // kRsFinTiles
     __shared__ unsigned long long s_w[kRsFinThreads / 32];
+    __shared__ unsigned long long s_run;
     __shared__ int s_bad;
+    __shared__ RsConst s_c;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
-    if (tid == 0) s_bad = 0;
-    __syncthreads();
-    // each thread scans a contiguous run of tile sums (up to 8 loads in
-    // flight at a time)
-    const int64_t per = (ntiles + kRsFinThreads - 1) / kRsFinThreads;
-    const int64_t t0 = (int64_t)tid * per;
-    const int64_t t1 = t0 + per < ntiles ? t0 + per : ntiles;
-    // up to 8 tiles per thread (M <= 2^24): the run stays in registers
-    // between the sum and the prefix writes
-    const bool in_regs = per <= 8;
-    unsigned long long v0[8];
-    unsigned long long own = 0;
-    bool ovf = false;
-    for (int64_t t = t0; t < t1; t += 8) {
-        unsigned long long v[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            v0[k] = v[k];
-            const unsigned long long n = own + v[k];
-            ovf |= n < own;
-            own = n;
-        }
-    }
-    // block exclusive scan of the runs
-    unsigned long long incl = own;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) {
-            ovf |= incl + v < incl;
-            incl += v;
-        }
-    }
-    if (lane == 31) s_w[wid] = incl;
-    if (ovf) s_bad = 1;
-    __syncthreads();
-    unsigned long long off = 0, S = 0;
-    bool ovf2 = s_bad != 0;
-    for (int w = 0; w < kRsFinThreads / 32; ++w) {
-        if (w < wid) off += s_w[w];
-        const unsigned long long n = S + s_w[w];
-        ovf2 |= n < S;
-        S = n;
-    }
-    unsigned long long run = off + incl - own;
-    if (in_regs) {
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            if (t0 + k < t1) sc.tile_sum[t0 + k] = run;
-            run += t0 + k < t1 ? v0[k] : 0ull;
-        }
-    } else {
-        for (int64_t t = t0; t < t1; t += 8) {
-            unsigned long long v[8];
-#pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] = t + k < t1 ? __ldcg(sc.tile_sum + t + k) : 0ull;
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                if (t + k < t1) sc.tile_sum[t + k] = run;
-                run += v[k];
-            }
-        }
-    }
-    if (tid == 0 && sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
     if (tid == 0) {
+        s_bad = 0;
+        s_run = 0;
+    }
+    __syncthreads();
+    for (int64_t base = 0; base < ntiles; base += kRsFinTiles) {
+        const int n = (int)(ntiles - base < kRsFinTiles ? ntiles - base : kRsFinTiles);
+        for (int i = tid; i < n; i += kRsFinThreads) s_t[i] = __ldcg(sc.tile_sum + base + i);
+        __syncthreads();
+        // warp wid scans tiles [256 wid, 256 wid + 256): round k holds tile
+        // 256 wid + 32 k + lane (conflict-free shared-memory accesses)
+        unsigned long long carry = 0;
+        bool ovf = false;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = wid * 256 + k * 32 + lane;
+            const unsigned long long v = i < n ? s_t[i] : 0ull;
+            unsigned long long incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                if (lane >= o) {
+                    ovf |= incl + u < incl;
+                    incl += u;
+                }
+            }
+            const unsigned long long ex = carry + incl - v;  // exclusive within the warp's run
+            ovf |= carry + incl < carry;
+            if (i < n) s_t[i] = ex;
+            carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+        }
+        if (lane == 0) s_w[wid] = carry;
+        if (ovf) s_bad = 1;
+        __syncthreads();
+        unsigned long long off = s_run, tot = 0;
+        bool ovf2 = false;
+        for (int w = 0; w < kRsFinThreads / 32; ++w) {
+            if (w < wid) off += s_w[w];
+            const unsigned long long nn = tot + s_w[w];
+            ovf2 |= nn < tot;
+            tot = nn;
+        }
+        if (ovf2 || s_run + tot < s_run) s_bad = 1;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = wid * 256 + k * 32 + lane;
+            if (i < n) s_t[i] += off;
+        }
+        __syncthreads();
+        for (int i = tid; i < n; i += kRsFinThreads) sc.tile_sum[base + i] = s_t[i];
+        if (tid == 0) s_run += tot;
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
+        const unsigned long long S = s_run;
         RsConst c;
         c.ok = 0;
-        if (S == 0 || S >= kMaxTotal || ovf2) {
-            raise_status(status, S == 0 && !ovf2 ? ST_ZERO_WEIGHT : ST_BADARG);
+        if (S == 0 || S >= kMaxTotal || s_bad) {
+            raise_status(status, S == 0 && !s_bad ? ST_ZERO_WEIGHT : ST_BADARG);
         } else {
             const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
             const unsigned long long MM = (unsigned long long)M;
@@ -344,11 +381,27 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
             c.m_over_s = (double)MM / (double)S;
             c.mfx = MM < S ? div_shift64(MM, S) : 0ull;
             c.ifx = S > 1 ? div_shift64(1ull, S) : 0ull;
-            // R + q M < 8 S + S < 2^64 while S < 2^60 (else every item is divided)
-            c.qheavy = S < (1ull << 60) && c.ifx ? (7ull * S) / MM : 0ull;
+            // items with q M <= 2^64 - S keep R + q M < 2^64, where the
+            // fixed-point quotient is off by at most one (heavier ones are
+            // divided afresh)
+            c.qheavy = c.ifx ? (0ull - S) / MM : 0ull;
             c.ok = 1;
         }
         *sc.cst = c;
+        s_c = c;
+    }
+    __syncthreads();
+    if (!qr || !s_c.ok) return;
+    // every tile's c_t M = Q_t S + R_t (the prefixes are still in shared
+    // memory when they all fit)
+    const RsConst c = s_c;
+    const bool in_smem = ntiles <= kRsFinTiles;
+    for (int64_t t = tid; t < ntiles; t += kRsFinThreads) {
+        const unsigned long long ct = in_smem ? s_t[t] : __ldcg(sc.tile_sum + t);
+        unsigned long long Q, R;
+        divmod_cm(ct, (unsigned long long)M, c, Q, R);
+        sc.tile_q[t] = Q;
+        sc.tile_r[t] = R;
     }
 }
 
@@ -358,22 +411,25 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
 #define SMC_RS_MINB 3
 #endif
 
-// Pass 2: one CTA per tile.
+// Pass 2, persistent over tiles (descending when `rev`, else ascending).
+// Per tile: each thread quantises its 8 weights and each warp scans its 256
+// items with shuffles; one barrier exchanges the warp totals; each thread
+// carries the tile's (Q_t, R_t) to its own offset and then item by item to
+// F at each inclusive prefix; each warp writes its items' offspring counts
+// and log-weight reset, and expands its own output range [lo, hi): through
+// shared memory when it holds at most kRsWarpStage slots, else as chunks
+// for k_resample_heavy (or, without that scratch, by the warp itself).
 static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
-    const double* __restrict__ W, int64_t M, uint64_t seed, uint64_t step,
-    const int32_t* do_flag, RsScratch sc, int32_t* __restrict__ anc,
-    int32_t* __restrict__ counts, double* __restrict__ lwreset, uint32_t* status) {
+    const double* __restrict__ W, int64_t M, int rev, const int32_t* do_flag, RsScratch sc,
+    int32_t* __restrict__ anc, int32_t* __restrict__ counts, double* __restrict__ lwreset,
+    uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
-    __shared__ uint32_t s_hi[kRsTile];            // F at each item's inclusive prefix
-    __shared__ int32_t s_anc[kRsStage];           // the tile's ancestors, staged for coalesced stores
-    __shared__ unsigned long long s_warp[kRsThreads / 32];
-    __shared__ uint32_t s_lo;
-    __shared__ unsigned long long s_qr[2];
+    __shared__ uint32_t s_hi[kRsTile];                          // inclusive F of each item
+    __shared__ int32_t s_anc[kRsThreads / 32][kRsWarpStage];    // a warp's staged slots
+    __shared__ unsigned long long s_warp[2][kRsThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
-    (void)seed;
-    (void)step;
 
     if (do_flag && *do_flag == 0) {  // no resampling this step: identity
         for (int64_t g = (int64_t)blockIdx.x * kRsThreads + tid; g < M;
@@ -391,166 +447,199 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
     const unsigned long long Rth = cst.Rth;
     const unsigned long long qheavy = cst.qheavy;
     const unsigned long long ifx = cst.ifx;
-    // persistent over tiles; the next tile's weights and prefix load while
-    // the current one is processed
-    int64_t tile = blockIdx.x;
+    // carry R + a M (< 2^64 for a <= qheavy) into Q: n = floor((R + a M) / S)
+    // from the fixed-point reciprocal ifx = floor(2^64 / S) (integer
+    // multiply-high, off by at most one below) and one correction
+    auto carry = [&](unsigned long long& Q, unsigned long long& R, unsigned long long a) {
+        const unsigned long long R2 = R + a * MM;
+        unsigned long long n = __umul64hi(R2, ifx);
+        unsigned long long r = R2 - n * S;
+        const bool hi1 = r >= S;
+        Q += n + (hi1 ? 1ull : 0ull);
+        R = r - (hi1 ? S : 0ull);
+    };
+    // persistent over tiles; the next tile's weights, prefix, Q and R load
+    // while the current one is processed
+    int64_t k = blockIdx.x;
+    auto tile_of = [&](int64_t kk) { return rev ? ntiles - 1 - kk : kk; };
     double vn[kRsIpt];
-    unsigned long long pn = 0;
-    if (tile < ntiles) {
-        load_tile_raw(W, M, tile, vn);
-        pn = __ldcg(sc.tile_sum + tile);
+    unsigned long long pn = 0, qn = 0, rn = 0;
+    if (k < ntiles) {
+        const int64_t t = tile_of(k);
+        load_tile_raw_cs(W, M, t, vn);
+        pn = __ldcg(sc.tile_sum + t);
+        qn = __ldcg(sc.tile_q + t);
+        rn = __ldcg(sc.tile_r + t);
     }
-    for (; tile < ntiles; tile += gridDim.x) {
+    for (int buf = 0; k < ntiles; k += gridDim.x, buf ^= 1) {
+        const int64_t tile = tile_of(k);
         const int64_t base = tile * kRsTile;
         unsigned long long q[kRsIpt];
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) quantise(vn[j], q[j]);  // pass 1 reported bad weights
-        const unsigned long long tpre = pn;  // the tile's exclusive prefix (finalize)
-        if (tile + gridDim.x < ntiles) {
-            load_tile_raw(W, M, tile + gridDim.x, vn);
-            pn = __ldcg(sc.tile_sum + tile + gridDim.x);
+        const unsigned long long tpre = pn, tq = qn, tr = rn;
+        if (k + gridDim.x < ntiles) {
+            const int64_t t = tile_of(k + gridDim.x);
+            load_tile_raw_cs(W, M, t, vn);
+            pn = __ldcg(sc.tile_sum + t);
+            qn = __ldcg(sc.tile_q + t);
+            rn = __ldcg(sc.tile_r + t);
         }
         unsigned long long tsum = 0;
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) tsum += q[j];
-        // ---- block exclusive scan of the thread sums
+        // ---- warp inclusive scan, then the warp totals across the block
         unsigned long long incl = tsum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const unsigned long long v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
             if (lane >= o) incl += v;
         }
-        __syncthreads();  // the previous tile is done with shared memory
-        if (lane == 31) s_warp[wid] = incl;
-        if (tid == 0) {  // the tile's own c M = Q S + R, divided once
-            unsigned long long Qt, Rt;
-            divmod_cm(tpre, MM, cst, Qt, Rt);
-            s_qr[0] = Qt;
-            s_qr[1] = Rt;
-        }
+        if (lane == 31) s_warp[buf][wid] = incl;
         __syncthreads();
         unsigned long long woff = 0;
 #pragma unroll
         for (int w = 0; w < kRsThreads / 32; ++w)
-            if (w < wid) woff += s_warp[w];
+            if (w < wid) woff += s_warp[buf][w];
         const unsigned long long off = woff + (incl - tsum);  // this thread's offset in the tile
         unsigned long long c = tpre + off;                    // C before this thread's item 0
-        unsigned long long Q = s_qr[0], R = s_qr[1];
-        if (off <= qheavy) {  // carry the tile's Q, R by off M (< 8 S)
-            const unsigned long long R2 = R + off * MM;
-            unsigned long long n = __umul64hi(R2, ifx);
-            unsigned long long r = R2 - n * S;
-            const bool hi1 = r >= S;
-            Q += n + (hi1 ? 1ull : 0ull);
-            R = r - (hi1 ? S : 0ull);
-        } else {
-            divmod_cm(c, MM, cst, Q, R);
-        }
-        const uint32_t F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-        if (tid == 0) s_lo = F0;
+        unsigned long long Q = tq, R = tr;
+        uint32_t Fv[kRsIpt];
+        uint32_t F0;
+        // the usual case, taken per warp: no heavy item and a small offset,
+        // every carry by a multiply-high (no division, no branch)
+        bool light = off <= qheavy;
 #pragma unroll
-        for (int j = 0; j < kRsIpt; ++j) {
-            c += q[j];
-            if (q[j] > qheavy) {  // rare: a heavy item, divided afresh
-                divmod_cm(c, MM, cst, Q, R);
-            } else {
-                // carry R + q M (< 9 S < 2^64) into Q without a data-dependent
-                // loop: n = floor((R + q M) / S) in [0, 8] from the
-                // fixed-point reciprocal ifx = floor(2^64 / S) (integer
-                // multiply-high, off by at most one below) and one correction
-                const unsigned long long R2 = R + q[j] * MM;
-                unsigned long long n = __umul64hi(R2, ifx);
-                unsigned long long r = R2 - n * S;
-                const bool hi1 = r >= S;
-                n += hi1 ? 1ull : 0ull;
-                r -= hi1 ? S : 0ull;
-                Q += n;
-                R = r;
+        for (int j = 0; j < kRsIpt; ++j) light &= q[j] <= qheavy;
+        if (__all_sync(0xFFFFFFFFu, light)) {
+            carry(Q, R, off);
+            F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+#pragma unroll
+            for (int j = 0; j < kRsIpt; ++j) {
+                carry(Q, R, q[j]);
+                const uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+                Fv[j] = Fn < (uint32_t)M ? Fn : (uint32_t)M;
             }
-            uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-            if (Fn > (uint32_t)M) Fn = (uint32_t)M;
-            s_hi[tid * kRsIpt + j] = Fn;
+        } else {
+            if (off <= qheavy) carry(Q, R, off);  // by off M
+            else divmod_cm(c, MM, cst, Q, R);
+            F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+#pragma unroll 1
+            for (int j = 0; j < kRsIpt; ++j) {
+                c += q[j];
+                if (q[j] > qheavy) divmod_cm(c, MM, cst, Q, R);  // a heavy item, divided afresh
+                else carry(Q, R, q[j]);
+                const uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+                Fv[j] = Fn < (uint32_t)M ? Fn : (uint32_t)M;
+            }
         }
-        __syncthreads();
-        // ---- offspring counts and the log-weight reset, item-major (coalesced)
-        const uint32_t lo = s_lo, hi = s_hi[kRsTile - 1];
-        if (counts)
-            for (int j = tid; j < kRsTile; j += kRsThreads)
-                if (base + j < M) counts[base + j] = (int32_t)(s_hi[j] - (j ? s_hi[j - 1] : lo));
+        // ---- offspring counts and log-weight reset: 8 consecutive per thread
+        const int64_t g0 = base + (int64_t)tid * kRsIpt;
+        const bool full = g0 + kRsIpt <= M;
+        if (counts) {
+#pragma unroll
+            for (int j = 0; j < kRsIpt; ++j)
+                if (g0 + j < M) __stcs(counts + g0 + j, (int32_t)(Fv[j] - (j ? Fv[j - 1] : F0)));
+        }
         if (lwreset) {
-            if (base + kRsTile <= M && ((reinterpret_cast<uintptr_t>(lwreset + base) & 15u) == 0)) {
-                double2* d2 = reinterpret_cast<double2*>(lwreset + base);
-                for (int j = tid; j < kRsTile / 2; j += kRsThreads) d2[j] = make_double2(0.0, 0.0);
+            if (full && ((reinterpret_cast<uintptr_t>(lwreset + g0) & 15u) == 0)) {
+                double2* d2 = reinterpret_cast<double2*>(lwreset + g0);
+#pragma unroll
+                for (int j = 0; j < kRsIpt / 2; ++j) __stcs(d2 + j, make_double2(0.0, 0.0));
             } else {
-                for (int j = tid; j < kRsTile; j += kRsThreads)
-                    if (base + j < M) lwreset[base + j] = 0.0;
+#pragma unroll
+                for (int j = 0; j < kRsIpt; ++j)
+                    if (g0 + j < M) __stcs(lwreset + g0 + j, 0.0);
             }
         }
-        // ---- expand the tile's output range [lo, hi).  Usual case (the range
-        // fits in shared memory): each thread writes its own items' slots there,
-        // then the block stores them slot-major.  A larger range (heavy weights)
-        // is split into chunks for k_resample_heavy, which all CTAs share;
-        // without that scratch the CTA expands it itself (contiguous blocks of
-        // slots per thread, stored directly).
+        // ---- this warp's output range [lo, hi)
+        const uint32_t lo = __shfl_sync(0xFFFFFFFFu, F0, 0);
+        const uint32_t hi = __shfl_sync(0xFFFFFFFFu, Fv[kRsIpt - 1], 31);
         if (hi < lo || hi > (uint32_t)M) {  // cannot happen with consistent sums
-            if (tid == 0) raise_status(status, ST_BADARG);
+            if (lane == 0) raise_status(status, ST_BADARG);
             continue;
         }
         const uint32_t range = hi - lo;
-        if (range <= (uint32_t)kRsStage) {  // uniform over the block
-            // each item writes its first 4 slots with predicated stores; the
-            // rare items with more slots finish in a loop
-            uint32_t f = F0;
-            const int32_t i0 = (int32_t)(base + (int64_t)tid * kRsIpt);
+        const int32_t i0 = (int32_t)g0;  // this thread's first item
+        if (range <= (uint32_t)kRsWarpStage) {  // uniform over the warp
+            // each item writes its slots with predicated stores: up to 2
+            // when no item of the warp has more (the usual case), else up to
+            // 4 and a loop for the rare items with more
+            int32_t* st = s_anc[wid];
+            uint32_t f = F0, most = 0;
 #pragma unroll
             for (int j = 0; j < kRsIpt; ++j) {
-                const uint32_t e = s_hi[tid * kRsIpt + j];
-#pragma unroll
-                for (uint32_t k = 0; k < 4; ++k)
-                    if (f + k < e) s_anc[f + k - lo] = i0 + j;
-                for (uint32_t sl = f + 4; sl < e; ++sl) s_anc[sl - lo] = i0 + j;
-                f = e;
+                const uint32_t nj = Fv[j] - (j ? Fv[j - 1] : F0);
+                most = nj > most ? nj : most;
             }
-            __syncthreads();
-            for (uint32_t k = tid; k < range; k += kRsThreads) anc[lo + k] = s_anc[k];
+            if (__all_sync(0xFFFFFFFFu, most <= 2u)) {
+#pragma unroll
+                for (int j = 0; j < kRsIpt; ++j) {
+                    const uint32_t e = Fv[j];
+                    if (f < e) st[f - lo] = i0 + j;
+                    if (f + 1 < e) st[f + 1 - lo] = i0 + j;
+                    f = e;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kRsIpt; ++j) {
+                    const uint32_t e = Fv[j];
+#pragma unroll
+                    for (uint32_t kk = 0; kk < 4; ++kk)
+                        if (f + kk < e) st[f + kk - lo] = i0 + j;
+                    for (uint32_t sl = f + 4; sl < e; ++sl) st[sl - lo] = i0 + j;
+                    f = e;
+                }
+            }
+            __syncwarp();
+            for (uint32_t kk = lane; kk < range; kk += 32) __stcs(anc + lo + kk, st[kk]);
+            __syncwarp();
             continue;
         }
+        // a long range (heavy weights): the items' inclusive F for the
+        // bisections, then chunks for k_resample_heavy or the warp itself
+        const int64_t sbase = base + (int64_t)wid * kRsSeg;  // the warp's first item
+        const int nit = (int)(M - sbase < kRsSeg ? M - sbase : kRsSeg);
+        uint32_t* fs = s_hi + wid * kRsSeg;
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) fs[lane * kRsIpt + j] = Fv[j];
+        __syncwarp();
         if (sc.heavy_list) {
-            for (int j = tid; j < kRsTile; j += kRsThreads)
-                if (base + j < M) sc.fpos[base + j] = s_hi[j];
-            if (tid == 0) {
+            for (int j = lane; j < nit; j += 32) sc.fpos[sbase + j] = fs[j];
+            if (lane == 0) {
                 const uint32_t nch = (range + kRsChunk - 1) / kRsChunk;
                 const unsigned long long r0 = atomicAdd(sc.heavy_count, (unsigned long long)nch);
-                for (uint32_t k = 0; k < nch; ++k) {
-                    const uint32_t b = lo + k * kRsChunk;
+                for (uint32_t kk = 0; kk < nch; ++kk) {
+                    const uint32_t b = lo + kk * kRsChunk;
                     const uint32_t e = b + kRsChunk < hi ? b + kRsChunk : hi;
-                    sc.heavy_list[r0 + k] = make_uint4((uint32_t)tile, lo, b, e);
+                    sc.heavy_list[r0 + kk] = make_uint4((uint32_t)sbase, (uint32_t)nit, b, e);
                 }
             }
             continue;
         }
-        const uint32_t per = (range + kRsThreads - 1) / kRsThreads;
-        const uint32_t s0 = lo + (uint32_t)tid * per;
+        const uint32_t per = (range + 31) / 32;
+        const uint32_t s0 = lo + (uint32_t)lane * per;
         const uint32_t s1 = s0 + per < hi ? s0 + per : hi;
         if (s0 < s1) {
-            int a = 0, b = kRsTile - 1;  // first item whose inclusive F exceeds s0
+            int a = 0, b = nit - 1;  // first item whose inclusive F exceeds s0
             while (a < b) {
                 const int mid = (a + b) >> 1;
-                if (s_hi[mid] > s0) b = mid;
+                if (fs[mid] > s0) b = mid;
                 else a = mid + 1;
             }
             int item = a;
             for (uint32_t sl = s0; sl < s1; ++sl) {
-                while (s_hi[item] <= sl) ++item;
-                anc[sl] = (int32_t)(base + item);
+                while (fs[item] <= sl) ++item;
+                anc[sl] = (int32_t)(sbase + item);
             }
         }
     }
 }
 
-// Pass 3: the chunks of heavy tiles, shared by all CTAs (grid-stride).  A
-// chunk's first item is found by bisection on the tile's inclusive F
-// values; its slots are staged in shared memory and stored slot-major.
+// Pass 3: the chunks of heavy warp segments, shared by all CTAs
+// (grid-stride).  A chunk's first item is found by bisection on the
+// segment's inclusive F values; its slots are staged in shared memory and
+// stored slot-major.
 static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
     const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
@@ -560,8 +649,8 @@ static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
     const unsigned long long n = __ldcg(sc.heavy_count);
     for (unsigned long long r = blockIdx.x; r < n; r += gridDim.x) {
         const uint4 rec = sc.heavy_list[r];
-        const int64_t base = (int64_t)rec.x * kRsTile;
-        const int nit = (int)(M - base < kRsTile ? M - base : kRsTile);
+        const int64_t base = (int64_t)rec.x;
+        const int nit = (int)rec.y;
         const uint32_t* f = sc.fpos + base;
         const uint32_t b = rec.z, e = rec.w;
         const uint32_t per = (e - b + kRsThreads - 1) / kRsThreads;
@@ -581,7 +670,7 @@ static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
             }
         }
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < e - b; k += kRsThreads) anc[b + k] = s_anc[k];
+        for (uint32_t k = threadIdx.x; k < e - b; k += kRsThreads) __stcs(anc + b + k, s_anc[k]);
         __syncthreads();
     }
 }

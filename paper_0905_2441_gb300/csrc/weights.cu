@@ -23,6 +23,17 @@ using namespace smc_host;
 
 namespace smc {
 
+// exp(dh + dl) for a non-positive difference given as float hi/lo parts,
+// per element: one FFMA, one FMUL and ex2.approx (flushes below 2^-126 to
+// 0).  The rounding of the base-2 argument t = (dh + dl) log2(e) is about
+// 2^-24 |t|, so the relative error is ~2^-22 + 4.1e-8 |t| -- within the
+// weights' stated error of 1e-6 + 1e-7 |ln(W / W_max)| at every t, and
+// below 2e-7 of a sum for the usual spread of log-weights.
+__device__ __forceinline__ float exp_hl(float dh, float dl) {
+    const float L2E = 1.44269504088896340736f;
+    return ex2(fmaf(dh, L2E, dl * L2E));
+}
+
 // exp(x) for an FP64 x <= 64 (FP32 accuracy, float result)
 __device__ __forceinline__ float expd(double x) {
     float hi, lo;
@@ -31,8 +42,8 @@ __device__ __forceinline__ float expd(double x) {
 }
 
 constexpr double kNegInf = -INFINITY;
-__device__ __forceinline__ bool is_neg_inf(double x) {
-    return __double_as_longlong(x) == (long long)0xFFF0000000000000ull;
+__device__ __forceinline__ bool is_neg_inf(double x) {  // on the 32-bit halves
+    return (uint32_t)__double2hiint(x) == 0xFFF00000u && __double2loint(x) == 0;
 }
 
 // Element loops take chunks of 8 consecutive doubles per thread and
@@ -50,6 +61,16 @@ __device__ __forceinline__ void load8(const double* __restrict__ p, double (&v)[
     double2 t[kChunk / 2];
 #pragma unroll
     for (int j = 0; j < kChunk / 2; ++j) t[j] = q[j];
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j) { v[2 * j] = t[j].x; v[2 * j + 1] = t[j].y; }
+}
+
+// load8 with the streaming hint (the data's last read)
+__device__ __forceinline__ void load8_cs(const double* __restrict__ p, double (&v)[kChunk]) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 t[kChunk / 2];
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j) t[j] = __ldcs(q + j);
 #pragma unroll
     for (int j = 0; j < kChunk / 2; ++j) { v[2 * j] = t[j].x; v[2 * j + 1] = t[j].y; }
 }
@@ -83,17 +104,70 @@ struct RefSums {
         if (!any) { r = x; rh = xh; rl = xl; s1 = 1.0f; s2 = 1.0f; any = true; return; }
         const float dh = xh - rh, dl = xl - rl;
         if (dh > 32.0f) {                     // move the reference up to x
-            const float f = exp_hilo(-dh, -dl);
+            const float f = exp_hl(-dh, -dl);
             s1 = fmaf(s1, f, 1.0f);
             s2 = fmaf(s2, f * f, 1.0f);
             r = x; rh = xh; rl = xl;
         } else {
-            const float e = exp_hilo(dh, dl);
+            const float e = exp_hl(dh, dl);
             s1 += e;
             s2 = fmaf(e, e, s2);
         }
     }
 };
+
+// Eight elements at once, with independent work for each: the chunk's exact
+// maximum cm (integer keys), e_j = exp(x_j - cm) on float hi/lo splits as
+// in RefSums::add, tree sums of e and e^2, then one merge into the running
+// sums (one exponential rescales whichever side has the smaller reference).
+// Zero weights (-inf) add nothing; a chunk of them leaves the sums as they
+// are.
+__device__ __forceinline__ void add8(RefSums& t, const double (&x)[kChunk]) {
+    long long k[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) k[j] = dkey(x[j]);
+    long long km = k[0];
+#pragma unroll
+    for (int j = 1; j < kChunk; ++j) km = k[j] > km ? k[j] : km;
+    const double cm = __longlong_as_double(km ^ ((km >> 63) & 0x7FFFFFFFFFFFFFFFLL));
+    if (is_neg_inf(cm)) return;
+    t.kmax = km > t.kmax ? km : t.kmax;
+    float mh, ml;
+    split_double(cm, mh, ml);
+    float e[kChunk], e2[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+        float xh, xl;
+        split_double(x[j], xh, xl);
+        e[j] = exp_hl(xh - mh, xl - ml);  // <= 1; a zero weight (-inf) splits to -1e30: 0
+        e2[j] = e[j] * e[j];
+    }
+#pragma unroll
+    for (int w = 1; w < kChunk; w <<= 1)
+#pragma unroll
+        for (int j = 0; j + w < kChunk; j += 2 * w) {
+            e[j] += e[j + w];
+            e2[j] += e2[j + w];
+        }
+    if (!t.any) {
+        t.r = cm;
+        split_double(cm, t.rh, t.rl);
+        t.s1 = e[0];
+        t.s2 = e2[0];
+        t.any = true;
+    } else if (km > dkey(t.r)) {  // the chunk holds a new reference
+        const float f = exp_hl(t.rh - mh, t.rl - ml);
+        t.s1 = fmaf(t.s1, f, e[0]);
+        t.s2 = fmaf(t.s2, f * f, e2[0]);
+        t.r = cm;
+        t.rh = mh;
+        t.rl = ml;
+    } else {
+        const float f = exp_hl(mh - t.rh, ml - t.rl);
+        t.s1 = fmaf(e[0], f, t.s1);
+        t.s2 = fmaf(e2[0], f * f, t.s2);
+    }
+}
 
 // block / grid level: FP64 sums relative to a reference m
 struct Lse {
@@ -347,7 +421,7 @@ __device__ __forceinline__ void combine_partials3(const double* partials, int nb
 // partial slot layout (doubles): [b*8 + 0..5] = {ref, s1, s2, ref_old, s_old, max}
 // final slot: {max, S1, S2, valid, lse, (float) 1/S1 in the low word of [5]},
 // S1 and S2 relative to the true maximum
-__global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restrict__ ll,
+__global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __restrict__ ll,
                                                          double dbeta, double* __restrict__ lw,
                                                          int64_t M, int has_inc,
                                                          double* __restrict__ partials,
@@ -370,24 +444,37 @@ __global__ void __launch_bounds__(256) k_reweight_reduce(const double* __restric
     // element per thread keeps each thread's dependent chain short
     const bool vec = aligned16(lw) && (!has_inc || aligned16(ll)) && M >= G * kChunk;
     const int64_t nchunk = vec ? M / kChunk : 0;
+    // the next chunk's loads are issued before this chunk's arithmetic
+    double xn[kChunk], vn[kChunk];
+    if (t0 < nchunk) {
+        load8_cs(lw + t0 * kChunk, xn);
+        if (has_inc) load8_cs(ll + t0 * kChunk, vn);
+    }
     for (int64_t ch = t0; ch < nchunk; ch += G) {
-        double x[kChunk];
-        load8(lw + ch * kChunk, x);
+        double x[kChunk], v[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            x[j] = xn[j];
+            v[j] = vn[j];
+        }
+        if (ch + G < nchunk) {
+            load8_cs(lw + (ch + G) * kChunk, xn);
+            if (has_inc) load8_cs(ll + (ch + G) * kChunk, vn);
+        }
         if (has_inc) {
-            double v[kChunk], n[kChunk];
-            load8(ll + ch * kChunk, v);
+            double n[kChunk];
 #pragma unroll
             for (int j = 0; j < kChunk; ++j) {
-                nan_seen |= disnan(x[j]) | disnan(v[j]);
                 n[j] = fma(dbeta, v[j], x[j]);
-                nan_seen |= disnan(n[j]);
+                nan_seen |= disnan(n[j]);  // a NaN in x or v makes n NaN
             }
             store8(lw + ch * kChunk, n);
-#pragma unroll
-            for (int j = 0; j < kChunk; ++j) { old.add(x[j]); cur.add(n[j]); }
+            add8(old, x);
+            add8(cur, n);
         } else {
 #pragma unroll
-            for (int j = 0; j < kChunk; ++j) { nan_seen |= disnan(x[j]); cur.add(x[j]); }
+            for (int j = 0; j < kChunk; ++j) nan_seen |= disnan(x[j]);
+            add8(cur, x);
         }
     }
     for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {  // tail / unaligned
@@ -468,21 +555,24 @@ __global__ void __launch_bounds__(256) k_reweight_normalize(const double* __rest
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nchunk = (aligned16(lw) && aligned16(W)) ? M / kChunk : 0;
-    for (int64_t ch = t0; ch < nchunk; ch += G) {
+    // descending: the reduction wrote the log-weights ascending, so the most
+    // recently written ones (still in L2) come first
+    for (int64_t k = t0; k < nchunk; k += G) {
+        const int64_t ch = nchunk - 1 - k;
         double x[kChunk], w[kChunk];
-        load8(lw + ch * kChunk, x);
+        load8_cs(lw + ch * kChunk, x);
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
             float xh, xl;
             split_double(x[j], xh, xl);
-            w[j] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
+            w[j] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
         }
         store8(W + ch * kChunk, w);
     }
     for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {
         float xh, xl;
         split_double(lw[i], xh, xl);
-        W[i] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
+        W[i] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
     }
 }
 
@@ -558,17 +648,20 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __
         inv = reinterpret_cast<const float*>(fin + 5)[0];
     }
     const int64_t ntiles = rs_tiles(M);
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    // descending: the reduction wrote the log-weights ascending (the most
+    // recent, still in L2, first); the resampling scan then runs ascending
+    for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+        const int64_t t = ntiles - 1 - k;
         unsigned long long acc = 0;
         if (valid) {
             double x[kRsIpt], w[kRsIpt];
-            load_tile_raw(lw, M, t, x);
+            load_tile_raw_cs(lw, M, t, x);
             const int64_t g0 = t * kRsTile + (int64_t)threadIdx.x * kRsIpt;
 #pragma unroll
             for (int j = 0; j < kRsIpt; ++j) {
                 float xh, xl;
                 split_double(x[j], xh, xl);
-                w[j] = f2d_bits(exp_hilo(xh - mh, xl - ml) * inv);
+                w[j] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
                 unsigned long long q;
                 quantise(w[j], q);  // w in [0, 1]
                 acc += g0 + j < M ? q : 0ull;
@@ -597,9 +690,10 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                            bool tiles_ready);
 
 // Up to cap * 256 elements: one element per thread (short dependent chains:
-// the reduction is latency-bound there); beyond, chunks of 8 per thread.
+// the reduction is latency-bound there); beyond, chunks of 8 per thread,
+// with at most as many blocks as are resident at once (two per SM).
 static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
-    int64_t cap = (int64_t)ctx->num_sms * 8;
+    int64_t cap = (int64_t)ctx->num_sms * 2;
     if (cap > kMaxPartialBlocks - 2) cap = kMaxPartialBlocks - 2;
     int64_t b = (M + 255) / 256;
     if (b > cap) b = (M + 256 * 8 - 1) / (256 * 8);
