@@ -242,7 +242,7 @@ smc_status smc_resample_residual(smc_ctx* ctx, const double* W, int64_t M, uint6
  * device memory: processes whose device memory is owned by a pool or a
  * fixed budget they must not bypass, and latency-critical loops that cannot
  * pay the device synchronisation cudaMalloc / cudaFree imply.  It needs no
- * smc_ctx and allocates nothing: its scratch is a 192 KiB static device
+ * smc_ctx and allocates nothing: its scratch is a 65 KiB static device
  * array inside libsmc.so, which every GPU that loads the library holds
  * until the process exits.  The paper has no counterpart to this entry
  * point; it exists for how the library is called, not for the method.

@@ -186,7 +186,7 @@ __device__ __forceinline__ long long dkey(double x) {
 // to an FP64 comparison, and the FP64 pipe is narrow on this part)
 __device__ __forceinline__ bool disnan(double x) {
     const uint32_t h = (uint32_t)__double2hiint(x) & 0x7FFFFFFFu;
-    return h > 0x7FF00000u || (h == 0x7FF00000u && __double2loint(x) != 0);
+    return (h > 0x7FF00000u) | ((h == 0x7FF00000u) & (__double2loint(x) != 0));
 }
 
 // float -> double by integer operations (subnormal floats give 0)

@@ -48,22 +48,12 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ anc,
 
 namespace smc_host {
 
-// The finalize kernel (one CTA, the tile sums staged through 64 KiB of
-// dynamic shared memory); qr: also every tile's (Q_t, R_t) for pass 2.
+// The finalize kernel (one CTA of kRsFinThreads).
 smc_status resample_finalize_launch(int64_t M, uint64_t seed, uint64_t step,
-                                    const int32_t* do_flag, const smc::RsScratch& sc, bool qr,
+                                    const int32_t* do_flag, const smc::RsScratch& sc,
                                     uint32_t* status, cudaStream_t s) {
-    static bool attr_set[64] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (!attr_set[dev]) {
-        SMC_CUDA(cudaFuncSetAttribute(smc::k_resample_finalize,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smc::kRsFinSmem));
-        attr_set[dev] = true;
-    }
-    return launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), smc::kRsFinSmem,
-                      s, M, seed, step, do_flag, sc, qr ? 1 : 0, status);
+    return launch_pdl(smc::k_resample_finalize, dim3(1), dim3(smc::kRsFinThreads), 0, s, M, seed,
+                      step, do_flag, sc, status);
 }
 
 // tiles_ready: the tile sums of pass 1 are already in sc (formed by the
@@ -84,7 +74,7 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
                         M, do_flag, sc, status);
         if (st != SMC_OK) return st;
     }
-    st = resample_finalize_launch(M, seed, step, do_flag, sc, true, status, s);
+    st = resample_finalize_launch(M, seed, step, do_flag, sc, status, s);
     if (st != SMC_OK) return st;
     // pass 2 is persistent: as many CTAs as are resident at once (per device)
     static int occ_of_dev[64] = {};
@@ -111,16 +101,13 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     return SMC_OK;
 }
 
-// scratch layout inside `base`: tile sums, the call constants, the tiles'
-// Q and R, then (when `heavy`) the heavy-chunk counter, the chunk records
-// and the items' inclusive F
+// scratch layout inside `base`: tile sums, the call constants, then (when
+// `heavy`) the heavy-chunk counter, the chunk records and the items'
+// inclusive F
 smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy) {
     smc::RsScratch sc;
-    const int64_t nt = smc::rs_tiles(M);
     sc.tile_sum = base;
-    sc.cst = reinterpret_cast<smc::RsConst*>(base + nt);
-    sc.tile_q = base + nt + smc::kRsConstWords;
-    sc.tile_r = sc.tile_q + nt;
+    sc.cst = reinterpret_cast<smc::RsConst*>(base + smc::rs_tiles(M));
     sc.heavy_count = nullptr;
     sc.heavy_list = nullptr;
     sc.fpos = nullptr;
@@ -184,8 +171,7 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
 namespace {
 
 constexpr int64_t kNoAllocMaxM = (int64_t)1 << 24;   // 16,777,216 weights
-// 8192 tile sums, the call constants, 8192 tile quotients and remainders:
-// about 192 KiB per device
+// 8192 tile sums + the call constants: about 64 KiB per device
 constexpr int64_t kNoAllocWords = smc::rs_words(kNoAllocMaxM);
 static_assert(sizeof(smc::RsConst) <= smc::kRsConstWords * sizeof(unsigned long long),
               "constants fit their words");

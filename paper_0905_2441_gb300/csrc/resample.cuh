@@ -7,13 +7,14 @@
 // (q = floor(W 2^52) from the FP64 bits) and reduced exactly; the tile's
 // integer sum is stored.
 // Between the passes (k_resample_finalize, one CTA): the tile sums become
-// exclusive prefixes c_t, the call's constants (S, the uniform, fixed-point
-// reciprocals) are formed once, and so is every tile's c_t M = Q_t S + R_t.
+// exclusive prefixes c_t and the call's constants (S, the uniform,
+// fixed-point reciprocals) are formed once.
 // Pass 2 (k_resample_scan, persistent over tiles): each tile reads its
-// prefix and (Q_t, R_t) (no waiting on other CTAs), each warp scans its 256
-// items, F is carried item by item from (Q_t, R_t), and each warp expands its
-// own contiguous output range through shared memory; ranges too long for a
-// warp go to k_resample_heavy.
+// prefix (no waiting on other CTAs), each warp scans its 256 items, each
+// thread divides its own starting c M = Q S + R by the fixed-point
+// reciprocal (one correction) and carries F item by item, and each warp
+// expands its own contiguous output range through shared memory; ranges
+// too long for a warp go to k_resample_heavy.
 //
 // The passes alternate direction over the tiles (pass 1 ascending, pass 2
 // descending after it, or ascending after a normalisation that wrote the
@@ -45,8 +46,6 @@ constexpr int kRsConstWords = 8;
 
 struct RsScratch {
     unsigned long long* tile_sum;   // [ntiles]: tile sums, then their exclusive prefixes
-    unsigned long long* tile_q;     // [ntiles]: Q_t of c_t M = Q_t S + R_t (finalize)
-    unsigned long long* tile_r;     // [ntiles]: R_t
     RsConst* cst;                   // after the tile sums
     // grid-wide expansion of tiles with many output slots (optional: when
     // null, such a tile is expanded by its own CTA)
@@ -56,9 +55,9 @@ struct RsScratch {
 };
 
 __host__ __device__ constexpr int64_t rs_tiles(int64_t M) { return (M + kRsTile - 1) / kRsTile; }
-// words of scratch for M weights: tile sums, constants, per-tile Q and R
+// words of scratch for M weights: tile sums, constants
 __host__ __device__ constexpr int64_t rs_words(int64_t M) {
-    return 3 * rs_tiles(M) + kRsConstWords;
+    return rs_tiles(M) + kRsConstWords;
 }
 // items of one warp's segment of a tile in pass 2, and the output slots a
 // warp stages in shared memory
@@ -85,6 +84,24 @@ __device__ __forceinline__ bool quantise(double w, unsigned long long& q) {
     const unsigned long long v = sh > 52u ? 0ull : (man >> (sh & 63u));
     q = (neg || above || e == 0u) ? 0ull : v;  // zero / subnormal / negative / invalid: 0
     return neg ? (hw == 0x80000000u && lw == 0u) : !above;  // -0 is a valid zero
+}
+
+// floor(w 2^52) for w in [0, 1] (what quantise gives there), without the
+// validity test: q_fast's result for an invalid w is unspecified, and
+// w_invalid tells whether w lies outside [0, 1] (or is NaN), -0 counting as
+// a valid zero.  Branch-free, on the 32-bit halves.
+__device__ __forceinline__ unsigned long long q_fast(double w) {
+    const uint32_t hw = (uint32_t)__double2hiint(w), lw = (uint32_t)__double2loint(w);
+    const uint32_t e = (hw >> 20) & 0x7FFu;
+    const uint32_t sh = 1023u - e;  // wraps for e > 1023 (invalid)
+    const unsigned long long man = ((unsigned long long)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
+    return sh > 52u ? 0ull : (man >> sh);
+}
+__device__ __forceinline__ bool w_invalid(double w) {
+    const uint32_t hw = (uint32_t)__double2hiint(w), lw = (uint32_t)__double2loint(w);
+    const bool neg_zero = (hw == 0x80000000u) & (lw == 0u);
+    const bool above_one = (hw > 0x3FF00000u) | ((hw == 0x3FF00000u) & (lw != 0u));
+    return above_one & !neg_zero;  // sign set, > 1, inf or NaN (all above 1.0's bits)
 }
 
 // this thread's kRsIpt weights of tile `tile`, quantised (0 past M)
@@ -180,13 +197,13 @@ static __global__ void __launch_bounds__(kRsThreads) k_resample_total(const doub
     int64_t tile = blockIdx.x;
     if (tile < ntiles) load_tile_raw(W, M, tile, vn);
     for (int buf = 0; tile < ntiles; tile += gridDim.x, buf ^= 1) {
-        unsigned long long q[kRsIpt];
+        unsigned long long acc = 0;  // <= 8 * 2^52: no wrap
 #pragma unroll
-        for (int j = 0; j < kRsIpt; ++j) bad |= !quantise(vn[j], q[j]);
+        for (int j = 0; j < kRsIpt; ++j) {
+            bad |= w_invalid(vn[j]);
+            acc += q_fast(vn[j]);
+        }
         if (tile + gridDim.x < ntiles) load_tile_raw(W, M, tile + gridDim.x, vn);
-        unsigned long long acc = 0;
-#pragma unroll
-        for (int j = 0; j < kRsIpt; ++j) acc += q[j];  // <= 8 * 2^52: no wrap
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if ((threadIdx.x & 31) == 0) sh[buf][wid] = acc;
@@ -230,15 +247,19 @@ __device__ __forceinline__ bool lt128(U128 a, U128 b) {
 // c times the fixed-point reciprocal mfx = floor(M 2^64 / S) (integer
 // multiply-high: off by at most one below), fixed up exactly; without it
 // (M >= S, degenerate totals) an FP64 estimate, fixed up the same way.
-static __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned long long M,
-                                       const RsConst& k, unsigned long long& Q,
-                                       unsigned long long& R) {
-    const unsigned long long S = k.S;
+struct QR {
+    unsigned long long Q, R;
+};
+// (the constants by value: a call with a reference to the caller's copy
+// would move that copy to local memory)
+static __device__ __noinline__ QR divmod_cm_v(unsigned long long c, unsigned long long M,
+                                              unsigned long long S, unsigned long long mfx,
+                                              double m_over_s) {
     unsigned long long q;
-    if (k.mfx) {
-        q = __umul64hi(c, k.mfx);
+    if (mfx) {
+        q = __umul64hi(c, mfx);
     } else {
-        const double qe = floor((double)c * k.m_over_s);
+        const double qe = floor((double)c * m_over_s);
         q = qe > 0.0 ? (unsigned long long)qe : 0ull;
     }
     const U128 P = mul64(c, M);
@@ -252,8 +273,28 @@ static __device__ __noinline__ void divmod_cm(unsigned long long c, unsigned lon
         ++q;
         r = sub128(r, U128{S, 0ull});
     }
-    Q = q;
-    R = r.lo;
+    return QR{q, r.lo};
+}
+__device__ __forceinline__ void divmod_cm(unsigned long long c, unsigned long long M,
+                                          const RsConst& k, unsigned long long& Q,
+                                          unsigned long long& R) {
+    const QR t = divmod_cm_v(c, M, k.S, k.mfx, k.m_over_s);
+    Q = t.Q;
+    R = t.R;
+}
+
+// c M = Q S + R exactly from the fixed-point reciprocal mfx = floor(M 2^64 /
+// S) (M < S, c <= S < 2^61): Q' = floor(c mfx / 2^64) is Q or Q - 1 (the
+// reciprocal's error times c is below 2^61 / 2^64), so one correction
+// suffices; inline, no loop.
+__device__ __forceinline__ void divmod_mfx(unsigned long long c, unsigned long long M,
+                                           unsigned long long S, unsigned long long mfx,
+                                           unsigned long long& Q, unsigned long long& R) {
+    unsigned long long q = __umul64hi(c, mfx);
+    const U128 r = sub128(mul64(c, M), mul64(q, S));  // < 2 S < 2^62: hi is 0
+    const bool up = r.lo >= S;
+    Q = q + (up ? 1ull : 0ull);
+    R = r.lo - (up ? S : 0ull);
 }
 
 // floor(hi 2^64 / d) for hi < d < 2^63 (once per call): an FP64 estimate
@@ -292,21 +333,20 @@ static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned
 }
 
 // Between the passes, one CTA: the exact total S from the tile sums, the
-// call's uniform and constants, every tile's exclusive prefix c_t (the tile
-// sums are replaced in place) and, with `qr`, every tile's c_t M = Q_t S +
-// R_t, so that no tile of pass 2 repeats this work.  The tile sums pass
-// through shared memory kRsFinTiles at a time (coalesced loads and stores);
-// each thread scans eight consecutive ones.
+// call's uniform and constants, and every tile's exclusive prefix c_t (the
+// tile sums are replaced in place), so that no tile of pass 2 repeats this
+// work.  kRsFinTiles tile sums at a time: each thread loads its 8 (all
+// loads in flight at once, coalesced across the warp), each warp scans 256
+// of them; the three fixed-point constants are formed by three warps side
+// by side.
 constexpr int kRsFinThreads = 1024;
 constexpr int kRsFinTiles = 8 * kRsFinThreads;
-constexpr size_t kRsFinSmem = (size_t)kRsFinTiles * sizeof(unsigned long long);
 static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
-    int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc, int qr,
+    int64_t M, uint64_t seed, uint64_t step, const int32_t* do_flag, RsScratch sc,
     uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
-    extern __shared__ unsigned long long s_t[];  // kRsFinTiles
     __shared__ unsigned long long s_w[kRsFinThreads / 32];
     __shared__ unsigned long long s_run;
     __shared__ int s_bad;
@@ -319,18 +359,20 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     }
     __syncthreads();
     for (int64_t base = 0; base < ntiles; base += kRsFinTiles) {
-        const int n = (int)(ntiles - base < kRsFinTiles ? ntiles - base : kRsFinTiles);
-        for (int i = tid; i < n; i += kRsFinThreads) s_t[i] = __ldcg(sc.tile_sum + base + i);
-        __syncthreads();
-        // warp wid scans tiles [256 wid, 256 wid + 256): round k holds tile
-        // 256 wid + 32 k + lane (conflict-free shared-memory accesses)
+        const int64_t n = ntiles - base < kRsFinTiles ? ntiles - base : kRsFinTiles;
+        // warp wid scans tiles [256 wid, 256 wid + 256) of this block: round
+        // k holds tile 256 wid + 32 k + lane
+        unsigned long long v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = wid * 256 + k * 32 + lane;
+            v[k] = i < n ? __ldcg(sc.tile_sum + base + i) : 0ull;
+        }
         unsigned long long carry = 0;
         bool ovf = false;
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int i = wid * 256 + k * 32 + lane;
-            const unsigned long long v = i < n ? s_t[i] : 0ull;
-            unsigned long long incl = v;
+            unsigned long long incl = v[k];
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
@@ -339,9 +381,9 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
                     incl += u;
                 }
             }
-            const unsigned long long ex = carry + incl - v;  // exclusive within the warp's run
+            const unsigned long long ex = carry + incl - v[k];  // exclusive within the warp's run
             ovf |= carry + incl < carry;
-            if (i < n) s_t[i] = ex;
+            v[k] = ex;
             carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
         }
         if (lane == 0) s_w[wid] = carry;
@@ -359,49 +401,40 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             const int i = wid * 256 + k * 32 + lane;
-            if (i < n) s_t[i] += off;
+            if (i < n) sc.tile_sum[base + i] = v[k] + off;
         }
         __syncthreads();
-        for (int i = tid; i < n; i += kRsFinThreads) sc.tile_sum[base + i] = s_t[i];
         if (tid == 0) s_run += tot;
         __syncthreads();
     }
-    if (tid == 0) {
-        if (sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
-        const unsigned long long S = s_run;
-        RsConst c;
-        c.ok = 0;
-        if (S == 0 || S >= kMaxTotal || s_bad) {
-            raise_status(status, S == 0 && !s_bad ? ST_ZERO_WEIGHT : ST_BADARG);
-        } else {
+    const unsigned long long S = s_run;
+    const unsigned long long MM = (unsigned long long)M;
+    const bool good = !(S == 0 || S >= kMaxTotal || s_bad);
+    // the constants, one per warp
+    if (lane == 0 && good) {
+        if (wid == 0) {
             const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
-            const unsigned long long MM = (unsigned long long)M;
-            c.S = S;
-            c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
-            c.m_over_s = (double)MM / (double)S;
-            c.mfx = MM < S ? div_shift64(MM, S) : 0ull;
-            c.ifx = S > 1 ? div_shift64(1ull, S) : 0ull;
-            // items with q M <= 2^64 - S keep R + q M < 2^64, where the
-            // fixed-point quotient is off by at most one (heavier ones are
-            // divided afresh)
-            c.qheavy = c.ifx ? (0ull - S) / MM : 0ull;
-            c.ok = 1;
+            s_c.S = S;
+            s_c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
+            s_c.m_over_s = (double)MM / (double)S;
+        } else if (wid == 1) {
+            s_c.mfx = MM < S ? div_shift64(MM, S) : 0ull;
+        } else if (wid == 2) {
+            s_c.ifx = S > 1 ? div_shift64(1ull, S) : 0ull;
+        } else if (wid == 3) {
+            // items (and thread runs) with q M <= 2^64 - S keep R + q M <
+            // 2^64, where the fixed-point quotient is off by at most one
+            // (heavier ones are divided afresh)
+            s_c.qheavy = S > 1 ? (0ull - S) / MM : 0ull;
         }
-        *sc.cst = c;
-        s_c = c;
     }
     __syncthreads();
-    if (!qr || !s_c.ok) return;
-    // every tile's c_t M = Q_t S + R_t (the prefixes are still in shared
-    // memory when they all fit)
-    const RsConst c = s_c;
-    const bool in_smem = ntiles <= kRsFinTiles;
-    for (int64_t t = tid; t < ntiles; t += kRsFinThreads) {
-        const unsigned long long ct = in_smem ? s_t[t] : __ldcg(sc.tile_sum + t);
-        unsigned long long Q, R;
-        divmod_cm(ct, (unsigned long long)M, c, Q, R);
-        sc.tile_q[t] = Q;
-        sc.tile_r[t] = R;
+    if (tid == 0) {
+        if (sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero
+        RsConst c = s_c;
+        c.ok = good ? 1u : 0u;
+        if (!good) raise_status(status, S == 0 && !s_bad ? ST_ZERO_WEIGHT : ST_BADARG);
+        *sc.cst = c;
     }
 }
 
@@ -426,7 +459,8 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     __shared__ uint32_t s_hi[kRsTile];                          // inclusive F of each item
-    __shared__ int32_t s_anc[kRsThreads / 32][kRsWarpStage];    // a warp's staged slots
+    // a warp's staged slots, from its range start rounded down to 4 slots
+    __shared__ __align__(16) int32_t s_anc[kRsThreads / 32][kRsWarpStage + 4];
     __shared__ unsigned long long s_warp[2][kRsThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
@@ -447,6 +481,8 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
     const unsigned long long Rth = cst.Rth;
     const unsigned long long qheavy = cst.qheavy;
     const unsigned long long ifx = cst.ifx;
+    const bool ifx32 = ifx != 0 && (ifx >> 32) == 0;  // S > 2^32
+    const bool anc16 = (reinterpret_cast<uintptr_t>(anc) & 15u) == 0;
     // carry R + a M (< 2^64 for a <= qheavy) into Q: n = floor((R + a M) / S)
     // from the fixed-point reciprocal ifx = floor(2^64 / S) (integer
     // multiply-high, off by at most one below) and one correction
@@ -463,27 +499,23 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
     int64_t k = blockIdx.x;
     auto tile_of = [&](int64_t kk) { return rev ? ntiles - 1 - kk : kk; };
     double vn[kRsIpt];
-    unsigned long long pn = 0, qn = 0, rn = 0;
+    unsigned long long pn = 0;
     if (k < ntiles) {
         const int64_t t = tile_of(k);
         load_tile_raw_cs(W, M, t, vn);
         pn = __ldcg(sc.tile_sum + t);
-        qn = __ldcg(sc.tile_q + t);
-        rn = __ldcg(sc.tile_r + t);
     }
     for (int buf = 0; k < ntiles; k += gridDim.x, buf ^= 1) {
         const int64_t tile = tile_of(k);
         const int64_t base = tile * kRsTile;
         unsigned long long q[kRsIpt];
 #pragma unroll
-        for (int j = 0; j < kRsIpt; ++j) quantise(vn[j], q[j]);  // pass 1 reported bad weights
-        const unsigned long long tpre = pn, tq = qn, tr = rn;
+        for (int j = 0; j < kRsIpt; ++j) q[j] = q_fast(vn[j]);  // pass 1 reported bad weights
+        const unsigned long long tpre = pn;
         if (k + gridDim.x < ntiles) {
             const int64_t t = tile_of(k + gridDim.x);
             load_tile_raw_cs(W, M, t, vn);
             pn = __ldcg(sc.tile_sum + t);
-            qn = __ldcg(sc.tile_q + t);
-            rn = __ldcg(sc.tile_r + t);
         }
         unsigned long long tsum = 0;
 #pragma unroll
@@ -503,28 +535,56 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
             if (w < wid) woff += s_warp[buf][w];
         const unsigned long long off = woff + (incl - tsum);  // this thread's offset in the tile
         unsigned long long c = tpre + off;                    // C before this thread's item 0
-        unsigned long long Q = tq, R = tr;
+        unsigned long long Q, R;
         uint32_t Fv[kRsIpt];
         uint32_t F0;
-        // the usual case, taken per warp: no heavy item and a small offset,
-        // every carry by a multiply-high (no division, no branch)
-        bool light = off <= qheavy;
-#pragma unroll
-        for (int j = 0; j < kRsIpt; ++j) light &= q[j] <= qheavy;
+        // the usual case, taken per warp: the starting quotient from the
+        // fixed-point reciprocal, and the thread's whole run light enough
+        // that R + d M < 2^64 for every prefix d of its run; then each item's
+        // F comes from the thread's (Q, R) independently of the other items
+        // (d_j = q_0 + ... + q_j: R + d_j M = n S + r, F = Q + n + [r > Rth]),
+        // so the eight divisions overlap instead of forming a chain
+        const bool light = cst.mfx != 0 && tsum <= qheavy;
         if (__all_sync(0xFFFFFFFFu, light)) {
-            carry(Q, R, off);
-            F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
+            divmod_mfx(c, MM, S, cst.mfx, Q, R);
+            F0 = (uint32_t)Q + (R > Rth ? 1u : 0u);
+            unsigned long long d = 0;
+            if (ifx32) {
+                // S > 2^32 (normalised weights give S ~ 2^52): the
+                // reciprocal and every n fit 32 bits, so n is a 96-bit
+                // multiply-high by 32-bit pieces
+                const uint32_t f32 = (uint32_t)ifx, m32 = (uint32_t)MM;
 #pragma unroll
-            for (int j = 0; j < kRsIpt; ++j) {
-                carry(Q, R, q[j]);
-                const uint32_t Fn = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-                Fv[j] = Fn < (uint32_t)M ? Fn : (uint32_t)M;
+                for (int j = 0; j < kRsIpt; ++j) {
+                    d += q[j];
+                    const unsigned long long X = R + (unsigned long long)(uint32_t)d * m32 +
+                                                 ((unsigned long long)((uint32_t)(d >> 32) * m32) << 32);
+                    const unsigned long long lo = ((unsigned long long)(uint32_t)X * f32) >> 32;
+                    const uint32_t n =
+                        (uint32_t)(((unsigned long long)(uint32_t)(X >> 32) * f32 + lo) >> 32);
+                    unsigned long long r = X - (unsigned long long)n * S;
+                    const bool up = r >= S;
+                    r -= up ? S : 0ull;
+                    const uint32_t Fn = (uint32_t)Q + n + (up ? 1u : 0u) + (r > Rth ? 1u : 0u);
+                    Fv[j] = Fn < (uint32_t)M ? Fn : (uint32_t)M;
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kRsIpt; ++j) {
+                    d += q[j];
+                    const unsigned long long X = R + d * MM;
+                    const unsigned long long n = __umul64hi(X, ifx);
+                    unsigned long long r = X - n * S;
+                    const bool up = r >= S;
+                    r -= up ? S : 0ull;
+                    const unsigned long long Fn = Q + n + (up ? 1ull : 0ull) + (r > Rth ? 1ull : 0ull);
+                    Fv[j] = Fn < MM ? (uint32_t)Fn : (uint32_t)M;
+                }
             }
         } else {
-            if (off <= qheavy) carry(Q, R, off);  // by off M
-            else divmod_cm(c, MM, cst, Q, R);
+            divmod_cm(c, MM, cst, Q, R);
             F0 = (uint32_t)(Q + (R > Rth ? 1ull : 0ull));
-#pragma unroll 1
+#pragma unroll
             for (int j = 0; j < kRsIpt; ++j) {
                 c += q[j];
                 if (q[j] > qheavy) divmod_cm(c, MM, cst, Q, R);  // a heavy item, divided afresh
@@ -564,7 +624,11 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
         if (range <= (uint32_t)kRsWarpStage) {  // uniform over the warp
             // each item writes its slots with predicated stores: up to 2
             // when no item of the warp has more (the usual case), else up to
-            // 4 and a loop for the rare items with more
+            // 4 and a loop for the rare items with more.  Slot sl is staged
+            // at sl - lo_al (lo_al = lo rounded down to 4 slots when the
+            // ancestors are 16-byte aligned), so that 4 staged slots map to
+            // one 16-byte store.
+            const uint32_t lo_al = anc16 ? (lo & ~3u) : lo;
             int32_t* st = s_anc[wid];
             uint32_t f = F0, most = 0;
 #pragma unroll
@@ -576,8 +640,8 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
 #pragma unroll
                 for (int j = 0; j < kRsIpt; ++j) {
                     const uint32_t e = Fv[j];
-                    if (f < e) st[f - lo] = i0 + j;
-                    if (f + 1 < e) st[f + 1 - lo] = i0 + j;
+                    if (f < e) st[f - lo_al] = i0 + j;
+                    if (f + 1 < e) st[f + 1 - lo_al] = i0 + j;
                     f = e;
                 }
             } else {
@@ -586,13 +650,29 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
                     const uint32_t e = Fv[j];
 #pragma unroll
                     for (uint32_t kk = 0; kk < 4; ++kk)
-                        if (f + kk < e) st[f + kk - lo] = i0 + j;
-                    for (uint32_t sl = f + 4; sl < e; ++sl) st[sl - lo] = i0 + j;
+                        if (f + kk < e) st[f + kk - lo_al] = i0 + j;
+                    for (uint32_t sl = f + 4; sl < e; ++sl) st[sl - lo_al] = i0 + j;
                     f = e;
                 }
             }
             __syncwarp();
-            for (uint32_t kk = lane; kk < range; kk += 32) __stcs(anc + lo + kk, st[kk]);
+            if (anc16) {
+                const uint32_t span = hi - lo_al;
+                for (uint32_t k = 4u * lane; k < span; k += 128u) {
+                    const int4 v = *reinterpret_cast<const int4*>(st + k);
+                    const uint32_t sl = lo_al + k;
+                    if (sl >= lo && sl + 4u <= hi) {
+                        __stcs(reinterpret_cast<int4*>(anc + sl), v);
+                    } else {  // the range's ragged ends
+                        if (sl >= lo && sl < hi) __stcs(anc + sl, v.x);
+                        if (sl + 1u >= lo && sl + 1u < hi) __stcs(anc + sl + 1u, v.y);
+                        if (sl + 2u >= lo && sl + 2u < hi) __stcs(anc + sl + 2u, v.z);
+                        if (sl + 3u < hi) __stcs(anc + sl + 3u, v.w);
+                    }
+                }
+            } else {
+                for (uint32_t kk = lane; kk < range; kk += 32) __stcs(anc + lo + kk, st[kk]);
+            }
             __syncwarp();
             continue;
         }

@@ -369,7 +369,7 @@ namespace smc_host {
 
 smc::RsScratch resample_scratch(unsigned long long* base, int64_t M, bool heavy);
 smc_status resample_finalize_launch(int64_t M, uint64_t seed, uint64_t step,
-                                    const int32_t* do_flag, const smc::RsScratch& sc, bool qr,
+                                    const int32_t* do_flag, const smc::RsScratch& sc,
                                     uint32_t* status, cudaStream_t s);
 
 }  // namespace smc_host
@@ -409,7 +409,7 @@ static smc_status resample_var(smc_ctx* ctx, bool residual, const double* W, int
     st = launch_pdl(smc::k_resample_total, dim3((unsigned)b1), dim3(smc::kRsThreads), 0, s, W, M,
                     do_flag, vs.rs, ctx->d_status);
     if (st != SMC_OK) return st;
-    st = resample_finalize_launch(M, seed, step, do_flag, vs.rs, false, ctx->d_status, s);
+    st = resample_finalize_launch(M, seed, step, do_flag, vs.rs, ctx->d_status, s);
     if (st != SMC_OK) return st;
     int64_t gt = tiles < (int64_t)ctx->num_sms * 4 ? tiles : (int64_t)ctx->num_sms * 4;
     int64_t gd = (M + 255) / 256;

@@ -662,9 +662,7 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __
                 float xh, xl;
                 split_double(x[j], xh, xl);
                 w[j] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
-                unsigned long long q;
-                quantise(w[j], q);  // w in [0, 1]
-                acc += g0 + j < M ? q : 0ull;
+                acc += g0 + j < M ? q_fast(w[j]) : 0ull;  // w in [0, 1]
             }
             if (g0 + kRsIpt <= M && aligned16(W + g0)) {
                 store8(W + g0, w);

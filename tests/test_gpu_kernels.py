@@ -291,6 +291,23 @@ def test_resample_bit_exact(smc, M, kind):
     assert np.all(np_(lwr) == 0.0)
 
 
+@pytest.mark.parametrize("M", [2049, 65537, 1 << 20])
+@pytest.mark.parametrize("scale", [2.0 ** -25, 2.0 ** -34])
+def test_resample_unnormalised_bit_exact(smc, M, scale):
+    """Weights that do not sum to one: a total S below 2^32 (the wide-carry
+    form) and, at the larger sizes, below M (the FP64 quotient estimates)."""
+    P, ctx = smc
+    W = _weights(M, "gauss", M + 7) * scale
+    W[M // 3] = scale  # a heavy item (q = scale 2^52): S > 0, yet S < 2^32
+    seed, step = 99 + M, 5
+    counts = torch.empty(M, dtype=torch.int32, device="cuda")
+    anc = P.resample_systematic(ctx, cu(W), seed, step, counts=counts)
+    ctx.check()
+    ranc, rcounts = oracle.resample_systematic(W, oracle.resample_u32(seed, step))
+    assert np.array_equal(np_(anc), ranc)
+    assert np.array_equal(np_(counts), rcounts)
+
+
 def test_resample_repeated_calls_and_identity_flag(smc):
     P, ctx = smc
     M = 50000
