@@ -58,8 +58,7 @@ smc_status resample_finalize_launch(int64_t M, uint64_t seed, uint64_t step,
 
 // tiles_ready: the tile sums of pass 1 are already in sc (formed by the
 // normalisation pass of smc_reweight_resample, which writes the weights in
-// descending tile order), so pass 1 is skipped and pass 2 runs ascending;
-// otherwise pass 1 runs ascending and pass 2 descending
+// descending tile order, as pass 1 reads them), so pass 1 is skipped
 smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t seed, uint64_t step,
                            int32_t* anc, int32_t* counts, const int32_t* do_flag, double* lwreset,
                            const smc::RsScratch& sc, uint32_t* status, cudaStream_t s,
@@ -91,7 +90,7 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     int64_t g2 = (int64_t)num_sms * occ;
     if (g2 > tiles) g2 = tiles;
     st = launch_pdl(smc::k_resample_scan, dim3((unsigned)g2), dim3(smc::kRsThreads), 0, s, W, M,
-                    tiles_ready ? 0 : 1, do_flag, sc, anc, counts, lwreset, status);
+                    do_flag, sc, anc, counts, lwreset, status);
     if (st != SMC_OK) return st;
     if (sc.heavy_list) {
         st = launch_pdl(smc::k_resample_heavy, dim3((unsigned)num_sms * 4), dim3(smc::kRsThreads),

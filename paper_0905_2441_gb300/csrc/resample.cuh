@@ -16,11 +16,11 @@
 // expands its own contiguous output range through shared memory; ranges
 // too long for a warp go to k_resample_heavy.
 //
-// The passes alternate direction over the tiles (pass 1 ascending, pass 2
-// descending after it, or ascending after a normalisation that wrote the
-// weights in descending order), so the second read of the weights finds
-// the most recently touched ones still in L2; loads and stores that are a
-// datum's last use carry the streaming (evict-first) hint.
+// Pass 1 (and the normalisation of smc_reweight_resample, which forms the
+// tile sums itself) runs over the tiles in descending order and pass 2 in
+// ascending order, so the second read of the weights finds the most
+// recently touched ones still in L2; loads and stores that are a datum's
+// last use carry the streaming (evict-first) hint.
 #pragma once
 #include "device.cuh"
 
@@ -30,7 +30,6 @@ constexpr int kRsThreads = 256;
 constexpr int kRsIpt = 8;                      // weights per thread
 constexpr int kRsTile = kRsThreads * kRsIpt;   // weights per tile
 constexpr unsigned long long kMaxTotal = 1ull << 61;   // S must stay below this
-constexpr int kRsStage = 2 * kRsTile;          // output slots of a tile staged in shared memory
 
 // constants of one resampling call, formed once by k_resample_finalize
 struct RsConst {
@@ -40,6 +39,7 @@ struct RsConst {
     unsigned long long mfx;     // floor(M 2^64 / S) when M < S, else 0 (use FP64)
     unsigned long long ifx;     // floor(2^64 / S) when S > 1, else 0
     double m_over_s;            // M / S (FP64 estimates, only when M >= S)
+    unsigned long long qlight;  // a thread run with total q up to this keeps every R' + d M < 2^64 - S
     uint32_t ok;                // 0: nothing to resample (status already raised)
 };
 constexpr int kRsConstWords = 8;
@@ -59,10 +59,12 @@ __host__ __device__ constexpr int64_t rs_tiles(int64_t M) { return (M + kRsTile 
 __host__ __device__ constexpr int64_t rs_words(int64_t M) {
     return rs_tiles(M) + kRsConstWords;
 }
-// items of one warp's segment of a tile in pass 2, and the output slots a
-// warp stages in shared memory
+// items of one warp's segment of a tile in pass 2; a warp's staging row in
+// shared memory (16 positions a lane) and the longest output range it
+// expands there (the range start may sit up to 3 positions into the row)
 constexpr int kRsSeg = 32 * kRsIpt;
-constexpr int kRsWarpStage = 2 * kRsSeg;
+constexpr int kRsWarpRow = 32 * 16;
+constexpr int kRsWarpFill = kRsWarpRow - 4;
 // output slots of one heavy-expansion chunk, and the most chunk records M
 // weights can produce (a segment's range is split into chunks; ranges add to M)
 constexpr int kRsChunk = 4096;
@@ -91,11 +93,17 @@ __device__ __forceinline__ bool quantise(double w, unsigned long long& q) {
 // w_invalid tells whether w lies outside [0, 1] (or is NaN), -0 counting as
 // a valid zero.  Branch-free, on the 32-bit halves.
 __device__ __forceinline__ unsigned long long q_fast(double w) {
+    // (2^52 + mantissa) >> sh with sh = 1023 - e, as 32-bit funnel shifts
+    // (clamped: a shift of 32 or more leaves the high word, or 0)
     const uint32_t hw = (uint32_t)__double2hiint(w), lw = (uint32_t)__double2loint(w);
     const uint32_t e = (hw >> 20) & 0x7FFu;
-    const uint32_t sh = 1023u - e;  // wraps for e > 1023 (invalid)
-    const unsigned long long man = ((unsigned long long)((hw & 0xFFFFFu) | 0x100000u) << 32) | lw;
-    return sh > 52u ? 0ull : (man >> sh);
+    const uint32_t sh = 1023u - e;  // wraps for e > 1023 (invalid); 1023 for e = 0
+    const uint32_t m21 = (hw & 0xFFFFFu) | 0x100000u;
+    const uint32_t lo_a = __funnelshift_rc(lw, m21, sh);         // sh < 32
+    const uint32_t lo_b = __funnelshift_rc(m21, 0u, sh - 32u);   // sh >= 32 (0 from 53 on)
+    const uint32_t hi = __funnelshift_rc(m21, 0u, sh);           // 0 for sh >= 32
+    const uint32_t lo = sh < 32u ? lo_a : lo_b;
+    return ((unsigned long long)hi << 32) | lo;
 }
 __device__ __forceinline__ bool w_invalid(double w) {
     const uint32_t hw = (uint32_t)__double2hiint(w), lw = (uint32_t)__double2loint(w);
@@ -181,7 +189,7 @@ __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v
 }
 
 // Pass 1: the exact integer sum of every tile; tiles dealt round-robin in
-// ascending order, the next tile's weights loading while one is reduced,
+// descending order, the next tile's weights loading while one is reduced,
 // one barrier per tile (the warp sums alternate between two arrays).
 static __global__ void __launch_bounds__(kRsThreads) k_resample_total(const double* __restrict__ W,
                                                                int64_t M, const int32_t* do_flag,
@@ -194,16 +202,17 @@ static __global__ void __launch_bounds__(kRsThreads) k_resample_total(const doub
     const int wid = threadIdx.x >> 5;
     bool bad = false;
     double vn[kRsIpt];
-    int64_t tile = blockIdx.x;
-    if (tile < ntiles) load_tile_raw(W, M, tile, vn);
-    for (int buf = 0; tile < ntiles; tile += gridDim.x, buf ^= 1) {
+    int64_t kk = blockIdx.x;  // the kk-th tile from the top
+    if (kk < ntiles) load_tile_raw(W, M, ntiles - 1 - kk, vn);
+    for (int buf = 0; kk < ntiles; kk += gridDim.x, buf ^= 1) {
+        const int64_t tile = ntiles - 1 - kk;
         unsigned long long acc = 0;  // <= 8 * 2^52: no wrap
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) {
             bad |= w_invalid(vn[j]);
             acc += q_fast(vn[j]);
         }
-        if (tile + gridDim.x < ntiles) load_tile_raw(W, M, tile + gridDim.x, vn);
+        if (kk + gridDim.x < ntiles) load_tile_raw(W, M, tile - gridDim.x, vn);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
         if ((threadIdx.x & 31) == 0) sh[buf][wid] = acc;
@@ -281,6 +290,41 @@ __device__ __forceinline__ void divmod_cm(unsigned long long c, unsigned long lo
     const QR t = divmod_cm_v(c, M, k.S, k.mfx, k.m_over_s);
     Q = t.Q;
     R = t.R;
+}
+
+// floor(Y / S) for Y = Rp + d M < 2^64 - S, S > 2^32 and a quotient below
+// 2^31, from the fixed-point reciprocal f = floor(2^64 / S) < 2^32: the
+// estimate n = floor(Y f / 2^64) (a 96-bit multiply-high by 32-bit pieces)
+// is the quotient or one below it, and n + 1 is taken when Y >= (n + 1) S.
+// Written in PTX so that every 64-bit step is one wide multiply-add.
+__device__ __forceinline__ uint32_t quot_fx32(unsigned long long Rp, unsigned long long d,
+                                              uint32_t m, uint32_t f, unsigned long long S) {
+    uint32_t n;
+    asm("{\n\t"
+        ".reg .u32 dl, dh, yl, yh, lo, q, q1, tl, th, sl, sh;\n\t"
+        ".reg .u64 Y, P, T, L;\n\t"
+        ".reg .pred ge;\n\t"
+        "mov.b64 {dl, dh}, %2;\n\t"
+        "mad.wide.u32 Y, dl, %3, %1;\n\t"
+        "mov.b64 {yl, yh}, Y;\n\t"
+        "mad.lo.u32 yh, dh, %3, yh;\n\t"
+        "mov.b64 Y, {yl, yh};\n\t"
+        "mul.hi.u32 lo, yl, %4;\n\t"
+        "cvt.u64.u32 L, lo;\n\t"
+        "mad.wide.u32 P, yh, %4, L;\n\t"
+        "mov.b64 {tl, q}, P;\n\t"
+        "add.u32 q1, q, 1;\n\t"
+        "mov.b64 {sl, sh}, %5;\n\t"
+        "mul.wide.u32 T, q1, sl;\n\t"
+        "mov.b64 {tl, th}, T;\n\t"
+        "mad.lo.u32 th, q1, sh, th;\n\t"
+        "mov.b64 T, {tl, th};\n\t"
+        "setp.ge.u64 ge, Y, T;\n\t"
+        "selp.u32 %0, q1, q, ge;\n\t"
+        "}"
+        : "=r"(n)
+        : "l"(Rp), "l"(d), "r"(m), "r"(f), "l"(S));
+    return n;
 }
 
 // c M = Q S + R exactly from the fixed-point reciprocal mfx = floor(M 2^64 /
@@ -426,6 +470,9 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
             // 2^64, where the fixed-point quotient is off by at most one
             // (heavier ones are divided afresh)
             s_c.qheavy = S > 1 ? (0ull - S) / MM : 0ull;
+        } else if (wid == 4) {
+            // R' < 2 S: d M <= 2^64 - 3 S keeps R' + d M below 2^64 - S
+            s_c.qlight = S > 1 ? (0ull - 3ull * S) / MM : 0ull;
         }
     }
     __syncthreads();
@@ -444,23 +491,24 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
 #define SMC_RS_MINB 3
 #endif
 
-// Pass 2, persistent over tiles (descending when `rev`, else ascending).
+// Pass 2, persistent over tiles in ascending order (each CTA's tiles too).
 // Per tile: each thread quantises its 8 weights and each warp scans its 256
 // items with shuffles; one barrier exchanges the warp totals; each thread
-// carries the tile's (Q_t, R_t) to its own offset and then item by item to
-// F at each inclusive prefix; each warp writes its items' offspring counts
-// and log-weight reset, and expands its own output range [lo, hi): through
-// shared memory when it holds at most kRsWarpStage slots, else as chunks
-// for k_resample_heavy (or, without that scratch, by the warp itself).
+// divides c M = Q S + R at its own offset c and forms F at each inclusive
+// prefix of its run from (Q, R); each warp writes its items' offspring
+// counts and log-weight reset, and expands its own output range [lo, hi):
+// by a fill-forward through shared memory when it holds at most kRsWarpFill
+// slots, else as chunks for k_resample_heavy (or, without that scratch, by
+// the warp itself).
 static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_scan(
-    const double* __restrict__ W, int64_t M, int rev, const int32_t* do_flag, RsScratch sc,
+    const double* __restrict__ W, int64_t M, const int32_t* do_flag, RsScratch sc,
     int32_t* __restrict__ anc, int32_t* __restrict__ counts, double* __restrict__ lwreset,
     uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     __shared__ uint32_t s_hi[kRsTile];                          // inclusive F of each item
     // a warp's staged slots, from its range start rounded down to 4 slots
-    __shared__ __align__(16) int32_t s_anc[kRsThreads / 32][kRsWarpStage + 4];
+    __shared__ __align__(16) int32_t s_anc[kRsThreads / 32][kRsWarpRow];
     __shared__ unsigned long long s_warp[2][kRsThreads / 32];
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
@@ -497,23 +545,28 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
     // persistent over tiles; the next tile's weights, prefix, Q and R load
     // while the current one is processed
     int64_t k = blockIdx.x;
-    auto tile_of = [&](int64_t kk) { return rev ? ntiles - 1 - kk : kk; };
+    {  // the staging rows start below every mark
+        int4* mine = reinterpret_cast<int4*>(s_anc[wid] + 16 * lane);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) mine[kk] = make_int4(-1, -1, -1, -1);
+        __syncwarp();
+    }
     double vn[kRsIpt];
     unsigned long long pn = 0;
     if (k < ntiles) {
-        const int64_t t = tile_of(k);
+        const int64_t t = k;
         load_tile_raw_cs(W, M, t, vn);
         pn = __ldcg(sc.tile_sum + t);
     }
     for (int buf = 0; k < ntiles; k += gridDim.x, buf ^= 1) {
-        const int64_t tile = tile_of(k);
+        const int64_t tile = k;
         const int64_t base = tile * kRsTile;
         unsigned long long q[kRsIpt];
 #pragma unroll
         for (int j = 0; j < kRsIpt; ++j) q[j] = q_fast(vn[j]);  // pass 1 reported bad weights
         const unsigned long long tpre = pn;
         if (k + gridDim.x < ntiles) {
-            const int64_t t = tile_of(k + gridDim.x);
+            const int64_t t = k + gridDim.x;
             load_tile_raw_cs(W, M, t, vn);
             pn = __ldcg(sc.tile_sum + t);
         }
@@ -540,44 +593,37 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
         uint32_t F0;
         // the usual case, taken per warp: the starting quotient from the
         // fixed-point reciprocal, and the thread's whole run light enough
-        // that R + d M < 2^64 for every prefix d of its run; then each item's
-        // F comes from the thread's (Q, R) independently of the other items
-        // (d_j = q_0 + ... + q_j: R + d_j M = n S + r, F = Q + n + [r > Rth]),
-        // so the eight divisions overlap instead of forming a chain
-        const bool light = cst.mfx != 0 && tsum <= qheavy;
+        // that R' + d M < 2^64 for every prefix d of its run.  With
+        // R' = R + S - 1 - Rth (< 2 S), floor((R' + d M) / S) counts the
+        // slots below the prefix beyond Q: writing R + d M = n S + r,
+        // R' + d M = n S + r + S - 1 - Rth, whose quotient is n + [r > Rth].
+        // So each item's F = Q + floor((R' + d_j M) / S) comes from the
+        // thread's (Q, R') independently of the other items, and the eight
+        // divisions overlap instead of forming a chain.
+        const bool light = cst.mfx != 0 && tsum <= cst.qlight;
         if (__all_sync(0xFFFFFFFFu, light)) {
             divmod_mfx(c, MM, S, cst.mfx, Q, R);
-            F0 = (uint32_t)Q + (R > Rth ? 1u : 0u);
+            const unsigned long long Rp = R + (S - 1ull - Rth);
+            F0 = (uint32_t)Q + (Rp >= S ? 1u : 0u);
             unsigned long long d = 0;
             if (ifx32) {
                 // S > 2^32 (normalised weights give S ~ 2^52): the
-                // reciprocal and every n fit 32 bits, so n is a 96-bit
-                // multiply-high by 32-bit pieces
+                // reciprocal and every quotient fit 32 bits
                 const uint32_t f32 = (uint32_t)ifx, m32 = (uint32_t)MM;
 #pragma unroll
                 for (int j = 0; j < kRsIpt; ++j) {
                     d += q[j];
-                    const unsigned long long X = R + (unsigned long long)(uint32_t)d * m32 +
-                                                 ((unsigned long long)((uint32_t)(d >> 32) * m32) << 32);
-                    const unsigned long long lo = ((unsigned long long)(uint32_t)X * f32) >> 32;
-                    const uint32_t n =
-                        (uint32_t)(((unsigned long long)(uint32_t)(X >> 32) * f32 + lo) >> 32);
-                    unsigned long long r = X - (unsigned long long)n * S;
-                    const bool up = r >= S;
-                    r -= up ? S : 0ull;
-                    const uint32_t Fn = (uint32_t)Q + n + (up ? 1u : 0u) + (r > Rth ? 1u : 0u);
+                    const uint32_t Fn = (uint32_t)Q + quot_fx32(Rp, d, m32, f32, S);
                     Fv[j] = Fn < (uint32_t)M ? Fn : (uint32_t)M;
                 }
             } else {
 #pragma unroll
                 for (int j = 0; j < kRsIpt; ++j) {
                     d += q[j];
-                    const unsigned long long X = R + d * MM;
-                    const unsigned long long n = __umul64hi(X, ifx);
-                    unsigned long long r = X - n * S;
-                    const bool up = r >= S;
-                    r -= up ? S : 0ull;
-                    const unsigned long long Fn = Q + n + (up ? 1ull : 0ull) + (r > Rth ? 1ull : 0ull);
+                    const unsigned long long Y = Rp + d * MM;
+                    const unsigned long long n = __umul64hi(Y, ifx);
+                    const bool up = Y - n * S >= S;
+                    const unsigned long long Fn = Q + n + (up ? 1ull : 0ull);
                     Fv[j] = Fn < MM ? (uint32_t)Fn : (uint32_t)M;
                 }
             }
@@ -621,57 +667,72 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
         }
         const uint32_t range = hi - lo;
         const int32_t i0 = (int32_t)g0;  // this thread's first item
-        if (range <= (uint32_t)kRsWarpStage) {  // uniform over the warp
-            // each item writes its slots with predicated stores: up to 2
-            // when no item of the warp has more (the usual case), else up to
-            // 4 and a loop for the rare items with more.  Slot sl is staged
-            // at sl - lo_al (lo_al = lo rounded down to 4 slots when the
-            // ancestors are 16-byte aligned), so that 4 staged slots map to
-            // one 16-byte store.
+        if (range <= (uint32_t)kRsWarpFill) {  // uniform over the warp
+            // Fill-forward through shared memory: each item with offspring
+            // marks its first slot with its index, and each slot's ancestor
+            // is the largest mark at or before it (items increase with
+            // their slots).  The rows are never cleared: a CTA's tiles
+            // ascend, so marks left by earlier tiles are smaller than this
+            // tile's, and the slot at lo always holds one of this tile's.
+            // Lane l owns row positions [16 l, 16 l + 16): the maximum of
+            // its 16, a warp maximum-scan across the lanes, then a running
+            // maximum from the lanes before.  Slot sl sits at sl - lo_al
+            // (lo_al = lo rounded down to 4 slots when the ancestors are
+            // 16-byte aligned, so 4 positions are one 16-byte store).  No
+            // loops and no divergence, whatever the offspring counts.
             const uint32_t lo_al = anc16 ? (lo & ~3u) : lo;
-            int32_t* st = s_anc[wid];
-            uint32_t f = F0, most = 0;
+            int32_t* row = s_anc[wid];
+            const int4* mine = reinterpret_cast<const int4*>(row + 16 * lane);
+            uint32_t f = F0;
 #pragma unroll
             for (int j = 0; j < kRsIpt; ++j) {
-                const uint32_t nj = Fv[j] - (j ? Fv[j - 1] : F0);
-                most = nj > most ? nj : most;
-            }
-            if (__all_sync(0xFFFFFFFFu, most <= 2u)) {
-#pragma unroll
-                for (int j = 0; j < kRsIpt; ++j) {
-                    const uint32_t e = Fv[j];
-                    if (f < e) st[f - lo_al] = i0 + j;
-                    if (f + 1 < e) st[f + 1 - lo_al] = i0 + j;
-                    f = e;
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kRsIpt; ++j) {
-                    const uint32_t e = Fv[j];
-#pragma unroll
-                    for (uint32_t kk = 0; kk < 4; ++kk)
-                        if (f + kk < e) st[f + kk - lo_al] = i0 + j;
-                    for (uint32_t sl = f + 4; sl < e; ++sl) st[sl - lo_al] = i0 + j;
-                    f = e;
-                }
+                const uint32_t e = Fv[j];
+                if (e > f) row[f - lo_al] = i0 + j;
+                f = e;
             }
             __syncwarp();
+            int32_t v[16];
+#pragma unroll
+            for (int kq = 0; kq < 4; ++kq) {
+                const int4 t = mine[kq];
+                v[4 * kq] = t.x;
+                v[4 * kq + 1] = t.y;
+                v[4 * kq + 2] = t.z;
+                v[4 * kq + 3] = t.w;
+            }
+            int32_t run = max(max(max(v[0], v[1]), max(v[2], v[3])),
+                              max(max(v[4], v[5]), max(v[6], v[7])));
+            run = max(run, max(max(max(v[8], v[9]), max(v[10], v[11])),
+                               max(max(v[12], v[13]), max(v[14], v[15]))));
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int32_t u = __shfl_up_sync(0xFFFFFFFFu, run, o);
+                if (lane >= o) run = max(run, u);
+            }
+            int32_t before = __shfl_up_sync(0xFFFFFFFFu, run, 1);
+            v[0] = lane ? max(v[0], before) : v[0];
+#pragma unroll
+            for (int kq = 1; kq < 16; ++kq) v[kq] = max(v[kq], v[kq - 1]);
+            const uint32_t s0 = lo_al + 16u * (uint32_t)lane;  // the slot of v[0]
             if (anc16) {
-                const uint32_t span = hi - lo_al;
-                for (uint32_t k = 4u * lane; k < span; k += 128u) {
-                    const int4 v = *reinterpret_cast<const int4*>(st + k);
-                    const uint32_t sl = lo_al + k;
-                    if (sl >= lo && sl + 4u <= hi) {
-                        __stcs(reinterpret_cast<int4*>(anc + sl), v);
-                    } else {  // the range's ragged ends
-                        if (sl >= lo && sl < hi) __stcs(anc + sl, v.x);
-                        if (sl + 1u >= lo && sl + 1u < hi) __stcs(anc + sl + 1u, v.y);
-                        if (sl + 2u >= lo && sl + 2u < hi) __stcs(anc + sl + 2u, v.z);
-                        if (sl + 3u < hi) __stcs(anc + sl + 3u, v.w);
+                // 4 slots a store; a group cut by the range's ends (at most
+                // one at each end of the warp's range) slot by slot
+#pragma unroll
+                for (int kq = 0; kq < 4; ++kq) {
+                    const uint32_t sg = s0 + 4u * kq;
+                    if (sg >= lo && sg + 4u <= hi) {
+                        __stcs(reinterpret_cast<int4*>(anc + sg),
+                               make_int4(v[4 * kq], v[4 * kq + 1], v[4 * kq + 2], v[4 * kq + 3]));
+                    } else if (sg < hi && sg + 4u > lo) {
+#pragma unroll
+                        for (int t = 0; t < 4; ++t)
+                            if (sg + t >= lo && sg + t < hi) __stcs(anc + sg + t, v[4 * kq + t]);
                     }
                 }
-            } else {
-                for (uint32_t kk = lane; kk < range; kk += 32) __stcs(anc + lo + kk, st[kk]);
+            } else if (s0 < hi) {
+#pragma unroll
+                for (int kq = 0; kq < 16; ++kq)
+                    if (s0 + kq < hi) __stcs(anc + s0 + kq, v[kq]);
             }
             __syncwarp();
             continue;
