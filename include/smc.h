@@ -391,6 +391,27 @@ smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
                    const float* x_in, const int32_t* anc, float* x_out, double* logg_out,
                    int64_t M, uint64_t seed, uint64_t t, void* stream);
 
+/* One whole bootstrap-filter step (Section 3.2) in one call: pf_step,
+ * smc_reweight with dbeta = 1 on its log g, and systematic resampling of
+ * the new weights with the normalisation forming the resampling's tile
+ * sums (as smc_reweight_resample) -- the kernels of those calls, launched
+ * back to back, so every output equals theirs bit for bit:
+ *   x_out, logg_out (double[M], required: log g passes through it): as
+ *     pf_step, from x_in gathered through anc;
+ *   logw[i] += log g_i; W_out, scalars_out, resample_flag_out, ess_frac:
+ *     as smc_reweight (resample_flag_out NULL: resample unconditionally);
+ *   anc (in/out, int32[M]): read as this step's ancestors, then overwritten
+ *     with the ancestors drawn from W_out (uniform word of (seed, RESAMPLE,
+ *     t)), or the identity when the flag says no resampling; logw is reset
+ *     to 0 when resampling happened; counts_out (nullable): offspring.
+ * Errors as pf_step, smc_reweight and smc_resample_systematic; M at most
+ * 2^31 - 1. */
+smc_status smc_pf_filter_step(smc_ctx* ctx, const smc_pf_model* model, const float* y_t,
+                              const float* x_in, int32_t* anc, float* x_out, double* logg_out,
+                              double* logw, int64_t M, double* W_out, double* scalars_out,
+                              int32_t* resample_flag_out, double ess_frac, uint64_t seed,
+                              uint64_t t, int32_t* counts_out, void* stream);
+
 /* ------------------------------------------------------------------- streams */
 
 /* MRG32k3a (L'Ecuyer 1999), the generator Section 2.5 parallelises: thread

@@ -24,7 +24,7 @@ EXPORTS = ("smc_create", "smc_destroy", "smc_reserve", "smc_ctx_check", "smc_sta
            "pf_step", "smc_rng_words", "smc_rng_normals", "smc_measure_peak",
            "smc_resample_systematic_noalloc", "smc_resample_multinomial",
            "smc_resample_residual", "smc_is_moments", "smc_rng_mrg32k3a",
-           "smc_reweight_resample", "smc_set_wait_limit")
+           "smc_reweight_resample", "smc_set_wait_limit", "smc_pf_filter_step")
 PEAK_EX2, PEAK_LG2, PEAK_FFMA, PEAK_DFMA = 0, 1, 2, 3
 
 
@@ -79,6 +79,8 @@ def _declare(L):
                                     _i32, C.c_float, _u64, _u64, _vp, _vp]
     L.pf_step.argtypes = [_vp, C.POINTER(SmcPfModel), _vp, _vp, _vp, _vp, _vp, _i64, _u64, _u64,
                           _vp]
+    L.smc_pf_filter_step.argtypes = [_vp, C.POINTER(SmcPfModel), _vp, _vp, _vp, _vp, _vp, _vp,
+                                     _i64, _vp, _vp, _vp, C.c_double, _u64, _u64, _vp, _vp]
     L.smc_rng_words.argtypes = [_vp, _u64, _u32, _u64, _u32, _u32, _vp, _vp]
     L.smc_rng_normals.argtypes = [_vp, _u64, _u32, _u64, _u32, _u32, _vp, _vp]
     L.smc_measure_peak.argtypes = [_i32, _i32, _i32, C.POINTER(C.c_double), C.POINTER(C.c_double)]

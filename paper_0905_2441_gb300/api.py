@@ -432,6 +432,36 @@ def pf_step(ctx: Context, model: PFModel, y_t, x_in, x_out, logg_out, seed: int,
                           _ptr(logg_out), M, int(seed), int(t), _stream(stream)), "pf_step")
 
 
+def pf_filter_step(ctx: Context, model: PFModel, y_t, x_in, x_out, anc, logw, W_out, logg_out,
+                   seed: int, t: int, scalars=None, flag=None, ess_frac: float = 0.5,
+                   counts=None, stream=None):
+    """One whole bootstrap-filter step in one call: pf_step, reweight
+    (dbeta = 1) and systematic resampling; anc is read as this step's
+    ancestors and overwritten with the next step's (the identity when flag
+    says no resampling)."""
+    if x_in.dim() != 2 or x_in.shape[0] != model.state_dim:
+        raise ValueError(f"x_in must be [{model.state_dim}, M] for this model, "
+                         f"got {tuple(x_in.shape)}")
+    d, M = x_in.shape
+    _need(y_t, torch.float32, "y_t", (model.obs_dim,))
+    _need(x_in, torch.float32, "x_in", (d, M))
+    _need(x_out, torch.float32, "x_out", (d, M))
+    _need(anc, torch.int32, "anc", (M,))
+    _need(logw, torch.float64, "logw", (M,))
+    _need(W_out, torch.float64, "W_out", (M,))
+    if logg_out is None:
+        raise TypeError("logg_out must be a CUDA tensor")
+    _need(logg_out, torch.float64, "logg_out", (M,))
+    _need(scalars, torch.float64, "scalars", (4,))
+    _need(flag, torch.int32, "flag", (1,))
+    _need(counts, torch.int32, "counts", (M,))
+    m = model.cstruct_cached()
+    _chk(L.load().smc_pf_filter_step(ctx.handle, C.byref(m), _ptr(y_t), _ptr(x_in), _ptr(anc),
+                                     _ptr(x_out), _ptr(logg_out), _ptr(logw), M, _ptr(W_out),
+                                     _ptr(scalars), _ptr(flag), float(ess_frac), int(seed), int(t),
+                                     _ptr(counts), _stream(stream)), "smc_pf_filter_step")
+
+
 @dataclass
 class ISProblem:
     """Gaussian-mixture target sum_k a_k N(mu_k, var), Gaussian proposal, test

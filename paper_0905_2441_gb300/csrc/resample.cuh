@@ -376,13 +376,43 @@ static __device__ unsigned long long div_shift64(unsigned long long hi, unsigned
     return q;
 }
 
+// The call's constants from the exact total S, into c: lane 0 of warps
+// 0..5 forms one each (integer divisions side by side, no FP64 loop); the
+// caller synchronises the block before reading c.  c.ok is not touched.
+static __device__ __noinline__ void rs_form_constants(unsigned long long S, int64_t M, uint64_t seed,
+                                                  uint64_t step, RsConst& c) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane != 0) return;
+    const unsigned long long MM = (unsigned long long)M;
+    if (wid == 0) {
+        const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
+        c.S = S;
+        c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
+    } else if (wid == 1) {
+        c.mfx = MM < S ? (unsigned long long)(((unsigned __int128)MM << 64) / S) : 0ull;
+    } else if (wid == 2) {
+        c.ifx = S > 1 ? (0ull - S) / S + 1ull : 0ull;  // floor(2^64 / S)
+    } else if (wid == 3) {
+        // items (and thread runs) with q M <= 2^64 - S keep R + q M < 2^64,
+        // where the fixed-point quotient is off by at most one (heavier
+        // ones are divided afresh)
+        c.qheavy = S > 1 ? (0ull - S) / MM : 0ull;
+    } else if (wid == 4) {
+        // R' < 2 S: d M <= 2^64 - 3 S keeps R' + d M below 2^64 - S
+        c.qlight = S > 1 ? (0ull - 3ull * S) / MM : 0ull;
+    } else if (wid == 5) {
+        c.m_over_s = (double)MM / (double)S;
+    }
+}
+
 // Between the passes, one CTA: the exact total S from the tile sums, the
 // call's uniform and constants, and every tile's exclusive prefix c_t (the
 // tile sums are replaced in place), so that no tile of pass 2 repeats this
-// work.  kRsFinTiles tile sums at a time: each thread loads its 8 (all
-// loads in flight at once, coalesced across the warp), each warp scans 256
-// of them; the three fixed-point constants are formed by three warps side
-// by side.
+// work.  kRsFinTiles tile sums at a time: each thread loads 8 consecutive
+// ones (all loads in flight at once) and sums them, a warp scan and one
+// scan of the 32 warp totals give every thread its offset, and each thread
+// writes its 8 prefixes.  The four fixed-point constants are formed by four
+// warps side by side (integer divisions, no FP64 loop).
 constexpr int kRsFinThreads = 1024;
 constexpr int kRsFinTiles = 8 * kRsFinThreads;
 static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
@@ -392,89 +422,78 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
     grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
     __shared__ unsigned long long s_w[kRsFinThreads / 32];
-    __shared__ unsigned long long s_run;
+    __shared__ unsigned long long s_tot;
     __shared__ int s_bad;
     __shared__ RsConst s_c;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int64_t ntiles = rs_tiles(M);
-    if (tid == 0) {
-        s_bad = 0;
-        s_run = 0;
-    }
-    __syncthreads();
+    if (tid == 0) s_bad = 0;
+    unsigned long long run = 0;  // total of the blocks before this one
+    bool ovf = false;
     for (int64_t base = 0; base < ntiles; base += kRsFinTiles) {
-        const int64_t n = ntiles - base < kRsFinTiles ? ntiles - base : kRsFinTiles;
-        // warp wid scans tiles [256 wid, 256 wid + 256) of this block: round
-        // k holds tile 256 wid + 32 k + lane
+        const int64_t i0 = base + (int64_t)tid * 8;
         unsigned long long v[8];
+        if (i0 + 8 <= ntiles && (reinterpret_cast<uintptr_t>(sc.tile_sum) & 15u) == 0) {
+            const ulonglong2* p = reinterpret_cast<const ulonglong2*>(sc.tile_sum + i0);
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = wid * 256 + k * 32 + lane;
-            v[k] = i < n ? __ldcg(sc.tile_sum + base + i) : 0ull;
+            for (int j = 0; j < 4; ++j) {
+                const ulonglong2 t = __ldcg(p + j);
+                v[2 * j] = t.x;
+                v[2 * j + 1] = t.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = i0 + j < ntiles ? __ldcg(sc.tile_sum + i0 + j) : 0ull;
         }
-        unsigned long long carry = 0;
-        bool ovf = false;
+        unsigned long long tsum = 0;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            unsigned long long incl = v[k];
+        for (int j = 0; j < 8; ++j) {
+            tsum += v[j];
+            ovf |= tsum < v[j];
+        }
+        unsigned long long incl = tsum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) {
+                incl += u;
+                ovf |= incl < u;
+            }
+        }
+        if (lane == 31) s_w[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {  // exclusive scan of the warp totals, in place
+            const unsigned long long t = s_w[lane];
+            unsigned long long x = t;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+                const unsigned long long u = __shfl_up_sync(0xFFFFFFFFu, x, o);
                 if (lane >= o) {
-                    ovf |= incl + u < incl;
-                    incl += u;
+                    x += u;
+                    ovf |= x < u;
                 }
             }
-            const unsigned long long ex = carry + incl - v[k];  // exclusive within the warp's run
-            ovf |= carry + incl < carry;
-            v[k] = ex;
-            carry += __shfl_sync(0xFFFFFFFFu, incl, 31);
+            s_w[lane] = x - t;
+            if (lane == 31) s_tot = x;
         }
-        if (lane == 0) s_w[wid] = carry;
-        if (ovf) s_bad = 1;
         __syncthreads();
-        unsigned long long off = s_run, tot = 0;
-        bool ovf2 = false;
-        for (int w = 0; w < kRsFinThreads / 32; ++w) {
-            if (w < wid) off += s_w[w];
-            const unsigned long long nn = tot + s_w[w];
-            ovf2 |= nn < tot;
-            tot = nn;
-        }
-        if (ovf2 || s_run + tot < s_run) s_bad = 1;
+        unsigned long long c = run + s_w[wid] + (incl - tsum);  // before this thread's first tile
+        ovf |= c < run;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int i = wid * 256 + k * 32 + lane;
-            if (i < n) sc.tile_sum[base + i] = v[k] + off;
+        for (int j = 0; j < 8; ++j) {
+            if (i0 + j < ntiles) sc.tile_sum[i0 + j] = c;
+            c += v[j];
         }
-        __syncthreads();
-        if (tid == 0) s_run += tot;
-        __syncthreads();
+        const unsigned long long nrun = run + s_tot;
+        ovf |= nrun < run;
+        run = nrun;
+        __syncthreads();  // s_w and s_tot are rewritten by the next block
     }
-    const unsigned long long S = s_run;
-    const unsigned long long MM = (unsigned long long)M;
+    if (ovf) s_bad = 1;
+    __syncthreads();
+    const unsigned long long S = run;
     const bool good = !(S == 0 || S >= kMaxTotal || s_bad);
-    // the constants, one per warp
-    if (lane == 0 && good) {
-        if (wid == 0) {
-            const uint32_t u32 = draw(seed, RNG_RESAMPLE, step, 0u, 0u).x;
-            s_c.S = S;
-            s_c.Rth = __umul64hi((unsigned long long)u32 << 32, S);  // floor(u32 S / 2^32)
-            s_c.m_over_s = (double)MM / (double)S;
-        } else if (wid == 1) {
-            s_c.mfx = MM < S ? div_shift64(MM, S) : 0ull;
-        } else if (wid == 2) {
-            s_c.ifx = S > 1 ? div_shift64(1ull, S) : 0ull;
-        } else if (wid == 3) {
-            // items (and thread runs) with q M <= 2^64 - S keep R + q M <
-            // 2^64, where the fixed-point quotient is off by at most one
-            // (heavier ones are divided afresh)
-            s_c.qheavy = S > 1 ? (0ull - S) / MM : 0ull;
-        } else if (wid == 4) {
-            // R' < 2 S: d M <= 2^64 - 3 S keeps R' + d M below 2^64 - S
-            s_c.qlight = S > 1 ? (0ull - 3ull * S) / MM : 0ull;
-        }
-    }
+    if (good) rs_form_constants(S, M, seed, step, s_c);
     __syncthreads();
     if (tid == 0) {
         if (sc.heavy_count) *sc.heavy_count = 0ull;  // the scan appends from zero

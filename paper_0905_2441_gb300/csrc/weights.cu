@@ -18,405 +18,11 @@
 #include "ctx.hpp"
 #include "device.cuh"
 #include "resample.cuh"
+#include "reweight.cuh"
 
 using namespace smc_host;
 
 namespace smc {
-
-// exp(dh + dl) for a non-positive difference given as float hi/lo parts,
-// per element: one FFMA, one FMUL and ex2.approx (flushes below 2^-126 to
-// 0).  The rounding of the base-2 argument t = (dh + dl) log2(e) is about
-// 2^-24 |t|, so the relative error is ~2^-22 + 4.1e-8 |t| -- within the
-// weights' stated error of 1e-6 + 1e-7 |ln(W / W_max)| at every t, and
-// below 2e-7 of a sum for the usual spread of log-weights.
-__device__ __forceinline__ float exp_hl(float dh, float dl) {
-    const float L2E = 1.44269504088896340736f;
-    return ex2(fmaf(dh, L2E, dl * L2E));
-}
-
-// exp(x) for an FP64 x <= 64 (FP32 accuracy, float result)
-__device__ __forceinline__ float expd(double x) {
-    float hi, lo;
-    split_double(x, hi, lo);
-    return exp_hilo(hi, lo);
-}
-
-constexpr double kNegInf = -INFINITY;
-__device__ __forceinline__ bool is_neg_inf(double x) {  // on the 32-bit halves
-    return (uint32_t)__double2hiint(x) == 0xFFF00000u && __double2loint(x) == 0;
-}
-
-// Element loops take chunks of 8 consecutive doubles per thread and
-// iteration (four 16-byte loads issued before any use), so each SM keeps
-// enough bytes in flight to cover HBM latency; a scalar loop handles the
-// tail and unaligned arrays.
-constexpr int kChunk = 8;
-
-__device__ __forceinline__ bool aligned16(const void* p) {
-    return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
-}
-
-__device__ __forceinline__ void load8(const double* __restrict__ p, double (&v)[kChunk]) {
-    const double2* q = reinterpret_cast<const double2*>(p);
-    double2 t[kChunk / 2];
-#pragma unroll
-    for (int j = 0; j < kChunk / 2; ++j) t[j] = q[j];
-#pragma unroll
-    for (int j = 0; j < kChunk / 2; ++j) { v[2 * j] = t[j].x; v[2 * j + 1] = t[j].y; }
-}
-
-// load8 with the streaming hint (the data's last read)
-__device__ __forceinline__ void load8_cs(const double* __restrict__ p, double (&v)[kChunk]) {
-    const double2* q = reinterpret_cast<const double2*>(p);
-    double2 t[kChunk / 2];
-#pragma unroll
-    for (int j = 0; j < kChunk / 2; ++j) t[j] = __ldcs(q + j);
-#pragma unroll
-    for (int j = 0; j < kChunk / 2; ++j) { v[2 * j] = t[j].x; v[2 * j + 1] = t[j].y; }
-}
-
-__device__ __forceinline__ void store8(double* __restrict__ p, const double (&v)[kChunk]) {
-    double2* q = reinterpret_cast<double2*>(p);
-#pragma unroll
-    for (int j = 0; j < kChunk / 2; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
-}
-
-// Thread-level sums against a slack reference r: e = exp(x - r) may exceed
-// 1 (up to e^32) so the reference moves only when an element exceeds it by
-// more than 32 nats, not at every new maximum.  No FP64 instruction per
-// element: x and r are split into float hi + lo parts by integer operations
-// and x - r is taken as the pair (xh - rh, xl - rl); the hi difference is
-// exact when x and r are within a factor 2 and otherwise rounded once
-// (relative error 2^-24 of the difference), which the exponential turns
-// into a relative error of at most 2^-24 |x - r| in e.
-struct RefSums {
-    double r = kNegInf;
-    float rh = 0.0f, rl = 0.0f;
-    float s1 = 0.0f, s2 = 0.0f;
-    bool any = false;
-    long long kmax = LLONG_MIN;               // key of the largest element
-    __device__ __forceinline__ void add(double x) {
-        if (is_neg_inf(x)) return;            // zero weight
-        const long long k = dkey(x);
-        kmax = k > kmax ? k : kmax;
-        float xh, xl;
-        split_double(x, xh, xl);
-        if (!any) { r = x; rh = xh; rl = xl; s1 = 1.0f; s2 = 1.0f; any = true; return; }
-        const float dh = xh - rh, dl = xl - rl;
-        if (dh > 32.0f) {                     // move the reference up to x
-            const float f = exp_hl(-dh, -dl);
-            s1 = fmaf(s1, f, 1.0f);
-            s2 = fmaf(s2, f * f, 1.0f);
-            r = x; rh = xh; rl = xl;
-        } else {
-            const float e = exp_hl(dh, dl);
-            s1 += e;
-            s2 = fmaf(e, e, s2);
-        }
-    }
-};
-
-// Eight elements at once, with independent work for each: the chunk's exact
-// maximum cm (integer keys), e_j = exp(x_j - cm) on float hi/lo splits as
-// in RefSums::add, tree sums of e and e^2, then one merge into the running
-// sums (one exponential rescales whichever side has the smaller reference).
-// Zero weights (-inf) add nothing; a chunk of them leaves the sums as they
-// are.
-__device__ __forceinline__ void add8(RefSums& t, const double (&x)[kChunk]) {
-    long long k[kChunk];
-#pragma unroll
-    for (int j = 0; j < kChunk; ++j) k[j] = dkey(x[j]);
-    long long km = k[0];
-#pragma unroll
-    for (int j = 1; j < kChunk; ++j) km = k[j] > km ? k[j] : km;
-    const double cm = __longlong_as_double(km ^ ((km >> 63) & 0x7FFFFFFFFFFFFFFFLL));
-    if (is_neg_inf(cm)) return;
-    t.kmax = km > t.kmax ? km : t.kmax;
-    float mh, ml;
-    split_double(cm, mh, ml);
-    float e[kChunk], e2[kChunk];
-#pragma unroll
-    for (int j = 0; j < kChunk; ++j) {
-        float xh, xl;
-        split_double(x[j], xh, xl);
-        e[j] = exp_hl(xh - mh, xl - ml);  // <= 1; a zero weight (-inf) splits to -1e30: 0
-        e2[j] = e[j] * e[j];
-    }
-#pragma unroll
-    for (int w = 1; w < kChunk; w <<= 1)
-#pragma unroll
-        for (int j = 0; j + w < kChunk; j += 2 * w) {
-            e[j] += e[j + w];
-            e2[j] += e2[j + w];
-        }
-    if (!t.any) {
-        t.r = cm;
-        split_double(cm, t.rh, t.rl);
-        t.s1 = e[0];
-        t.s2 = e2[0];
-        t.any = true;
-    } else if (km > dkey(t.r)) {  // the chunk holds a new reference
-        const float f = exp_hl(t.rh - mh, t.rl - ml);
-        t.s1 = fmaf(t.s1, f, e[0]);
-        t.s2 = fmaf(t.s2, f * f, e2[0]);
-        t.r = cm;
-        t.rh = mh;
-        t.rl = ml;
-    } else {
-        const float f = exp_hl(mh - t.rh, ml - t.rl);
-        t.s1 = fmaf(e[0], f, t.s1);
-        t.s2 = fmaf(e2[0], f * f, t.s2);
-    }
-}
-
-// block / grid level: FP64 sums relative to a reference m
-struct Lse {
-    double m, s1, s2;
-};
-
-__device__ __forceinline__ double key_to_double(long long k) {
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7FFFFFFFFFFFFFFFLL));
-}
-
-__device__ __forceinline__ long long warp_max_key(long long key) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const long long k2 = __shfl_xor_sync(0xFFFFFFFFu, key, o);
-        key = k2 > key ? k2 : key;
-    }
-    return key;
-}
-
-// Block combination of thread sums: the block's reference is the largest
-// thread reference (integer comparison of FP64 keys), every thread rescales
-// its FP32 sums to it with one exponential, then FP32 block sums.  Result
-// valid in thread 0.
-__device__ __forceinline__ Lse block_combine(const RefSums& t, long long* s_key, float* s_a,
-                                             float* s_b, double* max_out) {
-    long long key = warp_max_key(t.any ? dkey(t.r) : LLONG_MIN);
-    long long kmx = warp_max_key(t.kmax);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_key[w] = key; s_key[16 + w] = kmx; }
-    __syncthreads();
-    long long bk = LLONG_MIN, bm = LLONG_MIN;
-    for (int i = 0; i < nw; ++i) {
-        bk = s_key[i] > bk ? s_key[i] : bk;
-        bm = s_key[16 + i] > bm ? s_key[16 + i] : bm;
-    }
-    __syncthreads();
-    Lse out{kNegInf, 0.0, 0.0};
-    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
-    if (bk == LLONG_MIN) return out;  // every weight zero in this block
-    const double R = key_to_double(bk);
-    float a = 0.0f, b = 0.0f;
-    if (t.any) {
-        const float f = expd(t.r - R);  // <= 1
-        a = t.s1 * f;
-        b = t.s2 * f * f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-    }
-    if ((threadIdx.x & 31) == 0) { s_a[w] = a; s_b[w] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        float A = 0.0f, B = 0.0f;
-        for (int i = 0; i < nw; ++i) { A += s_a[i]; B += s_b[i]; }
-        out = Lse{R, f2d_bits(A), f2d_bits(B)};
-    }
-    __syncthreads();
-    return out;
-}
-
-// Combine the per-block partials in the last block: the common reference is
-// the largest block reference (integer keys), each partial is scaled to it
-// with one FP32 exponential and the sums are reduced in FP64 as a parallel
-// tree -- no long serial chain of FP64 operations (FP64 latency is long on
-// this part).  Result valid in thread 0; `off` selects {ref, s1, s2} at 0 or
-// {ref_old, s_old} at 3.
-__device__ __forceinline__ Lse combine_partials(const double* partials, int nblocks, int off,
-                                                long long* s_key) {
-    long long k = LLONG_MIN;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double r = __ldcg(partials + (size_t)b * 8 + off);
-        if (!is_neg_inf(r)) { const long long kk = dkey(r); k = kk > k ? kk : k; }
-    }
-    k = warp_max_key(k);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) s_key[w] = k;
-    __syncthreads();
-    long long bk = LLONG_MIN;
-    for (int i = 0; i < nw; ++i) bk = s_key[i] > bk ? s_key[i] : bk;
-    __syncthreads();
-    Lse out{kNegInf, 0.0, 0.0};
-    if (bk == LLONG_MIN) return out;
-    float Rh, Rl;
-    const double R = key_to_double(bk);
-    split_double(R, Rh, Rl);
-    // FP64 accumulation, but only short dependent chains: a few partials per
-    // thread, then a 5-level shuffle tree and 8 warp totals
-    double a = 0.0, bsum = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double* P = partials + (size_t)b * 8 + off;
-        const double r = __ldcg(P);
-        if (is_neg_inf(r)) continue;
-        float h, l;
-        split_double(r, h, l);
-        const float f = exp_hilo(h - Rh, l - Rl);  // <= 1
-        a = fma(__ldcg(P + 1), f2d_bits(f), a);
-        if (off == 0) bsum = fma(__ldcg(P + 2), f2d_bits(f * f), bsum);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, o);
-        bsum += __shfl_xor_sync(0xFFFFFFFFu, bsum, o);
-    }
-    __shared__ double s_da[32], s_db[32];
-    if ((threadIdx.x & 31) == 0) { s_da[w] = a; s_db[w] = bsum; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double A = 0.0, B = 0.0;
-        for (int i = 0; i < nw; ++i) { A += s_da[i]; B += s_db[i]; }
-        out = Lse{R, A, B};
-    }
-    __syncthreads();
-    return out;
-}
-
-__device__ __forceinline__ double max_partials(const double* partials, int nblocks, long long* sk) {
-    long long k = LLONG_MIN;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double v = __ldcg(partials + (size_t)b * 8 + 5);
-        if (!is_neg_inf(v)) { const long long kk = dkey(v); k = kk > k ? kk : k; }
-    }
-    k = warp_max_key(k);
-    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = k;
-    __syncthreads();
-    long long m = LLONG_MIN;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = sk[i] > m ? sk[i] : m;
-    __syncthreads();
-    return m == LLONG_MIN ? kNegInf : key_to_double(m);
-}
-
-// ln of a positive float sum, as lg2 * ln 2 (absolute error ~2^-22)
-__device__ __forceinline__ double ln_sum(double s) {
-    return (double)(lg2((float)s) * 0.69314718055994531f);
-}
-
-// Both block combinations of the reweight reduction in one pass (the new
-// log-weights' sums with their maximum, and the old ones' sums): the same
-// references, scalings and summation orders as two calls of block_combine,
-// with two barriers instead of eight.  Results valid in thread 0.
-__device__ __forceinline__ void block_combine2(const RefSums& c, const RefSums& o, bool has_old,
-                                               long long* s_key, float* s_f, Lse* outc,
-                                               Lse* outo, double* max_out) {
-    const long long kc = warp_max_key(c.any ? dkey(c.r) : LLONG_MIN);
-    const long long km = warp_max_key(c.kmax);
-    const long long ko = has_old ? warp_max_key(o.any ? dkey(o.r) : LLONG_MIN) : LLONG_MIN;
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_key[w] = kc; s_key[16 + w] = km; s_key[32 + w] = ko; }
-    __syncthreads();
-    long long bc = LLONG_MIN, bm = LLONG_MIN, bo = LLONG_MIN;
-    for (int i = 0; i < nw; ++i) {
-        bc = s_key[i] > bc ? s_key[i] : bc;
-        bm = s_key[16 + i] > bm ? s_key[16 + i] : bm;
-        bo = s_key[32 + i] > bo ? s_key[32 + i] : bo;
-    }
-    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
-    float a = 0.0f, b = 0.0f, ao = 0.0f;
-    if (bc != LLONG_MIN && c.any) {
-        const float f = expd(c.r - key_to_double(bc));  // <= 1
-        a = c.s1 * f;
-        b = c.s2 * f * f;
-    }
-    if (has_old && bo != LLONG_MIN && o.any) ao = o.s1 * expd(o.r - key_to_double(bo));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
-        b += __shfl_xor_sync(0xFFFFFFFFu, b, off);
-        ao += __shfl_xor_sync(0xFFFFFFFFu, ao, off);
-    }
-    if ((threadIdx.x & 31) == 0) { s_f[w] = a; s_f[32 + w] = b; s_f[64 + w] = ao; }
-    __syncthreads();
-    *outc = Lse{kNegInf, 0.0, 0.0};
-    *outo = Lse{kNegInf, 0.0, 0.0};
-    if (threadIdx.x == 0) {
-        float A = 0.0f, B = 0.0f, AO = 0.0f;
-        for (int i = 0; i < nw; ++i) { A += s_f[i]; B += s_f[32 + i]; AO += s_f[64 + i]; }
-        if (bc != LLONG_MIN) *outc = Lse{key_to_double(bc), f2d_bits(A), f2d_bits(B)};
-        if (bo != LLONG_MIN) *outo = Lse{key_to_double(bo), f2d_bits(AO), 0.0};
-    }
-}
-
-// The last block's three passes over the partials (new sums, old sums,
-// maximum) in one: the same references and summation orders as
-// combine_partials(0), combine_partials(3) and max_partials, with two
-// barriers instead of ten.  Results valid in thread 0.
-__device__ __forceinline__ void combine_partials3(const double* partials, int nblocks,
-                                                  bool has_old, long long* s_key, double* s_d,
-                                                  Lse* outc, Lse* outo, double* max_out) {
-    long long kc = LLONG_MIN, ko = LLONG_MIN, km = LLONG_MIN;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double* P = partials + (size_t)b * 8;
-        const double rc = __ldcg(P), ro = __ldcg(P + 3), mx = __ldcg(P + 5);
-        if (!is_neg_inf(rc)) { const long long k = dkey(rc); kc = k > kc ? k : kc; }
-        if (has_old && !is_neg_inf(ro)) { const long long k = dkey(ro); ko = k > ko ? k : ko; }
-        if (!is_neg_inf(mx)) { const long long k = dkey(mx); km = k > km ? k : km; }
-    }
-    kc = warp_max_key(kc);
-    ko = warp_max_key(ko);
-    km = warp_max_key(km);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_key[w] = kc; s_key[16 + w] = ko; s_key[32 + w] = km; }
-    __syncthreads();
-    long long bc = LLONG_MIN, bo = LLONG_MIN, bm = LLONG_MIN;
-    for (int i = 0; i < nw; ++i) {
-        bc = s_key[i] > bc ? s_key[i] : bc;
-        bo = s_key[16 + i] > bo ? s_key[16 + i] : bo;
-        bm = s_key[32 + i] > bm ? s_key[32 + i] : bm;
-    }
-    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
-    float Rch = 0.0f, Rcl = 0.0f, Roh = 0.0f, Rol = 0.0f;
-    if (bc != LLONG_MIN) split_double(key_to_double(bc), Rch, Rcl);
-    if (bo != LLONG_MIN) split_double(key_to_double(bo), Roh, Rol);
-    double a = 0.0, bs = 0.0, ao = 0.0;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double* P = partials + (size_t)b * 8;
-        const double rc = __ldcg(P);
-        if (bc != LLONG_MIN && !is_neg_inf(rc)) {
-            float h, l;
-            split_double(rc, h, l);
-            const float f = exp_hilo(h - Rch, l - Rcl);  // <= 1
-            a = fma(__ldcg(P + 1), f2d_bits(f), a);
-            bs = fma(__ldcg(P + 2), f2d_bits(f * f), bs);
-        }
-        const double ro = __ldcg(P + 3);
-        if (has_old && bo != LLONG_MIN && !is_neg_inf(ro)) {
-            float h, l;
-            split_double(ro, h, l);
-            const float f = exp_hilo(h - Roh, l - Rol);
-            ao = fma(__ldcg(P + 4), f2d_bits(f), ao);
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
-        bs += __shfl_xor_sync(0xFFFFFFFFu, bs, off);
-        ao += __shfl_xor_sync(0xFFFFFFFFu, ao, off);
-    }
-    if ((threadIdx.x & 31) == 0) { s_d[w] = a; s_d[32 + w] = bs; s_d[64 + w] = ao; }
-    __syncthreads();
-    *outc = Lse{kNegInf, 0.0, 0.0};
-    *outo = Lse{kNegInf, 0.0, 0.0};
-    if (threadIdx.x == 0) {
-        double A = 0.0, B = 0.0, AO = 0.0;
-        for (int i = 0; i < nw; ++i) { A += s_d[i]; B += s_d[32 + i]; AO += s_d[64 + i]; }
-        if (bc != LLONG_MIN) *outc = Lse{key_to_double(bc), A, B};
-        if (bo != LLONG_MIN) *outo = Lse{key_to_double(bo), AO, 0.0};
-    }
-}
 
 // partial slot layout (doubles): [b*8 + 0..5] = {ref, s1, s2, ref_old, s_old, max}
 // final slot: {max, S1, S2, valid, lse, (float) 1/S1 in the low word of [5]},
@@ -432,10 +38,6 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
                                                          uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
-    __shared__ long long s_key[48];
-    __shared__ float s_f[96];
-    __shared__ double s_d[96];
-    __shared__ bool last;
     RefSums cur, old;
     bool nan_seen = false;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
@@ -492,51 +94,8 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
         }
     }
     if (nan_seen) raise_status(status, ST_NONFINITE);
-    double bmax;
-    Lse c, o;
-    block_combine2(cur, old, has_inc != 0, s_key, s_f, &c, &o, &bmax);
-    if (threadIdx.x == 0) {
-        double* P = partials + (size_t)blockIdx.x * 8;
-        P[0] = c.m; P[1] = c.s1; P[2] = c.s2; P[3] = o.m; P[4] = o.s1; P[5] = bmax;
-        __threadfence();
-        const unsigned long long t = atomicAdd(ticket, 1ull);
-        last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    Lse tc, to;
-    double mx;
-    combine_partials3(partials, gridDim.x, has_inc != 0, s_key, s_d, &tc, &to, &mx);
-    if (threadIdx.x == 0) {
-        *ticket = 0ull;
-        double* F = partials + (size_t)final_slot * 8;
-        const bool valid = !is_neg_inf(tc.m) && !disnan(tc.m);
-        if (valid) {  // express the sums relative to the true maximum
-            const double f = f2d_bits(expd(tc.m - mx));
-            tc = Lse{mx, tc.s1 * f, tc.s2 * f * f};
-        }
-        if (!valid) {
-            if (!disnan(tc.m)) raise_status(status, ST_ZERO_WEIGHT);
-            F[3] = 0.0;
-            if (flag) *flag = 0;
-            return;
-        }
-        const double lse = tc.m + ln_sum(tc.s1);
-        const float s1f = (float)tc.s1;
-        const double ess = f2d_bits(s1f * (s1f / (float)tc.s2));  // FP32 division
-        F[0] = tc.m; F[1] = tc.s1; F[2] = tc.s2; F[3] = 1.0; F[4] = lse;
-        reinterpret_cast<float*>(F + 5)[0] = 1.0f / s1f;
-        if (scalars) {
-            double inc = 0.0;
-            if (has_inc) inc = lse - (to.m + ln_sum(to.s1));
-            scalars[0] = inc;
-            scalars[1] = ess;
-            scalars[2] = tc.m;
-            scalars[3] = lse;
-        }
-        if (flag) *flag = (ess < ess_frac * (double)M) ? 1 : 0;
-    }
+    reweight_finish(cur, old, has_inc, M, partials, ticket, scalars, flag, ess_frac, final_slot,
+                    status);
 }
 
 // W_i = exp(lw_i - m) / S1 with the difference taken on float hi/lo splits
@@ -730,6 +289,40 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
 
 size_t smc_resample_ws_bytes(int64_t M);
 
+// After a reweighting reduction whose final slot is in the context's
+// partials: W and the exact tile sums in one pass, then systematic
+// resampling from those tile sums (the ancestors, the log-weight reset).
+smc_status normalize_resample_launch(smc_ctx* ctx, double* logw, int64_t M, double* W_out,
+                                     int32_t* resample_flag, uint64_t seed, uint64_t step,
+                                     int32_t* ancestors_out, int32_t* counts_out, cudaStream_t s) {
+    smc_status st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
+    if (st != SMC_OK) return st;
+    const smc::RsScratch sc =
+        resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
+    const int final_slot = kMaxPartialBlocks - 1;
+    int64_t nb = smc::rs_tiles(M);
+    if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
+    st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
+                    (const double*)logw, M,
+                    (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out, sc);
+    if (st != SMC_OK) return st;
+    return resample_launch(ctx->num_sms, W_out, M, seed, step, ancestors_out, counts_out,
+                           resample_flag, logw, sc, ctx->d_status, s, true);
+}
+
+// The reweighting reduction (logw += dbeta loglik, the final slot, the
+// scalars and the flag) without the normalisation.
+smc_status reweight_reduce_launch(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
+                                  int64_t M, double* scalars_out, int32_t* resample_flag,
+                                  double ess_frac, cudaStream_t s) {
+    const int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
+    const int blocks = reduce_blocks(ctx, M);
+    const int final_slot = kMaxPartialBlocks - 1;
+    return launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw,
+                      M, has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET,
+                      scalars_out, resample_flag, ess_frac, final_slot, ctx->d_status);
+}
+
 extern "C" smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, double dbeta,
                                             double* logw, int64_t M, double* W_out,
                                             double* scalars_out, int32_t* resample_flag_out,
@@ -742,25 +335,11 @@ extern "C" smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, 
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
-    st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
+    st = reweight_reduce_launch(ctx, loglik, dbeta, logw, M, scalars_out, resample_flag_out,
+                                ess_frac, s);
     if (st != SMC_OK) return st;
-    const smc::RsScratch sc =
-        resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
-    const int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
-    const int blocks = reduce_blocks(ctx, M);
-    const int final_slot = kMaxPartialBlocks - 1;
-    st = launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw, M,
-                    has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET, scalars_out,
-                    resample_flag_out, ess_frac, final_slot, ctx->d_status);
-    if (st != SMC_OK) return st;
-    int64_t nb = smc::rs_tiles(M);
-    if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
-    st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
-                    (const double*)logw, M,
-                    (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out, sc);
-    if (st != SMC_OK) return st;
-    return resample_launch(ctx->num_sms, W_out, M, seed, step, ancestors_out, counts_out,
-                           resample_flag_out, logw, sc, ctx->d_status, s, true);
+    return normalize_resample_launch(ctx, logw, M, W_out, resample_flag_out, seed, step,
+                                     ancestors_out, counts_out, s);
 }
 
 extern "C" smc_status smc_ess(smc_ctx* ctx, const double* logw, int64_t M, double* ess_out,

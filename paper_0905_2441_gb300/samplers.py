@@ -342,15 +342,20 @@ class ParticleFilter(_Graphable):
         y_t, hist = self._views[t]
         lib, h, st = L.load(), self.ctx.handle, api._stream()
         # buffers checked at construction: straight to the C ABI
-        api._chk(lib.pf_step(h, C.byref(self.model.cstruct_cached()), y_t.data_ptr(),
-                             self.x[c].data_ptr(), self.anc.data_ptr(), self.x[n].data_ptr(),
-                             self.logg.data_ptr(), self.M, self.seed, t, st), "pf_step")
-        if self.resampler == "systematic":  # one call, one pass fewer
-            api._chk(lib.smc_reweight_resample(h, self.logg.data_ptr(), 1.0, self.lw.data_ptr(),
-                                               self.M, self.W.data_ptr(), hist.data_ptr(), None,
-                                               0.5, self.seed, t, self.anc.data_ptr(), None, st),
-                     "smc_reweight_resample")
+        if self.resampler == "systematic":
+            # one call: step, reweighting, normalisation with the tile sums,
+            # resampling into anc
+            api._chk(lib.smc_pf_filter_step(h, C.byref(self.model.cstruct_cached()),
+                                            y_t.data_ptr(), self.x[c].data_ptr(),
+                                            self.anc.data_ptr(), self.x[n].data_ptr(),
+                                            self.logg.data_ptr(),
+                                            self.lw.data_ptr(), self.M, self.W.data_ptr(),
+                                            hist.data_ptr(), None, 0.5, self.seed, t, None, st),
+                     "smc_pf_filter_step")
         else:
+            api._chk(lib.pf_step(h, C.byref(self.model.cstruct_cached()), y_t.data_ptr(),
+                                 self.x[c].data_ptr(), self.anc.data_ptr(), self.x[n].data_ptr(),
+                                 self.logg.data_ptr(), self.M, self.seed, t, st), "pf_step")
             api.reweight(self.ctx, self.logg, 1.0, self.lw, self.W, hist, None, 0.5)
             api.resample(self.ctx, self.resampler, self.W, self.seed, t, anc=self.anc,
                          logw_reset=self.lw)

@@ -598,6 +598,76 @@ def test_pf_step_state_dimensions(smc, kind, d):
     np.testing.assert_allclose(np_(lg), rlg, rtol=1e-5, atol=2e-5)
 
 
+def _fsv_or_msv(kind):
+    if kind == 2:
+        phi, Sigma, B, psi = synth.fsv_params()
+        return dict(kind=kind, phi=phi, L=synth.chol(Sigma), B=B, psi=psi), B.shape[0]
+    phi, Sigma, beta = synth.msv_params()
+    return dict(kind=kind, phi=phi, L=synth.chol(Sigma), beta=beta), 3
+
+
+@pytest.mark.parametrize("kind", [0, 1, 2])
+@pytest.mark.parametrize("M", [1, 2049, 100003, 1 << 20])
+@pytest.mark.parametrize("with_flag", [False, True])
+def test_pf_filter_step_equals_the_three_calls(smc, kind, M, with_flag):
+    """smc_pf_filter_step against pf_step + smc_reweight (dbeta = 1) +
+    smc_resample_systematic: the same states, log g, log-weights, W and
+    scalars bit for bit; the ancestors exactly the oracle's systematic
+    resampling of W (and the identity when the flag says no)."""
+    P, ctx = smc
+    spec, m = _fsv_or_msv(kind)
+    if kind == 2:
+        model = P.PFModel(P.PF_FSV, spec["phi"], spec["L"], B=spec["B"], psi=spec["psi"])
+    else:
+        model = P.PFModel(kind, spec["phi"], spec["L"], spec["beta"])
+    d = len(spec["phi"])
+    g = np.random.default_rng(M + kind)
+    x_in = g.normal(0, 1, (d, M)).astype(np.float32)
+    anc0 = np.sort(g.integers(0, M, M)).astype(np.int32)
+    yt = g.normal(0, 1, m).astype(np.float32)
+    lw0 = g.normal(0, 0.3, M)
+    seed, t = 31, 5
+    # the three calls
+    xo_a = torch.empty(d, M, device="cuda")
+    lg_a = torch.empty(M, dtype=torch.float64, device="cuda")
+    P.pf_step(ctx, model, cu(yt), cu(x_in), xo_a, lg_a, seed, t, anc=cu(anc0))
+    lw_a = cu(lw0)
+    W_a = torch.empty(M, dtype=torch.float64, device="cuda")
+    sc_a = torch.empty(4, dtype=torch.float64, device="cuda")
+    fl_a = torch.zeros(1, dtype=torch.int32, device="cuda") if with_flag else None
+    P.reweight(ctx, lg_a, 1.0, lw_a, W_a, sc_a, fl_a, 0.9)
+    ctx.check()
+    lw_new = np_(lw_a).copy()
+    # the fused call
+    xo_b = torch.empty(d, M, device="cuda")
+    lg_b = torch.empty(M, dtype=torch.float64, device="cuda")
+    anc_b = cu(anc0)
+    lw_b = cu(lw0)
+    W_b = torch.empty(M, dtype=torch.float64, device="cuda")
+    sc_b = torch.empty(4, dtype=torch.float64, device="cuda")
+    fl_b = torch.full((1,), 7, dtype=torch.int32, device="cuda") if with_flag else None
+    counts = torch.empty(M, dtype=torch.int32, device="cuda")
+    P.pf_filter_step(ctx, model, cu(yt), cu(x_in), xo_b, anc_b, lw_b, W_b, lg_b, seed, t,
+                     scalars=sc_b, flag=fl_b, ess_frac=0.9, counts=counts)
+    ctx.check()
+    assert np.array_equal(np_(xo_a), np_(xo_b))
+    assert np.array_equal(np_(lg_a), np_(lg_b))
+    assert np.array_equal(np_(W_a), np_(W_b))
+    assert np.array_equal(np_(sc_a), np_(sc_b))
+    resampled = True
+    if with_flag:
+        assert int(np_(fl_b)[0]) == int(np_(fl_a)[0])
+        resampled = bool(np_(fl_b)[0])
+    if resampled:
+        ranc, rcounts = oracle.resample_systematic(np_(W_b), oracle.resample_u32(seed, t))
+        assert np.array_equal(np_(anc_b), ranc)
+        assert np.array_equal(np_(counts), rcounts)
+        assert np.all(np_(lw_b) == 0.0)
+    else:
+        assert np.array_equal(np_(anc_b), np.arange(M))
+        assert np.array_equal(np_(lw_b), lw_new)
+
+
 @pytest.mark.parametrize("M", [1, 3, 2047, 2049, 100003, 1 << 20])
 @pytest.mark.parametrize("with_flag", [False, True])
 def test_reweight_resample_equals_the_two_calls(smc, M, with_flag):
