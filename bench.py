@@ -690,43 +690,18 @@ def bench_secondary(torch, P):
                               "ms_per_step_graph": 1e3 * t_graph / w.T,
                               "logZ_plain": z_plain, "logZ_graph": z_graph}
     ctx.check()
-    # the diagonal mixture on the tensor cores (d=32, K=16, N=65536, M=4096)
+    # the diagonal mixture on the tensor cores (d=32, K=16, N=65536, M=4096),
+    # and the widest shape the path takes (d=64, K=32)
     w = synth.DIAG32
-    truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
-    Y = torch.from_numpy(synth.diag_data(w.N, truth, seed=w.data_seed)).cuda()
-    th = torch.from_numpy(synth.diag_particles(w.M, truth, seed=w.particle_seed)).cuda()
-    tc = P.DiagGMM(w.K, w.sigma, d=w.d, precision=P.PREC_BF16SPLIT)
-    ll = torch.empty(w.M, dtype=torch.float64, device="cuda")
-    P.loglik_batch(ctx, tc, Y, th, out=ll)
-    reps = 10
-    t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
-    ctx.check()
+    out["diag_tensor_core"], snaps["diag_tensor_core"] = diag_tc_entry(
+        torch, P, ctx, flush, stream, ex2_rate, w.name, w.N, w.M, w.d, w.K, w.sigma, w.logw(),
+        w.truth_seed, w.data_seed, w.particle_seed)
     out["is_example"] = is_example(torch, P, ctx)
     out["mrg32k3a"] = mrg_blocks(torch, P, ctx)
-    # rooflines of the tensor-core likelihood: issued bf16 MMA flops (three
-    # split products) and MUFU ops (K ex2 + 1 lg2 per particle-datum)
-    kp = max(4, 1 << (w.K - 1).bit_length())
-    flops = 3 * 2.0 * (-(-w.N // 128) * 128) * (w.M * kp) * w.d
-    mufu = float(w.N) * w.M * (kp + 1)
-    pk = measured_peaks()
-    t_tcf = statistics.median([_whole_run(torch, flush, stream,
-                                          lambda: P.loglik_batch(ctx, tc, Y, th, out=ll))
-                               for _ in range(5)])
-    snaps["diag_tensor_core"] = {"w": w, "theta": th.cpu().numpy(), "ll": ll.cpu().numpy()}
-    out["diag_tensor_core"] = {
-        "workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
-        "ms_per_call": 1e3 * t_tc, "ms_per_call_l2_flushed": 1e3 * t_tcf,
-        "pd_per_s": w.M * w.N / t_tc,
-        "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory",
-        "roofline": {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": mufu / t_tcf / 1e9,
-                     "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": mufu / t_tcf / ex2_rate,
-                     "traffic": profile_traffic("k_dtc_main"),
-                     "kernel": "k_dtc_main (+ prep, combine)", "ops_per_launch": mufu,
-                     "launch_time": "one call after an L2 flush (median of 5)",
-                     "tensor": {"achieved": flops / t_tcf / 1e12, "peak": pk["bf16_tflops"],
-                                "unit": "TFLOP/s", "frac": flops / t_tcf / 1e12 / pk["bf16_tflops"],
-                                "flops_per_call": flops,
-                                "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst"}}}
+    K64 = 32
+    out["diag_tensor_core_d64"], snaps["diag_tensor_core_d64"] = diag_tc_entry(
+        torch, P, ctx, flush, stream, ex2_rate, "diag-d64-K32-N65536-M2048", 65536, 2048, 64,
+        K64, 1.3, np.full(K64, -np.log(K64)), 64, 65, 66)
     try:
         out["reweight_resample"], snaps["reweight_resample"] = reweight_resample_roofline(
             torch, P, ctx, 1 << 24, 20)
@@ -735,6 +710,49 @@ def bench_secondary(torch, P):
     ctx.close()
     out["_snaps"] = snaps
     return out
+
+
+def diag_tc_entry(torch, P, ctx, flush, stream, ex2_rate, name, N, M, d, K, sigma, logw,
+                  truth_seed, data_seed, particle_seed):
+    """The tensor-core diagonal-mixture likelihood on one synthetic shape:
+    time per call (warm and after an L2 flush) and its two rooflines, issued
+    bf16 MMA flops (three split products) and MUFU ops (K ex2 + 1 lg2 per
+    particle-datum, K padded to 4, 8, 16 or 32).  Returns the entry and the
+    snapshot for the oracle's check."""
+    import synth
+    truth = synth.diag_truth(K, d, seed=truth_seed)
+    Y = torch.from_numpy(synth.diag_data(N, truth, seed=data_seed)).cuda()
+    th = torch.from_numpy(synth.diag_particles(M, truth, seed=particle_seed)).cuda()
+    tc = P.DiagGMM(K, sigma, d=d, log_w=np.asarray(logw), precision=P.PREC_BF16SPLIT)
+    ll = torch.empty(M, dtype=torch.float64, device="cuda")
+    P.loglik_batch(ctx, tc, Y, th, out=ll)
+    reps = 10
+    t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
+    ctx.check()
+    kp = max(4, 1 << (K - 1).bit_length())
+    flops = 3 * 2.0 * (-(-N // 128) * 128) * (M * kp) * d
+    mufu = float(N) * M * (kp + 1)
+    pk = measured_peaks()
+    t_tcf = statistics.median([_whole_run(torch, flush, stream,
+                                          lambda: P.loglik_batch(ctx, tc, Y, th, out=ll))
+                               for _ in range(5)])
+    snap = {"N": N, "d": d, "K": K, "sigma": sigma, "logw": np.asarray(logw),
+            "seeds": (truth_seed, data_seed), "theta": th.cpu().numpy(), "ll": ll.cpu().numpy()}
+    entry = {
+        "workload": name, "d": d, "K": K, "N": N, "M": M,
+        "ms_per_call": 1e3 * t_tc, "ms_per_call_l2_flushed": 1e3 * t_tcf,
+        "pd_per_s": M * N / t_tc,
+        "form": "tcgen05 bf16 hi/lo split, FP32 accumulation in tensor memory",
+        "roofline": {"bound": "alu", "pipe": "MUFU (ex2)", "achieved": mufu / t_tcf / 1e9,
+                     "peak": ex2_rate / 1e9, "unit": "Gop/s", "frac": mufu / t_tcf / ex2_rate,
+                     "traffic": profile_traffic("k_dtc_main") if d == 32 else None,
+                     "kernel": "k_dtc_main (+ prep, combine)", "ops_per_launch": mufu,
+                     "launch_time": "one call after an L2 flush (median of 5)",
+                     "tensor": {"achieved": flops / t_tcf / 1e12, "peak": pk["bf16_tflops"],
+                                "unit": "TFLOP/s", "frac": flops / t_tcf / 1e12 / pk["bf16_tflops"],
+                                "flops_per_call": flops,
+                                "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst"}}}
+    return entry, snap
 
 
 def reweight_resample_roofline(torch, P, ctx, M, reps, seed=5):
@@ -821,18 +839,19 @@ def secondary_oracle_checks(snaps):
                             "max_rel_loglik_err_agreeing": float(np.max(
                                 np.abs(d["ll1"][slots][ok] - rl[ok]) / np.abs(rl[ok])))
                             if ok.any() else None}
-    if "diag_tensor_core" in snaps:
-        d = snaps["diag_tensor_core"]
-        w = d["w"]
+    for name in ("diag_tensor_core", "diag_tensor_core_d64"):
+        if name not in snaps:
+            continue
+        d = snaps[name]
         import synth
-        truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
-        Yh = synth.diag_data(w.N, truth, seed=w.data_seed)
-        idx = np.array([0, 1, w.M // 2 - 1, w.M // 2, w.M - 1])
-        ref = oracle.gmmdiag_loglik(Yh, w.logw(), w.sigma, d["theta"][idx])
-        res["diag_tensor_core"] = {"max_rel_loglik_err": float(np.max(np.abs(d["ll"][idx] - ref) /
-                                                                     np.abs(ref))),
-                                   "particles_checked": int(idx.size),
-                                   "tolerance": "relative 1e-3 (BF16 split)"}
+        truth = synth.diag_truth(d["K"], d["d"], seed=d["seeds"][0])
+        Yh = synth.diag_data(d["N"], truth, seed=d["seeds"][1])
+        M = d["theta"].shape[0]
+        idx = np.array([0, 1, M // 2 - 1, M // 2, M - 1])
+        ref = oracle.gmmdiag_loglik(Yh, d["logw"], d["sigma"], d["theta"][idx])
+        res[name] = {"max_rel_loglik_err": float(np.max(np.abs(d["ll"][idx] - ref) /
+                                                       np.abs(ref))),
+                     "particles_checked": int(idx.size), "tolerance": "relative 1e-3 (BF16 split)"}
     if "particle_filter" in snaps:
         d = snaps["particle_filter"]
         sl = rng.choice(d["x_in"].shape[1], 20000, replace=False)

@@ -138,7 +138,7 @@ typedef struct smc_gmm {
  * The prior box is not applied here.  Diag with SMC_PREC_BF16SPLIT forms
  * mu.y on the tensor cores from bf16 hi/lo splits of y and mu (products
  * hi.hi + hi.lo + lo.hi, FP32 accumulation; relative error of loglik well
- * below 1e-3) and takes d = 16 or 32 and K <= 16 (other shapes:
+ * below 1e-3) and takes d = 16, 32, 48 or 64 and K <= 32 (other shapes:
  * SMC_ERR_UNSUPPORTED, use SMC_PREC_FP32); it uses context scratch of about
  * N (4 d + 8 bytes) + M K (4 d + 32 bytes).  Errors: SMC_ERR_ARG for
  * M < 0, N < 0, K/d out of range, sigma <= 0, NULL pointers with M, N > 0;

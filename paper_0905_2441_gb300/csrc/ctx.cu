@@ -122,6 +122,7 @@ extern "C" smc_status smc_create(smc_ctx** out, int device) {
     c->num_sms = prop.multiProcessorCount;
     c->max_threads_per_sm = prop.maxThreadsPerMultiProcessor;
     c->smem_per_sm = (int)prop.sharedMemPerMultiprocessor;
+    c->smem_optin = (int)prop.sharedMemPerBlockOptin;
     c->smem_reserved = (int)prop.reservedSharedMemPerBlock;
     bool ok = cudaMalloc(&c->d_status, sizeof(uint32_t)) == cudaSuccess &&
               cudaMalloc(&c->d_counters, kCounters * sizeof(unsigned long long)) == cudaSuccess &&

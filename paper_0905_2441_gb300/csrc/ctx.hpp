@@ -12,6 +12,7 @@ struct smc_ctx {
     int num_sms = 0;
     int max_threads_per_sm = 0;
     int smem_per_sm = 0;            // shared memory per SM (bytes)
+    int smem_optin = 0;             // largest dynamic shared memory one CTA may opt in to
     int smem_reserved = 0;          // shared memory the system reserves per block
     uint32_t* d_status = nullptr;     // latched device errors (bit set)
     // fixed small area: counters and reduction partials

@@ -40,7 +40,7 @@ namespace dtc {
 constexpr int kRows = 128;     // data per tile = MMA M = TMEM lanes
 constexpr int kHalf = 128;     // particle-components per MMA (N) and per TMEM buffer
 constexpr int kBlockCols = 2 * kHalf;  // particle-components per particle block
-constexpr int kStages = 4;     // ring of data tiles
+constexpr int kStages = 4;     // ring of data tiles (at most; fewer at large d)
 constexpr int kEpiWarps = 16;  // four warpgroups: (tile parity, half) each
 constexpr int kThreads = 32 * (2 + kEpiWarps);
 constexpr int kTmemCols = 512; // 4 buffers of 128 FP32 columns
@@ -53,7 +53,7 @@ __host__ __device__ inline uint32_t cm_off(int r, int j, int d) {
 }
 
 struct Lw2 {
-    float v[16];  // log2 w_k, k < K (padding components: -inf)
+    float v[32];  // log2 w_k, k < K (padding components: -inf)
 };
 
 // shared-memory plan (bytes from a 1024-aligned base)
@@ -65,16 +65,19 @@ struct Plan {
     uint32_t bpart;   // one part of a particle block: 256 * d * 2
     uint32_t bblock;  // a particle block in memory: hi, lo, beta parts
     uint32_t y0, b0, ones0, acc0, bar0, tmemslot, total;
+    int ny, nb;       // data-tile stages (2..4) and particle-block buffers (1..2)
 };
 
-__host__ __device__ inline Plan plan(int d, int ppw) {
+__host__ __device__ inline Plan plan(int d, int ppw, int ny, int nb) {
     Plan p;
+    p.ny = ny;
+    p.nb = nb;
     p.ypart = (uint32_t)(kRows * d * 2);
     p.bpart = (uint32_t)(kBlockCols * d * 2);
     p.bblock = 2 * p.bpart + kBetaPart;
     p.y0 = 0;
-    p.b0 = p.y0 + kStages * 2 * p.ypart;
-    p.ones0 = p.b0 + 2 * p.bblock;
+    p.b0 = p.y0 + (uint32_t)ny * 2 * p.ypart;
+    p.ones0 = p.b0 + (uint32_t)nb * p.bblock;
     p.acc0 = p.ones0 + kOnesBytes;
     p.bar0 = p.acc0 + (uint32_t)(32 * kEpiWarps * ppw * 4);  // a float per thread and particle
     p.tmemslot = p.bar0 + 24 * 8;
@@ -312,12 +315,14 @@ __global__ void __launch_bounds__(256) k_dtc_prep_mu(const float* __restrict__ t
 template <int KP>
 __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
     const uint8_t* __restrict__ yt, const uint8_t* __restrict__ bt, int64_t N, int d,
-    int64_t ntiles, int nsplit, int64_t units, double* __restrict__ partial, uint32_t* status) {
+    int64_t ntiles, int nsplit, int64_t units, double* __restrict__ partial, uint32_t* status,
+    int ny, int nbuf) {
     constexpr int PPW = 64 / KP;          // particles per epilogue warp
     extern __shared__ __align__(1024) uint8_t smraw[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smraw) + 1023) &
                                              ~(uintptr_t)1023);
-    const Plan pl = plan(d, PPW);
+    const Plan pl = plan(d, PPW, ny, nbuf);
+    const int NY = pl.ny, NB = pl.nb;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar = smem_u32(sm + pl.bar0);
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
 
     if (threadIdx.x == 0) {
         s_abort = 0;
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NY; ++s) {
             mbar_init(B(B_FULL + s), 1);
             mbar_init(B(B_EMPTY + s), 1);
         }
@@ -371,9 +376,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
             int ui = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
-                const int bb = ui & 1;
+                const int bb = ui % NB;
                 const int64_t pb = u / nsplit, sp = u % nsplit;
-                if (ui >= 2 && !mbar_wait(B(B_BFREE + bb), ((ui >> 1) - 1) & 1, abort)) {
+                if (ui >= NB && !mbar_wait(B(B_BFREE + bb), ((ui / NB) - 1) & 1, abort)) {
                     ok = false;
                     break;
                 }
@@ -382,9 +387,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                          pl.bblock, B(B_BFULL + bb));
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
-                    const int s = (int)(it % kStages);
-                    if (it >= kStages &&
-                        !mbar_wait(B(B_EMPTY + s), (uint32_t)(((it / kStages) - 1) & 1), abort)) {
+                    const int s = (int)(it % NY);
+                    if (it >= NY &&
+                        !mbar_wait(B(B_EMPTY + s), (uint32_t)(((it / NY) - 1) & 1), abort)) {
                         ok = false;
                         break;
                     }
@@ -396,10 +401,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
             if (!ok) fail();
             // drain: every copy issued has landed before the CTA ends (fill
             // number k of a stage or buffer completes phase k)
-            for (int s = 0; s < kStages; ++s)
-                if (it > s) mbar_wait(B(B_FULL + s), (uint32_t)(((it - 1 - s) / kStages) & 1), nullptr);
-            for (int b2 = 0; b2 < 2; ++b2)
-                if (ui > b2) mbar_wait(B(B_BFULL + b2), (uint32_t)(((ui - 1 - b2) / 2) & 1), nullptr);
+            for (int s = 0; s < NY; ++s)
+                if (it > s) mbar_wait(B(B_FULL + s), (uint32_t)(((it - 1 - s) / NY) & 1), nullptr);
+            for (int b2 = 0; b2 < NB; ++b2)
+                if (ui > b2) mbar_wait(B(B_BFULL + b2), (uint32_t)(((ui - 1 - b2) / NB) & 1), nullptr);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
@@ -410,9 +415,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
             const uint32_t sbo = (uint32_t)d * 16u;
             const int ksteps = d / 16;
             for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
-                const int bb = ui & 1;
+                const int bb = ui % NB;
                 const int64_t sp = u % nsplit;
-                if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui >> 1) & 1), abort)) {
+                if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui / NB) & 1), abort)) {
                     ok = false;
                     break;
                 }
@@ -424,13 +429,13 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
                     const int j = (int)(it & 1);
-                    const int s = (int)(it % kStages);
+                    const int s = (int)(it % NY);
                     if (it >= 2 &&
                         !mbar_wait(B(B_TEMPTY + j), (uint32_t)(((it >> 1) - 1) & 1), abort)) {
                         ok = false;
                         break;
                     }
-                    if (!mbar_wait(B(B_FULL + s), (uint32_t)((it / kStages) & 1), abort)) {
+                    if (!mbar_wait(B(B_FULL + s), (uint32_t)((it / NY) & 1), abort)) {
                         ok = false;
                         break;
                     }
@@ -530,7 +535,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                         ms[ip] += m;
                     }
                 }
-                if (++ngroup == 16) {  // 16 sums of at most 16 each: below 2^64
+                if (++ngroup == 16) {  // 16 sums of at most KP <= 32 each: below 2^80
 #pragma unroll
                     for (int i = 0; i < PPW; ++i) {
                         sacc[i * 32 * kEpiWarps] += ms[i] + lg2(pr[i]);
@@ -603,17 +608,35 @@ namespace {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// components padded to 4, 8, 16 or 32
+int comp_pad(int K) { return K <= 4 ? 4 : (K <= 8 ? 8 : (K <= 16 ? 16 : 32)); }
+
+// the deepest pipeline whose shared-memory plan fits one CTA (with 1 KiB of
+// alignment slack): data-tile stages 4..2 with two particle-block buffers,
+// then 4..2 with one
+bool pick_plan(const smc_ctx* ctx, int d, int ppw, int* ny, int* nb) {
+    const size_t cap = ctx->smem_optin > 0 ? (size_t)ctx->smem_optin : (size_t)227 * 1024;
+    for (int b = 2; b >= 1; --b)
+        for (int y = smc::dtc::kStages; y >= 2; --y)
+            if (smc::dtc::plan(d, ppw, y, b).total + 1024 + 1088 <= cap) {  // + static shared memory
+                *ny = y;
+                *nb = b;
+                return true;
+            }
+    return false;
+}
+
 template <int KP>
 smc_status launch_main(const smc_ctx* ctx, int64_t grid, size_t smem, const uint8_t* yt,
                        const uint8_t* bt, int64_t N, int d, int64_t ntiles, int nsplit,
-                       int64_t units, double* partial, cudaStream_t s) {
+                       int64_t units, double* partial, cudaStream_t s, int ny, int nb) {
     auto kern = smc::dtc::k_dtc_main<KP>;
     cudaFuncAttributes fa;
     SMC_CUDA(cudaFuncGetAttributes(&fa, kern));
     if (fa.maxThreadsPerBlock < smc::dtc::kThreads) return SMC_ERR_UNSUPPORTED;
     SMC_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<(unsigned)grid, smc::dtc::kThreads, smem, s>>>(yt, bt, N, d, ntiles, nsplit, units,
-                                                         partial, ctx->d_status);
+                                                         partial, ctx->d_status, ny, nb);
     return cuda_ok(cudaGetLastError());
 }
 
@@ -622,7 +645,7 @@ smc_status launch_main(const smc_ctx* ctx, int64_t grid, size_t smem, const uint
 // Workspace bytes of one call (data tiles, particle blocks, beta, partials).
 size_t smc_diag_tc_ws_bytes(int64_t N, int64_t M, int K, int d, int sms) {
     using namespace smc::dtc;
-    const int KP = K <= 4 ? 4 : (K <= 8 ? 8 : 16);
+    const int KP = comp_pad(K);
     const int64_t ntiles = (N + kRows - 1) / kRows;
     const int64_t nblocks = (M + kBlockCols / KP - 1) / (kBlockCols / KP);
     int nsplit = 1;
@@ -641,10 +664,14 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
                               const float* theta, int64_t M, double* out, cudaStream_t s) {
     using namespace smc::dtc;
     const int K = model->K, d = model->d;
-    // tensor-core path: K <= 16 components, d a multiple of 16 up to 32
-    if (K > 16 || (d != 16 && d != 32)) return SMC_ERR_UNSUPPORTED;
+    // tensor-core path: K <= 32 components, d a multiple of 16 up to 64
+    if (K < 1 || K > 32 || d < 16 || d > 64 || d % 16 != 0) return SMC_ERR_UNSUPPORTED;
+    // the shared-memory plan: as many data-tile stages and particle-block
+    // buffers as fit (4 and 2 up to d = 32; fewer at d = 48, 64)
+    const int KP = comp_pad(K);
+    int ny = 0, nb = 0;
+    if (!pick_plan(ctx, d, 64 / KP, &ny, &nb)) return SMC_ERR_UNSUPPORTED;
     if (N == 0) return cuda_ok(cudaMemsetAsync(out, 0, (size_t)M * sizeof(double), s));
-    const int KP = K <= 4 ? 4 : (K <= 8 ? 8 : 16);
     const int64_t ntiles = (N + kRows - 1) / kRows;
     const int64_t nblocks = (M + kBlockCols / KP - 1) / (kBlockCols / KP);
     int nsplit = 1;
@@ -666,14 +693,14 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
     const double sg = (double)model->sigma;
     const double alpha = smc::kLog2e / (sg * sg);
     Lw2 lw2;
-    for (int k = 0; k < 16; ++k)
+    for (int k = 0; k < 32; ++k)
         lw2.v[k] = k < K ? (float)((double)model->log_w[k] * smc::kLog2e) : -INFINITY;
     k_dtc_prep_y<<<(unsigned)gblocks, 256, 0, s>>>(Y, N, d, ntiles, yt, gpart);
     SMC_CUDA(cudaGetLastError());
     k_dtc_prep_mu<<<(unsigned)((nblocks * kBlockCols + 255) / 256), 256, 0, s>>>(
         theta, M, K, KP, d, nblocks, (float)alpha, lw2, bt);
     SMC_CUDA(cudaGetLastError());
-    const Plan pl = plan(d, 64 / KP);
+    const Plan pl = plan(d, 64 / KP, ny, nb);
     // + alignment slack; at least half an SM's shared memory so that one CTA
     // (and one 512-column tensor-memory allocation) runs per SM
     size_t smem = pl.total + 1024;
@@ -681,9 +708,10 @@ smc_status smc_diag_tc_loglik(smc_ctx* ctx, const smc_gmm* model, const float* Y
         smem = (size_t)ctx->smem_per_sm / 2 + 1024;
     int64_t grid = units < ctx->num_sms ? units : ctx->num_sms;
     switch (KP) {
-        case 4: st = launch_main<4>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
-        case 8: st = launch_main<8>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
-        default: st = launch_main<16>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s); break;
+        case 4: st = launch_main<4>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s, ny, nb); break;
+        case 8: st = launch_main<8>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s, ny, nb); break;
+        case 16: st = launch_main<16>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s, ny, nb); break;
+        default: st = launch_main<32>(ctx, grid, smem, yt, bt, N, d, ntiles, nsplit, units, partial, s, ny, nb); break;
     }
     if (st != SMC_OK) return st;
     const double ncst = (double)N * (-0.5 * d * std::log(2.0 * M_PI * sg * sg));

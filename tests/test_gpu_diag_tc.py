@@ -58,6 +58,12 @@ def run_tc(P, ctx, Y, th, K, d, sigma=1.0, log_w=None):
     (1, 32, 16, 3),        # a single datum
     (2000, 16, 3, 129),    # K padded to 4
     (5000, 32, 16, 17),    # several units per block (data split)
+    (700, 48, 12, 40),     # d = 48: three K steps, three data stages
+    (3000, 64, 32, 70),    # d = 64, K = 32: two data stages, 8 particles a block
+    (1500, 64, 4, 300),    # d = 64, K = 4: one particle-block buffer
+    (257, 16, 32, 9),      # K = 32 at the smallest d
+    (2049, 64, 20, 33),    # K padded to 32
+    (600, 48, 32, 5),
 ])
 def test_diag_tc_parity(smc, N, d, K, M):
     P, ctx = smc
@@ -113,6 +119,25 @@ def test_diag_tc_full_size_sampled(smc):
     assert np.array_equal(got, again)
 
 
+@pytest.mark.parametrize("d,K", [(64, 32), (48, 16)])
+def test_diag_tc_large_shape_sampled(smc, d, K):
+    """d = 64 / K = 32 (and d = 48) at N = 65536 data, M = 2048 particles:
+    every particle on the GPU, sampled ones on the oracle."""
+    P, ctx = smc
+    N, M = 65536, 2048
+    truth = synth.diag_truth(K, d, seed=d + K)
+    Y = synth.diag_data(N, truth, seed=d)
+    th = synth.diag_particles(M, truth, seed=K)
+    logw = np.log(np.random.default_rng(d).dirichlet(np.ones(K)))
+    got = run_tc(P, ctx, Y, th, K, d, sigma=1.3, log_w=logw)
+    assert np.all(np.isfinite(got))
+    idx = np.array([0, 5, 1023, 1024, M - 1])
+    ref = oracle.gmmdiag_loglik(Y, logw, 1.3, th[idx])
+    rel = np.abs(got[idx] - ref) / np.abs(ref)
+    print(f"d={d} K={K} sampled rel err", rel)
+    assert np.all(rel <= TOL) and np.all(rel <= TIGHT)
+
+
 def test_diag_tc_edges(smc):
     P, ctx = smc
     Y, th = case(50, 32, 16, 4, seed=3)
@@ -124,7 +149,11 @@ def test_diag_tc_edges(smc):
     Y7, th7 = case(50, 7, 4, 4, seed=3)
     with pytest.raises(P.SmcError):
         P.loglik_batch(ctx, P.DiagGMM(4, 1.0, d=7, precision=P.PREC_BF16SPLIT), cu(Y7), cu(th7))
-    Y17, th17 = case(50, 16, 17, 4, seed=3)
+    Y33, th33 = case(50, 16, 33, 4, seed=3)
     with pytest.raises(P.SmcError):
-        P.loglik_batch(ctx, P.DiagGMM(17, 1.0, d=16, precision=P.PREC_BF16SPLIT), cu(Y17),
-                       cu(th17))
+        P.loglik_batch(ctx, P.DiagGMM(33, 1.0, d=16, precision=P.PREC_BF16SPLIT), cu(Y33),
+                       cu(th33))
+    Y80, th80 = case(50, 80, 4, 4, seed=3)
+    with pytest.raises(P.SmcError):
+        P.loglik_batch(ctx, P.DiagGMM(4, 1.0, d=80, precision=P.PREC_BF16SPLIT), cu(Y80),
+                       cu(th80))
