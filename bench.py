@@ -727,7 +727,14 @@ def diag_tc_entry(torch, P, ctx, flush, stream, ex2_rate, name, N, M, d, K, sigm
     ll = torch.empty(M, dtype=torch.float64, device="cuda")
     P.loglik_batch(ctx, tc, Y, th, out=ll)
     reps = 10
-    t_tc = timed(lambda: [P.loglik_batch(ctx, tc, Y, th, out=ll) for _ in range(reps)]) / reps
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        P.loglik_batch(ctx, tc, Y, th, out=ll)
+    b.record()
+    b.synchronize()
+    t_tc = a.elapsed_time(b) / 1e3 / reps
     ctx.check()
     kp = max(4, 1 << (K - 1).bit_length())
     flops = 3 * 2.0 * (-(-N // 128) * 128) * (M * kp) * d

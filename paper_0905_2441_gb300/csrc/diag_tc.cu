@@ -372,30 +372,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
     if (warp == 0) {
         // ---------------------------------------------------------- producer
         if (lane == 0) {
+            // ring positions kept incrementally (no division in the loops):
+            // stage s of fill round k for the data tiles, buffer bb of round
+            // kb for the particle blocks
             int64_t it = 0;
-            int ui = 0;
+            int ui = 0, s = 0, bb = 0;
+            uint32_t k = 0, kb = 0;
             bool ok = true;
             for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
-                const int bb = ui % NB;
                 const int64_t pb = u / nsplit, sp = u % nsplit;
-                if (ui >= NB && !mbar_wait(B(B_BFREE + bb), ((ui / NB) - 1) & 1, abort)) {
+                if (kb > 0 && !mbar_wait(B(B_BFREE + bb), (kb - 1) & 1, abort)) {
                     ok = false;
                     break;
                 }
                 mbar_expect_tx(B(B_BFULL + bb), pl.bblock);
                 bulk_g2s(smem_u32(sm + pl.b0 + bb * pl.bblock), bt + (size_t)pb * pl.bblock,
                          pl.bblock, B(B_BFULL + bb));
+                if (++bb == NB) { bb = 0; ++kb; }
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
-                    const int s = (int)(it % NY);
-                    if (it >= NY &&
-                        !mbar_wait(B(B_EMPTY + s), (uint32_t)(((it / NY) - 1) & 1), abort)) {
+                    if (k > 0 && !mbar_wait(B(B_EMPTY + s), (k - 1) & 1, abort)) {
                         ok = false;
                         break;
                     }
                     mbar_expect_tx(B(B_FULL + s), tile_bytes);
                     bulk_g2s(smem_u32(sm + pl.y0 + s * tile_bytes), yt + (size_t)t * tile_bytes,
                              tile_bytes, B(B_FULL + s));
+                    if (++s == NY) { s = 0; ++k; }
                 }
             }
             if (!ok) fail();
@@ -410,14 +413,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
         // ---------------------------------------------------------- MMA issuer
         if (lane == 0) {
             int64_t it = 0;
-            int ui = 0;
+            int ui = 0, s = 0, bb = 0;
+            uint32_t k = 0, kb = 0;  // as the producer's
             bool ok = true;
             const uint32_t sbo = (uint32_t)d * 16u;
             const int ksteps = d / 16;
             for (int64_t u = blockIdx.x; u < units && ok; u += gridDim.x, ++ui) {
-                const int bb = ui % NB;
                 const int64_t sp = u % nsplit;
-                if (!mbar_wait(B(B_BFULL + bb), (uint32_t)((ui / NB) & 1), abort)) {
+                if (!mbar_wait(B(B_BFULL + bb), kb & 1, abort)) {
                     ok = false;
                     break;
                 }
@@ -429,13 +432,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                 const int64_t t0 = sp * ntiles / nsplit, t1 = (sp + 1) * ntiles / nsplit;
                 for (int64_t t = t0; t < t1; ++t, ++it) {
                     const int j = (int)(it & 1);
-                    const int s = (int)(it % NY);
                     if (it >= 2 &&
                         !mbar_wait(B(B_TEMPTY + j), (uint32_t)(((it >> 1) - 1) & 1), abort)) {
                         ok = false;
                         break;
                     }
-                    if (!mbar_wait(B(B_FULL + s), (uint32_t)((it / NY) & 1), abort)) {
+                    if (!mbar_wait(B(B_FULL + s), k & 1, abort)) {
                         ok = false;
                         break;
                     }
@@ -456,8 +458,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dtc_main(
                     mma_bf16(dtm, dones, dbeta, 1);
                     mma_commit(B(B_EMPTY + s));
                     mma_commit(B(B_TFULL + j));
+                    if (++s == NY) { s = 0; ++k; }
                 }
                 mma_commit(B(B_BFREE + bb));
+                if (++bb == NB) { bb = 0; ++kb; }
             }
             if (!ok) fail();
             // every MMA issued has completed before tensor memory is freed
