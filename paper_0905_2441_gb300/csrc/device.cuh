@@ -124,27 +124,24 @@ constexpr double kLn2 = 0.6931471805599453094;
 constexpr double kLog2e = 1.4426950408889634074;
 
 // ---------------------------------------------------------------- FP64-light helpers
-// Exact split of a double into hi + lo floats by integer operations only
-// (no FP64 pipe): hi keeps the top 24 significant bits (truncated), lo the
-// next 24 (rounded).  Magnitudes below 2^-74 give 0 and magnitudes of 2^100
-// and above (and infinities) give +-1e30: the callers only exponentiate
-// non-positive differences, for which both ends are exact enough.
+// Split of a double into hi + lo floats by integer operations only (no
+// FP64 pipe): hi keeps the top 24 significant bits (truncated), lo the next
+// 23 (truncated), so hi + lo is within 2^-46 of the double, relatively.  The magnitude
+// is first clamped to [2^-74, 2^100) by the exponent field: smaller values
+// (zero included) become +-2^-74 and larger ones (infinities too) about
+// +-2^100 -- the callers only exponentiate differences of such splits, for
+// which both ends are exact enough.  Branch-free.
 __device__ __forceinline__ void split_double(double d, float& hi, float& lo) {
-    // branch-free: both ends are formed and selected, so a warp whose
-    // elements span the ranges does not diverge
     const uint32_t hw = (uint32_t)__double2hiint(d), lw = (uint32_t)__double2loint(d);
-    const int e = (int)((hw >> 20) & 0x7FFu);
     const uint32_t sign = hw & 0x80000000u;
-    const uint32_t fh = sign | ((uint32_t)(e - 1023 + 127) << 23) | ((hw & 0xFFFFFu) << 3) |
-                        (lw >> 29);
-    // the top 23 of the 29 remaining bits, times 2^(e-1069): the 6 dropped
-    // bits lie 2^-46 below hi
-    const float r = u23_to_f((lw & 0x1FFFFFFFu) >> 6);
-    const float scale = __uint_as_float((uint32_t)(e - 1069 + 127) << 23);
-    const float l = sign ? -(r * scale) : r * scale;
-    const bool small = e < 949, big = e >= 1023 + 100;
-    hi = small ? 0.0f : (big ? (sign ? -1e30f : 1e30f) : __uint_as_float(fh));
-    lo = (small || big) ? 0.0f : l;
+    // |d|'s high word with the exponent clamped to [1023 - 74, 1023 + 99]
+    const uint32_t a = min(max(hw & 0x7FFFFFFFu, 0x3B500000u), 0x462FFFFFu);
+    // hi: exponent re-biased from 1023 to 127, 20 + 3 mantissa bits
+    hi = __uint_as_float(sign | __funnelshift_l(lw, a - 0x38000000u, 3));
+    // lo: the next 23 mantissa bits m, worth m 2^(e - 1075 + 6): the float
+    // (2^23 + m) 2^(e - 1069 - 23) less 2^(e - 1069), signs alike (exact)
+    const uint32_t eb = sign | (((a & 0x7FF00000u) - (919u << 20)) << 3);
+    lo = __uint_as_float(eb | ((lw >> 6) & 0x7FFFFFu)) - __uint_as_float(eb);
 }
 
 // exp(d) for an FP64 d <= 0 given as hi + lo floats, in FP32: the argument

@@ -70,6 +70,33 @@ __device__ __forceinline__ void store8(double* __restrict__ p, const double (&v)
     for (int j = 0; j < kChunk / 2; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
 }
 
+// FP32 sum with its rounding error carried (Knuth's two-sum): the running
+// error stays below 2^-24 of the sum's magnitude times a few, without the
+// long-latency FP64 pipe.
+struct F2Sum {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float x) {
+        const float t = s + x;
+        const float bb = t - s;
+        c += (s - (t - bb)) + (x - bb);
+        s = t;
+    }
+    __device__ __forceinline__ void add(const F2Sum& o) {
+        add(o.s);
+        c += o.c;
+    }
+    __device__ __forceinline__ void warp_sum() {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            F2Sum o;
+            o.s = __shfl_xor_sync(0xFFFFFFFFu, s, off);
+            o.c = __shfl_xor_sync(0xFFFFFFFFu, c, off);
+            add(o);
+        }
+    }
+    __device__ __forceinline__ double value() const { return f2d_bits(s) + f2d_bits(c); }
+};
+
 // Thread-level sums against a slack reference r: e = exp(x - r) may exceed
 // 1 (up to e^32) so the reference moves only when an element exceeds it by
 // more than 32 nats, not at every new maximum.  No FP64 instruction per
@@ -80,10 +107,13 @@ __device__ __forceinline__ void store8(double* __restrict__ p, const double (&v)
 // into a relative error of at most 2^-24 |x - r| in e.
 struct RefSums {
     double r = kNegInf;
-    float rh = 0.0f, rl = 0.0f;
+    float rh = -1e30f, rl = 0.0f;            // (below every weight until one arrives)
     float s1 = 0.0f, s2 = 0.0f;
+    float c1 = 0.0f, c2 = 0.0f;              // rounding errors carried by add8's merges
     bool any = false;
     long long kmax = LLONG_MIN;               // key of the largest element
+    __device__ __forceinline__ float sum1() const { return s1 + c1; }
+    __device__ __forceinline__ float sum2() const { return s2 + c2; }
     __device__ __forceinline__ void add(double x) {
         if (is_neg_inf(x)) return;            // zero weight
         const long long k = dkey(x);
@@ -105,30 +135,59 @@ struct RefSums {
     }
 };
 
-// Eight elements at once, with independent work for each: the chunk's exact
-// maximum cm (integer keys), e_j = exp(x_j - cm) on float hi/lo splits as
-// in RefSums::add, tree sums of e and e^2, then one merge into the running
-// sums (one exponential rescales whichever side has the smaller reference).
-// Zero weights (-inf) add nothing; a chunk of them leaves the sums as they
-// are.
-__device__ __forceinline__ void add8(RefSums& t, const double (&x)[kChunk]) {
-    long long k[kChunk];
+// Eight elements at once against the thread's running reference r (no
+// exact chunk maximum, no key compares unless the maximum is tracked): e_j
+// = exp(x_j - r) on float hi/lo splits as in RefSums::add, tree sums of e
+// and e^2, then a two-sum merge into the running sums (the rounding errors
+// carried in c1, c2).  The reference moves to a chunk element whose hi part
+// exceeds it (the sums are rescaled by one exponential, at most 1), so the
+// dominant terms keep small exponents and their FP32 arguments small
+// errors; the first chunk holding a weight sets it.  Zero weights (-inf,
+// split to -1e30) add nothing.  With track_max the exact maximum (integer
+// keys) is kept too.
+__device__ __forceinline__ void add8(RefSums& t, const double (&x)[kChunk], bool track_max) {
+    float xh[kChunk], xl[kChunk];
 #pragma unroll
-    for (int j = 0; j < kChunk; ++j) k[j] = dkey(x[j]);
-    long long km = k[0];
+    for (int j = 0; j < kChunk; ++j) split_double(x[j], xh[j], xl[j]);
+    if (track_max) {
+        long long km = dkey(x[0]);
 #pragma unroll
-    for (int j = 1; j < kChunk; ++j) km = k[j] > km ? k[j] : km;
-    const double cm = __longlong_as_double(km ^ ((km >> 63) & 0x7FFFFFFFFFFFFFFFLL));
-    if (is_neg_inf(cm)) return;
-    t.kmax = km > t.kmax ? km : t.kmax;
-    float mh, ml;
-    split_double(cm, mh, ml);
+        for (int j = 1; j < kChunk; ++j) {
+            const long long k = dkey(x[j]);
+            km = k > km ? k : km;
+        }
+        t.kmax = km > t.kmax ? km : t.kmax;
+    }
+    float mh = xh[0];
+#pragma unroll
+    for (int j = 1; j < kChunk; ++j) mh = fmaxf(mh, xh[j]);
+    if (mh > t.rh) {  // a new reference: the (last) element with the largest hi part
+        double rn = x[0];
+        float nh = xh[0], nl = xl[0];
+#pragma unroll
+        for (int j = 1; j < kChunk; ++j) {
+            const bool m = xh[j] == mh;
+            rn = m ? x[j] : rn;
+            nh = m ? xh[j] : nh;
+            nl = m ? xl[j] : nl;
+        }
+        if (t.any) {
+            const float f = exp_hl(t.rh - nh, t.rl - nl);
+            t.s1 *= f;
+            t.c1 *= f;
+            t.s2 *= f * f;
+            t.c2 *= f * f;
+        }
+        t.r = rn;
+        t.rh = nh;
+        t.rl = nl;
+        t.any = true;
+    }
+    if (!t.any) return;  // only zero weights so far
     float e[kChunk], e2[kChunk];
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) {
-        float xh, xl;
-        split_double(x[j], xh, xl);
-        e[j] = exp_hl(xh - mh, xl - ml);  // <= 1; a zero weight (-inf) splits to -1e30: 0
+        e[j] = exp_hl(xh[j] - t.rh, xl[j] - t.rl);  // ~<= 1
         e2[j] = e[j] * e[j];
     }
 #pragma unroll
@@ -138,24 +197,13 @@ __device__ __forceinline__ void add8(RefSums& t, const double (&x)[kChunk]) {
             e[j] += e[j + w];
             e2[j] += e2[j + w];
         }
-    if (!t.any) {
-        t.r = cm;
-        split_double(cm, t.rh, t.rl);
-        t.s1 = e[0];
-        t.s2 = e2[0];
-        t.any = true;
-    } else if (km > dkey(t.r)) {  // the chunk holds a new reference
-        const float f = exp_hl(t.rh - mh, t.rl - ml);
-        t.s1 = fmaf(t.s1, f, e[0]);
-        t.s2 = fmaf(t.s2, f * f, e2[0]);
-        t.r = cm;
-        t.rh = mh;
-        t.rl = ml;
-    } else {
-        const float f = exp_hl(mh - t.rh, ml - t.rl);
-        t.s1 = fmaf(e[0], f, t.s1);
-        t.s2 = fmaf(e2[0], f * f, t.s2);
-    }
+    F2Sum a{t.s1, t.c1}, b{t.s2, t.c2};
+    a.add(e[0]);
+    b.add(e2[0]);
+    t.s1 = a.s;
+    t.c1 = a.c;
+    t.s2 = b.s;
+    t.c2 = b.c;
 }
 
 // block / grid level: FP64 sums relative to a reference m
@@ -200,8 +248,8 @@ __device__ __forceinline__ Lse block_combine(const RefSums& t, long long* s_key,
     float a = 0.0f, b = 0.0f;
     if (t.any) {
         const float f = expd(t.r - R);  // <= 1
-        a = t.s1 * f;
-        b = t.s2 * f * f;
+        a = t.sum1() * f;
+        b = t.sum2() * f * f;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -316,10 +364,10 @@ __device__ __forceinline__ void block_combine2(const RefSums& c, const RefSums& 
     float a = 0.0f, b = 0.0f, ao = 0.0f;
     if (bc != LLONG_MIN && c.any) {
         const float f = expd(c.r - key_to_double(bc));  // <= 1
-        a = c.s1 * f;
-        b = c.s2 * f * f;
+        a = c.sum1() * f;
+        b = c.sum2() * f * f;
     }
-    if (has_old && bo != LLONG_MIN && o.any) ao = o.s1 * expd(o.r - key_to_double(bo));
+    if (has_old && bo != LLONG_MIN && o.any) ao = o.sum1() * expd(o.r - key_to_double(bo));
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         a += __shfl_xor_sync(0xFFFFFFFFu, a, off);
@@ -347,33 +395,6 @@ __device__ __forceinline__ float d2f_exact(double d) {
                        (lo >> 29);
     return e == 0u ? 0.0f : __uint_as_float(f);
 }
-
-// FP32 sum with its rounding error carried (Knuth's two-sum): the running
-// error stays below 2^-24 of the sum's magnitude times a few, without the
-// long-latency FP64 pipe.
-struct F2Sum {
-    float s = 0.0f, c = 0.0f;
-    __device__ __forceinline__ void add(float x) {
-        const float t = s + x;
-        const float bb = t - s;
-        c += (s - (t - bb)) + (x - bb);
-        s = t;
-    }
-    __device__ __forceinline__ void add(const F2Sum& o) {
-        add(o.s);
-        c += o.c;
-    }
-    __device__ __forceinline__ void warp_sum() {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            F2Sum o;
-            o.s = __shfl_xor_sync(0xFFFFFFFFu, s, off);
-            o.c = __shfl_xor_sync(0xFFFFFFFFu, c, off);
-            add(o);
-        }
-    }
-    __device__ __forceinline__ double value() const { return f2d_bits(s) + f2d_bits(c); }
-};
 
 // The last block's three passes over the partials (new sums, old sums,
 // maximum) in one, with two barriers: the largest block references and the

@@ -71,12 +71,12 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
                 nan_seen |= disnan(n[j]);  // a NaN in x or v makes n NaN
             }
             store8(lw + ch * kChunk, n);
-            add8(old, x);
-            add8(cur, n);
+            add8(old, x, false);
+            add8(cur, n, true);
         } else {
 #pragma unroll
             for (int j = 0; j < kChunk; ++j) nan_seen |= disnan(x[j]);
-            add8(cur, x);
+            add8(cur, x, true);
         }
     }
     for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {  // tail / unaligned
