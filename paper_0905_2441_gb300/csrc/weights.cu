@@ -19,6 +19,7 @@
 #include "device.cuh"
 #include "resample.cuh"
 #include "reweight.cuh"
+#include "bulk.cuh"
 
 using namespace smc_host;
 
@@ -129,6 +130,90 @@ __global__ void __launch_bounds__(256) k_reweight_normalize(const double* __rest
         store8(W + ch * kChunk, w);
     }
     for (int64_t i = nchunk * kChunk + t0; i < M; i += G) {
+        float xh, xl;
+        split_double(lw[i], xh, xl);
+        W[i] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
+    }
+}
+
+// k_reweight_normalize with the tiles moved by bulk copies: whole tiles of
+// kNrmTile log-weights are loaded into a ring of kNrmStages shared-memory
+// buffers (one cp.async.bulk each, completion on an mbarrier), turned into
+// weights in shared memory and stored back by one bulk copy per tile, so a
+// tile costs two memory instructions instead of 2 x 4 per thread per 8
+// elements (the per-thread form is throttled by the load/store queues).
+// Tiles are taken in descending order (the reduction wrote the log-weights
+// ascending: the most recent, still in L2, come first); the elements past
+// the last whole tile take the per-thread form.  Same values as
+// k_reweight_normalize.
+constexpr int kNrmThreads = 256;
+constexpr int kNrmTile = 2048;  // doubles: 16 KB
+constexpr int kNrmStages = 3;
+constexpr size_t kNrmSmem = (size_t)(kNrmStages + 2) * kNrmTile * sizeof(double) + 64;
+__global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
+    const double* __restrict__ lw, int64_t M, const double* __restrict__ fin,
+    double* __restrict__ W, uint32_t* status, uint32_t limit) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
+    if (fin[3] == 0.0) return;
+    extern __shared__ __align__(128) double nsm[];
+    double* in = nsm;                               // [kNrmStages][kNrmTile]
+    double* out = nsm + kNrmStages * kNrmTile;      // [2][kNrmTile]
+    uint64_t* full = reinterpret_cast<uint64_t*>(out + 2 * kNrmTile);
+    float mh, ml;
+    split_double(fin[0], mh, ml);
+    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
+    const int tid = threadIdx.x;
+    const int64_t ntiles = M / kNrmTile;
+    const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t k) { return ntiles - 1 - (blockIdx.x + k * gridDim.x); };
+    constexpr uint32_t kBytes = kNrmTile * sizeof(double);
+    if (tid == 0) {
+        for (int st = 0; st < kNrmStages; ++st) mb_init(&full[st], 1);
+        mb_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < kNrmStages && k < nmine; ++k) {
+            mb_expect_tx(&full[k], kBytes);
+            bulk_load(in + k * kNrmTile, lw + tile_of(k) * kNrmTile, kBytes, &full[k]);
+        }
+    int st = 0;
+    uint32_t round = 0;
+    for (int64_t k = 0; k < nmine; ++k) {
+        const int ob = (int)(k & 1);
+        mb_wait(&full[st], round & 1, status, limit);
+        if (tid == 0 && k >= 2) bulk_wait_read<1>();  // out[ob]'s last store has read it
+        __syncthreads();
+        const double2* src = reinterpret_cast<const double2*>(in + st * kNrmTile);
+        double2* dst = reinterpret_cast<double2*>(out + ob * kNrmTile);
+#pragma unroll
+        for (int j = 0; j < kNrmTile / 2 / kNrmThreads; ++j) {
+            const double2 x = src[tid + j * kNrmThreads];
+            float h0, l0, h1, l1;
+            split_double(x.x, h0, l0);
+            split_double(x.y, h1, l1);
+            dst[tid + j * kNrmThreads] = make_double2(f2d_bits(exp_hl(h0 - mh, l0 - ml) * inv),
+                                                      f2d_bits(exp_hl(h1 - mh, l1 - ml) * inv));
+        }
+        fence_async_shared();
+        __syncthreads();
+        if (tid == 0) {
+            bulk_store(W + tile_of(k) * kNrmTile, out + ob * kNrmTile, kBytes);
+            bulk_commit();
+            if (k + kNrmStages < nmine) {  // the ring slot just read takes tile k + stages
+                fence_async_shared();
+                mb_expect_tx(&full[st], kBytes);
+                bulk_load(in + st * kNrmTile, lw + tile_of(k + kNrmStages) * kNrmTile, kBytes,
+                          &full[st]);
+            }
+        }
+        if (++st == kNrmStages) { st = 0; ++round; }
+    }
+    if (tid == 0) bulk_wait_all();
+    // the elements past the last whole tile
+    const int64_t G = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = ntiles * kNrmTile + (int64_t)blockIdx.x * blockDim.x + tid; i < M; i += G) {
         float xh, xl;
         split_double(lw[i], xh, xl);
         W[i] = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
@@ -249,6 +334,8 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
 // Up to cap * 256 elements: one element per thread (short dependent chains:
 // the reduction is latency-bound there); beyond, chunks of 8 per thread,
 // with at most as many blocks as are resident at once (two per SM).
+static bool aligned16h(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
 static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
     int64_t cap = (int64_t)ctx->num_sms * 2;
     if (cap > kMaxPartialBlocks - 2) cap = kMaxPartialBlocks - 2;
@@ -261,6 +348,10 @@ static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
 
 }  // namespace smc_host
 
+smc_status reweight_reduce_launch(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
+                                  int64_t M, double* scalars_out, int32_t* resample_flag,
+                                  double ess_frac, cudaStream_t s);
+
 extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double dbeta,
                                    double* logw, int64_t M, double* W_out, double* scalars_out,
                                    int32_t* resample_flag_out, double ess_frac, void* stream) {
@@ -268,20 +359,32 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
-    int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
-    int blocks = reduce_blocks(ctx, M);
     const int final_slot = kMaxPartialBlocks - 1;
-    st = launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw, M,
-                    has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET, scalars_out,
-                    resample_flag_out, ess_frac, final_slot, ctx->d_status);
+    st = reweight_reduce_launch(ctx, loglik, dbeta, logw, M, scalars_out, resample_flag_out,
+                                ess_frac, s);
     if (st != SMC_OK) return st;
     if (W_out) {
-        int nb = (int)((M + 256 * 8 - 1) / (256 * 8));
-        int cap = ctx->num_sms * 8;
-        if (nb > cap) nb = cap;
-        st = launch_pdl(smc::k_reweight_normalize, dim3(nb), dim3(256), 0, s,
-                        (const double*)logw, M,
-                        (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out);
+        const double* fin = ctx->d_partials + (size_t)final_slot * 8;
+        if (aligned16h(logw) && aligned16h(W_out) && M >= (int64_t)smc::kNrmTile * ctx->num_sms) {
+            // bulk tiles: two 80 KB blocks per SM
+            static bool attr_set[64] = {};
+            const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+            if (!attr_set[dev]) {
+                SMC_CUDA(cudaFuncSetAttribute(smc::k_reweight_normalize_bulk,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)smc::kNrmSmem));
+                attr_set[dev] = true;
+            }
+            st = launch_pdl(smc::k_reweight_normalize_bulk, dim3((unsigned)ctx->num_sms * 2),
+                            dim3(smc::kNrmThreads), smc::kNrmSmem, s, (const double*)logw, M, fin,
+                            W_out, ctx->d_status, ctx->wait_limit);
+        } else {
+            int nb = (int)((M + 256 * 8 - 1) / (256 * 8));
+            int cap = ctx->num_sms * 8;
+            if (nb > cap) nb = cap;
+            st = launch_pdl(smc::k_reweight_normalize, dim3(nb), dim3(256), 0, s,
+                            (const double*)logw, M, fin, W_out);
+        }
         if (st != SMC_OK) return st;
     }
     return SMC_OK;
