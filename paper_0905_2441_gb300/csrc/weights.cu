@@ -321,6 +321,115 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __
     }
 }
 
+// k_normalize_tiles with the whole tiles moved by bulk copies (a ring of
+// kNtStages 16 KB slots for the log-weights, two for the weights; thread t
+// takes elements t + 256 j), tiles descending as there; the partial last
+// tile, if any, goes to block 0 in the per-thread form first.  Same weights
+// and tile sums.
+constexpr int kNtStages = 3;
+constexpr size_t kNtSmem = (size_t)(kNtStages + 2) * kRsTile * sizeof(double) + 64;
+__global__ void __launch_bounds__(kRsThreads) k_normalize_tiles_bulk(
+    const double* __restrict__ lw, int64_t M, const double* __restrict__ fin,
+    double* __restrict__ W, RsScratch sc, uint32_t* status, uint32_t limit) {
+    grid_dep_wait();  // the previous kernel's writes are visible from here on
+    grid_dep_launch();
+    extern __shared__ __align__(128) double ntm[];
+    double* in = ntm;                            // [kNtStages][kRsTile]
+    double* out = ntm + kNtStages * kRsTile;     // [2][kRsTile]
+    uint64_t* full = reinterpret_cast<uint64_t*>(out + 2 * kRsTile);
+    __shared__ unsigned long long sh[2][kRsThreads / 32];
+    const int tid = threadIdx.x, wid = tid >> 5;
+    const int64_t nfull = M / kRsTile;
+    if (fin[3] == 0.0) {  // no valid weights: zero tile sums, W untouched
+        for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < rs_tiles(M);
+             t += (int64_t)gridDim.x * blockDim.x)
+            sc.tile_sum[t] = 0ull;
+        return;
+    }
+    float mh, ml;
+    split_double(fin[0], mh, ml);
+    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
+    int buf = 0;
+    auto tile_total = [&](unsigned long long acc) {  // valid in thread 0 after the barrier
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if ((tid & 31) == 0) sh[buf][wid] = acc;
+        __syncthreads();
+        unsigned long long ts = 0;
+        if (tid == 0)
+#pragma unroll
+            for (int w = 0; w < kRsThreads / 32; ++w) ts += sh[buf][w];
+        buf ^= 1;
+        return ts;
+    };
+    if (blockIdx.x == 0 && nfull * kRsTile < M) {  // the partial last tile
+        double x[kRsIpt];
+        load_tile_raw_cs(lw, M, nfull, x);
+        const int64_t g0 = nfull * kRsTile + (int64_t)tid * kRsIpt;
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) {
+            if (g0 + j < M) {
+                float xh, xl;
+                split_double(x[j], xh, xl);
+                const double w = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
+                W[g0 + j] = w;
+                acc += q_fast(w);
+            }
+        }
+        const unsigned long long ts = tile_total(acc);
+        if (tid == 0) sc.tile_sum[nfull] = ts;
+    }
+    const int64_t nmine = nfull > blockIdx.x ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t k) { return nfull - 1 - (blockIdx.x + k * gridDim.x); };
+    constexpr uint32_t kBytes = kRsTile * sizeof(double);
+    if (tid == 0) {
+        for (int st = 0; st < kNtStages; ++st) mb_init(&full[st], 1);
+        mb_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < kNtStages && k < nmine; ++k) {
+            mb_expect_tx(&full[k], kBytes);
+            bulk_load(in + k * kRsTile, lw + tile_of(k) * kRsTile, kBytes, &full[k]);
+        }
+    int st = 0;
+    uint32_t round = 0;
+    for (int64_t k = 0; k < nmine; ++k) {
+        const int ob = (int)(k & 1);
+        mb_wait(&full[st], round & 1, status, limit);
+        if (tid == 0 && k >= 2) bulk_wait_read<1>();  // out[ob]'s last store has read it
+        __syncthreads();
+        const double* src = in + st * kRsTile;
+        double* dst = out + ob * kRsTile;
+        unsigned long long acc = 0;
+#pragma unroll
+        for (int j = 0; j < kRsIpt; ++j) {
+            float xh, xl;
+            split_double(src[tid + kRsThreads * j], xh, xl);
+            const double w = f2d_bits(exp_hl(xh - mh, xl - ml) * inv);
+            dst[tid + kRsThreads * j] = w;
+            acc += q_fast(w);  // w in [0, 1]
+        }
+        fence_async_shared();
+        const unsigned long long ts = tile_total(acc);  // its barrier: slot st read, out[ob] written
+        if (tid == 0) {
+            const int64_t t = tile_of(k);
+            sc.tile_sum[t] = ts;
+            bulk_store(W + t * kRsTile, dst, kBytes);
+            bulk_commit();
+            if (k + kNtStages < nmine) {
+                fence_async_shared();
+                mb_expect_tx(&full[st], kBytes);
+                bulk_load(in + st * kRsTile, lw + tile_of(k + kNtStages) * kRsTile, kBytes,
+                          &full[st]);
+            }
+        }
+        if (++st == kNtStages) { st = 0; ++round; }
+    }
+    if (tid == 0) bulk_wait_all();
+}
+
 }  // namespace smc
 
 namespace smc_host {
@@ -403,11 +512,27 @@ smc_status normalize_resample_launch(smc_ctx* ctx, double* logw, int64_t M, doub
     const smc::RsScratch sc =
         resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
     const int final_slot = kMaxPartialBlocks - 1;
-    int64_t nb = smc::rs_tiles(M);
-    if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
-    st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
-                    (const double*)logw, M,
-                    (const double*)(ctx->d_partials + (size_t)final_slot * 8), W_out, sc);
+    const double* fin = ctx->d_partials + (size_t)final_slot * 8;
+    if (aligned16h(logw) && aligned16h(W_out) &&
+        M >= (int64_t)smc::kRsTile * ctx->num_sms * 2) {
+        // whole tiles by bulk copies: two 80 KB blocks per SM
+        static bool attr_set[64] = {};
+        const int dev = ctx->device >= 0 && ctx->device < 64 ? ctx->device : 0;
+        if (!attr_set[dev]) {
+            SMC_CUDA(cudaFuncSetAttribute(smc::k_normalize_tiles_bulk,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)smc::kNtSmem));
+            attr_set[dev] = true;
+        }
+        st = launch_pdl(smc::k_normalize_tiles_bulk, dim3((unsigned)ctx->num_sms * 2),
+                        dim3(smc::kRsThreads), smc::kNtSmem, s, (const double*)logw, M, fin,
+                        W_out, sc, ctx->d_status, ctx->wait_limit);
+    } else {
+        int64_t nb = smc::rs_tiles(M);
+        if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
+        st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
+                        (const double*)logw, M, fin, W_out, sc);
+    }
     if (st != SMC_OK) return st;
     return resample_launch(ctx->num_sms, W_out, M, seed, step, ancestors_out, counts_out,
                            resample_flag, logw, sc, ctx->d_status, s, true);
