@@ -481,8 +481,18 @@ static __global__ void __launch_bounds__(kRsFinThreads) k_resample_finalize(
         ovf |= c < run;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            if (i0 + j < ntiles) sc.tile_sum[i0 + j] = c;
-            c += v[j];
+            const unsigned long long x = v[j];
+            v[j] = c;
+            c += x;
+        }
+        if (i0 + 8 <= ntiles && (reinterpret_cast<uintptr_t>(sc.tile_sum) & 15u) == 0) {
+            ulonglong2* p = reinterpret_cast<ulonglong2*>(sc.tile_sum + i0);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) p[j] = make_ulonglong2(v[2 * j], v[2 * j + 1]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (i0 + j < ntiles) sc.tile_sum[i0 + j] = v[j];
         }
         const unsigned long long nrun = run + s_tot;
         ovf |= nrun < run;
