@@ -319,7 +319,7 @@ def bench_popmcmc(args, torch, dist):
     M, N = smp.M, w.N
     # launch shape: the binned sweep (data in shared memory) has one shape;
     # the lanes-per-chain sweep (longer data) is autotuned
-    binned = 1 <= N <= 4096 and w.K <= 16
+    binned = 512 <= N <= 4096 and w.K <= 16
     if binned:
         lanes, threads, tune = 0, 512, {"binned": "one 512-thread CTA per SM, chain groups of 32"}
     else:
@@ -1162,6 +1162,9 @@ def bench_diag(args, torch, dist):
     import synth
     import oracle
     w = synth.DIAG32
+    if args.diag_shape == "d64k32":  # the widest shape the tensor-core path takes
+        w = synth.DiagWorkload(name="diag-d64-K32-N65536-M2048", d=64, K=32, N=65536, M=2048,
+                               sigma=1.3, truth_seed=64, data_seed=65, particle_seed=66)
     truth = synth.diag_truth(w.K, w.d, seed=w.truth_seed)
     Yh = synth.diag_data(w.N, truth, seed=w.data_seed)
     thh = synth.diag_particles(w.M, truth, seed=w.particle_seed + dist.rank)
@@ -1206,14 +1209,15 @@ def bench_diag(args, torch, dist):
     t_fp = float(np.mean([e[0].elapsed_time(e[1]) / 1e3 for e in recf]))
     # rooflines: issued bf16 MMA flops (3 split products) and MUFU ops
     t_call = float(per.mean())
-    kp = 16
+    kp = max(4, 1 << (w.K - 1).bit_length())
     flops = 3 * 2.0 * (-(-w.N // 128) * 128) * (w.M * kp) * w.d
     mufu = float(w.N) * w.M * (kp + 1)
     pk = measured_peaks()
     ex2_rate, _ = measure_peak(P, 0)
     tens = {"bound": "tensor", "achieved": flops / t_call / 1e12, "peak": pk["bf16_tflops"],
             "unit": "TFLOP/s", "frac": flops / t_call / 1e12 / pk["bf16_tflops"],
-            "traffic": profile_traffic("k_dtc_main"), "kernel": "k_dtc_main<16> (+ prep, combine)",
+            "traffic": profile_traffic("k_dtc_main") if w.d == 32 else None,
+            "kernel": f"k_dtc_main<{kp}> (+ prep, combine)",
             "flops_per_call": flops,
             "peak_source": "MEASURED_PEAKS.json bf16_tflops, burst (of measured)"}
     mu = {"achieved": mufu / t_call / 1e9, "peak": ex2_rate / 1e9, "unit": "Gop/s",
@@ -1563,6 +1567,8 @@ def main():
                                                               "diag", "fsv", "tables", "mala",
                                                               "is", "mrg", "peaks"])
     ap.add_argument("--graph-sweeps", type=int, default=1000)
+    ap.add_argument("--diag-shape", default="d32k16", choices=["d32k16", "d64k32"],
+                    help="--workload diag: d = 32 / K = 16 (default) or d = 64 / K = 32")
     ap.add_argument("--retune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-secondary", action="store_true", help="skip the sampler / filter lines")

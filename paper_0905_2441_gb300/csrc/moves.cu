@@ -472,7 +472,7 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
 }
 
 // ------------------------------------------------------------------ binned population sweep
-// The sweep for data sets held whole in shared memory (1 <= N <= 4096,
+// The sweep for data sets held whole in shared memory (512 <= N <= 4096,
 // K <= 16), with the data sorted into bins once per sweep by every CTA
 // (binned.cuh).  A warp's 32 lanes take 32 consecutive chains (a chain
 // group) over the same slots of the sorted list, so bins, loop counts and
@@ -875,7 +875,7 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
                              uint64_t sweep, uint64_t* stats, const smc::Gmm1dArgs& P, int L,
                              int Kr, bool inline_ex) {
     if constexpr (K <= 16) {
-        if (N >= 1 && N <= smc::kBinnedMaxN)
+        if (N >= smc::kBinnedMinN && N <= smc::kBinnedMaxN)
             return launch_pop_binned<K>(ctx, s, y, N, th, l, Mt, beta, off, n_pops, scale, seed,
                                         sweep, stats, P, Kr, inline_ex);
     }

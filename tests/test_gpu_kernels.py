@@ -469,7 +469,7 @@ def test_popmcmc_sweep_parity(smc, N):
     assert s[2] == rst[2] and abs(int(s[0]) - int(rst[0])) <= 2 and abs(int(s[1]) - int(rst[1])) <= 2
 
 
-@pytest.mark.parametrize("N", [300, 5000])  # binned sweep (shape fixed) / lanes-per-chain sweep
+@pytest.mark.parametrize("N", [600, 5000])  # binned sweep (shape fixed) / lanes-per-chain sweep
 @pytest.mark.parametrize("lanes,threads", [(1, 256), (8, 128), (16, 128), (32, 256)])
 def test_popmcmc_sweep_launch_shapes(smc, lanes, threads, N):
     """Every sweep shape the autotuner may choose gives the oracle's sweep."""
