@@ -319,11 +319,9 @@ def bench_popmcmc(args, torch, dist):
     M, N = smp.M, w.N
     # launch shape: the binned sweep (data in shared memory) has one shape;
     # the lanes-per-chain sweep (longer data) is autotuned
-    binned = 512 <= N <= 4096 and w.K <= 16
-    if binned:
-        lanes, threads, tune = 0, 512, {"binned": "one 512-thread CTA per SM, chain groups of 32"}
-    else:
-        lanes, threads, tune = autotune.tune_popmcmc(ctx, smp, use_cache=not args.retune)
+    binned = (autotune.BINNED_MIN_N <= N <= autotune.BINNED_MAX_N and
+              w.K <= autotune.BINNED_MAX_K)
+    lanes, threads, tune = autotune.tune_popmcmc(ctx, smp, use_cache=not args.retune)
     smp.theta.copy_(torch.from_numpy(th0).cuda())
     P.loglik_batch(ctx, model, smp.y, smp.theta, out=smp.ll)
     ctx.check()

@@ -103,9 +103,20 @@ def tune_loglik(ctx, model, y, theta, **kw):
                 lambda: api.loglik_batch(ctx, model, y, theta, out=out), **kw)
 
 
+# data counts and components for which smc_popmcmc_sweep takes the binned
+# sweep (data sorted into bins in shared memory), whose launch shape is fixed
+BINNED_MIN_N, BINNED_MAX_N, BINNED_MAX_K = 512, 4096, 16
+
+
 def tune_popmcmc(ctx, sampler, **kw):
     """Chains-per-block / lanes for the persistent sweep of a PopulationMCMC.
-    Candidate sweeps advance the chains; the caller re-initialises if needed."""
+    Candidate sweeps advance the chains; the caller re-initialises if needed.
+    Where the library takes the binned sweep (one 512-thread block per SM,
+    chain groups of 32: no launch parameter to choose) nothing is timed and
+    (0, 512, entry) is returned."""
+    n, k = sampler.y.numel(), sampler.model.K
+    if BINNED_MIN_N <= n <= BINNED_MAX_N and k <= BINNED_MAX_K:
+        return 0, 512, {"binned": "one 512-thread CTA per SM, chain groups of 32"}
     s = [10_000]
 
     def fn():
