@@ -8,6 +8,7 @@
 
 #include "ctx.hpp"
 #include "device.cuh"
+#include "reweight.cuh"
 
 using namespace smc_host;
 
@@ -244,10 +245,11 @@ extern "C" smc_status pf_step(smc_ctx* ctx, const smc_pf_model* model, const flo
 // resampling half of smc_reweight_resample (weights.cu)
 smc_status reweight_reduce_launch(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
                                   int64_t M, double* scalars_out, int32_t* resample_flag,
-                                  double ess_frac, cudaStream_t s);
-smc_status normalize_resample_launch(smc_ctx* ctx, double* logw, int64_t M, double* W_out,
-                                     int32_t* resample_flag, uint64_t seed, uint64_t step,
-                                     int32_t* ancestors_out, int32_t* counts_out, cudaStream_t s);
+                                  double ess_frac, cudaStream_t s, smc::RwArgs* defer_to);
+smc_status normalize_resample_launch(smc_ctx* ctx, const smc::RwArgs& rw, double* logw,
+                                     int64_t M, double* W_out, int32_t* resample_flag,
+                                     uint64_t seed, uint64_t step, int32_t* ancestors_out,
+                                     int32_t* counts_out, cudaStream_t s);
 
 extern "C" smc_status smc_pf_filter_step(smc_ctx* ctx, const smc_pf_model* model,
                                          const float* y_t, const float* x_in, int32_t* anc,
@@ -262,9 +264,10 @@ extern "C" smc_status smc_pf_filter_step(smc_ctx* ctx, const smc_pf_model* model
     smc_status st = pf_step(ctx, model, y_t, x_in, anc, x_out, logg_out, M, seed, t, stream);
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
+    smc::RwArgs rw;
     st = reweight_reduce_launch(ctx, logg_out, 1.0, logw, M, scalars_out, resample_flag_out,
-                                ess_frac, s);
+                                ess_frac, s, &rw);
     if (st != SMC_OK) return st;
-    return normalize_resample_launch(ctx, logw, M, W_out, resample_flag_out, seed, t, anc,
+    return normalize_resample_launch(ctx, rw, logw, M, W_out, resample_flag_out, seed, t, anc,
                                      counts_out, s);
 }

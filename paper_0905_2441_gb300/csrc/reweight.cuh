@@ -322,21 +322,6 @@ __device__ __forceinline__ Lse combine_partials(const double* partials, int nblo
     return out;
 }
 
-__device__ __forceinline__ double max_partials(const double* partials, int nblocks, long long* sk) {
-    long long k = LLONG_MIN;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double v = __ldcg(partials + (size_t)b * 8 + 5);
-        if (!is_neg_inf(v)) { const long long kk = dkey(v); k = kk > k ? kk : k; }
-    }
-    k = warp_max_key(k);
-    if ((threadIdx.x & 31) == 0) sk[threadIdx.x >> 5] = k;
-    __syncthreads();
-    long long m = LLONG_MIN;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = sk[i] > m ? sk[i] : m;
-    __syncthreads();
-    return m == LLONG_MIN ? kNegInf : key_to_double(m);
-}
-
 __device__ __forceinline__ double ln_sum(double s) {
     return (double)(lg2((float)s) * 0.69314718055994531f);
 }
@@ -396,95 +381,172 @@ __device__ __forceinline__ float d2f_exact(double d) {
     return e == 0u ? 0.0f : __uint_as_float(f);
 }
 
-// The last block's three passes over the partials (new sums, old sums,
-// maximum) in one, with two barriers: the largest block references and the
-// maximum by integer keys, then every partial's sums scaled to the common
-// reference by one FP32 exponential and added as FP32 two-sums (the block
-// sums are FP32 values: only the one final addition of each total runs on
-// the FP64 pipe).  Results valid in thread 0.
-__device__ __forceinline__ void combine_partials3(const double* partials, int nblocks,
-                                                  bool has_old, long long* s_key, double* s_d,
-                                                  Lse* outc, Lse* outo, double* max_out) {
+// The final combination of a reweighting reduction: the per-block partials
+// {ref, s1, s2, ref_old, s_old, max} of at most kRwMaxParts blocks are read
+// once into registers (two per thread at 256 threads), the common
+// references and the maximum are found by integer keys, every partial's sums
+// are scaled to its reference by one FP32 exponential and added as FP32
+// two-sums (the block sums are FP32 values: only the final addition of each
+// total runs on the FP64 pipe), then the sums are expressed relative to the
+// true maximum.  Every thread of the calling block calls it and gets the
+// normalisation constants; with `write` (one block) the final slot {max, S1,
+// S2, valid, LSE, 1/S1 (float)}, the scalars {log Z increment, ESS, max,
+// LSE} and the resampling flag are written too.  It runs either in the
+// reduction's last block or, redundantly, in every block of the kernel that
+// consumes the weights, whose first tile loads are then already in flight.
+constexpr int kRwMaxParts = 512;
+
+struct RwFinal {
+    double m;     // maximum log-weight
+    float inv;    // 1 / sum exp(logw - m), FP32
+    bool valid;   // some weight positive, no NaN
+};
+
+__device__ __forceinline__ RwFinal reweight_combine(double* partials,
+                                                    int nblocks, int has_inc, int64_t M,
+                                                    bool write, double* __restrict__ scalars,
+                                                    int32_t* __restrict__ flag, double ess_frac,
+                                                    int final_slot, uint32_t* status) {
+    __shared__ long long s_key[96];
+    __shared__ float s_f[192];
+    __shared__ double s_m;
+    __shared__ float s_inv;
+    __shared__ int s_valid;
+    const bool has_old = has_inc != 0;
+    const int tid = threadIdx.x, w = tid >> 5, nw = blockDim.x >> 5;
+    double rc[2], s1[2], s2[2], ro[2], so[2];
     long long kc = LLONG_MIN, ko = LLONG_MIN, km = LLONG_MIN;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double* P = partials + (size_t)b * 8;
-        const double rc = __ldcg(P), ro = __ldcg(P + 3), mx = __ldcg(P + 5);
-        if (!is_neg_inf(rc)) { const long long k = dkey(rc); kc = k > kc ? k : kc; }
-        if (has_old && !is_neg_inf(ro)) { const long long k = dkey(ro); ko = k > ko ? k : ko; }
-        if (!is_neg_inf(mx)) { const long long k = dkey(mx); km = k > km ? k : km; }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int b = tid + p * (int)blockDim.x;
+        rc[p] = kNegInf; ro[p] = kNegInf;
+        s1[p] = 0.0; s2[p] = 0.0; so[p] = 0.0;
+        if (b < nblocks) {
+            const double2* P = reinterpret_cast<const double2*>(partials + (size_t)b * 8);
+            const double2 u = __ldcg(P), v = __ldcg(P + 1), x = __ldcg(P + 2);
+            rc[p] = u.x; s1[p] = u.y; s2[p] = v.x; ro[p] = v.y; so[p] = x.x;
+            if (!is_neg_inf(u.x)) { const long long k = dkey(u.x); kc = k > kc ? k : kc; }
+            if (has_old && !is_neg_inf(v.y)) { const long long k = dkey(v.y); ko = k > ko ? k : ko; }
+            if (!is_neg_inf(x.y)) { const long long k = dkey(x.y); km = k > km ? k : km; }
+        }
     }
     kc = warp_max_key(kc);
     ko = warp_max_key(ko);
     km = warp_max_key(km);
-    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if ((threadIdx.x & 31) == 0) { s_key[w] = kc; s_key[16 + w] = ko; s_key[32 + w] = km; }
+    if ((tid & 31) == 0) { s_key[w] = kc; s_key[32 + w] = ko; s_key[64 + w] = km; }
     __syncthreads();
     long long bc = LLONG_MIN, bo = LLONG_MIN, bm = LLONG_MIN;
     for (int i = 0; i < nw; ++i) {
         bc = s_key[i] > bc ? s_key[i] : bc;
-        bo = s_key[16 + i] > bo ? s_key[16 + i] : bo;
-        bm = s_key[32 + i] > bm ? s_key[32 + i] : bm;
+        bo = s_key[32 + i] > bo ? s_key[32 + i] : bo;
+        bm = s_key[64 + i] > bm ? s_key[64 + i] : bm;
     }
-    *max_out = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
     float Rch = 0.0f, Rcl = 0.0f, Roh = 0.0f, Rol = 0.0f;
     if (bc != LLONG_MIN) split_double(key_to_double(bc), Rch, Rcl);
     if (bo != LLONG_MIN) split_double(key_to_double(bo), Roh, Rol);
     F2Sum a, bs, ao;
-    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
-        const double* P = partials + (size_t)b * 8;
-        const double rc = __ldcg(P);
-        if (bc != LLONG_MIN && !is_neg_inf(rc)) {
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        if (bc != LLONG_MIN && !is_neg_inf(rc[p])) {
             float h, l;
-            split_double(rc, h, l);
+            split_double(rc[p], h, l);
             const float f = exp_hilo(h - Rch, l - Rcl);  // <= 1
-            a.add(d2f_exact(__ldcg(P + 1)) * f);
-            bs.add(d2f_exact(__ldcg(P + 2)) * (f * f));
+            a.add(d2f_exact(s1[p]) * f);
+            bs.add(d2f_exact(s2[p]) * (f * f));
         }
-        const double ro = __ldcg(P + 3);
-        if (has_old && bo != LLONG_MIN && !is_neg_inf(ro)) {
+        if (has_old && bo != LLONG_MIN && !is_neg_inf(ro[p])) {
             float h, l;
-            split_double(ro, h, l);
-            ao.add(d2f_exact(__ldcg(P + 4)) * exp_hilo(h - Roh, l - Rol));
+            split_double(ro[p], h, l);
+            ao.add(d2f_exact(so[p]) * exp_hilo(h - Roh, l - Rol));
         }
     }
     a.warp_sum();
     bs.warp_sum();
     ao.warp_sum();
-    float* s_f = reinterpret_cast<float*>(s_d);
-    if ((threadIdx.x & 31) == 0) {
+    if ((tid & 31) == 0) {
         s_f[2 * w] = a.s; s_f[2 * w + 1] = a.c;
-        s_f[32 + 2 * w] = bs.s; s_f[32 + 2 * w + 1] = bs.c;
-        s_f[64 + 2 * w] = ao.s; s_f[64 + 2 * w + 1] = ao.c;
+        s_f[64 + 2 * w] = bs.s; s_f[64 + 2 * w + 1] = bs.c;
+        s_f[128 + 2 * w] = ao.s; s_f[128 + 2 * w + 1] = ao.c;
     }
     __syncthreads();
-    *outc = Lse{kNegInf, 0.0, 0.0};
-    *outo = Lse{kNegInf, 0.0, 0.0};
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         F2Sum A, B, AO;
         for (int i = 0; i < nw; ++i) {
             A.add(F2Sum{s_f[2 * i], s_f[2 * i + 1]});
-            B.add(F2Sum{s_f[32 + 2 * i], s_f[32 + 2 * i + 1]});
-            AO.add(F2Sum{s_f[64 + 2 * i], s_f[64 + 2 * i + 1]});
+            B.add(F2Sum{s_f[64 + 2 * i], s_f[64 + 2 * i + 1]});
+            AO.add(F2Sum{s_f[128 + 2 * i], s_f[128 + 2 * i + 1]});
         }
-        if (bc != LLONG_MIN) *outc = Lse{key_to_double(bc), A.value(), B.value()};
-        if (bo != LLONG_MIN) *outo = Lse{key_to_double(bo), AO.value(), 0.0};
+        Lse tc{kNegInf, 0.0, 0.0}, to{kNegInf, 0.0, 0.0};
+        if (bc != LLONG_MIN) tc = Lse{key_to_double(bc), A.value(), B.value()};
+        if (bo != LLONG_MIN) to = Lse{key_to_double(bo), AO.value(), 0.0};
+        const double mx = bm == LLONG_MIN ? kNegInf : key_to_double(bm);
+        double* F = partials + (size_t)final_slot * 8;
+        const bool valid = !is_neg_inf(tc.m) && !disnan(tc.m);
+        float inv = 0.0f;
+        if (valid) {  // express the sums relative to the true maximum
+            const double f = f2d_bits(expd(tc.m - mx));
+            tc = Lse{mx, tc.s1 * f, tc.s2 * f * f};
+            const double lse = tc.m + ln_sum(tc.s1);
+            const float s1f = (float)tc.s1;
+            inv = 1.0f / s1f;
+            if (write) {
+                const double ess = f2d_bits(s1f * (s1f / (float)tc.s2));  // FP32 division
+                F[0] = tc.m; F[1] = tc.s1; F[2] = tc.s2; F[3] = 1.0; F[4] = lse;
+                reinterpret_cast<float*>(F + 5)[0] = inv;
+                if (scalars) {
+                    double inc = 0.0;
+                    if (has_inc) inc = lse - (to.m + ln_sum(to.s1));
+                    scalars[0] = inc;
+                    scalars[1] = ess;
+                    scalars[2] = tc.m;
+                    scalars[3] = lse;
+                }
+                if (flag) *flag = (ess < ess_frac * (double)M) ? 1 : 0;
+            }
+        } else if (write) {
+            if (!disnan(tc.m)) raise_status(status, ST_ZERO_WEIGHT);
+            F[3] = 0.0;
+            if (flag) *flag = 0;
+        }
+        s_m = tc.m;
+        s_inv = inv;
+        s_valid = valid ? 1 : 0;
     }
+    __syncthreads();
+    return RwFinal{s_m, s_inv, s_valid != 0};
 }
 
-// The end of a reweighting reduction: the block's sums (thread sums cur of
+// What a kernel that consumes a deferred reduction's weights needs to
+// combine its partials (reweight_combine); block 0 writes the results.
+struct RwArgs {
+    double* partials;
+    int nparts;          // blocks of the reduction
+    int has_inc;
+    int64_t M;
+    double* scalars;     // may be null
+    int32_t* flag;       // may be null
+    double ess_frac;
+    int final_slot;
+};
+
+__device__ __forceinline__ RwFinal rw_final(const RwArgs& a, uint32_t* status) {
+    return reweight_combine(a.partials, a.nparts, a.has_inc, a.M, blockIdx.x == 0, a.scalars,
+                            a.flag, a.ess_frac, a.final_slot, status);
+}
+
+// The end of a reweighting reduction's block: its sums (thread sums cur of
 // the new log-weights and old of the old ones) go to the block's partial
-// slot; the last block to finish combines every partial and writes the
-// final slot {max, S1, S2, valid, LSE, 1/S1 (float)} and the scalars
-// {log Z increment, ESS, max, LSE} and the resampling flag.  Every thread
-// of the block calls it once, after its element loop.
+// slot.  Unless `defer` (the kernel that consumes the weights combines the
+// partials itself), the last block to finish runs reweight_combine and
+// writes the final slot, the scalars and the flag.  Every thread of the
+// block calls it once, after its element loop.
 __device__ __forceinline__ void reweight_finish(const RefSums& cur, const RefSums& old,
                                                 int has_inc, int64_t M, double* __restrict__ partials,
-                                                unsigned long long* ticket,
+                                                unsigned long long* ticket, int defer,
                                                 double* __restrict__ scalars, int32_t* __restrict__ flag,
                                                 double ess_frac, int final_slot, uint32_t* status) {
     __shared__ long long s_key[48];
     __shared__ float s_f[96];
-    __shared__ double s_d[96];
     __shared__ bool last;
     double bmax;
     Lse c, o;
@@ -492,46 +554,19 @@ __device__ __forceinline__ void reweight_finish(const RefSums& cur, const RefSum
     if (threadIdx.x == 0) {
         double* P = partials + (size_t)blockIdx.x * 8;
         P[0] = c.m; P[1] = c.s1; P[2] = c.s2; P[3] = o.m; P[4] = o.s1; P[5] = bmax;
-        __threadfence();
-        const unsigned long long t = atomicAdd(ticket, 1ull);
-        last = (t == gridDim.x - 1);
+        if (!defer) {
+            __threadfence();
+            const unsigned long long t = atomicAdd(ticket, 1ull);
+            last = (t == gridDim.x - 1);
+        }
     }
+    if (defer) return;
     __syncthreads();
     if (!last) return;
     __threadfence();
-    Lse tc, to;
-    double mx;
-    combine_partials3(partials, gridDim.x, has_inc != 0, s_key, s_d, &tc, &to, &mx);
-    if (threadIdx.x == 0) {
-        *ticket = 0ull;
-        double* F = partials + (size_t)final_slot * 8;
-        const bool valid = !is_neg_inf(tc.m) && !disnan(tc.m);
-        if (valid) {  // express the sums relative to the true maximum
-            const double f = f2d_bits(expd(tc.m - mx));
-            tc = Lse{mx, tc.s1 * f, tc.s2 * f * f};
-        }
-        if (!valid) {
-            if (!disnan(tc.m)) raise_status(status, ST_ZERO_WEIGHT);
-            F[3] = 0.0;
-            if (flag) *flag = 0;
-            return;
-        }
-        const double lse = tc.m + ln_sum(tc.s1);
-        const float s1f = (float)tc.s1;
-        const double ess = f2d_bits(s1f * (s1f / (float)tc.s2));  // FP32 division
-        F[0] = tc.m; F[1] = tc.s1; F[2] = tc.s2; F[3] = 1.0; F[4] = lse;
-        reinterpret_cast<float*>(F + 5)[0] = 1.0f / s1f;
-        if (scalars) {
-            double inc = 0.0;
-            if (has_inc) inc = lse - (to.m + ln_sum(to.s1));
-            scalars[0] = inc;
-            scalars[1] = ess;
-            scalars[2] = tc.m;
-            scalars[3] = lse;
-        }
-        if (flag) *flag = (ess < ess_frac * (double)M) ? 1 : 0;
-    }
+    if (threadIdx.x == 0) *ticket = 0ull;
+    reweight_combine(partials, gridDim.x, has_inc, M, true, scalars, flag, ess_frac, final_slot,
+                     status);
 }
-
 
 }  // namespace smc

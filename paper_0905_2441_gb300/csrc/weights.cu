@@ -5,11 +5,12 @@
 //
 // One grid-stride pass reads l and logw, writes the new logw and reduces
 // (sum e, sum e^2) of the new log-weights and (sum e) of the old ones
-// against slack references, plus the exact maximum (integer keys); the last
-// block to finish combines the per-block partials in FP64 and writes the
-// scalars.  A second pass writes W = e / S1 (smc_reweight_resample: the
-// same pass also forms the exact tile sums of pass 1 of systematic
-// resampling from the W it writes).  Per element the only FP64
+// against slack references, plus the exact maximum (integer keys), into
+// per-block partials.  A second pass writes W = e / S1 (smc_reweight_resample:
+// the same pass also forms the exact tile sums of pass 1 of systematic
+// resampling from the W it writes); every block of that pass combines the
+// partials itself while its first tiles load, and its block 0 writes the
+// scalars.  Without a second pass the reduction's last block combines them.  Per element the only FP64
 // instruction is the log-weight update (GB300 issues FP64 at ~1/64 of
 // FP32); differences and exponentials run in FP32 on hi/lo splits.
 #include <climits>
@@ -32,7 +33,7 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
                                                          double dbeta, double* __restrict__ lw,
                                                          int64_t M, int has_inc,
                                                          double* __restrict__ partials,
-                                                         unsigned long long* ticket,
+                                                         unsigned long long* ticket, int defer,
                                                          double* __restrict__ scalars,
                                                          int32_t* __restrict__ flag,
                                                          double ess_frac, int final_slot,
@@ -95,23 +96,24 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
         }
     }
     if (nan_seen) raise_status(status, ST_NONFINITE);
-    reweight_finish(cur, old, has_inc, M, partials, ticket, scalars, flag, ess_frac, final_slot,
-                    status);
+    reweight_finish(cur, old, has_inc, M, partials, ticket, defer, scalars, flag, ess_frac,
+                    final_slot, status);
 }
 
 // W_i = exp(lw_i - m) / S1 with the difference taken on float hi/lo splits
 // as in RefSums (no FP64 instruction per element); values below 2^-126 are
 // written as 0.
 __global__ void __launch_bounds__(256) k_reweight_normalize(const double* __restrict__ lw,
-                                                            int64_t M,
-                                                            const double* __restrict__ fin,
-                                                            double* __restrict__ W) {
+                                                            int64_t M, RwArgs rw,
+                                                            double* __restrict__ W,
+                                                            uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
-    if (fin[3] == 0.0) return;
+    const RwFinal fin = rw_final(rw, status);
+    if (!fin.valid) return;
     float mh, ml;
-    split_double(fin[0], mh, ml);
-    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
+    split_double(fin.m, mh, ml);
+    const float inv = fin.inv;
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nchunk = (aligned16(lw) && aligned16(W)) ? M / kChunk : 0;
@@ -151,18 +153,14 @@ constexpr int kNrmTile = 2048;  // doubles: 16 KB
 constexpr int kNrmStages = 3;
 constexpr size_t kNrmSmem = (size_t)(kNrmStages + 2) * kNrmTile * sizeof(double) + 64;
 __global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
-    const double* __restrict__ lw, int64_t M, const double* __restrict__ fin,
-    double* __restrict__ W, uint32_t* status, uint32_t limit) {
+    const double* __restrict__ lw, int64_t M, RwArgs rw, double* __restrict__ W,
+    uint32_t* status, uint32_t limit) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
-    if (fin[3] == 0.0) return;
     extern __shared__ __align__(128) double nsm[];
     double* in = nsm;                               // [kNrmStages][kNrmTile]
     double* out = nsm + kNrmStages * kNrmTile;      // [2][kNrmTile]
     uint64_t* full = reinterpret_cast<uint64_t*>(out + 2 * kNrmTile);
-    float mh, ml;
-    split_double(fin[0], mh, ml);
-    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
     const int tid = threadIdx.x;
     const int64_t ntiles = M / kNrmTile;
     const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -178,6 +176,15 @@ __global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
             mb_expect_tx(&full[k], kBytes);
             bulk_load(in + k * kNrmTile, lw + tile_of(k) * kNrmTile, kBytes, &full[k]);
         }
+    // the normalisation constants, while the first tiles load
+    const RwFinal fin = rw_final(rw, status);
+    if (!fin.valid) {  // no weights to write: let the loads in flight land first
+        for (int k = 0; k < kNrmStages && k < nmine; ++k) mb_wait(&full[k], 0, status, limit);
+        return;
+    }
+    float mh, ml;
+    split_double(fin.m, mh, ml);
+    const float inv = fin.inv;
     int st = 0;
     uint32_t round = 0;
     for (int64_t k = 0; k < nmine; ++k) {
@@ -278,18 +285,18 @@ __global__ void __launch_bounds__(256) k_ess_reduce(const double* __restrict__ l
 // weights (the reduction found none positive) leave zero tile sums, so the
 // resampling that follows reports SMC_ERR_ZERO_WEIGHT and writes nothing.
 __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __restrict__ lw,
-                                                                int64_t M,
-                                                                const double* __restrict__ fin,
+                                                                int64_t M, RwArgs rw,
                                                                 double* __restrict__ W,
-                                                                RsScratch sc) {
+                                                                RsScratch sc, uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     __shared__ unsigned long long sh[kRsThreads / 32];
-    const bool valid = fin[3] != 0.0;
+    const RwFinal fin = rw_final(rw, status);
+    const bool valid = fin.valid;
     float mh = 0.0f, ml = 0.0f, inv = 0.0f;
     if (valid) {
-        split_double(fin[0], mh, ml);
-        inv = reinterpret_cast<const float*>(fin + 5)[0];
+        split_double(fin.m, mh, ml);
+        inv = fin.inv;
     }
     const int64_t ntiles = rs_tiles(M);
     // descending: the reduction wrote the log-weights ascending (the most
@@ -329,8 +336,8 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles(const double* __
 constexpr int kNtStages = 3;
 constexpr size_t kNtSmem = (size_t)(kNtStages + 2) * kRsTile * sizeof(double) + 64;
 __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles_bulk(
-    const double* __restrict__ lw, int64_t M, const double* __restrict__ fin,
-    double* __restrict__ W, RsScratch sc, uint32_t* status, uint32_t limit) {
+    const double* __restrict__ lw, int64_t M, RwArgs rw, double* __restrict__ W, RsScratch sc,
+    uint32_t* status, uint32_t limit) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     extern __shared__ __align__(128) double ntm[];
@@ -340,15 +347,31 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles_bulk(
     __shared__ unsigned long long sh[2][kRsThreads / 32];
     const int tid = threadIdx.x, wid = tid >> 5;
     const int64_t nfull = M / kRsTile;
-    if (fin[3] == 0.0) {  // no valid weights: zero tile sums, W untouched
+    const int64_t nmine = nfull > blockIdx.x ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    auto tile_of = [&](int64_t k) { return nfull - 1 - (blockIdx.x + k * gridDim.x); };
+    constexpr uint32_t kBytes = kRsTile * sizeof(double);
+    if (tid == 0) {
+        for (int st = 0; st < kNtStages; ++st) mb_init(&full[st], 1);
+        mb_init_fence();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int k = 0; k < kNtStages && k < nmine; ++k) {
+            mb_expect_tx(&full[k], kBytes);
+            bulk_load(in + k * kRsTile, lw + tile_of(k) * kRsTile, kBytes, &full[k]);
+        }
+    // the normalisation constants, while the first tiles load
+    const RwFinal fin = rw_final(rw, status);
+    if (!fin.valid) {  // no valid weights: zero tile sums, W untouched
         for (int64_t t = (int64_t)blockIdx.x * blockDim.x + tid; t < rs_tiles(M);
              t += (int64_t)gridDim.x * blockDim.x)
             sc.tile_sum[t] = 0ull;
+        for (int k = 0; k < kNtStages && k < nmine; ++k) mb_wait(&full[k], 0, status, limit);
         return;
     }
     float mh, ml;
-    split_double(fin[0], mh, ml);
-    const float inv = reinterpret_cast<const float*>(fin + 5)[0];
+    split_double(fin.m, mh, ml);
+    const float inv = fin.inv;
     int buf = 0;
     auto tile_total = [&](unsigned long long acc) {  // valid in thread 0 after the barrier
 #pragma unroll
@@ -380,19 +403,6 @@ __global__ void __launch_bounds__(kRsThreads) k_normalize_tiles_bulk(
         const unsigned long long ts = tile_total(acc);
         if (tid == 0) sc.tile_sum[nfull] = ts;
     }
-    const int64_t nmine = nfull > blockIdx.x ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    auto tile_of = [&](int64_t k) { return nfull - 1 - (blockIdx.x + k * gridDim.x); };
-    constexpr uint32_t kBytes = kRsTile * sizeof(double);
-    if (tid == 0) {
-        for (int st = 0; st < kNtStages; ++st) mb_init(&full[st], 1);
-        mb_init_fence();
-    }
-    __syncthreads();
-    if (tid == 0)
-        for (int k = 0; k < kNtStages && k < nmine; ++k) {
-            mb_expect_tx(&full[k], kBytes);
-            bulk_load(in + k * kRsTile, lw + tile_of(k) * kRsTile, kBytes, &full[k]);
-        }
     int st = 0;
     uint32_t round = 0;
     for (int64_t k = 0; k < nmine; ++k) {
@@ -447,7 +457,7 @@ static bool aligned16h(const void* p) { return (reinterpret_cast<uintptr_t>(p) &
 
 static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
     int64_t cap = (int64_t)ctx->num_sms * 2;
-    if (cap > kMaxPartialBlocks - 2) cap = kMaxPartialBlocks - 2;
+    if (cap > smc::kRwMaxParts) cap = smc::kRwMaxParts;  // what one combination reads
     int64_t b = (M + 255) / 256;
     if (b > cap) b = (M + 256 * 8 - 1) / (256 * 8);
     if (b > cap) b = cap;
@@ -459,7 +469,7 @@ static int reduce_blocks(const smc_ctx* ctx, int64_t M) {
 
 smc_status reweight_reduce_launch(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
                                   int64_t M, double* scalars_out, int32_t* resample_flag,
-                                  double ess_frac, cudaStream_t s);
+                                  double ess_frac, cudaStream_t s, smc::RwArgs* defer_to);
 
 extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double dbeta,
                                    double* logw, int64_t M, double* W_out, double* scalars_out,
@@ -468,12 +478,11 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
-    const int final_slot = kMaxPartialBlocks - 1;
+    smc::RwArgs rw;
     st = reweight_reduce_launch(ctx, loglik, dbeta, logw, M, scalars_out, resample_flag_out,
-                                ess_frac, s);
+                                ess_frac, s, W_out ? &rw : nullptr);
     if (st != SMC_OK) return st;
     if (W_out) {
-        const double* fin = ctx->d_partials + (size_t)final_slot * 8;
         if (aligned16h(logw) && aligned16h(W_out) && M >= (int64_t)smc::kNrmTile * ctx->num_sms) {
             // bulk tiles: two 80 KB blocks per SM
             static bool attr_set[64] = {};
@@ -485,14 +494,14 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
                 attr_set[dev] = true;
             }
             st = launch_pdl(smc::k_reweight_normalize_bulk, dim3((unsigned)ctx->num_sms * 2),
-                            dim3(smc::kNrmThreads), smc::kNrmSmem, s, (const double*)logw, M, fin,
+                            dim3(smc::kNrmThreads), smc::kNrmSmem, s, (const double*)logw, M, rw,
                             W_out, ctx->d_status, ctx->wait_limit);
         } else {
             int nb = (int)((M + 256 * 8 - 1) / (256 * 8));
             int cap = ctx->num_sms * 8;
             if (nb > cap) nb = cap;
             st = launch_pdl(smc::k_reweight_normalize, dim3(nb), dim3(256), 0, s,
-                            (const double*)logw, M, fin, W_out);
+                            (const double*)logw, M, rw, W_out, ctx->d_status);
         }
         if (st != SMC_OK) return st;
     }
@@ -501,18 +510,18 @@ extern "C" smc_status smc_reweight(smc_ctx* ctx, const double* loglik, double db
 
 size_t smc_resample_ws_bytes(int64_t M);
 
-// After a reweighting reduction whose final slot is in the context's
-// partials: W and the exact tile sums in one pass, then systematic
-// resampling from those tile sums (the ancestors, the log-weight reset).
-smc_status normalize_resample_launch(smc_ctx* ctx, double* logw, int64_t M, double* W_out,
-                                     int32_t* resample_flag, uint64_t seed, uint64_t step,
-                                     int32_t* ancestors_out, int32_t* counts_out, cudaStream_t s) {
+// After a deferred reweighting reduction (rw: its partials and outputs): W
+// and the exact tile sums in one pass that also combines the partials, then
+// systematic resampling from those tile sums (the ancestors, the log-weight
+// reset).
+smc_status normalize_resample_launch(smc_ctx* ctx, const smc::RwArgs& rw, double* logw,
+                                     int64_t M, double* W_out, int32_t* resample_flag,
+                                     uint64_t seed, uint64_t step, int32_t* ancestors_out,
+                                     int32_t* counts_out, cudaStream_t s) {
     smc_status st = ensure_ws(ctx, smc_resample_ws_bytes(M), s);
     if (st != SMC_OK) return st;
     const smc::RsScratch sc =
         resample_scratch(reinterpret_cast<unsigned long long*>(ctx->ws), M, true);
-    const int final_slot = kMaxPartialBlocks - 1;
-    const double* fin = ctx->d_partials + (size_t)final_slot * 8;
     if (aligned16h(logw) && aligned16h(W_out) &&
         M >= (int64_t)smc::kRsTile * ctx->num_sms * 2) {
         // whole tiles by bulk copies: two 80 KB blocks per SM
@@ -525,30 +534,36 @@ smc_status normalize_resample_launch(smc_ctx* ctx, double* logw, int64_t M, doub
             attr_set[dev] = true;
         }
         st = launch_pdl(smc::k_normalize_tiles_bulk, dim3((unsigned)ctx->num_sms * 2),
-                        dim3(smc::kRsThreads), smc::kNtSmem, s, (const double*)logw, M, fin,
+                        dim3(smc::kRsThreads), smc::kNtSmem, s, (const double*)logw, M, rw,
                         W_out, sc, ctx->d_status, ctx->wait_limit);
     } else {
         int64_t nb = smc::rs_tiles(M);
         if (nb > (int64_t)ctx->num_sms * 8) nb = (int64_t)ctx->num_sms * 8;
         st = launch_pdl(smc::k_normalize_tiles, dim3((unsigned)nb), dim3(smc::kRsThreads), 0, s,
-                        (const double*)logw, M, fin, W_out, sc);
+                        (const double*)logw, M, rw, W_out, sc, ctx->d_status);
     }
     if (st != SMC_OK) return st;
     return resample_launch(ctx->num_sms, W_out, M, seed, step, ancestors_out, counts_out,
                            resample_flag, logw, sc, ctx->d_status, s, true);
 }
 
-// The reweighting reduction (logw += dbeta loglik, the final slot, the
-// scalars and the flag) without the normalisation.
+// The reweighting reduction (logw += dbeta loglik, the per-block partials).
+// With defer_to null its last block also writes the final slot, the scalars
+// and the flag; otherwise *defer_to receives what the kernel that consumes
+// the weights (launched next on the same stream) needs to do that itself.
 smc_status reweight_reduce_launch(smc_ctx* ctx, const double* loglik, double dbeta, double* logw,
                                   int64_t M, double* scalars_out, int32_t* resample_flag,
-                                  double ess_frac, cudaStream_t s) {
+                                  double ess_frac, cudaStream_t s, smc::RwArgs* defer_to) {
     const int has_inc = (loglik != nullptr && dbeta != 0.0) ? 1 : 0;
     const int blocks = reduce_blocks(ctx, M);
     const int final_slot = kMaxPartialBlocks - 1;
+    if (defer_to)
+        *defer_to = smc::RwArgs{ctx->d_partials, blocks,        has_inc,   M,
+                                scalars_out,     resample_flag, ess_frac, final_slot};
     return launch_pdl(smc::k_reweight_reduce, dim3(blocks), dim3(256), 0, s, loglik, dbeta, logw,
                       M, has_inc, ctx->d_partials, ctx->d_counters + CNT_REWEIGHT_TICKET,
-                      scalars_out, resample_flag, ess_frac, final_slot, ctx->d_status);
+                      defer_to ? 1 : 0, scalars_out, resample_flag, ess_frac, final_slot,
+                      ctx->d_status);
 }
 
 extern "C" smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, double dbeta,
@@ -563,10 +578,11 @@ extern "C" smc_status smc_reweight_resample(smc_ctx* ctx, const double* loglik, 
     smc_status st = use_device(ctx);
     if (st != SMC_OK) return st;
     cudaStream_t s = as_stream(stream);
+    smc::RwArgs rw;
     st = reweight_reduce_launch(ctx, loglik, dbeta, logw, M, scalars_out, resample_flag_out,
-                                ess_frac, s);
+                                ess_frac, s, &rw);
     if (st != SMC_OK) return st;
-    return normalize_resample_launch(ctx, logw, M, W_out, resample_flag_out, seed, step,
+    return normalize_resample_launch(ctx, rw, logw, M, W_out, resample_flag_out, seed, step,
                                      ancestors_out, counts_out, s);
 }
 
