@@ -49,6 +49,28 @@ L2_BYTES = 129 * 2**20
 FLUSH_BYTES = 256 * 2**20
 
 
+def l2_note(what):
+    return (f"256 MiB buffer (2x L2) written, then another read, before every timed {what}, "
+            "outside its events")
+
+
+class L2Flush:
+    """Between timed iterations: write a 256 MiB buffer (twice L2), then read
+    a second one, so that L2 holds none of the timed data and none of the
+    flush's own dirty lines either (their write-back to HBM happens here,
+    outside the events, instead of inside the next timed kernel)."""
+
+    def __init__(self, torch):
+        self.torch = torch
+        self.w = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.r = torch.zeros(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+        self.out = torch.empty((), dtype=torch.float32, device="cuda")
+
+    def __call__(self, v=0.5):
+        self.w.fill_(float(v))
+        self.torch.sum(self.r, dim=0, out=self.out)
+
+
 # ------------------------------------------------------------------ helpers
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 100 ms in the
@@ -325,7 +347,7 @@ def bench_popmcmc(args, torch, dist):
     smp.theta.copy_(torch.from_numpy(th0).cuda())
     P.loglik_batch(ctx, model, smp.y, smp.theta, out=smp.ll)
     ctx.check()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     stream = torch.cuda.current_stream()
     S = args.graph_sweeps
     # ---- the captured run of S sweeps
@@ -348,7 +370,7 @@ def bench_popmcmc(args, torch, dist):
     with ClockSampler(torch.cuda.current_device()) as clk:
         t0 = time.perf_counter()
         for i in range(args.steps):
-            flush.fill_(float(i))
+            flush(i)
             ev[i][0].record(stream)
             g.replay()
             ev[i][1].record(stream)
@@ -373,7 +395,8 @@ def bench_popmcmc(args, torch, dist):
     evp = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(Kp)]
     for i in range(Kp):
-        flush.fill_(float(i))
+        flush(i)
+        _hold(torch)
         evp[i][0].record(stream)
         smp.sweep(200_000 + i)
         evp[i][1].record(stream)
@@ -422,7 +445,7 @@ def bench_popmcmc(args, torch, dist):
                            "sweep counters fixed at capture)",
                    "launch": tune.get("binned") if binned else
                    {"lanes_per_chain": lanes, "threads_per_block": threads},
-                   "l2": "256 MiB buffer (2x L2) written before every timed step, outside its events",
+                   "l2": l2_note("step"),
                    "parallelism": f"independent populations per rank x{dist.world}"},
         "forms": {"graph_captured": {"sweeps": S, "value": float(M) * N / t_sweep,
                                      "us_per_sweep": 1e6 * t_sweep},
@@ -596,7 +619,7 @@ def bench_secondary(torch, P):
     ctx = P.Context()
     ex2_rate, ex2_ms = measure_peak(P, 0)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
 
     def timed(fn):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -781,7 +804,7 @@ def reweight_resample_roofline(torch, P, ctx, M, reps, seed=5):
     anc = torch.empty(M, dtype=torch.int32, device="cuda")
     sc = torch.empty(4, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     rw = lambda: P.reweight(ctx, ll, 1.0, lw, W, sc, None, 0.5)
     rs = lambda: P.resample_systematic(ctx, W, 9, 1, anc=anc, logw_reset=lw)
     for _ in range(3):
@@ -895,7 +918,7 @@ def is_example(torch, P, ctx, reps=10):
     x_h = x_d.cpu().pin_memory()
     res = torch.empty(3, dtype=torch.float64, device="cuda")
     res_h = torch.empty(3, dtype=torch.float64).pin_memory()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     stream = torch.cuda.current_stream()
     for _ in range(3):
         P.is_moments(ctx, prob, x_d, out=res)
@@ -913,7 +936,7 @@ def is_example(torch, P, ctx, reps=10):
             x_d.copy_(x_h, non_blocking=True)
             P.is_moments(ctx, prob, x_d, out=res)
             res_h.copy_(res, non_blocking=True)
-        e = _flush_timed(torch, flush, stream, [e2e])
+        e = _flush_timed(torch, flush, stream, [e2e], hold=False)
         torch.cuda.synchronize()
         t_e2e.append(e[0].elapsed_time(e[1]) / 1e3)
     ctx.check()
@@ -934,7 +957,7 @@ def mrg_blocks(torch, P, ctx, reps=10):
     call, medians over `reps`."""
     nt, per = 152 * 256 * 4, 1024
     mrg = torch.empty(nt * per, dtype=torch.float32, device="cuda")
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     stream = torch.cuda.current_stream()
     for _ in range(3):
         P.rng_mrg32k3a(ctx, (12345,) * 6, 0, nt, per, out=mrg)
@@ -972,7 +995,7 @@ def bench_is(args, torch, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 per draw, f64 sums",
             "data": "synthetic (N(0,1) draws, seed 3)",
             "config": {"workload": r["workload"], "N": r["N"],
-                       "l2": "256 MiB buffer written before every timed call, outside its events"},
+                       "l2": l2_note("call")},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "traffic": profile_traffic("k_is_moments"),
                          "bytes_per_draw": 4},
@@ -999,17 +1022,31 @@ def bench_mrg(args, torch, dist):
             "data": "synthetic (seed 12345 x 6)",
             "config": {"workload": "mrg32k3a-155648x1024", "threads": r["threads"],
                        "per_thread": r["per_thread"],
-                       "l2": "256 MiB buffer written before every timed call, outside its events"},
+                       "l2": l2_note("call")},
             "roofline": {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                          "frac": ach / hbm, "traffic": profile_traffic("k_mrg32k3a"),
                          "bytes_per_number": 4},
             "mrg32k3a": r, "gpu_launches": 2 * reps, "clocks": clk.summary()}
 
 
-def _flush_timed(torch, flush, stream, fns):
+# A spin of about 0.13 ms on the device, queued after the L2 flush and
+# before the first event: the host issues the timed calls meanwhile, so the
+# events time the device work rather than the host's launch overhead (short
+# calls after a flush would otherwise start when their launch arrives).
+HOLD_CYCLES = 1 << 18
+
+
+def _hold(torch):
+    torch.cuda._sleep(HOLD_CYCLES)
+
+
+def _flush_timed(torch, flush, stream, fns, hold=True):
     """Flush L2, then time each callable of one step with CUDA events on the
-    launching stream; returns per-callable elapsed seconds."""
-    flush.fill_(0.5)
+    launching stream; returns per-callable elapsed seconds.  hold=False for
+    an end-to-end measurement, whose host side belongs to what it times."""
+    flush()
+    if hold:
+        _hold(torch)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)]
     evs[0].record(stream)
     for i, f in enumerate(fns):
@@ -1030,7 +1067,7 @@ def bench_pf(args, torch, dist):
     ctx = P.Context()
     pf = samplers.ParticleFilter(ctx, P.PFModel(P.PF_MSV, phi, synth.chol(Sigma), beta), yobs,
                                  w.M, seed=w.method_seed + dist.rank)
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     stream = torch.cuda.current_stream()
     for t in range(1, args.warmup + 1):
         pf.step(t)
@@ -1071,7 +1108,7 @@ def bench_pf(args, torch, dist):
            "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded MSV observations)",
            "config": {"workload": w.name, "M": w.M, "d": w.d,
-                      "l2": "256 MiB buffer written before every timed step, outside its events",
+                      "l2": l2_note("step"),
                       "parallelism": f"independent filters per rank x{dist.world}"},
            "per_call_ms": {n: 1e3 * float(per[:, i].mean()) for i, n in enumerate(names)},
            "per_call_share": {n: float(share[i]) for i, n in enumerate(names)},
@@ -1102,7 +1139,7 @@ def bench_resample(args, torch, dist):
     anc = torch.empty(M, dtype=torch.int32, device="cuda")
     sc = torch.empty(4, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     fns = [lambda: P.reweight(ctx, ll, 1.0, lw, W, sc, None, 0.5),
            lambda: P.resample_systematic(ctx, W, 9, 1, anc=anc, logw_reset=lw)]
     for _ in range(args.warmup):
@@ -1141,7 +1178,7 @@ def bench_resample(args, torch, dist):
            "ms_per_step": 1e3 * t_max / K, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic (log-likelihoods ~ N(0,1))",
            "config": {"workload": "reweight+resample-M16777216", "M": M,
-                      "l2": "256 MiB buffer written before every timed step, outside its events"},
+                      "l2": l2_note("step")},
            "per_call_gbs": {"reweight": b_rw * M / per[:, 0].mean() / 1e9,
                             "resample": ach_rs},
            "per_call_ms": {"reweight": 1e3 * per[:, 0].mean(), "resample": 1e3 * per[:, 1].mean()},
@@ -1177,7 +1214,7 @@ def bench_diag(args, torch, dist):
     fp = P.DiagGMM(w.K, w.sigma, d=w.d)
     out = torch.empty(w.M, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     call = lambda: P.loglik_batch(ctx, tc, Y, th, out=out)
     for _ in range(args.warmup):
         call()
@@ -1238,7 +1275,7 @@ def bench_diag(args, torch, dist):
            "scaling": "weak", "vs_baseline": None, "dtype": "bf16x3->f32",
            "data": "synthetic (seeded mixture data and particles; no dataset)",
            "config": {"workload": w.name, "d": w.d, "K": w.K, "N": w.N, "M": w.M,
-                      "l2": "256 MiB buffer written before every timed call, outside its events",
+                      "l2": l2_note("call"),
                       "parallelism": f"independent particle sets per rank x{dist.world}"},
            "forms": {"tensor_bf16_split": {"ms_per_call": 1e3 * t_call, "max_rel_err": err},
                      "cuda_core_fp32": {"ms_per_call": 1e3 * t_fp, "value": pd / t_fp}},
@@ -1266,7 +1303,7 @@ def bench_fsv(args, torch, dist):
     ctx = P.Context()
     mod = P.PFModel(P.PF_FSV, phi, synth.chol(U), B=B, psi=psi)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     reps = max(1, min(args.steps, 10))
     rows = {}
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -1306,7 +1343,7 @@ def bench_fsv(args, torch, dist):
            "vs_baseline_note": "against Table 3's GTX 280 time for the same N (another machine: context)",
            "dtype": "f32", "data": "synthetic (observations simulated from the model, seed 7)",
            "config": {"workload": w.name, "N": N, "T": w.T, "m": 5, "K": 3,
-                      "l2": "256 MiB buffer written before every timed filter run, outside its events",
+                      "l2": l2_note("filter run"),
                       "parallelism": f"independent filters per rank x{dist.world}"},
            "table3": rows, "gpu_launches": 7 * w.T * reps, "clocks": clk.summary()}
     ctx.close()
@@ -1331,7 +1368,7 @@ def bench_mala(args, torch, dist):
     smp = samplers.SMCSampler(ctx, model, y, th0, betas, kind=P.MOVE_MALA, scale=w.scale,
                               seed=w.method_seed + dist.rank)
     stream = torch.cuda.current_stream()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     for _ in range(max(1, args.warmup // 3)):
         smp.reset(th0)
         smp.run()
@@ -1371,8 +1408,7 @@ def bench_mala(args, torch, dist):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32 terms, f64 totals",
             "data": "synthetic (8-component mixture, 1000 simulated data, seed 1)",
             "config": {"workload": w.name, "M": w.M, "K": w.K, "N": w.N, "T": w.T, "h": w.scale,
-                       "l2": "256 MiB buffer written before every timed run / move, outside "
-                             "its events",
+                       "l2": l2_note("run / move"),
                        "parallelism": f"independent samplers per rank x{dist.world}"},
             "move_ms": 1e3 * tm,
             "roofline": {"bound": "alu", "pipe": "MUFU", "achieved": ops / tm / 1e9,
@@ -1491,7 +1527,7 @@ def bench_tables(args, torch, dist):
     import synth
     w = synth.PAPER_TABLES
     ctx = P.Context()
-    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     reps = max(1, min(args.steps, 5))
     with ClockSampler(torch.cuda.current_device()) as clk:
         tab = paper_tables(torch, P, ctx, flush, reps=reps, rank=dist.rank)
@@ -1513,7 +1549,7 @@ def bench_tables(args, torch, dist):
             "data": "synthetic (Section 4.1 model, 100 simulated observations, seed 1)",
             "config": {"workload": w.name, "N": N, "T": w.table2_T, "moves": w.table2_moves,
                        "m": w.N, "k": w.K,
-                       "l2": "256 MiB buffer written before every timed run, outside its events",
+                       "l2": l2_note("run"),
                        "parallelism": f"independent samplers per rank x{dist.world}"},
             "table1": tab["table1"], "table2": tab["table2"], "table2_ais": tab["table2_ais"],
             "gpu_launches": launches,
@@ -1622,7 +1658,7 @@ def main():
             out["secondary"] = {"error": repr(e)}
         try:
             ctx = P.Context()
-            flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+            flush = L2Flush(torch)
             out["secondary"]["paper_tables"] = paper_tables(torch, P, ctx, flush, reps=1)
             ctx.close()
         except Exception as e:  # noqa: BLE001
