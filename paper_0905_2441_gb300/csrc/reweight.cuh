@@ -70,6 +70,21 @@ __device__ __forceinline__ void store8(double* __restrict__ p, const double (&v)
     for (int j = 0; j < kChunk / 2; ++j) q[j] = make_double2(v[2 * j], v[2 * j + 1]);
 }
 
+// An L2 eviction policy that keeps lines longer than the default (the
+// data's next read follows soon in the same call), and store8 with it.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ void store8_keep(double* __restrict__ p, const double (&v)[kChunk],
+                                            uint64_t pol) {
+#pragma unroll
+    for (int j = 0; j < kChunk / 2; ++j)
+        asm volatile("st.global.L2::cache_hint.v2.f64 [%0], {%1, %2}, %3;"
+                     :: "l"(p + 2 * j), "d"(v[2 * j]), "d"(v[2 * j + 1]), "l"(pol) : "memory");
+}
+
 // FP32 sum with its rounding error carried (Knuth's two-sum): the running
 // error stays below 2^-24 of the sum's magnitude times a few, without the
 // long-latency FP64 pipe.

@@ -48,6 +48,9 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
     // element per thread keeps each thread's dependent chain short
     const bool vec = aligned16(lw) && (!has_inc || aligned16(ll)) && M >= G * kChunk;
     const int64_t nchunk = vec ? M / kChunk : 0;
+    // the new log-weights stay in L2 in preference to the data read once
+    // (the normalisation reads them back, last written first)
+    const uint64_t keep = l2_evict_last_policy();
     // the next chunk's loads are issued before this chunk's arithmetic
     double xn[kChunk], vn[kChunk];
     if (t0 < nchunk) {
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(256, 2) k_reweight_reduce(const double* __rest
                 n[j] = fma(dbeta, v[j], x[j]);
                 nan_seen |= disnan(n[j]);  // a NaN in x or v makes n NaN
             }
-            store8(lw + ch * kChunk, n);
+            store8_keep(lw + ch * kChunk, n, keep);
             add8(old, x, false);
             add8(cur, n, true);
         } else {
@@ -166,6 +169,7 @@ __global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
     const int64_t nmine = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     auto tile_of = [&](int64_t k) { return ntiles - 1 - (blockIdx.x + k * gridDim.x); };
     constexpr uint32_t kBytes = kNrmTile * sizeof(double);
+    const uint64_t drop = l2_evict_first_policy();  // the log-weights' last read
     if (tid == 0) {
         for (int st = 0; st < kNrmStages; ++st) mb_init(&full[st], 1);
         mb_init_fence();
@@ -174,7 +178,7 @@ __global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
     if (tid == 0)
         for (int k = 0; k < kNrmStages && k < nmine; ++k) {
             mb_expect_tx(&full[k], kBytes);
-            bulk_load(in + k * kNrmTile, lw + tile_of(k) * kNrmTile, kBytes, &full[k]);
+            bulk_load_hint(in + k * kNrmTile, lw + tile_of(k) * kNrmTile, kBytes, &full[k], drop);
         }
     // the normalisation constants, while the first tiles load
     const RwFinal fin = rw_final(rw, status);
@@ -206,13 +210,13 @@ __global__ void __launch_bounds__(kNrmThreads) k_reweight_normalize_bulk(
         fence_async_shared();
         __syncthreads();
         if (tid == 0) {
-            bulk_store(W + tile_of(k) * kNrmTile, out + ob * kNrmTile, kBytes);
+            bulk_store_hint(W + tile_of(k) * kNrmTile, out + ob * kNrmTile, kBytes, drop);
             bulk_commit();
             if (k + kNrmStages < nmine) {  // the ring slot just read takes tile k + stages
                 fence_async_shared();
                 mb_expect_tx(&full[st], kBytes);
-                bulk_load(in + st * kNrmTile, lw + tile_of(k + kNrmStages) * kNrmTile, kBytes,
-                          &full[st]);
+                bulk_load_hint(in + st * kNrmTile, lw + tile_of(k + kNrmStages) * kNrmTile,
+                               kBytes, &full[st], drop);
             }
         }
         if (++st == kNrmStages) { st = 0; ++round; }
