@@ -21,6 +21,7 @@
 // by the max-shifted direct form.
 #pragma once
 #include <climits>
+#include <cstddef>
 
 #include "device.cuh"
 
@@ -35,7 +36,9 @@ constexpr int kBinnedMaxN = 4096;               // data held in shared memory
 constexpr int kBinnedMinN = 512;
 constexpr int kBinnedMaxWarps = 16;
 
-struct BinTable {
+struct __align__(16) BinTable {
+    // (start .. dconst form the table's core: what the sweep reads after the
+    // partition; the cached layout holds exactly these bytes)
     int start[kClasses + 1];  // first slot of each class in the sorted list (even);
                               // start[kClasses] = padded length of the list
     int count[kClasses];
@@ -238,6 +241,28 @@ __device__ void bin_pieces(const BinTable& bt, int3* pieces, int* np) {
     if (nr) pieces[totf + incr - 1] = make_int3(a + nf * kPieceSlots, a + n, l);
     if (l == 31) *np = totf + incr;
     __syncwarp();
+}
+
+// The binned layout of one data set, kept in global memory between sweeps
+// (it depends only on the data, the bin width and c): a 16-byte header
+// {N, piece count, bin width bits, c bits}, a copy of the data (to check
+// that the data are still those), the sorted list, the table's core and the
+// pieces -- each section a multiple of 16 bytes, so that a sweep moves each
+// by one bulk copy into the place its own partition would have filled.
+constexpr size_t kBinCoreBytes = (offsetof(BinTable, cnt) + 15) / 16 * 16;
+constexpr size_t kPiecesBytes = (kMaxPieces * sizeof(int3) + 15) / 16 * 16;
+static_assert(offsetof(BinTable, dconst) + sizeof(double) <= kBinCoreBytes, "core ends at dconst");
+static_assert(kBinCoreBytes <= offsetof(BinTable, cnt), "the core does not reach the scratch");
+__host__ __device__ inline size_t bcache_ycopy_bytes(int64_t N) { return (size_t)((N + 3) & ~3LL) * 4; }
+__host__ __device__ inline size_t bcache_yb_off(int64_t N) { return 16 + bcache_ycopy_bytes(N); }
+__host__ __device__ inline size_t bcache_core_off(int64_t N, int yb_len) {
+    return bcache_yb_off(N) + (size_t)yb_len * 4;
+}
+__host__ __device__ inline size_t bcache_pieces_off(int64_t N, int yb_len) {
+    return bcache_core_off(N, yb_len) + kBinCoreBytes;
+}
+__host__ __device__ inline size_t bcache_bytes(int64_t N, int yb_len) {
+    return bcache_pieces_off(N, yb_len) + kPiecesBytes;
 }
 
 // log2 of sum_k w_k 2^(-c (y - mu_k)^2), max-shifted (the class outside the bins)

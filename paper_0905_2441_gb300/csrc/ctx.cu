@@ -106,6 +106,8 @@ namespace smc_host {
 void mrg_power_table(uint32_t* tab);
 }
 
+size_t smc_binned_cache_bytes();  // moves.cu
+
 extern "C" smc_status smc_create(smc_ctx** out, int device) {
     if (!out) return SMC_ERR_ARG;
     *out = nullptr;
@@ -131,6 +133,12 @@ extern "C" smc_status smc_create(smc_ctx** out, int device) {
               cudaMemset(c->d_status, 0, sizeof(uint32_t)) == cudaSuccess &&
               cudaMemset(c->d_counters, 0, kCounters * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMalloc(&c->d_mrg_pow, 64 * 18 * sizeof(uint32_t)) == cudaSuccess;
+    if (ok) {  // the binned sweep's layout buffer, at its largest data set (tens of KB)
+        c->bcache_bytes = smc_binned_cache_bytes();
+        ok = cudaMalloc(reinterpret_cast<void**>(&c->d_bcache), c->bcache_bytes) == cudaSuccess &&
+             cudaMemset(c->d_bcache, 0, c->bcache_bytes) == cudaSuccess;
+        if (!ok) c->bcache_bytes = 0;
+    }
     if (ok) {
         uint32_t tab[64 * 18];
         mrg_power_table(tab);
@@ -156,6 +164,7 @@ extern "C" smc_status smc_destroy(smc_ctx* ctx) {
     if (ctx->d_popdone) cudaFree(ctx->d_popdone);
     if (ctx->d_grpdone) cudaFree(ctx->d_grpdone);
     if (ctx->d_grppart) cudaFree(ctx->d_grppart);
+    if (ctx->d_bcache) cudaFree(ctx->d_bcache);
     if (ctx->d_mrg_pow) cudaFree(ctx->d_mrg_pow);
     delete ctx;
     return SMC_OK;

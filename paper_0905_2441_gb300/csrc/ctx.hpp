@@ -29,6 +29,15 @@ struct smc_ctx {
     uint32_t* d_grpdone = nullptr;
     double* d_grppart = nullptr;
     int64_t grp_cap = 0;
+    // binned sweep: the binned layout of the last data set seen (built by
+    // k_bin_prepare; allocated with the context at the largest N) and the
+    // host's key for it; the sweep checks the data against the layout's own
+    // copy before using it
+    char* d_bcache = nullptr;
+    size_t bcache_bytes = 0;
+    const void* bkey_y = nullptr;
+    int64_t bkey_n = -1;
+    uint32_t bkey_binw = 0, bkey_cf = 0;
     // MRG32k3a skip-ahead table: A1^(2^k), A2^(2^k), k < 64 (filled at creation)
     uint32_t* d_mrg_pow = nullptr;
     // polls of the first bounded wait on a bulk data copy before it gives up

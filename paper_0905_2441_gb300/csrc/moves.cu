@@ -3,9 +3,11 @@
 // of tempered chains in one persistent launch, chains dealt in equal items).
 // Sections 3.1, 4.1.1, 4.1.2 of Lee, Yau, Giles, Doucet & Holmes (2009).
 #include <cmath>
+#include <cstring>
 
 #include "ctx.hpp"
 #include "binned.cuh"
+#include "bulk.cuh"
 #include "gmm1d.cuh"
 
 using namespace smc_host;
@@ -503,12 +505,59 @@ __host__ __device__ inline int binned_rk_len(int64_t N) {  // floats holding N u
 // dynamic shared memory: staged data, mbarrier, sorted list, ranks, the
 // chains' fixed-point totals [16 groups][32 lanes], then per chain slot: old
 // log-likelihood, proposal (normals before it), temperature, accept word,
-// in-box flag; last the population offsets (when at most kOffSmem + 1)
+// in-box flag; the population offsets (when at most kOffSmem + 1); last,
+// 16-byte aligned, the cached layout's copy of the data
 __host__ __device__ inline size_t binned_smem_bytes(int64_t N, int K, int64_t n_pops) {
     const int yc = ychunk_for(N);
     const size_t off = n_pops + 1 <= kOffSmem ? (size_t)(n_pops + 1) * 4 : 0;
     return ((size_t)yc + 4 + (size_t)binned_yb_len(N) + (size_t)binned_rk_len(N)) * 4 +
-           (size_t)kBinThreads * 8 + (size_t)kBinThreads * (8 + 4 * (size_t)K + 12) + off;
+           (size_t)kBinThreads * 8 + (size_t)kBinThreads * (8 + 4 * (size_t)K + 12) + off + 16 +
+           bcache_ycopy_bytes(N);
+}
+// shared memory of k_bin_prepare: staged data, mbarrier slot, sorted list, ranks
+__host__ __device__ inline size_t bin_prepare_smem_bytes(int64_t N) {
+    return ((size_t)ychunk_for(N) + 4 + (size_t)binned_yb_len(N) + (size_t)binned_rk_len(N)) * 4;
+}
+
+// The binned layout of a data set (sorted list, table core, pieces) built
+// once by one CTA and stored with a copy of the data (binned.cuh), for the
+// sweeps that follow.  Launched without programmatic dependent launch and
+// never releasing its dependents early, so a sweep that reads the layout
+// before its own dependency wait finds it complete.
+__global__ void __launch_bounds__(kBinThreads) k_bin_prepare(const float* __restrict__ y, int64_t N,
+                                                             float binw, float binw_inv, float cf,
+                                                             char* __restrict__ bcache) {
+    extern __shared__ __align__(16) float pm[];
+    const int yc = ychunk_for(N), ybl = binned_yb_len(N);
+    float* ys = pm;
+    float* yb = ys + yc + 4;
+    uint16_t* rk = reinterpret_cast<uint16_t*>(yb + ybl);
+    __shared__ BinTable bt;
+    __shared__ __align__(16) int s_piece_w[kPiecesBytes / 4];
+    __shared__ int s_np;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < N; i += blockDim.x) ys[i] = y[i];
+    __syncthreads();
+    bin_partition(ys, (int)N, yb, rk, bt, binw, binw_inv, cf);
+    bin_pieces(bt, reinterpret_cast<int3*>(s_piece_w), &s_np);
+    __syncthreads();
+    if (tid == 0) {
+        int* h = reinterpret_cast<int*>(bcache);
+        h[0] = (int)N;
+        h[1] = s_np;
+        h[2] = __float_as_int(binw);
+        h[3] = __float_as_int(cf);
+    }
+    float* yc_out = reinterpret_cast<float*>(bcache + 16);
+    for (int i = tid; i < (int)(bcache_ycopy_bytes(N) / 4); i += blockDim.x)
+        yc_out[i] = i < N ? ys[i] : 0.0f;
+    float* yb_out = reinterpret_cast<float*>(bcache + bcache_yb_off(N));
+    for (int i = tid; i < ybl; i += blockDim.x) yb_out[i] = yb[i];  // past the list: never read
+    const uint32_t* core = reinterpret_cast<const uint32_t*>(&bt);
+    uint32_t* core_out = reinterpret_cast<uint32_t*>(bcache + bcache_core_off(N, ybl));
+    for (int i = tid; i < (int)(kBinCoreBytes / 4); i += blockDim.x) core_out[i] = core[i];
+    int* pc_out = reinterpret_cast<int*>(bcache + bcache_pieces_off(N, ybl));
+    for (int i = tid; i < (int)(kPiecesBytes / 4); i += blockDim.x) pc_out[i] = s_piece_w[i];
 }
 
 // first pair slot of CTA b's range: floor(b Wt / B)
@@ -529,7 +578,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
     const float* __restrict__ beta, const int32_t* __restrict__ offsets, int32_t n_pops,
     float scale, uint64_t seed, uint64_t sweep, unsigned long long* stats, uint32_t* pop_done,
     uint32_t* grp_done, long long* grp_part, Gmm1dArgs P, int Kreal, int inline_ex,
-    uint32_t* status) {
+    const char* __restrict__ bcache, uint32_t* status) {
     grid_dep_launch();
     extern __shared__ __align__(16) float sm[];
     constexpr int T = kBinThreads, NW = T / 32;
@@ -544,12 +593,19 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
     uint32_t* s_aw = reinterpret_cast<uint32_t*>(s_beta + T);
     int* s_inb = reinterpret_cast<int*>(s_aw + T);
     int32_t* s_off = reinterpret_cast<int32_t*>(s_inb + T);
+    float* s_ycopy = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(s_off + (n_pops + 1 <= kOffSmem ? n_pops + 1 : 0)) + 15) &
+        ~(uintptr_t)15);
     __shared__ BinTable bt;
-    __shared__ int3 s_piece[kMaxPieces];
+    __shared__ __align__(16) int s_piece_w[kPiecesBytes / 4];
+    int3* s_piece = reinterpret_cast<int3*>(s_piece_w);
     __shared__ int4 s_exb[T + 1];
     __shared__ int s_nex, s_next, s_np;
     __shared__ int s_fin[NW];  // a round's groups decided by this CTA
     __shared__ uint32_t s_mh, s_sw, s_try;
+    __shared__ uint64_t s_cmb;                  // the cached layout's copies
+    __shared__ __align__(16) int s_hdr[4];
+    if (threadIdx.x == 0 && bcache) mb_init(&s_cmb, 1);  // (fenced by init_mbar)
     init_mbar(ychunk_mbar(ys, yc));
     if (threadIdx.x == 0) { s_mh = 0; s_sw = 0; s_try = 0; }
     const int tid = (int)threadIdx.x, warp = tid >> 5, l32 = tid & 31;
@@ -589,6 +645,20 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
     // them (a prefetch reads no value; the states are read after the wait)
     uint32_t phase = 0;
     const bool bulk = stage_y_issue(ys, y, 0, (int)N, ychunk_mbar(ys, yc));
+    // the cached layout (k_bin_prepare, complete before this launch began):
+    // header, data copy, sorted list, table core and pieces, each by one
+    // bulk copy into the place the partition below would fill
+    const int ybl = binned_yb_len(N);
+    if (bcache && tid == 0) {
+        const uint32_t ycb = (uint32_t)bcache_ycopy_bytes(N);
+        mb_expect_tx(&s_cmb, 16u + ycb + (uint32_t)ybl * 4u + (uint32_t)kBinCoreBytes +
+                                 (uint32_t)kPiecesBytes);
+        bulk_load(s_hdr, bcache, 16u, &s_cmb);
+        bulk_load(s_ycopy, bcache + 16, ycb, &s_cmb);
+        bulk_load(yb, bcache + bcache_yb_off(N), (uint32_t)ybl * 4u, &s_cmb);
+        bulk_load(&bt, bcache + bcache_core_off(N, ybl), (uint32_t)kBinCoreBytes, &s_cmb);
+        bulk_load(s_piece_w, bcache + bcache_pieces_off(N, ybl), (uint32_t)kPiecesBytes, &s_cmb);
+    }
     // (each thread's first offset is loaded into a register and stored after
     // the draws, so the thread does not wait for it)
     const int32_t* offs = offsets;
@@ -611,9 +681,23 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
     }
     if (off_smem && tid <= n_pops) s_off[tid] = off0;
     stage_y_wait(bulk, ychunk_mbar(ys, yc), phase, status, P.wait_limit);
-    // ---- the data sorted into bins, cut into pieces
-    bin_partition(ys, (int)N, yb, rk, bt, P.binw, P.binw_inv, P.cf);
-    bin_pieces(bt, s_piece, &s_np);
+    // ---- the data sorted into bins, cut into pieces: the cached layout when
+    // it was built from these very data, bin width and c, else partitioned here
+    bool fresh = true;
+    if (bcache) {
+        mb_wait(&s_cmb, 0, status, P.wait_limit);
+        bool bad = false;
+        for (int i = tid; i < N; i += T) bad |= __float_as_uint(ys[i]) != __float_as_uint(s_ycopy[i]);
+        if (tid == 0)
+            bad |= s_hdr[0] != (int)N || s_hdr[2] != __float_as_int(P.binw) ||
+                   s_hdr[3] != __float_as_int(P.cf) || s_hdr[1] < 1 || s_hdr[1] > kMaxPieces;
+        fresh = __syncthreads_or(bad) != 0;
+        if (!fresh && tid == 0) s_np = s_hdr[1];
+    }
+    if (fresh) {
+        bin_partition(ys, (int)N, yb, rk, bt, P.binw, P.binw_inv, P.cf);
+        bin_pieces(bt, s_piece, &s_np);
+    }
     __syncthreads();
     const int np = s_np;
     const int64_t H = bt.start[kClasses] >> 1;
@@ -789,6 +873,12 @@ __global__ void __launch_bounds__(256) k_popmcmc_exchange(
 
 }  // namespace smc
 
+// bytes of the binned layout buffer at the largest binned data set (the
+// context allocates it once, so sweeps captured in a graph can use it)
+size_t smc_binned_cache_bytes() {
+    return smc::bcache_bytes(smc::kBinnedMaxN, smc::binned_yb_len(smc::kBinnedMaxN));
+}
+
 namespace smc_host {
 
 smc_status gmm1d_prepare(const smc_gmm* model, int64_t N, smc::Gmm1dArgs* P, int* Kpad,
@@ -828,6 +918,31 @@ static smc_status dispatch_move(bool mala, bool eqw, int blocks, int threads, cu
 #define SMC_POP_PDL 1
 #endif
 
+// The binned layout of y for the sweep: rebuilt (one small launch, captured
+// like any other when the stream is capturing) when the data pointer, N, the
+// bin width or c differ from the context's last ones; null (the sweep
+// partitions the data itself) without a buffer.  Data changed in place
+// under the same pointer are caught by the sweep's own check.
+static const char* binned_cache(smc_ctx* ctx, const float* y, int64_t N,
+                                const smc::Gmm1dArgs& P, cudaStream_t s) {
+    if (!ctx->d_bcache || ctx->bcache_bytes < smc::bcache_bytes(N, smc::binned_yb_len(N)))
+        return nullptr;
+    uint32_t bw, cf;
+    std::memcpy(&bw, &P.binw, 4);
+    std::memcpy(&cf, &P.cf, 4);
+    if (ctx->bkey_y != y || ctx->bkey_n != N || ctx->bkey_binw != bw || ctx->bkey_cf != cf) {
+        ctx->bkey_y = nullptr;
+        smc::k_bin_prepare<<<1, smc::kBinThreads, smc::bin_prepare_smem_bytes(N), s>>>(
+            y, N, P.binw, P.binw_inv, P.cf, ctx->d_bcache);
+        if (cudaGetLastError() != cudaSuccess) return nullptr;
+        ctx->bkey_y = y;
+        ctx->bkey_n = N;
+        ctx->bkey_binw = bw;
+        ctx->bkey_cf = cf;
+    }
+    return ctx->d_bcache;
+}
+
 // The binned sweep (data held whole in shared memory): one 512-thread CTA
 // per SM, each with an equal share of the work.
 template <int K>
@@ -846,6 +961,7 @@ static smc_status launch_pop_binned(smc_ctx* ctx, cudaStream_t s, const float* y
     if (st0 != SMC_OK) return st0;
     int64_t grid = ctx->num_sms;
     if (grid > groups) grid = groups;
+    const char* bc = binned_cache(ctx, y, N, P, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)threads);
@@ -859,7 +975,8 @@ static smc_status launch_pop_binned(smc_ctx* ctx, cudaStream_t s, const float* y
     smc_status st = cuda_ok(cudaLaunchKernelEx(
         &cfg, kern, y, N, th, l, Mt, beta, off, n_pops, scale, seed, sweep,
         reinterpret_cast<unsigned long long*>(stats), ctx->d_popdone, ctx->d_grpdone,
-        reinterpret_cast<long long*>(ctx->d_grppart), P, Kr, inline_ex ? 1 : 0, ctx->d_status));
+        reinterpret_cast<long long*>(ctx->d_grppart), P, Kr, inline_ex ? 1 : 0, bc,
+        ctx->d_status));
     if (st != SMC_OK || inline_ex) return st;
     int64_t xb = (Mt + 255) / 256;
     if (xb > (int64_t)ctx->num_sms * 8) xb = (int64_t)ctx->num_sms * 8;

@@ -492,6 +492,32 @@ def test_popmcmc_sweep_launch_shapes(smc, lanes, threads, N):
     assert rep.unexplained == [] and len(rep.differing) <= 1, rep
 
 
+def test_popmcmc_binned_layout_follows_the_data(smc):
+    """The binned sweep keeps the data's binned layout between calls (keyed
+    on the data pointer, N, the bin width and c) and checks the data against
+    the layout's own copy: data overwritten in place under the same pointer,
+    or another sigma on the same data, still give the oracle's sweep."""
+    P, ctx = smc
+    K, N = 4, 800
+    off = np.array([0, 2, 9, 40, 41, 130, 131, 300], np.int32)
+    beta = synth.population_betas(off)
+    logw = np.full(K, -np.log(K))
+    y_d = cu(synth.gmm1d_data(N, [-3, 0, 3, 6], SIG, seed=4))
+    cases = [(synth.gmm1d_data(N, [-3, 0, 3, 6], SIG, seed=4), SIG),   # builds the layout
+             (synth.gmm1d_data(N, [-3, 0, 3, 6], SIG, seed=4), SIG),   # uses it
+             (synth.gmm1d_data(N, [-2, 1, 2, 7], SIG, seed=5), SIG),   # overwritten in place
+             (synth.gmm1d_data(N, [-2, 1, 2, 7], SIG, seed=5), 1.5 * SIG)]  # another bin width
+    for i, (y, sig) in enumerate(cases):
+        y_d.copy_(cu(y))
+        th = synth.population_particles(K, off, seed=10 + i)
+        ll = oracle.gmm1d_loglik(y, logw, sig, th)
+        tt, lt = cu(th), cu(ll)
+        P.popmcmc_sweep(ctx, P.GMM(K, sig), y_d, tt, lt, cu(beta), cu(off), 0.3, 77, i)
+        ctx.check()
+        rep = explain_sweep(y, logw, sig, BOX, th, ll, beta, off, 0.3, 77, i, np_(tt), np_(lt))
+        assert rep.unexplained == [] and len(rep.differing) <= 1, (i, rep)
+
+
 def test_popmcmc_full_size_runs_and_reuses_queue(smc):
     P, ctx = smc
     w = synth.GMM8_POP
