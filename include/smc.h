@@ -54,7 +54,9 @@ typedef enum smc_status {
     SMC_ERR_NONFINITE = -3,    /* NaN log-likelihood / log-weight seen by a kernel */
     SMC_ERR_ZERO_WEIGHT = -4,  /* every weight is zero (all log-weights -inf) */
     SMC_ERR_TIMEOUT = -5,      /* a bounded device wait gave up */
-    SMC_ERR_UNSUPPORTED = -6   /* configuration not built (e.g. K too large) */
+    SMC_ERR_UNSUPPORTED = -6,  /* configuration not built (e.g. K too large) */
+    SMC_ERR_BOUNDS = -7        /* debug build only: an index failed its bounds check
+                                  (the access was skipped; e.g. an ancestor outside [0, M)) */
 } smc_status;
 
 typedef struct smc_ctx smc_ctx;

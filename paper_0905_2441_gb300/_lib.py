@@ -5,10 +5,14 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libsmc.so")
+# SMC_LIB_VARIANT=debug selects the bounds-checked build (libsmc_debug.so,
+# build.build(debug=True)); there is no fallback between the two
+LIB_PATH = os.path.join(_HERE, "libsmc_debug.so" if os.environ.get("SMC_LIB_VARIANT") == "debug"
+                        else "libsmc.so")
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_CUDA, SMC_ERR_NONFINITE = 0, -1, -2, -3
 SMC_ERR_ZERO_WEIGHT, SMC_ERR_TIMEOUT, SMC_ERR_UNSUPPORTED = -4, -5, -6
+SMC_ERR_BOUNDS = -7
 RNG_MOVE, RNG_ACCEPT, RNG_RESAMPLE, RNG_EXCHANGE, RNG_PFNOISE, RNG_MULTINOMIAL = 1, 2, 3, 4, 5, 6
 RNG_PROPOSAL = 7
 OP_LOGLIK, OP_MOVE, OP_POPMCMC = 0, 1, 2

@@ -6,6 +6,7 @@
 
 #include "ctx.hpp"
 #include "device.cuh"
+#include "bounds.cuh"
 
 using namespace smc_host;
 
@@ -198,6 +199,7 @@ extern "C" smc_status smc_ctx_check(smc_ctx* ctx, void* stream) {
     SMC_CUDA(cudaMemcpy(&v, ctx->d_status, sizeof(v), cudaMemcpyDeviceToHost));
     if (v) SMC_CUDA(cudaMemset(ctx->d_status, 0, sizeof(uint32_t)));
     SMC_CUDA(cudaDeviceSynchronize());
+    if (v & smc::ST_BOUNDS) return SMC_ERR_BOUNDS;
     if (v & smc::ST_TIMEOUT) return SMC_ERR_TIMEOUT;
     if (v & smc::ST_NONFINITE) return SMC_ERR_NONFINITE;
     if (v & smc::ST_BADARG) return SMC_ERR_ARG;
@@ -214,6 +216,7 @@ extern "C" const char* smc_status_string(smc_status s) {
         case SMC_ERR_ZERO_WEIGHT: return "all weights are zero";
         case SMC_ERR_TIMEOUT: return "bounded device wait expired";
         case SMC_ERR_UNSUPPORTED: return "unsupported configuration";
+        case SMC_ERR_BOUNDS: return "index out of bounds (debug build)";
     }
     return "unknown status";
 }

@@ -9,6 +9,7 @@
 #include "binned.cuh"
 #include "bulk.cuh"
 #include "gmm1d.cuh"
+#include "bounds.cuh"
 
 using namespace smc_host;
 
@@ -73,6 +74,7 @@ __global__ void __launch_bounds__(256, (K <= 8 ? SMC_MOVE_MINB : 1)) k_mh_move(
 
     int64_t src = p;
     if (active && anc && (!do_flag || *do_flag != 0)) src = anc[p];
+    if (active && !SMC_IN_BOUNDS(src >= 0 && src < M, status)) src = p;
     float mu[K], g[K], z[K], prop[K];
     double l = 0.0;
     float b = 0.0f;
@@ -206,12 +208,14 @@ template <int K>
 __device__ __forceinline__ bool exchange_pair(float* theta, double* ll, int64_t Mtot,
                                               const float* __restrict__ beta, int64_t base,
                                               int Mq, uint32_t par, int q, int j, int Kreal,
-                                              uint64_t seed, uint64_t sweep) {
+                                              uint64_t seed, uint64_t sweep, uint32_t* status) {
     int ia, ib;
     if (par == 0) { ia = 2 * j; ib = 2 * j + 1; }
     else if (j < (Mq - 1) / 2) { ia = 2 * j + 1; ib = 2 * j + 2; }
     else { ia = Mq - 1; ib = 0; }
     const int64_t ga = base + ia, gb = base + ib;
+    // (chain indices come from the caller's population offsets)
+    if (!SMC_IN_BOUNDS(base >= 0 && ga < Mtot && gb < Mtot, status)) return false;
     const double la = __ldcg(ll + ga), lb = __ldcg(ll + gb);
     float ta[K], tb[K];
 #pragma unroll
@@ -299,7 +303,7 @@ __device__ __forceinline__ void pop_exchange(float* theta, double* ll, int64_t M
                                              uint64_t seed, uint64_t sweep, uint32_t* pop_done,
                                              int64_t c0, int64_t c1, int qlo, int64_t qa,
                                              int64_t qb, int4* exb, int* s_nex, uint32_t* s_sw,
-                                             uint32_t* s_try, int Kreal) {
+                                             uint32_t* s_try, int Kreal, uint32_t* status) {
     const int warp = threadIdx.x >> 5, l32 = threadIdx.x & 31;
     if (threadIdx.x == 0) *s_nex = 0;
     __syncthreads();  // the moves are done (and ordered before warp 0's release)
@@ -343,7 +347,7 @@ __device__ __forceinline__ void pop_exchange(float* theta, double* ll, int64_t M
             }
             const int4 d = exb[e];
             swaps += exchange_pair<K>(theta, ll, Mtot, beta, d.y, d.z, (uint32_t)d.w, d.x, j, Kreal,
-                                      seed, sweep);
+                                      seed, sweep, status);
         }
         if (swaps) atomicAdd(s_sw, swaps);
         for (int e = threadIdx.x; e < nex; e += blockDim.x) {
@@ -462,7 +466,8 @@ __global__ void __launch_bounds__(256, SMC_POP_MINB) k_popmcmc_sweep(
         if (!inline_ex) continue;  // the exchanges run in k_popmcmc_exchange
         const int buf = (int)((iter - 1) & 1);  // double-buffered list: no third barrier
         pop_exchange<K>(theta, ll, Mtot, beta, offsets, n_pops, seed, sweep, pop_done, c0, c1,
-                        qlo, qa, qb, s_exb + buf * lcap, &s_nex[buf], &s_sw, &s_try, Kreal);
+                        qlo, qa, qb, s_exb + buf * lcap, &s_nex[buf], &s_sw, &s_try, Kreal,
+                        status);
     }
     if (iter == 0) grid_dep_wait();  // a block without items still orders its stats
     __syncthreads();
@@ -813,7 +818,8 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
             int64_t c1 = (g0 + gz) * 32;
             if (c1 > Mtot) c1 = Mtot;
             pop_exchange<K>(theta, ll, Mtot, beta, offs, n_pops, seed, sweep, pop_done, c0,
-                            c1 > c0 ? c1 : c0, qlo, qa, qb, s_exb, &s_nex, &s_sw, &s_try, Kreal);
+                            c1 > c0 ? c1 : c0, qlo, qa, qb, s_exb, &s_nex, &s_sw, &s_try, Kreal,
+                            status);
         }
         __syncthreads();  // the round's shared arrays are free again
     }
@@ -834,7 +840,7 @@ template <int K>
 __global__ void __launch_bounds__(256) k_popmcmc_exchange(
     float* theta, double* ll, int64_t Mtot, const float* __restrict__ beta,
     const int32_t* __restrict__ offsets, int32_t n_pops, uint64_t seed, uint64_t sweep,
-    unsigned long long* stats, int Kreal) {
+    unsigned long long* stats, int Kreal, uint32_t* status) {
     grid_dep_wait();  // the sweep's moves are visible from here on
     grid_dep_launch();
     __shared__ uint32_t s_sw, s_try;
@@ -854,7 +860,8 @@ __global__ void __launch_bounds__(256) k_popmcmc_exchange(
         else if (par == 1u && r == Mq - 1 && (Mq & 1) == 0) j = (Mq - 1) / 2;  // (Mq-1, 0)
         if (j < 0) continue;
         ++tries;
-        sw += exchange_pair<K>(theta, ll, Mtot, beta, base, Mq, par, q, j, Kreal, seed, sweep);
+        sw += exchange_pair<K>(theta, ll, Mtot, beta, base, Mq, par, q, j, Kreal, seed, sweep,
+                               status);
     }
     for (int o = 16; o > 0; o >>= 1) {
         sw += __shfl_xor_sync(0xFFFFFFFFu, sw, o);
@@ -982,7 +989,7 @@ static smc_status launch_pop_binned(smc_ctx* ctx, cudaStream_t s, const float* y
     if (xb > (int64_t)ctx->num_sms * 8) xb = (int64_t)ctx->num_sms * 8;
     return launch_pdl(smc::k_popmcmc_exchange<K>, dim3((unsigned)xb), dim3(256), 0, s, th, l, Mt,
                       beta, off, n_pops, seed, sweep, reinterpret_cast<unsigned long long*>(stats),
-                      Kr);
+                      Kr, ctx->d_status);
 }
 
 template <int K, bool EQW>
@@ -1050,7 +1057,7 @@ static smc_status launch_pop(smc_ctx* ctx, int threads, cudaStream_t s, const fl
     if (xb > (int64_t)ctx->num_sms * 8) xb = (int64_t)ctx->num_sms * 8;
     return launch_pdl(smc::k_popmcmc_exchange<K>, dim3((unsigned)xb), dim3(256), 0, s, th, l, Mt,
                       beta, off, n_pops, seed, sweep, reinterpret_cast<unsigned long long*>(stats),
-                      Kr);
+                      Kr, ctx->d_status);
 }
 
 }  // namespace smc_host

@@ -8,6 +8,7 @@
 
 #include "ctx.hpp"
 #include "device.cuh"
+#include "bounds.cuh"
 #include "reweight.cuh"
 
 using namespace smc_host;
@@ -35,7 +36,8 @@ __global__ void __launch_bounds__(256) k_pf_step(PfArgs A, const float* __restri
 #pragma unroll
     for (int j = 0; j < D; ++j) y[j] = yt[j];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
-        const int64_t src = anc ? (int64_t)anc[i] : i;
+        int64_t src = anc ? (int64_t)anc[i] : i;
+        if (!SMC_IN_BOUNDS(src >= 0 && src < M, status)) src = i;
         float z[D], xn[D];
         normals<D>(seed, RNG_PFNOISE, t, (uint32_t)i, D, z);
         float lg = 0.0f;
@@ -100,7 +102,8 @@ __global__ void __launch_bounds__(256) k_pf_fsv(FsvArgs A, const float* __restri
     }
     constexpr float kLog2e = 1.4426950408889634f;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
-        const int64_t src = anc ? (int64_t)anc[i] : i;
+        int64_t src = anc ? (int64_t)anc[i] : i;
+        if (!SMC_IN_BOUNDS(src >= 0 && src < M, status)) src = i;
         float z[D], x[D];
         normals<D>(seed, RNG_PFNOISE, t, (uint32_t)i, D, z);
         float sx = 0.0f;

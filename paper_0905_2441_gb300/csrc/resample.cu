@@ -16,6 +16,7 @@
 // dependent launch, so each one's launch overlaps the previous one's tail.
 #include "ctx.hpp"
 #include "device.cuh"
+#include "bounds.cuh"
 #include "resample.cuh"
 
 using namespace smc_host;
@@ -33,12 +34,13 @@ __global__ void __launch_bounds__(256) k_gather(const int32_t* __restrict__ anc,
                                                 int rows, const float* __restrict__ src,
                                                 float* __restrict__ dst,
                                                 const double* __restrict__ src64,
-                                                double* __restrict__ dst64) {
+                                                double* __restrict__ dst64, uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     const int64_t G = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += G) {
         int64_t a = anc ? (int64_t)anc[i] : i;
+        if (!SMC_IN_BOUNDS(a >= 0 && a < M, status)) a = i;
         for (int r = 0; r < rows; ++r) dst[(int64_t)r * M + i] = src[(int64_t)r * M + a];
         if (src64 && dst64) dst64[i] = src64[a];
     }
@@ -94,7 +96,7 @@ smc_status resample_launch(int num_sms, const double* W, int64_t M, uint64_t see
     if (st != SMC_OK) return st;
     if (sc.heavy_list) {
         st = launch_pdl(smc::k_resample_heavy, dim3((unsigned)num_sms * 4), dim3(smc::kRsThreads),
-                        0, s, do_flag, sc, M, anc);
+                        0, s, do_flag, sc, M, anc, status);
         if (st != SMC_OK) return st;
     }
     return SMC_OK;
@@ -153,7 +155,7 @@ extern "C" smc_status smc_gather(smc_ctx* ctx, const int32_t* anc, int64_t M, in
     int64_t b = (M + 255) / 256;
     if (b > (int64_t)ctx->num_sms * 16) b = (int64_t)ctx->num_sms * 16;
     return launch_pdl(smc::k_gather, dim3((unsigned)b), dim3(256), 0, as_stream(stream), anc, M,
-                      rows_f32, src_f32, dst_f32, src_f64, dst_f64);
+                      rows_f32, src_f32, dst_f32, src_f64, dst_f64, ctx->d_status);
 }
 
 // ------------------------------------------------------------------ no-allocation variant

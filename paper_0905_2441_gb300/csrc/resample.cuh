@@ -23,6 +23,7 @@
 // last use carry the streaming (evict-first) hint.
 #pragma once
 #include "device.cuh"
+#include "bounds.cuh"
 
 namespace smc {
 
@@ -799,8 +800,9 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
             }
             int item = a;
             for (uint32_t sl = s0; sl < s1; ++sl) {
-                while (fs[item] <= sl) ++item;
-                anc[sl] = (int32_t)(sbase + item);
+                while (SMC_IN_BOUNDS(item < nit, status) && fs[item] <= sl) ++item;
+                if (SMC_IN_BOUNDS(sl < (uint32_t)M && item < nit, status))
+                    anc[sl] = (int32_t)(sbase + item);
             }
         }
     }
@@ -811,7 +813,8 @@ static __global__ void __launch_bounds__(kRsThreads, SMC_RS_MINB) k_resample_sca
 // segment's inclusive F values; its slots are staged in shared memory and
 // stored slot-major.
 static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
-    const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc) {
+    const int32_t* do_flag, RsScratch sc, int64_t M, int32_t* __restrict__ anc,
+    uint32_t* status) {
     grid_dep_wait();  // the previous kernel's writes are visible from here on
     grid_dep_launch();
     if (do_flag && *do_flag == 0) return;
@@ -835,12 +838,15 @@ static __global__ void __launch_bounds__(kRsThreads) k_resample_heavy(
             }
             int item = a;
             for (uint32_t sl = s0; sl < s1; ++sl) {
-                while (f[item] <= sl) ++item;
-                s_anc[sl - b] = (int32_t)(base + item);
+                while (SMC_IN_BOUNDS(item < nit, status) && f[item] <= sl) ++item;
+                if (SMC_IN_BOUNDS(sl - b < (uint32_t)kRsChunk && item < nit, status))
+                    s_anc[sl - b] = (int32_t)(base + item);
             }
         }
         __syncthreads();
-        for (uint32_t k = threadIdx.x; k < e - b; k += kRsThreads) __stcs(anc + b + k, s_anc[k]);
+        for (uint32_t k = threadIdx.x; k < e - b; k += kRsThreads)
+            if (SMC_IN_BOUNDS(k < (uint32_t)kRsChunk && (int64_t)b + k < M, status))
+                __stcs(anc + b + k, s_anc[k]);
         __syncthreads();
     }
 }

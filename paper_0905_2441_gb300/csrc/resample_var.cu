@@ -279,7 +279,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rd_expand(const double* __restri
             uint32_t s0 = F0;
             for (int j = 0; j < kRsIpt; ++j) {
                 const uint32_t s1 = s_hi[tid * kRsIpt + j];
-                for (uint32_t sl = s0; sl < s1; ++sl) s_anc[sl - lo] = (int32_t)(g0 + j);
+                for (uint32_t sl = s0; sl < s1; ++sl)
+                    if (SMC_IN_BOUNDS(sl - lo < (uint32_t)kRdStage, status))
+                        s_anc[sl - lo] = (int32_t)(g0 + j);
                 s0 = s1;
             }
             __syncthreads();
@@ -297,8 +299,9 @@ __global__ void __launch_bounds__(kRsThreads) k_rd_expand(const double* __restri
                 }
                 int item = a;
                 for (uint32_t sl = s0; sl < s1; ++sl) {
-                    while (s_hi[item] <= sl) ++item;
-                    anc[sl] = (int32_t)(base + item);
+                    while (SMC_IN_BOUNDS(item < kRsTile, status) && s_hi[item] <= sl) ++item;
+                    if (SMC_IN_BOUNDS(sl < (uint32_t)M && item < kRsTile, status))
+                        anc[sl] = (int32_t)(base + item);
                 }
             }
         }
