@@ -8,6 +8,8 @@ computes any part of the method.
 from __future__ import annotations
 
 import ctypes as C
+import functools
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -538,3 +540,31 @@ def rng_normals(ctx: Context, seed: int, purpose: int, step: int, n_index: int, 
     _chk(L.load().smc_rng_normals(ctx.handle, int(seed), purpose, int(step), n_index, n,
                                   _ptr(out), _stream(stream)), "smc_rng_normals")
     return out.view(n_index, n)
+
+
+# NVTX ranges (environment SMC_NVTX=1 at import): every call of the functions
+# below runs inside a range named after it (torch.cuda.nvtx), so that a
+# profiler can attribute the kernels a call launches (ncu --nvtx
+# --nvtx-include "smc.reweight/").  Off by default: no wrapper, no cost.
+RANGED = ("loglik_batch", "reweight", "reweight_resample", "ess", "resample_systematic",
+          "resample_multinomial", "resample_residual", "resample", "gather", "mh_move",
+          "popmcmc_sweep", "pf_step", "pf_filter_step", "is_moments", "rng_mrg32k3a", "rng_words",
+          "rng_normals")
+
+
+def _ranged(fn):
+    name = "smc." + fn.__name__
+
+    @functools.wraps(fn)
+    def call(*args, **kwargs):
+        torch.cuda.nvtx.range_push(name)
+        try:
+            return fn(*args, **kwargs)
+        finally:
+            torch.cuda.nvtx.range_pop()
+    return call
+
+
+if os.environ.get("SMC_NVTX") == "1":
+    for _name in RANGED:
+        globals()[_name] = _ranged(globals()[_name])

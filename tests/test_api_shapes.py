@@ -88,3 +88,19 @@ def test_gather_pairs_and_shapes():
     with pytest.raises(ValueError, match=r"dst_f32 must be"):
         P.gather(None, None, torch.zeros(3, 5), torch.zeros(3, 4),
                  torch.zeros(5, dtype=torch.float64), torch.zeros(5, dtype=torch.float64))
+
+
+def test_nvtx_ranges_wrap_the_calls_when_asked():
+    """SMC_NVTX=1 at import wraps every ranged call (checked without a GPU, in
+    a child interpreter); without it the functions are the plain ones."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("import paper_0905_2441_gb300.api as a; "
+            "print(all(hasattr(getattr(a, n), '__wrapped__') for n in a.RANGED))")
+    for flag, want in (("1", "True"), ("0", "False")):
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True,
+                           env=dict(os.environ, SMC_NVTX=flag), timeout=300)
+        assert r.returncode == 0, r.stderr
+        assert r.stdout.strip() == want
