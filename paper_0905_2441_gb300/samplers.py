@@ -12,6 +12,7 @@ counters, so their outputs are bitwise equal.
 from __future__ import annotations
 
 import ctypes as C
+import math
 
 import numpy as np
 import torch
@@ -77,6 +78,13 @@ def _check_replacement(name, old, new):
     elif old is None and isinstance(new, torch.Tensor):
         raise ValueError(f"{name} is not used by this sampler")
 
+
+
+def _sum_increments(hist, t_done: int) -> float:
+    """log Z = the sum of the per-step increments the reweighting kernels
+    wrote to hist[t, 0]: at most T numbers, read once and added exactly
+    rounded on the host (no device arithmetic outside the library)."""
+    return math.fsum(hist[1:t_done + 1, 0].cpu().tolist())
 
 class _Graphable:
     """run(graph=True) captures `_body(...)` once and replays it.  Device
@@ -215,7 +223,7 @@ class SMCSampler(_Graphable):
         return self.log_evidence()
 
     def log_evidence(self) -> float:
-        return float(self.hist[1:self.t_done + 1, 0].sum().item())
+        return _sum_increments(self.hist, self.t_done)
 
     def history(self) -> list:
         """Per-step metrics of the completed steps (see step_records)."""
@@ -378,7 +386,7 @@ class ParticleFilter(_Graphable):
                 for t in range(t0, t1 + 1):
                     self.step(t)
             self.t_done = t1
-        return float(self.hist[1:self.t_done + 1, 0].sum().item())
+        return _sum_increments(self.hist, self.t_done)
 
     def state_dict(self) -> dict:
         """The particles, log-weights, ancestors of the last resampling (the
