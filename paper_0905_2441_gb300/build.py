@@ -108,4 +108,4 @@ def build(force: bool = False, verbose: bool = False, extra=(), debug: bool = Fa
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))
