@@ -622,6 +622,7 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
     const int64_t gEub = ((int64_t)blockIdx.x + 1) * G / B +
                          ((((int64_t)blockIdx.x + 1) * G) % B != 0 ? 1 : 0);
     const int npair = (Kreal + 1) >> 1;  // Box-Muller pairs per chain
+    const int nblk = (npair + 1) >> 1;   // Philox blocks (two pairs each) per chain
     // Draws of round g0 (nothing a sweep writes): task t is Box-Muller pair
     // t % (npair + 1) of chain slot t / (npair + 1), or its accept word; the
     // normals wait in s_prop.  Also the temperatures (read-only).
@@ -629,18 +630,27 @@ __global__ void __launch_bounds__(kBinThreads, 1) k_popmcmc_binned(
         const int64_t cfirst = g0 * 32;
         const int64_t cb = cfirst + tid;
         const float bt_c = (tid < nslot && cb < Mtot) ? beta[cb] : 0.0f;  // stored after the draws
-        for (int t = tid; t < nslot * (npair + 1); t += T) {
-            const int slot = t / (npair + 1), j = t - slot * (npair + 1);
+        // task j < nblk: Philox block j of the chain's move words, i.e. the
+        // Box-Muller pairs 2j (words x, y) and 2j + 1 (z, w); task nblk: the
+        // accept word
+        for (int t = tid; t < nslot * (nblk + 1); t += T) {
+            const int slot = t / (nblk + 1), j = t - slot * (nblk + 1);
             const uint32_t c = (uint32_t)(cfirst + slot);
-            if (j == npair) {
+            if (j == nblk) {
                 s_aw[slot] = draw(seed, RNG_ACCEPT, sweep, c, 0u).x;
             } else {
-                const uint4 w = draw(seed, RNG_MOVE, sweep, c, (uint32_t)(j >> 1));
-                float z0, z1;
-                if (j & 1) box_muller(w.z, w.w, z0, z1);
-                else box_muller(w.x, w.y, z0, z1);
-                s_prop[(2 * j) * T + slot] = z0;
-                if (2 * j + 1 < K) s_prop[(2 * j + 1) * T + slot] = z1;
+                const uint4 w = draw(seed, RNG_MOVE, sweep, c, (uint32_t)j);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int jp = 2 * j + h;  // the Box-Muller pair
+                    if (jp < npair) {
+                        float z0, z1;
+                        if (h) box_muller(w.z, w.w, z0, z1);
+                        else box_muller(w.x, w.y, z0, z1);
+                        s_prop[(2 * jp) * T + slot] = z0;
+                        if (2 * jp + 1 < K) s_prop[(2 * jp + 1) * T + slot] = z1;
+                    }
+                }
             }
         }
         s_beta[tid] = bt_c;
