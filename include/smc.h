@@ -16,7 +16,8 @@
  *     exhausted wait limit) are latched in a device status word of the
  *     context and reported by smc_ctx_check().
  *   - Scratch memory (reduction partials, scan tile descriptors, queue
- *     counters, the status word) lives in the context.  smc_reserve() sizes
+ *     counters, the status word, the binned layout of the last data set a
+ *     population sweep saw) lives in the context.  smc_reserve() sizes
  *     it up front; a call that needs more grows it, which is refused with
  *     SMC_ERR_ARG while the stream is being captured into a CUDA graph.
  *     Calls on one context share that scratch, so they must run one after
@@ -36,7 +37,9 @@
  *   - Index arrays passed in device memory (ancestors, population offsets)
  *     are used as given: their values are not read on the host, so the
  *     library cannot check them.  Ancestors must lie in [0, M); those this
- *     library's resampling calls write always do.
+ *     library's resampling calls write always do.  The debug build of the
+ *     library (libsmc_debug.so, -DSMC_DEBUG_BOUNDS) checks them in the
+ *     kernels and reports SMC_ERR_BOUNDS instead of reading outside.
  */
 #ifndef SMC_GB300_H
 #define SMC_GB300_H
@@ -323,7 +326,13 @@ smc_status smc_mh_move(smc_ctx* ctx, const smc_gmm* model, const float* y, int64
  * values make the launch access chains outside [0, M_total)).
  * stats (device uint64[3], nullable) accumulates {MH accepts, swaps
  *   accepted, swaps attempted}.  Uses n_pops counters of context scratch
- *   (smc_reserve's max_pops sizes them before graph capture). */
+ *   (smc_reserve's max_pops sizes them before graph capture).
+ * For 512 <= N <= 4096 and K <= 16 the data are sorted into bins once per
+ *   data set (a small extra launch when y, N or sigma differ from the
+ *   context's previous call, recorded like any launch while capturing) and
+ *   the layout is kept in the context; every sweep compares y with the
+ *   layout's copy of the data and sorts them itself when they differ, so y
+ *   may be overwritten between calls. */
 smc_status smc_popmcmc_sweep(smc_ctx* ctx, const smc_gmm* model, const float* y, int64_t N,
                              float* theta, double* loglik, int64_t M_total, const float* beta,
                              const int32_t* pop_offsets, int32_t n_pops, float scale,
