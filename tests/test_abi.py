@@ -46,8 +46,17 @@ def test_binding_declares_every_symbol():
 def test_status_strings_without_gpu(libsmc):
     libsmc.smc_status_string.restype = ctypes.c_char_p
     libsmc.smc_status_string.argtypes = [ctypes.c_int]
-    for s in range(0, -7, -1):
-        assert libsmc.smc_status_string(s)
+    for s in range(0, -8, -1):
+        assert libsmc.smc_status_string(s) != b"unknown status"
+
+
+def test_debug_library_builds_and_exports_every_declared_symbol():
+    """The bounds-checked variant (build(debug=True)) compiles and keeps the
+    same C ABI (its kernels only add index checks)."""
+    from paper_0905_2441_gb300 import build
+    lib = ctypes.CDLL(build.build(debug=True))
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
 
 
 def test_argument_errors_are_reported_on_host(libsmc):
