@@ -10,9 +10,10 @@
 // the same pass also forms the exact tile sums of pass 1 of systematic
 // resampling from the W it writes); every block of that pass combines the
 // partials itself while its first tiles load, and its block 0 writes the
-// scalars.  Without a second pass the reduction's last block combines them.  Per element the only FP64
-// instruction is the log-weight update (GB300 issues FP64 at ~1/64 of
-// FP32); differences and exponentials run in FP32 on hi/lo splits.
+// scalars.  Without a second pass the reduction's last block combines them.
+// Per element the only FP64 instruction is the log-weight update (GB300
+// issues FP64 at ~1/64 of FP32); differences and exponentials run in FP32
+// on hi/lo splits.
 #include <climits>
 #include <cmath>
 
