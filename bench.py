@@ -1037,7 +1037,9 @@ HOLD_CYCLES = 1 << 18
 
 
 def _hold(torch):
-    torch.cuda._sleep(HOLD_CYCLES)
+    spin = getattr(torch.cuda, "_sleep", None)  # torch's device spin kernel
+    if spin is not None:
+        spin(HOLD_CYCLES)
 
 
 def _flush_timed(torch, flush, stream, fns, hold=True):
